@@ -1,0 +1,165 @@
+/*
+ * npsolve.h -- C ABI of the B300 (sm_103a) neural-preconditioned Poisson
+ * solver: NPSDO (Sec. 4.1, Algorithm 1 of arXiv 2310.00177) with the
+ * image-conditioned multilevel network P_net of Sec. 4.2 (Algorithm 2).
+ *
+ * The problem (Sec. 3.2): a voxel grid of nx*ny*nz cells, each labelled
+ * fluid, air (Dirichlet p = 0) or solid (Neumann; the region outside the grid
+ * counts as solid).  A is the masked 7-point Laplacian on the fluid cells
+ * (stencil points outside the fluid dropped, diagonal = number of fluid-or-air
+ * neighbours, rows/columns of non-fluid cells empty).  Every vector is stored
+ * on the full grid, x fastest: index p = (z*ny + y)*nx + x; entries at
+ * non-fluid cells are ignored on input and written as 0 on output (this is
+ * the paper's reduced system A~ x~ = b~ without the gather/scatter).
+ *
+ * Labels: uint8, 0 = solid, 1 = fluid, 2 = air (0 is solid so that a
+ * zero-filled halo is the paper's solid padding, Sec. 4.2.1).  Any other code
+ * is rejected with NPSOLVE_BAD_LABELS.
+ *
+ * Memory and ownership: unless a name ends in _host, every array argument is
+ * a DEVICE pointer on the current CUDA device, owned by the caller, and must
+ * stay valid until the call returns (all calls are synchronous with respect
+ * to the host; work is issued on `stream`, a cudaStream_t, 0 = legacy default
+ * stream).  The handle owns its scratch memory (Krylov state, image pyramid,
+ * network intermediates), allocates it on first use for a grid size, reuses
+ * it for equal or smaller grids, and frees it in npsolve_destroy.  There is
+ * no CPU fallback: without a usable sm_103a device every call fails with
+ * NPSOLVE_CUDA_ERROR.
+ *
+ * Errors: every int-returning call returns an npsolve_status; on failure a
+ * message is available from npsolve_last_error(handle) (or
+ * npsolve_last_error(NULL) for errors of calls without a handle, per thread).
+ * A handle must not be used from two host threads at once.
+ */
+#ifndef NPSOLVE_H
+#define NPSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct npsolve *npsolve_t;
+
+typedef enum {
+  NPSOLVE_OK = 0,
+  NPSOLVE_BAD_ARG = 1,        /* null pointer, bad tolerance, non-finite b, ... */
+  NPSOLVE_BAD_DIMS = 2,       /* a dimension not divisible by 2^(L-1) (Sec. 4.2.1) */
+  NPSOLVE_BAD_LABELS = 3,     /* a label outside {0, 1, 2} */
+  NPSOLVE_NO_CONVERGENCE = 4, /* max_iter reached; x, iters, residual still written */
+  NPSOLVE_BREAKDOWN = 5,      /* d^T A d <= 0 or non-finite in Alg. 1; x so far written */
+  NPSOLVE_OOM = 6,            /* device allocation failed */
+  NPSOLVE_CUDA_ERROR = 7      /* a CUDA call failed (message has the CUDA error) */
+} npsolve_status;
+
+enum { NPSOLVE_LABEL_SOLID = 0, NPSOLVE_LABEL_FLUID = 1, NPSOLVE_LABEL_AIR = 2 };
+
+/* Precision forms of the network evaluation.  Vectors are FP32, dot products
+ * and orthogonalisation coefficients FP64 and x FP64 in both forms. */
+enum {
+  NPSOLVE_FP32 = 0, /* per-cell kernels generated to FP32 accuracy */
+  NPSOLVE_BF16 = 1  /* kernel generation with BF16 weights on the tensor cores, FP32 accumulation */
+};
+
+/* Residual update of Alg. 1. */
+enum {
+  NPSOLVE_RESIDUAL_RECURRENCE = 0, /* r_k = r_{k-1} - alpha_k A d_k; on exit the FP64 true residual
+                                      is checked and, if above tolerance, r is replaced by b - A x and
+                                      the iteration continues (at most 4 times) */
+  NPSOLVE_RESIDUAL_EXPLICIT = 1    /* r_k = b - A x_k every iteration, as printed in Alg. 1 */
+};
+
+typedef struct {
+  int levels;        /* L, number of network levels, 1..7 (paper: 6; L = 4 ~ 16k parameters) */
+  int n_ortho;       /* directions to A-orthogonalise against, 0..4 (paper: 2, Sec. 4.1) */
+  int precision;     /* NPSOLVE_FP32 or NPSOLVE_BF16 */
+  int residual_mode; /* NPSOLVE_RESIDUAL_RECURRENCE or NPSOLVE_RESIDUAL_EXPLICIT */
+} npsolve_config;
+
+/* Number of FP32 network parameters for L levels (Alg. 2): for each level
+ * l < L the blocks CConv1 (W 27x3x27, B 27), CConv2 (same), Aff1 (Wbar 3x27,
+ * Bbar 1), Aff2 (same), in that order, then CConv1 of level L.
+ * W[a][c][l]: a = output tap, c = image channel (0 fluid, 1 air, 2 solid),
+ * l = image window offset; taps/offsets t = 9(dz+1) + 3(dy+1) + (dx+1).
+ * L = 4 gives 15,990; L = 6 gives 25,174. */
+size_t npsolve_weight_count(int levels);
+
+/* Create a solver handle on the current device.  `weights_host` (host
+ * memory, n_weights == npsolve_weight_count(cfg->levels) floats) is copied.
+ * Returns NPSOLVE_BAD_ARG for an invalid config, NPSOLVE_CUDA_ERROR when no
+ * sm_103a device is usable. */
+int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t n_weights, npsolve_t *out);
+
+/* Replace / read back the network weights (host memory, FP32). */
+int npsolve_set_weights(npsolve_t h, const float *weights_host, size_t n_weights);
+int npsolve_get_weights(npsolve_t h, float *weights_host, size_t n_weights);
+
+/* Release the handle and all device memory it owns.  NULL is ignored. */
+void npsolve_destroy(npsolve_t h);
+
+/* Last error message of the handle (or of this thread for h == NULL);
+ * valid until the next call on the same handle/thread. */
+const char *npsolve_last_error(npsolve_t h);
+
+/* Solve A x = b with NPSDO (Alg. 1): x_0 = 0, r_0 = b; while ||r_k|| >=
+ * tol*||b||: d_k = P_net(I, r_{k-1}/||r_{k-1}||) (Alg. 2), A-orthogonalise
+ * d_k against the last n_ortho directions, exact line search
+ * alpha_k = r_{k-1}^T d_k / d_k^T A d_k, x_k = x_{k-1} + alpha_k d_k.
+ *   labels [nz][ny][nx] uint8 (device); b [nz][ny][nx] FP32 (device);
+ *   tol relative tolerance (> 0; the paper uses 1e-6, Sec. 5);
+ *   max_iter iteration cap (>= 0); stream cudaStream_t;
+ *   x [nz][ny][nx] FP64 (device, written; 0 off fluid);
+ *   iters (host, written) network applications performed;
+ *   rel_residual (host, written) FP64 ||b - A x|| / ||b|| of the returned x.
+ * Each dimension must be divisible by 2^(L-1).  Returns NPSOLVE_OK,
+ * NPSOLVE_NO_CONVERGENCE or NPSOLVE_BREAKDOWN with all outputs written, or an
+ * argument/CUDA error with outputs unspecified. */
+int npsolve_solve(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol,
+                  int max_iter, void *stream, double *x, int *iters, double *rel_residual);
+
+/* npsolve_solve on HOST buffers: labels_host, b_host are copied to the device,
+ * the solve runs, and x_host (FP64) is copied back, all inside the call.
+ * Pinned (page-locked) host memory gives the fastest copies. */
+int npsolve_solve_host(npsolve_t h, const uint8_t *labels_host, int nx, int ny, int nz, const float *b_host,
+                       double tol, int max_iter, void *stream, double *x_host, int *iters, double *rel_residual);
+
+/* Per-iteration residual norms ||r_k|| (FP64, k = 0..iters) of the last
+ * solve on this handle, copied to `hist_host` (at most `cap` entries).
+ * Returns the number of entries written in *count. */
+int npsolve_residual_history(npsolve_t h, double *hist_host, int cap, int *count);
+
+/* One evaluation of the network z = P_net(I, r) (Alg. 2): r is zeroed off
+ * fluid before use (the reduced vector padded with zeros) and z is written
+ * as 0 off fluid.  labels, r (FP32), z (FP32) are device arrays. */
+int npsolve_apply_network(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r, float *z,
+                          void *stream);
+
+/* One network evaluation, returning an intermediate of level `level`
+ * (1..L) instead of z (for per-level parity checks of Alg. 2):
+ *   which = 0 x1^l (CConv1 output), 1 r2^l (interpolated input of CConv2),
+ *           2 x2^l (CConv2 output), 3 x^l (combined output), 4 r1^l (CConv1 input).
+ * out has (nx>>(l-1))*(ny>>(l-1))*(nz>>(l-1)) FP32 entries (device).
+ * c12_host (2 doubles, may be NULL) receives Aff1^l, Aff2^l. */
+int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r,
+                                 int level, int which, float *out, double *c12_host, void *stream);
+
+/* q = A d, the masked 7-point Laplacian of Sec. 3.2, FP32 (device arrays). */
+int npsolve_apply_laplacian(const uint8_t *labels, int nx, int ny, int nz, const float *d, float *q, void *stream);
+
+/* FP64 relative residual ||b - A x|| / ||b|| over the fluid cells (device
+ * arrays; result on the host). */
+int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const float *b, const double *x,
+                          double *rel_residual, void *stream);
+
+/* Jacobi-preconditioned CG (M = diag(A) on fluid cells) with the same
+ * conventions as npsolve_solve; the same-device comparison solver. */
+int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol, int max_iter,
+                       void *stream, double *x, int *iters, double *rel_residual);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NPSOLVE_H */

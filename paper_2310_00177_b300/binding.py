@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libnpsolve.so (the C ABI of include/npsolve.h).
+
+Argument marshalling only: device arrays are torch CUDA tensors passed by
+``data_ptr()``, the stream is torch's current stream, host arrays are NumPy.
+Every computation runs in the library's CUDA kernels; when the library cannot
+be loaded every call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libnpsolve.so")
+
+OK, BAD_ARG, BAD_DIMS, BAD_LABELS, NO_CONVERGENCE, BREAKDOWN, OOM, CUDA_ERROR = range(8)
+FP32, BF16 = 0, 1
+RECURRENCE, EXPLICIT = 0, 1
+STATUS_NAMES = ["OK", "BAD_ARG", "BAD_DIMS", "BAD_LABELS", "NO_CONVERGENCE", "BREAKDOWN", "OOM", "CUDA_ERROR"]
+
+
+class NpsolveError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("n_ortho", ctypes.c_int), ("precision", ctypes.c_int),
+                ("residual_mode", ctypes.c_int)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+# Exported symbols and their argument types (mirrors include/npsolve.h).
+SIGNATURES = {
+    "npsolve_weight_count": ([_i], ctypes.c_size_t),
+    "npsolve_create": ([ctypes.POINTER(_Config), _vp, ctypes.c_size_t, ctypes.POINTER(_vp)], _i),
+    "npsolve_set_weights": ([_vp, _vp, ctypes.c_size_t], _i),
+    "npsolve_get_weights": ([_vp, _vp, ctypes.c_size_t], _i),
+    "npsolve_destroy": ([_vp], None),
+    "npsolve_last_error": ([_vp], ctypes.c_char_p),
+    "npsolve_solve": ([_vp, _vp, _i, _i, _i, _vp, _d, _i, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_d)], _i),
+    "npsolve_solve_host": ([_vp, _vp, _i, _i, _i, _vp, _d, _i, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_d)],
+                           _i),
+    "npsolve_residual_history": ([_vp, _vp, _i, ctypes.POINTER(_i)], _i),
+    "npsolve_apply_network": ([_vp, _vp, _i, _i, _i, _vp, _vp, _vp], _i),
+    "npsolve_network_intermediate": ([_vp, _vp, _i, _i, _i, _vp, _i, _i, _vp, _vp, _vp], _i),
+    "npsolve_apply_laplacian": ([_vp, _i, _i, _i, _vp, _vp, _vp], _i),
+    "npsolve_true_residual": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
+    "npsolve_jacobi_pcg": ([_vp, _i, _i, _i, _vp, _d, _i, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_d)], _i),
+}
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Load libnpsolve.so (raises OSError when it is missing or unloadable)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise OSError(f"{_LIB_PATH} not built; run paper_2310_00177_b300/build.py")
+        lib = ctypes.CDLL(_LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dims(labels):
+    if labels.dim() != 3:
+        raise ValueError("labels must be (nz, ny, nx)")
+    nz, ny, nx = labels.shape
+    return int(nx), int(ny), int(nz)
+
+
+def _check(st, h=None):
+    if st != OK:
+        msg = load_library().npsolve_last_error(h).decode()
+        raise NpsolveError(st, msg)
+
+
+def weight_count(levels: int) -> int:
+    return int(load_library().npsolve_weight_count(levels))
+
+
+class Solver:
+    """A solver handle: network weights + device workspace (npsolve_t)."""
+
+    def __init__(self, weights, levels=4, n_ortho=2, precision=FP32, residual_mode=RECURRENCE):
+        lib = load_library()
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        cfg = _Config(levels, n_ortho, precision, residual_mode)
+        h = ctypes.c_void_p()
+        st = lib.npsolve_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, ctypes.byref(h))
+        if st != OK:
+            raise NpsolveError(st, lib.npsolve_last_error(None).decode())
+        self._h = h
+        self.levels, self.n_ortho, self.precision, self.residual_mode = levels, n_ortho, precision, residual_mode
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().npsolve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, weights):
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        _check(load_library().npsolve_set_weights(self._h, w.ctypes.data_as(_vp), w.size), self._h)
+
+    def get_weights(self):
+        n = weight_count(self.levels)
+        w = np.empty(n, np.float32)
+        _check(load_library().npsolve_get_weights(self._h, w.ctypes.data_as(_vp), n), self._h)
+        return w
+
+    def solve(self, labels, b, tol=1e-6, max_iter=1000, x=None):
+        """NPSDO solve on device tensors.  Returns (x, iters, rel_residual, status);
+        status is OK, NO_CONVERGENCE or BREAKDOWN, other failures raise."""
+        import torch
+
+        nx, ny, nz = _dims(labels)
+        if x is None:
+            x = torch.empty(labels.shape, dtype=torch.float64, device=labels.device)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load_library().npsolve_solve(self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                          _ptr(b, torch.float32, "b"), float(tol), int(max_iter), _stream(),
+                                          _ptr(x, torch.float64, "x"), ctypes.byref(it), ctypes.byref(rr))
+        if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
+            _check(st, self._h)
+        return x, it.value, rr.value, st
+
+    def solve_host(self, labels, b, tol=1e-6, max_iter=1000, x=None):
+        """The same solve on host NumPy arrays (copies inside the library call)."""
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        nz, ny, nx = labels.shape
+        if x is None:
+            x = np.empty(labels.shape, np.float64)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        st = load_library().npsolve_solve_host(self._h, labels.ctypes.data_as(_vp), nx, ny, nz,
+                                               b.ctypes.data_as(_vp), float(tol), int(max_iter), _stream(),
+                                               x.ctypes.data_as(_vp), ctypes.byref(it), ctypes.byref(rr))
+        if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
+            _check(st, self._h)
+        return x, it.value, rr.value, st
+
+    def residual_history(self, cap=100000):
+        out = np.zeros(cap, np.float64)
+        cnt = ctypes.c_int(0)
+        _check(load_library().npsolve_residual_history(self._h, out.ctypes.data_as(_vp), cap, ctypes.byref(cnt)),
+               self._h)
+        return out[: cnt.value].copy()
+
+    def apply_network(self, labels, r, z=None):
+        import torch
+
+        nx, ny, nz = _dims(labels)
+        if z is None:
+            z = torch.empty(labels.shape, dtype=torch.float32, device=labels.device)
+        _check(load_library().npsolve_apply_network(self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                                    _ptr(r, torch.float32, "r"), _ptr(z, torch.float32, "z"),
+                                                    _stream()), self._h)
+        return z
+
+    def network_intermediate(self, labels, r, level, which):
+        """which: 'x1', 'r2', 'x2', 'x', 'r1'.  Returns (field, (c1, c2))."""
+        import torch
+
+        code = {"x1": 0, "r2": 1, "x2": 2, "x": 3, "r1": 4}[which]
+        nx, ny, nz = _dims(labels)
+        s = 1 << (level - 1)
+        out = torch.empty((nz // s, ny // s, nx // s), dtype=torch.float32, device=labels.device)
+        c12 = np.zeros(2, np.float64)
+        _check(load_library().npsolve_network_intermediate(
+            self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz, _ptr(r, torch.float32, "r"), level, code,
+            _ptr(out, torch.float32, "out"), c12.ctypes.data_as(_vp), _stream()), self._h)
+        return out, (float(c12[0]), float(c12[1]))
+
+
+def apply_laplacian(labels, d, q=None):
+    import torch
+
+    nx, ny, nz = _dims(labels)
+    if q is None:
+        q = torch.empty(labels.shape, dtype=torch.float32, device=labels.device)
+    _check(load_library().npsolve_apply_laplacian(_ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                                  _ptr(d, torch.float32, "d"), _ptr(q, torch.float32, "q"),
+                                                  _stream()))
+    return q
+
+
+def true_residual(labels, b, x):
+    import torch
+
+    nx, ny, nz = _dims(labels)
+    rr = ctypes.c_double(0.0)
+    _check(load_library().npsolve_true_residual(_ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                                _ptr(b, torch.float32, "b"), _ptr(x, torch.float64, "x"),
+                                                ctypes.byref(rr), _stream()))
+    return rr.value
+
+
+def jacobi_pcg(labels, b, tol=1e-6, max_iter=100000, x=None):
+    import torch
+
+    nx, ny, nz = _dims(labels)
+    if x is None:
+        x = torch.empty(labels.shape, dtype=torch.float64, device=labels.device)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = load_library().npsolve_jacobi_pcg(_ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                           _ptr(b, torch.float32, "b"), float(tol), int(max_iter), _stream(),
+                                           _ptr(x, torch.float64, "x"), ctypes.byref(it), ctypes.byref(rr))
+    if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
+        _check(st)
+    return x, it.value, rr.value, st

@@ -1,0 +1,300 @@
+// Network kernels of Alg. 2 on CUDA cores (FP32): image pyramid, Aff
+// reductions, the spatially varying convolution CConv (Sec. 4.2.1), 2x2x2
+// average pooling, x2 trilinear interpolation and the per-level combination
+// x^l = c1 x1^l + c2 x2^l.  These are the FP32 reference kernels of the
+// library; the tensor-core CConv lives in kernels_umma.cu.
+#include "nps_common.cuh"
+#include "nps_kernels.h"
+
+namespace nps {
+
+// ---------------------------------------------------------------------------
+// Image pyramid (Alg. 2 "Pooling" of I): exact integer counts of fluid and
+// air fine cells per coarse cell.  Level 2 from the labels, level l+1 from
+// level l.
+// ---------------------------------------------------------------------------
+__global__ void k_pyramid_from_labels(const uint8_t *__restrict__ lab, Dims fine, ushort2 *__restrict__ out) {
+  const Dims c{fine.nx / 2, fine.ny / 2, fine.nz / 2};
+  const long long n = c.n();
+  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < n; P += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(P, c, x, y, z);
+    unsigned nf = 0, na = 0;
+    for (int k = 0; k < 2; ++k)
+      for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i) {
+          const uint8_t l = lab[((long long)(2 * z + k) * fine.ny + (2 * y + j)) * fine.nx + (2 * x + i)];
+          nf += l == kFluid;
+          na += l == kAir;
+        }
+    out[P] = make_ushort2((unsigned short)nf, (unsigned short)na);
+  }
+}
+
+__global__ void k_pyramid_next(const ushort2 *__restrict__ in, Dims fine, ushort2 *__restrict__ out) {
+  const Dims c{fine.nx / 2, fine.ny / 2, fine.nz / 2};
+  const long long n = c.n();
+  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < n; P += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(P, c, x, y, z);
+    unsigned nf = 0, na = 0;
+    for (int k = 0; k < 2; ++k)
+      for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i) {
+          const ushort2 v = in[((long long)(2 * z + k) * fine.ny + (2 * y + j)) * fine.nx + (2 * x + i)];
+          nf += v.x;
+          na += v.y;
+        }
+    out[P] = make_ushort2((unsigned short)nf, (unsigned short)na);
+  }
+}
+
+// Image feature pair (fluid count, air count) at (x,y,z) of a level; zero
+// outside the grid (solid padding).  Level 1 reads labels, levels >= 2 counts.
+struct ImgSrc {
+  const uint8_t *lab;     // level 1
+  const ushort2 *counts;  // level >= 2
+};
+
+__device__ __forceinline__ float2 img_at(const ImgSrc &im, const Dims &dm, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= dm.nx || y >= dm.ny || z >= dm.nz) return make_float2(0.f, 0.f);
+  const long long p = ((long long)z * dm.ny + y) * dm.nx + x;
+  if (im.lab) {
+    const uint8_t l = im.lab[p];
+    return make_float2(l == kFluid ? 1.f : 0.f, l == kAir ? 1.f : 0.f);
+  }
+  const ushort2 c = im.counts[p];
+  return make_float2((float)c.x, (float)c.y);
+}
+
+// ---------------------------------------------------------------------------
+// Aff (Sec. 4.2.1): partial sums of sum_l (wf[l] nF(p+l) + wa[l] nA(p+l)) for
+// the two Aff blocks of a level, in FP64 per block.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRedThreads) k_aff_partial(ImgSrc im, Dims dm, const AffW *__restrict__ a1,
+                                                               const AffW *__restrict__ a2, double *__restrict__ part) {
+  const long long n = dm.n();
+  double v[2] = {0.0, 0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, dm, x, y, z);
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      const float2 f = img_at(im, dm, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
+      s1 += a1->wf[l] * f.x + a1->wa[l] * f.y;
+      s2 += a2->wf[l] * f.x + a2->wa[l] * f.y;
+    }
+    v[0] += s1;
+    v[1] += s2;
+  }
+  block_sum_store<2>(v, part + (size_t)blockIdx.x * 2);
+}
+
+__global__ void k_aff_final(const double *part, int nblocks, const AffW *a1, const AffW *a2, long long n,
+                            double *out) {
+  double t[2];
+  reduce_partials<2>(part, nblocks, t);
+  if (threadIdx.x != 0) return;
+  out[0] = a1->bconst + t[0] / (27.0 * (double)n);
+  out[1] = a2->bconst + t[1] / (27.0 * (double)n);
+}
+
+// ---------------------------------------------------------------------------
+// CConv on CUDA cores (FP32):
+//   K_a(p) = bp[a] + sum_l (wf[a][l] nF(p+l) + wa[a][l] nA(p+l))
+//   out_p  = sum_a K_a(p) v(p+a) * vscale,  v zero outside the grid.
+// When mask_input is set (level-1 CConv1), v is also zeroed off fluid (the
+// reduced input vector padded with zeros, Sec. 4.2).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_cconv_f32(ImgSrc im, Dims dm, const CConvW *__restrict__ w,
+                                                     const float *__restrict__ v, const float *__restrict__ vscale,
+                                                     int mask_input, float *__restrict__ out,
+                                                     const SolveState *st) {
+  if (st && st->done) return;
+  __shared__ CConvW sw;
+  {
+    const float *src = (const float *)w;
+    float *dst = (float *)&sw;
+    for (int i = threadIdx.x; i < (int)(sizeof(CConvW) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const float sc = vscale ? *vscale : 1.f;
+  const long long n = dm.n();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, dm, x, y, z);
+    float nf[27], na[27], vv[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
+      const float2 f = img_at(im, dm, xx, yy, zz);
+      nf[t] = f.x;
+      na[t] = f.y;
+      float val = 0.f;
+      if (xx >= 0 && yy >= 0 && zz >= 0 && xx < dm.nx && yy < dm.ny && zz < dm.nz) {
+        val = v[((long long)zz * dm.ny + yy) * dm.nx + xx];
+        if (mask_input && f.x == 0.f) val = 0.f;  // level 1: f.x == 1 exactly on fluid
+      }
+      vv[t] = val * sc;
+    }
+    float acc = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < 27; ++a) {
+      float k = sw.bp[a];
+#pragma unroll
+      for (int l = 0; l < 27; ++l) k = fmaf(sw.wf[a][l], nf[l], fmaf(sw.wa[a][l], na[l], k));
+      acc = fmaf(k, vv[a], acc);
+    }
+    out[p] = acc;
+  }
+}
+
+// 2x2x2 average pooling of a vector: out[P] = mean of its 8 children.
+__global__ void k_pool(const float *__restrict__ in, Dims fine, float *__restrict__ out, const SolveState *st) {
+  if (st && st->done) return;
+  const Dims c{fine.nx / 2, fine.ny / 2, fine.nz / 2};
+  const long long n = c.n();
+  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < n; P += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(P, c, x, y, z);
+    float s = 0.f;
+    for (int k = 0; k < 2; ++k)
+      for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i) s += in[((long long)(2 * z + k) * fine.ny + (2 * y + j)) * fine.nx + (2 * x + i)];
+    out[P] = 0.125f * s;
+  }
+}
+
+// One axis of x2 linear upsampling with half-pixel centres and edge clamp:
+// even f = 2j: 0.25 c[j-1] + 0.75 c[j] (c[0] at j = 0);
+// odd  f = 2j+1: 0.75 c[j] + 0.25 c[j+1] (c[n-1] at j = n-1).
+__device__ __forceinline__ void up_taps(int f, int nc, int &i0, int &i1, float &w1) {
+  const int j = f >> 1;
+  if (f & 1) {
+    i0 = j;
+    i1 = j + 1 < nc ? j + 1 : nc - 1;
+    w1 = 0.25f;
+  } else if (j > 0) {
+    i0 = j - 1;
+    i1 = j;
+    w1 = 0.75f;
+  } else {
+    i0 = 0;
+    i1 = 0;
+    w1 = 0.f;
+  }
+}
+
+__global__ void k_interp(const float *__restrict__ in, Dims coarse, float *__restrict__ out, const SolveState *st) {
+  if (st && st->done) return;
+  const Dims f{coarse.nx * 2, coarse.ny * 2, coarse.nz * 2};
+  const long long n = f.n();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, f, x, y, z);
+    int x0, x1, y0, y1, z0, z1;
+    float wx, wy, wz;
+    up_taps(x, coarse.nx, x0, x1, wx);
+    up_taps(y, coarse.ny, y0, y1, wy);
+    up_taps(z, coarse.nz, z0, z1, wz);
+    auto C = [&](int zz, int yy, int xx) { return in[((long long)zz * coarse.ny + yy) * coarse.nx + xx]; };
+    const float c00 = (1.f - wx) * C(z0, y0, x0) + wx * C(z0, y0, x1);
+    const float c01 = (1.f - wx) * C(z0, y1, x0) + wx * C(z0, y1, x1);
+    const float c10 = (1.f - wx) * C(z1, y0, x0) + wx * C(z1, y0, x1);
+    const float c11 = (1.f - wx) * C(z1, y1, x0) + wx * C(z1, y1, x1);
+    const float c0 = (1.f - wy) * c00 + wy * c01;
+    const float c1 = (1.f - wy) * c10 + wy * c11;
+    out[p] = (1.f - wz) * c0 + wz * c1;
+  }
+}
+
+// x^l = c1 x1 + c2 x2 (levels >= 2, no masking).
+__global__ void k_combine(long long n, const float *__restrict__ x1, const float *__restrict__ x2,
+                          const double *__restrict__ c12, float *__restrict__ out, const SolveState *st) {
+  if (st && st->done) return;
+  const float c1 = (float)c12[0], c2 = (float)c12[1];
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    out[p] = fmaf(c1, x1[p], c2 * x2[p]);
+}
+
+// Level 1: z = mask_fluid(c1 x1 + c2 x2) (the output restriction of Sec.
+// 4.2) and, inside a solve, the partial dot products z.(A d_i) for the
+// previous directions i = k-1, k-2, ... (Alg. 1 orthogonalisation).
+__global__ void __launch_bounds__(kRedThreads) k_combine1(const uint8_t *__restrict__ lab, long long n,
+                                                            const float *__restrict__ x1, const float *__restrict__ x2,
+                                                            const double *__restrict__ c12, float *__restrict__ z,
+                                                            const float *__restrict__ qring, double *__restrict__ part,
+                                                            const SolveState *st) {
+  if (st && st->done) return;
+  const float c1 = (float)c12[0], c2 = (float)c12[1];
+  const float *qs[kMaxOrtho];
+  int cnt = 0;
+  if (st) {
+    const int k1 = st->k + 1, no = st->n_ortho;
+    for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) qs[cnt++] = qring + (size_t)ring_slot(i, no) * n;
+  }
+  double v[kMaxOrtho] = {0.0, 0.0, 0.0, 0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    const float val = lab[p] == kFluid ? fmaf(c1, x1[p], c2 * x2[p]) : 0.f;
+    z[p] = val;
+    for (int j = 0; j < cnt; ++j) v[j] += (double)val * (double)qs[j][p];
+  }
+  if (st) block_sum_store<kMaxOrtho>(v, part + (size_t)blockIdx.x * kMaxOrtho);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------
+static inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 148LL * 16) b = 148LL * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+void launch_pyramid(const uint8_t *lab, Dims d1, ushort2 *const *counts, int L, cudaStream_t s) {
+  Dims d = d1;
+  for (int l = 2; l <= L; ++l) {
+    const long long nc = (long long)(d.nx / 2) * (d.ny / 2) * (d.nz / 2);
+    if (l == 2) k_pyramid_from_labels<<<grid_for(nc, 256), 256, 0, s>>>(lab, d, counts[2]);
+    else k_pyramid_next<<<grid_for(nc, 256), 256, 0, s>>>(counts[l - 1], d, counts[l]);
+    d = Dims{d.nx / 2, d.ny / 2, d.nz / 2};
+  }
+}
+
+void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,
+                double *out, cudaStream_t s) {
+  ImgSrc im{lab, counts};
+  if (counts) im.lab = nullptr;
+  const int nb = red_blocks(dm.n());
+  k_aff_partial<<<nb, kRedThreads, 0, s>>>(im, dm, a1, a2, part);
+  k_aff_final<<<1, kRedThreads, 0, s>>>(part, nb, a1, a2, dm.n(), out);
+}
+
+void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,
+                      const float *vscale, int mask_input, float *out, const SolveState *st, cudaStream_t s) {
+  ImgSrc im{lab, counts};
+  if (counts) im.lab = nullptr;
+  k_cconv_f32<<<grid_for(dm.n(), 128), 128, 0, s>>>(im, dm, w, v, vscale, mask_input, out, st);
+}
+
+void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, cudaStream_t s) {
+  const long long nc = (long long)(fine.nx / 2) * (fine.ny / 2) * (fine.nz / 2);
+  k_pool<<<grid_for(nc, 256), 256, 0, s>>>(in, fine, out, st);
+}
+
+void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s) {
+  k_interp<<<grid_for(coarse.n() * 8, 256), 256, 0, s>>>(in, coarse, out, st);
+}
+
+void launch_combine(long long n, const float *x1, const float *x2, const double *c12, float *out,
+                    const SolveState *st, cudaStream_t s) {
+  k_combine<<<grid_for(n, 256), 256, 0, s>>>(n, x1, x2, c12, out, st);
+}
+
+void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
+                     const float *qring, double *part, const SolveState *st, cudaStream_t s) {
+  k_combine1<<<red_blocks(n), kRedThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, st);
+}
+
+}  // namespace nps

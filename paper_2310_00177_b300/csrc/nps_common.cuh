@@ -1,0 +1,135 @@
+// Shared device-side definitions of the npsolve CUDA library (sm_103a).
+//
+// Layout conventions (all vectors full-grid, x fastest):
+//   p = (z*ny + y)*nx + x; labels uint8 0 solid, 1 fluid, 2 air; the region
+//   outside the grid is solid (Sec. 3.1) and vectors are zero there (Sec. 4.2.1).
+//   Level l of the network has dims (nx, ny, nz) >> (l-1); at l >= 2 the image
+//   is stored as exact integer counts of fluid and air fine cells (ushort2),
+//   the solid count being 8^(l-1) - fluid - air.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nps {
+
+constexpr int kSolid = 0, kFluid = 1, kAir = 2;
+constexpr int kMaxLevels = 7;
+constexpr int kMaxOrtho = 4;
+constexpr int kRing = kMaxOrtho + 1;
+constexpr int kRedThreads = 256;   // threads of every reduction kernel
+constexpr int kRedMaxBlocks = 1184; // 148 SMs x 8
+constexpr int kMaxPartials = 8;    // quantities reduced per kernel
+
+// Prepared weights of one CConv block (Sec. 4.2.1), folded with the fact that
+// the image channels sum to one (Sec. 3.2): I_solid = 1 - I_fluid - I_air, so
+//   K_a(p) = Bp[a] + sum_l ( Wf[a][l] nF(p+l) + Wa[a][l] nA(p+l) )
+// with Wf = (W[a][fluid][l] - W[a][solid][l]) / 8^(lvl-1),
+//      Wa = (W[a][air][l]   - W[a][solid][l]) / 8^(lvl-1),
+//      Bp = B[a] + sum_l W[a][solid][l],
+// and nF, nA the integer fluid/air counts (0/1 at level 1, 0 outside the grid).
+struct CConvW {
+  float wf[27][27];
+  float wa[27][27];
+  float bp[27];
+};
+
+// Per-level device copy of the Aff weights in the same folded form:
+//   Aff = bconst + (1/(27 n)) sum_p sum_l ( wf[l] nF(p+l) + wa[l] nA(p+l) ).
+struct AffW {
+  float wf[27];
+  float wa[27];
+  double bconst;  // Bbar + (1/27) sum_l Wbar[solid][l]
+};
+
+// Device-resident state of one NPSDO solve (Alg. 1).  Written only by the
+// single-block scalar kernels; read by every iteration kernel.
+struct SolveState {
+  double bnorm2;        // ||b||^2
+  double eps2;          // (tol ||b||)^2: converged when ||r||^2 < eps2
+  double rnorm2;        // ||r_k||^2
+  double alpha;         // line-search step of the current iteration
+  double coef[kMaxOrtho];  // orthogonalisation coefficients of the current iteration
+  double dAd[kRing];    // d_i^T A d_i per ring slot
+  float rscale;         // 1/||r_k||, the network input normalisation
+  int k;                // completed iterations
+  int done;             // 0 running, 1 converged, 2 breakdown, 3 non-finite input
+  int max_iter;
+  int n_ortho;
+  int pad_;
+};
+
+enum { kDoneRunning = 0, kDoneConverged = 1, kDoneBreakdown = 2, kDoneBadInput = 3 };
+
+__host__ __device__ inline int ring_slot(int iter1, int n_ortho) { return (iter1 - 1) % (n_ortho + 1); }
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: fixed grid, fixed tree, FP64 above the thread.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum NV per-thread values over the block (1-D block of kRedThreads) and
+// store them at out[0..NV) (thread 0).
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double *out) {
+  __shared__ double sm[NV][kRedThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sm[i][warp] = v[i];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = lane < kRedThreads / 32 ? sm[i][lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) out[i] = t;
+    }
+  }
+}
+
+// Reduce `nblocks` rows of NV partials (row-major) inside one block of
+// kRedThreads threads; every thread gets the totals in tot[].
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double *part, int nblocks, double (&tot)[NV]) {
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int j = threadIdx.x; j < nblocks; j += kRedThreads) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += part[(size_t)j * NV + i];
+  }
+  __shared__ double res[NV];
+  block_sum_store<NV>(v, res);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) tot[i] = res[i];
+}
+
+inline int red_blocks(long long n) {
+  long long b = (n + kRedThreads - 1) / kRedThreads;
+  if (b > kRedMaxBlocks) b = kRedMaxBlocks;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+struct Dims {
+  int nx, ny, nz;
+  __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
+};
+
+__device__ __forceinline__ void cell_xyz(long long p, const Dims &d, int &x, int &y, int &z) {
+  x = (int)(p % d.nx);
+  long long t = p / d.nx;
+  y = (int)(t % d.ny);
+  z = (int)(t / d.ny);
+}
+
+}  // namespace nps

@@ -1,0 +1,49 @@
+// Host-side launchers of the npsolve kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nps_common.cuh"
+
+namespace nps {
+
+// kernels_vec.cu
+void launch_lap(const uint8_t *lab, Dims dm, const float *d, float *q, cudaStream_t s);
+void launch_check_labels(const uint8_t *lab, long long n, unsigned int *bad, cudaStream_t s);
+void launch_init(const uint8_t *lab, long long n, const float *b, float *r, double *x, double *part, double tol,
+                 int max_iter, int n_ortho, SolveState *st, double *hist, cudaStream_t s);
+void launch_ortho_final(const double *part, long long n, SolveState *st, cudaStream_t s);
+void launch_direction(long long n, const float *z, float *dring, const SolveState *st, cudaStream_t s);
+void launch_lap_ring(const uint8_t *lab, Dims dm, const float *dring, float *qring, const float *r, double *part,
+                     SolveState *st, cudaStream_t s);
+void launch_update(bool recurrence, long long n, double *x, float *r, const float *dring, const float *qring,
+                   double *part, SolveState *st, double *hist, cudaStream_t s);
+void launch_explicit_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, double *part,
+                              SolveState *st, double *hist, cudaStream_t s);
+void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, double *part,
+                             SolveState *st, int *reopened, cudaStream_t s);
+void launch_relres(const uint8_t *lab, Dims dm, const float *b, const double *x, double *part, double *out,
+                   cudaStream_t s);
+size_t pcg_state_bytes();
+void launch_pcg_init(const uint8_t *lab, Dims dm, const float *b, float *r, float *p, double *x, double *part,
+                     double tol, void *st, double *hist, cudaStream_t s);
+void launch_pcg_iter(const uint8_t *lab, Dims dm, double *x, float *r, float *p, float *q, double *part, void *st,
+                     double *hist, cudaStream_t s);
+int pcg_done_offset();
+int pcg_k_offset();
+
+// kernels_net.cu
+void launch_pyramid(const uint8_t *lab, Dims d1, ushort2 *const *counts, int L, cudaStream_t s);
+void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,
+                double *out, cudaStream_t s);
+void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,
+                      const float *vscale, int mask_input, float *out, const SolveState *st, cudaStream_t s);
+void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, cudaStream_t s);
+void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s);
+void launch_combine(long long n, const float *x1, const float *x2, const double *c12, float *out,
+                    const SolveState *st, cudaStream_t s);
+void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
+                     const float *qring, double *part, const SolveState *st, cudaStream_t s);
+
+}  // namespace nps

@@ -1,0 +1,687 @@
+// Host runtime and C ABI of the npsolve library (declared in include/npsolve.h).
+//
+// One handle = one network (weights in device memory, prepared once) plus a
+// workspace grown on demand for the largest grid seen.  A solve is:
+//   setup (once per solve, depends only on the labels): label check, image
+//     pyramid, Aff coefficients c1^l, c2^l of every level (Sec. 4.2.1);
+//   the NPSDO iteration (Alg. 1), device-resident: the network (Alg. 2), the
+//     orthogonalisation coefficients, the direction and q = A d with fused dot
+//     products, the line search, the x/r update and the stop test.  One
+//     iteration is captured once as a CUDA graph and replayed; the kernels
+//     turn into no-ops after the device-side stop flag is set, and the host
+//     polls that flag asynchronously every few iterations;
+//   a final FP64 true-residual check (with residual replacement in the
+//     recurrence mode).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/npsolve.h"
+#include "nps_common.cuh"
+#include "nps_kernels.h"
+
+using namespace nps;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+constexpr int kCConvParams = 27 * 3 * 27 + 27;
+constexpr int kAffParams = 3 * 27 + 1;
+constexpr int kPollEvery = 4;      // iterations per captured graph / poll
+constexpr int kMaxRestarts = 4;    // residual replacements in the recurrence mode
+
+size_t weight_count(int L) {
+  if (L < 1 || L > kMaxLevels) return 0;
+  return (size_t)(L - 1) * (2 * kCConvParams + 2 * kAffParams) + kCConvParams;
+}
+
+struct Workspace {
+  Dims dims{0, 0, 0};
+  long long cap = 0;  // cells of level 1 the buffers were sized for
+  float *r = nullptr, *z = nullptr, *dring = nullptr, *qring = nullptr;
+  float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
+        *xc[kMaxLevels + 1] = {};
+  ushort2 *counts[kMaxLevels + 1] = {};
+  double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
+  int hist_cap = 0;
+  SolveState *st = nullptr;
+  void *pcg_st = nullptr;
+  unsigned int *bad = nullptr;
+  int *reopened = nullptr;
+  // pinned host mirrors for polling, and the events that guard them
+  SolveState *h_st = nullptr;
+  int *h_flag = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // device staging buffers of npsolve_solve_host
+  uint8_t *stage_lab = nullptr;
+  float *stage_b = nullptr;
+  double *stage_x = nullptr;
+  // captured iteration graph
+  cudaGraphExec_t graph = nullptr;
+  Dims graph_dims{0, 0, 0};
+  const uint8_t *graph_lab = nullptr;
+  const float *graph_b = nullptr;
+  double *graph_x = nullptr;
+  int graph_pcg = 0;
+};
+
+}  // namespace
+
+struct npsolve {
+  npsolve_config cfg;
+  int device = 0;
+  std::vector<float> weights;      // host copy of the flat blob
+  CConvW *cw = nullptr;            // [(kMaxLevels+1)*2], index lvl*2 + (type-1)
+  AffW *aw = nullptr;              // [(kMaxLevels+1)*2]
+  double *unit_c12 = nullptr;      // {1, 0} for L = 1
+  Workspace ws;
+  cudaStream_t cap_stream = nullptr;
+  std::string err;
+  std::vector<double> last_hist;
+};
+
+namespace {
+
+int fail(npsolve *h, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  g_thread_error = buf;
+  return code;
+}
+
+#define CK(h, call)                                                                                 \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? NPSOLVE_OOM : NPSOLVE_CUDA_ERROR,          \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);      \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, count * sizeof(T) + 256);
+}
+
+void free_ws(Workspace &w) {
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  w.graph = nullptr;
+  cudaFree(w.r);
+  cudaFree(w.z);
+  cudaFree(w.dring);
+  cudaFree(w.qring);
+  for (int l = 0; l <= kMaxLevels; ++l) {
+    cudaFree(w.x1[l]);
+    cudaFree(w.r1[l]);
+    cudaFree(w.r2[l]);
+    cudaFree(w.x2[l]);
+    cudaFree(w.xc[l]);
+    cudaFree(w.counts[l]);
+  }
+  cudaFree(w.part);
+  cudaFree(w.affc);
+  cudaFree(w.relres);
+  cudaFree(w.hist);
+  cudaFree(w.st);
+  cudaFree(w.pcg_st);
+  cudaFree(w.bad);
+  cudaFree(w.reopened);
+  cudaFreeHost(w.h_st);
+  cudaFreeHost(w.h_flag);
+  for (int i = 0; i < 2; ++i)
+    if (w.ev[i]) cudaEventDestroy(w.ev[i]);
+  cudaFree(w.stage_lab);
+  cudaFree(w.stage_b);
+  cudaFree(w.stage_x);
+  w = Workspace{};
+}
+
+// Make sure the workspace holds buffers for a grid of dims (L levels).
+int ensure_ws(npsolve *h, Dims d, int hist_cap) {
+  Workspace &w = h->ws;
+  const int L = h->cfg.levels;
+  const long long n = d.n();
+  bool fits = w.r && n <= w.cap;
+  if (fits) {
+    // per-level sizes must fit too (they do when n <= cap only for the same shape family;
+    // re-allocate when any level would overflow)
+    long long cap_l = w.cap;
+    for (int l = 1; l <= L; ++l, cap_l /= 8) {
+      const long long nl = (long long)(d.nx >> (l - 1)) * (d.ny >> (l - 1)) * (d.nz >> (l - 1));
+      if (nl > cap_l) fits = false;
+    }
+  }
+  if (!fits) {
+    free_ws(w);
+    const long long cap = n;
+    const int R = kRing;
+    CK(h, dalloc(&w.r, cap));
+    CK(h, dalloc(&w.z, cap));
+    CK(h, dalloc(&w.dring, cap * R));
+    CK(h, dalloc(&w.qring, cap * R));
+    long long cl = cap;
+    for (int l = 1; l <= L; ++l, cl = (cl + 7) / 8) {
+      CK(h, dalloc(&w.x1[l], cl));
+      if (l >= 2) {
+        CK(h, dalloc(&w.r1[l], cl));
+        CK(h, dalloc(&w.counts[l], cl));
+      }
+      if (l < L) {
+        CK(h, dalloc(&w.r2[l], cl));
+        CK(h, dalloc(&w.x2[l], cl));
+        if (l >= 2) CK(h, dalloc(&w.xc[l], cl));
+      }
+    }
+    CK(h, dalloc(&w.part, (size_t)kRedMaxBlocks * kMaxPartials));
+    CK(h, dalloc(&w.affc, (size_t)(kMaxLevels + 1) * 2));
+    CK(h, dalloc(&w.relres, 2));
+    CK(h, dalloc(&w.st, 1));
+    CK(h, cudaMalloc(&w.pcg_st, pcg_state_bytes()));
+    CK(h, dalloc(&w.bad, 1));
+    CK(h, dalloc(&w.reopened, 1));
+    CK(h, cudaHostAlloc((void **)&w.h_st, sizeof(SolveState) * 2, cudaHostAllocDefault));
+    CK(h, cudaHostAlloc((void **)&w.h_flag, sizeof(int) * 8, cudaHostAllocDefault));
+    for (int i = 0; i < 2; ++i) CK(h, cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming));
+    w.cap = cap;
+  }
+  if (hist_cap > w.hist_cap) {
+    if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old history buffer
+    w.graph = nullptr;
+    cudaFree(w.hist);
+    w.hist = nullptr;
+    CK(h, dalloc(&w.hist, (size_t)hist_cap));
+    w.hist_cap = hist_cap;
+  }
+  w.dims = d;
+  return NPSOLVE_OK;
+}
+
+// Fold the blob into the device form of every CConv / Aff block (Sec. 4.2.1
+// with the channel-sum-to-one identity; see CConvW / AffW).
+int upload_weights(npsolve *h) {
+  const int L = h->cfg.levels;
+  const float *w = h->weights.data();
+  std::vector<CConvW> cw((kMaxLevels + 1) * 2);
+  std::vector<AffW> aw((kMaxLevels + 1) * 2);
+  memset(cw.data(), 0, cw.size() * sizeof(CConvW));
+  memset(aw.data(), 0, aw.size() * sizeof(AffW));
+  const size_t per = 2 * kCConvParams + 2 * kAffParams;
+  auto fold_conv = [&](const float *blk, int lvl, CConvW &o) {
+    const double scale = 1.0 / pow(8.0, lvl - 1);
+    for (int a = 0; a < 27; ++a) {
+      double bp = blk[2187 + a];
+      for (int l = 0; l < 27; ++l) {
+        const double wf = blk[(a * 3 + 0) * 27 + l], wa = blk[(a * 3 + 1) * 27 + l], ws = blk[(a * 3 + 2) * 27 + l];
+        o.wf[a][l] = (float)((wf - ws) * scale);
+        o.wa[a][l] = (float)((wa - ws) * scale);
+        bp += ws;
+      }
+      o.bp[a] = (float)bp;
+    }
+  };
+  auto fold_aff = [&](const float *blk, int lvl, AffW &o) {
+    const double scale = 1.0 / pow(8.0, lvl - 1);
+    double bc = blk[81];
+    for (int l = 0; l < 27; ++l) {
+      const double wf = blk[l], wa = blk[27 + l], ws = blk[54 + l];
+      o.wf[l] = (float)((wf - ws) * scale);
+      o.wa[l] = (float)((wa - ws) * scale);
+      bc += ws / 27.0;
+    }
+    o.bconst = bc;
+  };
+  for (int lvl = 1; lvl <= L; ++lvl) {
+    const float *base = w + (size_t)(lvl - 1) * per;
+    fold_conv(base, lvl, cw[lvl * 2 + 0]);
+    if (lvl < L) {
+      fold_conv(base + kCConvParams, lvl, cw[lvl * 2 + 1]);
+      fold_aff(base + 2 * kCConvParams, lvl, aw[lvl * 2 + 0]);
+      fold_aff(base + 2 * kCConvParams + kAffParams, lvl, aw[lvl * 2 + 1]);
+    }
+  }
+  CK(h, cudaMemcpy(h->cw, cw.data(), cw.size() * sizeof(CConvW), cudaMemcpyHostToDevice));
+  CK(h, cudaMemcpy(h->aw, aw.data(), aw.size() * sizeof(AffW), cudaMemcpyHostToDevice));
+  return NPSOLVE_OK;
+}
+
+Dims level_dims(Dims d, int lvl) { return Dims{d.nx >> (lvl - 1), d.ny >> (lvl - 1), d.nz >> (lvl - 1)}; }
+
+int check_dims(npsolve *h, int nx, int ny, int nz) {
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
+    return fail(h, NPSOLVE_BAD_DIMS, "dims %dx%dx%d out of range", nx, ny, nz);
+  if ((long long)nx * ny * nz > (1LL << 31) - 1) return fail(h, NPSOLVE_BAD_DIMS, "grid too large");
+  const int m = 1 << (h->cfg.levels - 1);
+  if (nx % m || ny % m || nz % m)
+    return fail(h, NPSOLVE_BAD_DIMS, "dims %dx%dx%d not divisible by 2^(L-1) = %d", nx, ny, nz, m);
+  return NPSOLVE_OK;
+}
+
+// One CConv block of level lvl (type 1 or 2).
+void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *vscale,
+           int mask_input, float *out, const SolveState *st, cudaStream_t s) {
+  Workspace &w = h->ws;
+  const Dims dl = level_dims(d1, lvl);
+  const CConvW *cw = h->cw + lvl * 2 + (type - 1);
+  launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, cw, in, vscale, mask_input,
+                   out, st, s);
+}
+
+// The network z = P_net(I, r) of Alg. 2 on the prepared pyramid and Aff
+// coefficients.  Inside a solve (st != null) the level-1 input is scaled by
+// 1/||r|| from the state and the orthogonalisation dots are fused into the
+// last combination.
+void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const float *vscale, float *z,
+                 const SolveState *st, cudaStream_t s) {
+  Workspace &w = h->ws;
+  const int L = h->cfg.levels;
+  for (int l = 1; l < L; ++l) {
+    cconv(h, lab, d1, l, 1, l == 1 ? r : w.r1[l], l == 1 ? vscale : nullptr, l == 1, w.x1[l], st, s);
+    launch_pool(w.x1[l], level_dims(d1, l), w.r1[l + 1], st, s);
+  }
+  cconv(h, lab, d1, L, 1, L == 1 ? r : w.r1[L], L == 1 ? vscale : nullptr, L == 1, w.x1[L], st, s);
+  if (L == 1) {
+    launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.part, st, s);
+    return;
+  }
+  for (int l = L - 1; l >= 1; --l) {
+    const float *coarse = (l + 1 == L) ? w.x1[L] : w.xc[l + 1];
+    launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+    cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
+    if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], w.affc + 2 * l, w.xc[l], st, s);
+    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], w.affc + 2, z, w.qring, w.part, st, s);
+  }
+}
+
+// Label check, pyramid and Aff coefficients for this grid.
+int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool check) {
+  Workspace &w = h->ws;
+  const int L = h->cfg.levels;
+  if (check) {
+    CK(h, cudaMemsetAsync(w.bad, 0, sizeof(unsigned int), s));
+    launch_check_labels(lab, d1.n(), w.bad, s);
+  }
+  launch_pyramid(lab, d1, w.counts, L, s);
+  for (int l = 1; l < L; ++l)
+    launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
+               h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s);
+  CK(h, cudaGetLastError());
+  return NPSOLVE_OK;
+}
+
+// Enqueue one NPSDO iteration (Alg. 1 loop body) on stream s.
+void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x, cudaStream_t s) {
+  Workspace &w = h->ws;
+  const long long n = d1.n();
+  run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s);
+  launch_ortho_final(w.part, n, w.st, s);
+  launch_direction(n, w.z, w.dring, w.st, s);
+  launch_lap_ring(lab, d1, w.dring, w.qring, w.r, w.part, w.st, s);
+  const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
+  launch_update(recur, n, x, w.r, w.dring, w.qring, w.part, w.st, w.hist, s);
+  if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
+}
+
+int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x) {
+  Workspace &w = h->ws;
+  if (w.graph && w.graph_dims.nx == d1.nx && w.graph_dims.ny == d1.ny && w.graph_dims.nz == d1.nz &&
+      w.graph_lab == lab && w.graph_b == b && w.graph_x == x && !w.graph_pcg)
+    return NPSOLVE_OK;
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  w.graph = nullptr;
+  cudaGraph_t g;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < kPollEvery; ++i) enqueue_iteration(h, lab, d1, b, x, h->cap_stream);
+  CK(h, cudaStreamEndCapture(h->cap_stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&w.graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(h, e);
+  w.graph_dims = d1;
+  w.graph_lab = lab;
+  w.graph_b = b;
+  w.graph_x = x;
+  w.graph_pcg = 0;
+  return NPSOLVE_OK;
+}
+
+int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const float *b, double tol, int max_iter,
+               cudaStream_t s, double *x, int *iters, double *rel_residual) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!lab || !b || !x || !iters || !rel_residual) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (!(tol > 0.0) || !isfinite(tol)) return fail(h, NPSOLVE_BAD_ARG, "tolerance must be finite and > 0");
+  if (max_iter < 0) return fail(h, NPSOLVE_BAD_ARG, "max_iter must be >= 0");
+  int st = check_dims(h, nx, ny, nz);
+  if (st) return st;
+  CK(h, cudaSetDevice(h->device));
+  const Dims d1{nx, ny, nz};
+  st = ensure_ws(h, d1, max_iter + 1);
+  if (st) return st;
+  Workspace &w = h->ws;
+  st = setup_image(h, lab, d1, s, true);
+  if (st) return st;
+  launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(w.h_flag, w.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(w.h_st, w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (w.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
+  if (w.h_st[0].done == kDoneBadInput) return fail(h, NPSOLVE_BAD_ARG, "b has non-finite entries on fluid cells");
+  st = get_graph(h, lab, d1, b, x);
+  if (st) return st;
+  int launched = 0, restarts = 0;
+  SolveState hs = w.h_st[0];
+  for (;;) {
+    // Replay the captured iterations until the device flags completion or the
+    // cap is reached.  The state copy of batch i is read only after batch i+1
+    // has been queued, so the GPU does not wait for the host between batches.
+    int nb = 0;
+    while (hs.done == kDoneRunning && launched < max_iter) {
+      if (max_iter - launched >= kPollEvery) {
+        CK(h, cudaGraphLaunch(w.graph, s));
+        launched += kPollEvery;
+      } else {
+        enqueue_iteration(h, lab, d1, b, x, s);
+        CK(h, cudaGetLastError());
+        launched += 1;
+      }
+      CK(h, cudaMemcpyAsync(&w.h_st[nb & 1], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaEventRecord(w.ev[nb & 1], s));
+      if (nb >= 1) {
+        CK(h, cudaEventSynchronize(w.ev[(nb - 1) & 1]));
+        hs = w.h_st[(nb - 1) & 1];
+      }
+      nb += 1;
+    }
+    CK(h, cudaStreamSynchronize(s));
+    if (nb) hs = w.h_st[(nb - 1) & 1];
+    if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&
+        restarts < kMaxRestarts) {
+      launch_replace_residual(lab, d1, b, x, w.r, w.part, w.st, w.reopened, s);
+      CK(h, cudaMemcpyAsync(w.h_flag, w.reopened, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaStreamSynchronize(s));
+      hs = w.h_st[0];
+      if (w.h_flag[0]) {
+        restarts += 1;
+        launched = hs.k;
+        continue;
+      }
+    }
+    break;
+  }
+  launch_relres(lab, d1, b, x, w.part, w.relres, s);
+  double rr[2];
+  CK(h, cudaMemcpyAsync(rr, w.relres, sizeof(rr), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  hs = w.h_st[0];
+  *iters = hs.k;
+  *rel_residual = rr[0];
+  h->last_hist.resize(hs.k + 1);
+  CK(h, cudaMemcpy(h->last_hist.data(), w.hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost));
+  if (hs.done == kDoneBreakdown) return fail(h, NPSOLVE_BREAKDOWN, "breakdown: d^T A d <= 0 or non-finite at iteration %d", hs.k + 1);
+  if (hs.done != kDoneConverged) return fail(h, NPSOLVE_NO_CONVERGENCE, "no convergence in %d iterations", hs.k);
+  h->err.clear();
+  return NPSOLVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t npsolve_weight_count(int levels) { return weight_count(levels); }
+
+int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t n_weights, npsolve_t *out) {
+  if (!cfg || !out) return fail(nullptr, NPSOLVE_BAD_ARG, "null argument");
+  *out = nullptr;
+  if (cfg->levels < 1 || cfg->levels > kMaxLevels) return fail(nullptr, NPSOLVE_BAD_ARG, "levels must be 1..%d", kMaxLevels);
+  if (cfg->n_ortho < 0 || cfg->n_ortho > kMaxOrtho) return fail(nullptr, NPSOLVE_BAD_ARG, "n_ortho must be 0..%d", kMaxOrtho);
+  if (cfg->precision != NPSOLVE_FP32 && cfg->precision != NPSOLVE_BF16)
+    return fail(nullptr, NPSOLVE_BAD_ARG, "precision must be NPSOLVE_FP32 or NPSOLVE_BF16");
+  if (cfg->residual_mode != NPSOLVE_RESIDUAL_RECURRENCE && cfg->residual_mode != NPSOLVE_RESIDUAL_EXPLICIT)
+    return fail(nullptr, NPSOLVE_BAD_ARG, "bad residual_mode");
+  if (!weights_host || n_weights != weight_count(cfg->levels))
+    return fail(nullptr, NPSOLVE_BAD_ARG, "expected %zu weights for %d levels", weight_count(cfg->levels), cfg->levels);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(nullptr, NPSOLVE_CUDA_ERROR, "no CUDA device: %s", cudaGetErrorString(e));
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return fail(nullptr, NPSOLVE_CUDA_ERROR, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+  if (prop.major * 10 + prop.minor != 103)
+    return fail(nullptr, NPSOLVE_CUDA_ERROR, "device %s is sm_%d%d; this library is built for sm_103a", prop.name,
+                prop.major, prop.minor);
+  npsolve *h = new npsolve();
+  h->cfg = *cfg;
+  h->device = dev;
+  h->weights.assign(weights_host, weights_host + n_weights);
+  int st = NPSOLVE_OK;
+  {
+    cudaError_t e1 = cudaMalloc(&h->cw, sizeof(CConvW) * (kMaxLevels + 1) * 2);
+    cudaError_t e2 = cudaMalloc(&h->aw, sizeof(AffW) * (kMaxLevels + 1) * 2);
+    cudaError_t e3 = cudaMalloc(&h->unit_c12, 2 * sizeof(double));
+    cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e1 || e2 || e3 || e4) st = fail(nullptr, NPSOLVE_OOM, "device allocation failed");
+  }
+  if (!st) {
+    const double one_zero[2] = {1.0, 0.0};
+    if (cudaMemcpy(h->unit_c12, one_zero, sizeof(one_zero), cudaMemcpyHostToDevice) != cudaSuccess)
+      st = fail(nullptr, NPSOLVE_CUDA_ERROR, "cudaMemcpy failed");
+  }
+  if (!st) st = upload_weights(h);
+  if (st) {
+    g_thread_error = h->err.empty() ? g_thread_error : h->err;
+    npsolve_destroy(h);
+    return st;
+  }
+  *out = h;
+  return NPSOLVE_OK;
+}
+
+int npsolve_set_weights(npsolve_t h, const float *weights_host, size_t n) {
+  if (!h || !weights_host) return fail(h, NPSOLVE_BAD_ARG, "null argument");
+  if (n != h->weights.size()) return fail(h, NPSOLVE_BAD_ARG, "expected %zu weights", h->weights.size());
+  CK(h, cudaSetDevice(h->device));
+  h->weights.assign(weights_host, weights_host + n);
+  return upload_weights(h);
+}
+
+int npsolve_get_weights(npsolve_t h, float *weights_host, size_t n) {
+  if (!h || !weights_host) return fail(h, NPSOLVE_BAD_ARG, "null argument");
+  if (n != h->weights.size()) return fail(h, NPSOLVE_BAD_ARG, "expected %zu weights", h->weights.size());
+  memcpy(weights_host, h->weights.data(), n * sizeof(float));
+  return NPSOLVE_OK;
+}
+
+void npsolve_destroy(npsolve_t h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  free_ws(h->ws);
+  cudaFree(h->cw);
+  cudaFree(h->aw);
+  cudaFree(h->unit_c12);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+const char *npsolve_last_error(npsolve_t h) { return h ? h->err.c_str() : g_thread_error.c_str(); }
+
+int npsolve_solve(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol,
+                  int max_iter, void *stream, double *x, int *iters, double *rel_residual) {
+  return solve_impl(h, labels, nx, ny, nz, b, tol, max_iter, (cudaStream_t)stream, x, iters, rel_residual);
+}
+
+int npsolve_solve_host(npsolve_t h, const uint8_t *labels_host, int nx, int ny, int nz, const float *b_host,
+                       double tol, int max_iter, void *stream, double *x_host, int *iters, double *rel_residual) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!labels_host || !b_host || !x_host) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  int st = check_dims(h, nx, ny, nz);
+  if (st) return st;
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ensure_ws(h, Dims{nx, ny, nz}, max_iter + 1);
+  if (st) return st;
+  Workspace &w = h->ws;
+  const size_t n = (size_t)nx * ny * nz;
+  if (!w.stage_lab) {  // staging buffers live as long as the workspace
+    CK(h, dalloc(&w.stage_lab, (size_t)w.cap));
+    CK(h, dalloc(&w.stage_b, (size_t)w.cap));
+    CK(h, dalloc(&w.stage_x, (size_t)w.cap));
+  }
+  CK(h, cudaMemcpyAsync(w.stage_lab, labels_host, n, cudaMemcpyHostToDevice, s));
+  CK(h, cudaMemcpyAsync(w.stage_b, b_host, n * sizeof(float), cudaMemcpyHostToDevice, s));
+  int ret = solve_impl(h, w.stage_lab, nx, ny, nz, w.stage_b, tol, max_iter, s, w.stage_x, iters, rel_residual);
+  if (ret == NPSOLVE_OK || ret == NPSOLVE_NO_CONVERGENCE || ret == NPSOLVE_BREAKDOWN) {
+    CK(h, cudaMemcpyAsync(x_host, w.stage_x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+  }
+  return ret;
+}
+
+int npsolve_residual_history(npsolve_t h, double *hist_host, int cap, int *count) {
+  if (!h || !hist_host || !count) return fail(h, NPSOLVE_BAD_ARG, "null argument");
+  const int m = (int)h->last_hist.size() < cap ? (int)h->last_hist.size() : cap;
+  memcpy(hist_host, h->last_hist.data(), sizeof(double) * (m > 0 ? m : 0));
+  *count = m;
+  return NPSOLVE_OK;
+}
+
+int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r,
+                                 int level, int which, float *out, double *c12_host, void *stream) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!labels || !r || !out) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  const int L = h->cfg.levels;
+  if (level < 0 || level > L || which < 0 || which > 4) return fail(h, NPSOLVE_BAD_ARG, "bad level/which");
+  int st = check_dims(h, nx, ny, nz);
+  if (st) return st;
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d1{nx, ny, nz};
+  st = ensure_ws(h, d1, 1);
+  if (st) return st;
+  Workspace &w = h->ws;
+  st = setup_image(h, labels, d1, s, true);
+  if (st) return st;
+  CK(h, cudaMemcpyAsync(w.h_flag, w.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (w.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
+  run_network(h, labels, d1, r, nullptr, w.z, nullptr, s);
+  CK(h, cudaGetLastError());
+  if (level == 0) {  // the network output z
+    CK(h, cudaMemcpyAsync(out, w.z, sizeof(float) * d1.n(), cudaMemcpyDeviceToDevice, s));
+  } else {
+    const long long nl = level_dims(d1, level).n();
+    const float *src = nullptr;
+    if (which == 0) src = w.x1[level];
+    else if (which == 1) src = level < L ? w.r2[level] : nullptr;
+    else if (which == 2) src = level < L ? w.x2[level] : nullptr;
+    else if (which == 3) src = level == L ? w.x1[L] : (level == 1 ? w.z : w.xc[level]);
+    else src = level == 1 ? r : w.r1[level];
+    if (!src) return fail(h, NPSOLVE_BAD_ARG, "level %d has no such intermediate", level);
+    CK(h, cudaMemcpyAsync(out, src, sizeof(float) * nl, cudaMemcpyDeviceToDevice, s));
+    if (c12_host) {
+      if (level < L) CK(h, cudaMemcpyAsync(c12_host, w.affc + 2 * level, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      else c12_host[0] = c12_host[1] = 0.0;
+    }
+  }
+  CK(h, cudaStreamSynchronize(s));
+  return NPSOLVE_OK;
+}
+
+int npsolve_apply_network(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r, float *z,
+                          void *stream) {
+  return npsolve_network_intermediate(h, labels, nx, ny, nz, r, 0, 0, z, nullptr, stream);
+}
+
+int npsolve_apply_laplacian(const uint8_t *labels, int nx, int ny, int nz, const float *d, float *q, void *stream) {
+  if (!labels || !d || !q) return fail(nullptr, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
+    return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
+  launch_lap(labels, Dims{nx, ny, nz}, d, q, (cudaStream_t)stream);
+  CK(nullptr, cudaGetLastError());
+  CK(nullptr, cudaStreamSynchronize((cudaStream_t)stream));
+  return NPSOLVE_OK;
+}
+
+int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const float *b, const double *x,
+                          double *rel_residual, void *stream) {
+  if (!labels || !b || !x || !rel_residual) return fail(nullptr, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
+    return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *part = nullptr;
+  CK(nullptr, cudaMallocAsync((void **)&part, sizeof(double) * (kRedMaxBlocks * 2 + 2), s));
+  launch_relres(labels, Dims{nx, ny, nz}, b, x, part, part + kRedMaxBlocks * 2, s);
+  double rr[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(rr, part + kRedMaxBlocks * 2, sizeof(rr), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(part, s);
+  CK(nullptr, e);
+  CK(nullptr, cudaStreamSynchronize(s));
+  *rel_residual = rr[0];
+  return NPSOLVE_OK;
+}
+
+int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol, int max_iter,
+                       void *stream, double *x, int *iters, double *rel_residual) {
+  if (!labels || !b || !x || !iters || !rel_residual) return fail(nullptr, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
+    return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
+  if (!(tol > 0.0) || max_iter < 0) return fail(nullptr, NPSOLVE_BAD_ARG, "bad tol/max_iter");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims dm{nx, ny, nz};
+  const size_t n = dm.n();
+  float *r = nullptr, *p = nullptr, *q = nullptr;
+  double *part = nullptr, *hist = nullptr;
+  void *st = nullptr;
+  int *hst = nullptr;
+  CK(nullptr, cudaMalloc(&r, n * 4));
+  CK(nullptr, cudaMalloc(&p, n * 4));
+  CK(nullptr, cudaMalloc(&q, n * 4));
+  CK(nullptr, cudaMalloc(&part, sizeof(double) * (kRedMaxBlocks * 2 + 2)));
+  CK(nullptr, cudaMalloc(&hist, sizeof(double) * (max_iter + 1)));
+  CK(nullptr, cudaMalloc(&st, pcg_state_bytes()));
+  CK(nullptr, cudaHostAlloc((void **)&hst, 64, cudaHostAllocDefault));
+  launch_pcg_init(labels, dm, b, r, p, x, part, tol, st, hist, s);
+  int launched = 0, done = 0, k = 0;
+  while (launched < max_iter) {
+    const int batch = (max_iter - launched) < 16 ? (max_iter - launched) : 16;
+    for (int i = 0; i < batch; ++i) launch_pcg_iter(labels, dm, x, r, p, q, part, st, hist, s);
+    launched += batch;
+    cudaMemcpyAsync(hst, st, pcg_state_bytes() < 64 ? pcg_state_bytes() : 64, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    done = *(int *)((char *)hst + pcg_done_offset());
+    if (done) break;
+  }
+  cudaMemcpyAsync(hst, st, pcg_state_bytes() < 64 ? pcg_state_bytes() : 64, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  done = *(int *)((char *)hst + pcg_done_offset());
+  k = *(int *)((char *)hst + pcg_k_offset());
+  launch_relres(labels, dm, b, x, part, part + kRedMaxBlocks * 2, s);
+  double rr[2] = {0, 0};
+  cudaMemcpyAsync(rr, part + kRedMaxBlocks * 2, sizeof(rr), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(r);
+  cudaFree(p);
+  cudaFree(q);
+  cudaFree(part);
+  cudaFree(hist);
+  cudaFree(st);
+  cudaFreeHost(hst);
+  CK(nullptr, e);
+  *iters = k;
+  *rel_residual = rr[0];
+  if (done == kDoneBadInput) return fail(nullptr, NPSOLVE_BAD_ARG, "non-finite b");
+  if (done == kDoneBreakdown) return fail(nullptr, NPSOLVE_BREAKDOWN, "PCG breakdown");
+  if (done != kDoneConverged) return fail(nullptr, NPSOLVE_NO_CONVERGENCE, "no convergence in %d iterations", k);
+  return NPSOLVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (FP32 form; the oracle is FP64):
+* Laplacian: integer stencil on FP32 data, each output is a sum of at most
+  7 FP32 terms computed as differences: |q - q_oracle| <= 4 eps32 (sum of |terms|).
+* Network intermediates / output: every CConv output is a 27-term dot product
+  of kernels that are 55-term FP32 sums; rounding compounds over the levels.
+  Norm-wise relative error <= 1e-5 (measured ~1e-7 .. 1e-6), element-wise
+  <= 1e-4 of the field's max.
+* Solve: identical iteration count, ||x - x_oracle|| / ||x_oracle|| <= 1e-5
+  (the FP32 form target), with constants removed on pure-Neumann components
+  (the solution is unique only up to them).  The count must match exactly
+  when the oracle's last two residuals are at least 5% away from the
+  threshold tol*||b||: the FP32 recurrence residual drifts from the FP64 one
+  by about eps32 ||b|| per iteration, which moves ||r_k|| by far less than
+  5% at ||r_k|| ~ 1e-6 ||b||.  Inside that band a difference of one is allowed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_00177_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _binding():
+    from paper_2310_00177_b300 import binding
+
+    return binding
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _rng_labels(shape, seed, p=(0.2, 0.6, 0.2)):
+    rng = np.random.default_rng(seed)
+    return rng.choice(np.array([0, 1, 2], np.uint8), size=shape, p=p)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _remove_neumann_constants(labels, x):
+    comp, pure = synth.neumann_components(labels)
+    x = x.copy()
+    for c in pure:
+        m = comp == c
+        x[m] -= x[m].mean()
+    return x
+
+
+SHAPES = [(32, 32, 32), (24, 40, 56), (8, 16, 8)]
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(5, 7, 9)])
+def test_laplacian_matches_oracle(shape):
+    b = _binding()
+    lab = _rng_labels(shape, 1)
+    d = np.random.default_rng(2).standard_normal(shape).astype(np.float32)
+    q = b.apply_laplacian(_dev(lab, torch.uint8), _dev(d, torch.float32)).cpu().numpy()
+    qo = oracle.lap_apply(lab, d.astype(np.float64))
+    scale = 7 * np.abs(d).max()
+    assert np.abs(q - qo).max() <= 4 * np.finfo(np.float32).eps * scale
+    assert not q[lab != 1].any()
+
+
+@pytest.mark.parametrize("shape,L", [((32, 32, 32), 4), ((24, 40, 56), 4), ((16, 8, 24), 3), ((8, 8, 8), 1)])
+def test_network_levels_match_oracle(shape, L):
+    b = _binding()
+    lab = _rng_labels(shape, 3) if shape != (32, 32, 32) else synth.pool_scene(32, 1000)
+    w = synth.init_weights(L, 11, spread=0.05)
+    r = np.random.default_rng(4).standard_normal(shape).astype(np.float32)
+    s = b.Solver(w, levels=L)
+    lab_d, r_d = _dev(lab, torch.uint8), _dev(r, torch.float32)
+    # network output
+    z = s.apply_network(lab_d, r_d).cpu().numpy()
+    zo = oracle.network(lab, L, w.astype(np.float32).astype(np.float64), r.astype(np.float64))
+    assert _rel(z, zo) <= 1e-5
+    assert np.abs(z - zo).max() <= 1e-4 * np.abs(zo).max()
+    assert not z[lab != 1].any()
+    # every intermediate of every level, and the Aff coefficients
+    for lvl in range(1, L + 1):
+        names = ["x1", "r1"] + (["r2", "x2", "x"] if lvl < L else [])
+        for which in names:
+            if lvl == 1 and which in ("r1", "x"):  # the level-1 output is z, compared above
+                continue
+            g, c12 = s.network_intermediate(lab_d, r_d, lvl, which)
+            o, oc12 = oracle.network_level(lab, L, w.astype(np.float32).astype(np.float64), r.astype(np.float64),
+                                           lvl, which)
+            assert _rel(g.cpu().numpy(), o) <= 1e-5, (lvl, which, _rel(g.cpu().numpy(), o))
+            if lvl < L:
+                np.testing.assert_allclose(c12, oc12, rtol=1e-6)
+    s.close()
+
+
+def _config1():
+    lab = synth.pool_scene(32, 1000)
+    rhs = synth.rhs_normal(lab, 1001).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    return lab, rhs, w
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_solve_config1_matches_oracle(mode):
+    b = _binding()
+    lab, rhs, w = _config1()
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-6, max_iter=500,
+                        residual_mode=mode)
+    assert ores["status"] == oracle.OK
+    # stopping margin of the oracle: last two residuals are well separated from tol*||b||
+    h = ores["res_hist"] / ores["res_hist"][0]
+    assert h[-1] < 0.95e-6 and h[-2] > 1.05e-6
+    s = b.Solver(w, levels=4, n_ortho=2, residual_mode=mode)
+    x, iters, relres, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-6, max_iter=500)
+    assert st == b.OK
+    assert iters == ores["iters"]
+    assert relres < 1e-6
+    xg = x.cpu().numpy()
+    assert _rel(_remove_neumann_constants(lab, xg), _remove_neumann_constants(lab, ores["x"])) <= 1e-5
+    hist = s.residual_history()
+    assert len(hist) == iters + 1
+    np.testing.assert_allclose(hist / hist[0], h, rtol=1e-3, atol=1e-9)
+    s.close()
+
+
+@pytest.mark.parametrize("n_ortho,L,tol", [(0, 4, 1e-4), (1, 3, 1e-5), (3, 4, 1e-5), (2, 5, 1e-5)])
+def test_solve_variants_match_oracle(n_ortho, L, tol):
+    b = _binding()
+    lab = synth.slosh_scene(32, 77)
+    rhs = synth.rhs_normal(lab, 78).astype(np.float32)
+    w = synth.init_weights(L, 79).astype(np.float32)
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=L, w=w.astype(np.float64), tol=tol, max_iter=3000,
+                        n_ortho=n_ortho)
+    s = b.Solver(w, levels=L, n_ortho=n_ortho)
+    x, iters, relres, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=tol, max_iter=3000)
+    h = ores["res_hist"] / ores["res_hist"][0]
+    if h[-1] < 0.95 * tol and h[-2] > 1.05 * tol:
+        assert iters == ores["iters"]
+    else:  # the oracle's stop is within rounding distance of the threshold
+        assert abs(iters - ores["iters"]) <= 1
+    assert st == b.OK and relres < tol
+    assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 2e-5
+    s.close()
+
+
+def test_solve_host_equals_device_solve():
+    b = _binding()
+    lab, rhs, w = _config1()
+    s = b.Solver(w)
+    x, it, rr, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32))
+    xh, ith, rrh, sth = s.solve_host(lab, rhs)
+    assert st == sth == b.OK and it == ith and rr == rrh
+    np.testing.assert_array_equal(x.cpu().numpy(), xh)
+    # and a repeated device solve is bitwise identical (deterministic reductions)
+    x2, it2, rr2, _ = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32))
+    assert it2 == it and rr2 == rr
+    assert torch.equal(x, x2)
+    s.close()
+
+
+def test_true_residual_matches_oracle():
+    b = _binding()
+    lab, rhs, _ = _config1()
+    x = np.random.default_rng(5).standard_normal(lab.shape)
+    g = b.true_residual(_dev(lab, torch.uint8), _dev(rhs, torch.float32), _dev(x, torch.float64))
+    bm = np.where(lab == 1, rhs.astype(np.float64), 0.0)
+    ref = np.linalg.norm(bm - oracle.lap_apply(lab, x)) / np.linalg.norm(bm)
+    assert g == pytest.approx(ref, rel=1e-12)
+
+
+def test_jacobi_pcg_matches_oracle():
+    b = _binding()
+    lab, rhs, _ = _config1()
+    ores = oracle.jacobi_pcg(lab, rhs.astype(np.float64), tol=1e-6)
+    x, iters, relres, st = b.jacobi_pcg(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-6)
+    assert st == b.OK and relres < 1.2e-6
+    assert abs(iters - ores["iters"]) <= max(2, ores["iters"] // 50)
+    assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-4
+
+
+def test_error_statuses():
+    b = _binding()
+    lab, rhs, w = _config1()
+    s = b.Solver(w)
+    labd, rhsd = _dev(lab, torch.uint8), _dev(rhs, torch.float32)
+    # iteration cap: NO_CONVERGENCE with x, iters, residual written
+    x, it, rr, st = s.solve(labd, rhsd, max_iter=3)
+    assert st == b.NO_CONVERGENCE and it == 3 and 0 < rr < 1
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), max_iter=3)
+    assert _rel(x.cpu().numpy(), ores["x"]) <= 1e-5
+    # zero right-hand side: converged in 0 iterations, x = 0
+    x, it, rr, st = s.solve(labd, torch.zeros_like(rhsd))
+    assert st == b.OK and it == 0 and not x.any()
+    # bad labels / dims / NaN
+    bad = lab.copy()
+    bad[3, 3, 3] = 7
+    with pytest.raises(b.NpsolveError) as e:
+        s.solve(_dev(bad, torch.uint8), rhsd)
+    assert e.value.status == b.BAD_LABELS
+    with pytest.raises(b.NpsolveError) as e:
+        s.solve(labd[:, :, :30].contiguous(), rhsd[:, :, :30].contiguous())
+    assert e.value.status == b.BAD_DIMS
+    nanb = rhs.copy()
+    nanb[tuple(np.argwhere(lab == 1)[0])] = np.nan
+    with pytest.raises(b.NpsolveError) as e:
+        s.solve(labd, _dev(nanb, torch.float32))
+    assert e.value.status == b.BAD_ARG
+    s.close()
+    # an all-zero network yields d = 0: breakdown
+    z = b.Solver(np.zeros(b.weight_count(2), np.float32), levels=2)
+    x, it, rr, st = z.solve(labd, rhsd, max_iter=5)
+    assert st == b.BREAKDOWN
+    z.close()
+
+
+def test_solve_slosh_64_matches_oracle():
+    b = _binding()
+    lab = synth.slosh_scene(64, 2000)
+    rhs = synth.rhs_normal(lab, 2001).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-6, max_iter=1000)
+    s = b.Solver(w)
+    x, iters, relres, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-6, max_iter=1000)
+    h = ores["res_hist"] / ores["res_hist"][0]
+    margin_ok = h[-1] < 0.95e-6 and h[-2] > 1.05e-6
+    assert st == b.OK and relres < 1e-6
+    if margin_ok:
+        assert iters == ores["iters"]
+    else:
+        assert abs(iters - ores["iters"]) <= 1
+    assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-5
+    s.close()
