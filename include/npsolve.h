@@ -59,8 +59,10 @@ enum { NPSOLVE_LABEL_SOLID = 0, NPSOLVE_LABEL_FLUID = 1, NPSOLVE_LABEL_AIR = 2 }
 /* Precision forms of the network evaluation.  Vectors are FP32, dot products
  * and orthogonalisation coefficients FP64 and x FP64 in both forms. */
 enum {
-  NPSOLVE_FP32 = 0, /* per-cell kernels generated to FP32 accuracy */
-  NPSOLVE_BF16 = 1  /* kernel generation with BF16 weights on the tensor cores, FP32 accumulation */
+  NPSOLVE_FP32 = 0, /* per-cell kernels generated to FP32 accuracy (on the tensor cores: the FP32
+                       weights split into three BF16 terms, FP32 accumulation) */
+  NPSOLVE_BF16 = 1  /* CConv weights rounded to BF16 (one tensor-core pass, FP32 accumulation);
+                       vectors, Aff coefficients and the solver as in the FP32 form */
 };
 
 /* Residual update of Alg. 1. */
@@ -71,11 +73,19 @@ enum {
   NPSOLVE_RESIDUAL_EXPLICIT = 1    /* r_k = b - A x_k every iteration, as printed in Alg. 1 */
 };
 
+/* Where the per-cell kernel generation of CConv runs. */
+enum {
+  NPSOLVE_PATH_TENSOR = 0,  /* tcgen05 tensor cores on levels 1-3 (image counts exact in BF16),
+                               CUDA cores on coarser levels */
+  NPSOLVE_PATH_CUDA_CORE = 1 /* CUDA cores (FP32 FMA) on every level; the reference path */
+};
+
 typedef struct {
   int levels;        /* L, number of network levels, 1..7 (paper: 6; L = 4 ~ 16k parameters) */
   int n_ortho;       /* directions to A-orthogonalise against, 0..4 (paper: 2, Sec. 4.1) */
   int precision;     /* NPSOLVE_FP32 or NPSOLVE_BF16 */
   int residual_mode; /* NPSOLVE_RESIDUAL_RECURRENCE or NPSOLVE_RESIDUAL_EXPLICIT */
+  int kernel_path;   /* NPSOLVE_PATH_TENSOR or NPSOLVE_PATH_CUDA_CORE */
 } npsolve_config;
 
 /* Number of FP32 network parameters for L levels (Alg. 2): for each level
@@ -157,6 +167,14 @@ int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const f
  * conventions as npsolve_solve; the same-device comparison solver. */
 int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol, int max_iter,
                        void *stream, double *x, int *iters, double *rel_residual);
+
+/* Self-test of the tensor-core data path (tcgen05.mma with the A operand in
+ * tensor memory and the B operand in shared memory, as used by CConv): one
+ * 128 x 32 x 64 BF16 product of exactly representable values, compared with
+ * the CUDA-core result.  *max_abs_err (host) receives the largest absolute
+ * difference (0 when the path is correct).  Returns NPSOLVE_CUDA_ERROR if the
+ * device is not sm_103a or the MMA did not complete within 1 s. */
+int npsolve_selftest_tensor_core(double *max_abs_err);
 
 #ifdef __cplusplus
 }

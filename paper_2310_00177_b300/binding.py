@@ -17,6 +17,7 @@ _LIB_PATH = os.path.join(HERE, "libnpsolve.so")
 
 OK, BAD_ARG, BAD_DIMS, BAD_LABELS, NO_CONVERGENCE, BREAKDOWN, OOM, CUDA_ERROR = range(8)
 FP32, BF16 = 0, 1
+PATH_TENSOR, PATH_CUDA_CORE = 0, 1
 RECURRENCE, EXPLICIT = 0, 1
 STATUS_NAMES = ["OK", "BAD_ARG", "BAD_DIMS", "BAD_LABELS", "NO_CONVERGENCE", "BREAKDOWN", "OOM", "CUDA_ERROR"]
 
@@ -29,7 +30,7 @@ class NpsolveError(RuntimeError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("n_ortho", ctypes.c_int), ("precision", ctypes.c_int),
-                ("residual_mode", ctypes.c_int)]
+                ("residual_mode", ctypes.c_int), ("kernel_path", ctypes.c_int)]
 
 
 _lib = None
@@ -54,6 +55,7 @@ SIGNATURES = {
     "npsolve_apply_laplacian": ([_vp, _i, _i, _i, _vp, _vp, _vp], _i),
     "npsolve_true_residual": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_jacobi_pcg": ([_vp, _i, _i, _i, _vp, _d, _i, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_d)], _i),
+    "npsolve_selftest_tensor_core": ([ctypes.POINTER(_d)], _i),
 }
 
 
@@ -114,16 +116,18 @@ def weight_count(levels: int) -> int:
 class Solver:
     """A solver handle: network weights + device workspace (npsolve_t)."""
 
-    def __init__(self, weights, levels=4, n_ortho=2, precision=FP32, residual_mode=RECURRENCE):
+    def __init__(self, weights, levels=4, n_ortho=2, precision=FP32, residual_mode=RECURRENCE,
+                 kernel_path=PATH_TENSOR):
         lib = load_library()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
-        cfg = _Config(levels, n_ortho, precision, residual_mode)
+        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path)
         h = ctypes.c_void_p()
         st = lib.npsolve_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, ctypes.byref(h))
         if st != OK:
             raise NpsolveError(st, lib.npsolve_last_error(None).decode())
         self._h = h
         self.levels, self.n_ortho, self.precision, self.residual_mode = levels, n_ortho, precision, residual_mode
+        self.kernel_path = kernel_path
 
     def close(self):
         if getattr(self, "_h", None):
@@ -249,3 +253,10 @@ def jacobi_pcg(labels, b, tol=1e-6, max_iter=100000, x=None):
     if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
         _check(st)
     return x, it.value, rr.value, st
+
+
+def selftest_tensor_core():
+    """Max abs error of one tcgen05 BF16 MMA (A in TMEM, B in smem) vs CUDA cores."""
+    e = ctypes.c_double(-1.0)
+    _check(load_library().npsolve_selftest_tensor_core(ctypes.byref(e)))
+    return e.value

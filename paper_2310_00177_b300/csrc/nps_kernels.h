@@ -46,4 +46,12 @@ void launch_combine(long long n, const float *x1, const float *x2, const double 
 void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
                      const float *qring, double *part, const SolveState *st, cudaStream_t s);
 
+// kernels_umma.cu
+void prepare_umma_weights(const CConvW &w, int nsplit, uint8_t *out);
+int umma_weight_bytes(int nsplit);
+void launch_cconv_umma(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
+                       const float *v, const float *vscale, int mask_input, float *out, const SolveState *st,
+                       int *err, int num_sms, cudaStream_t s);
+void launch_umma_selftest(float *d_out, float *d_ref, int *err, cudaStream_t s);
+
 }  // namespace nps

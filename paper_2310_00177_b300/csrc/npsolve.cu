@@ -78,6 +78,10 @@ struct npsolve {
   int device = 0;
   std::vector<float> weights;      // host copy of the flat blob
   CConvW *cw = nullptr;            // [(kMaxLevels+1)*2], index lvl*2 + (type-1)
+  uint8_t *uw = nullptr;           // tensor-core W splits, [(kMaxLevels+1)*2][umma_weight_bytes(3)]
+  int nsplit = 3;                  // BF16 terms of W on the tensor cores (3: FP32 form, 1: BF16 form)
+  int num_sms = 148;
+  int *umma_err = nullptr;         // set by a tensor-core kernel whose MMA wait timed out
   AffW *aw = nullptr;              // [(kMaxLevels+1)*2]
   double *unit_c12 = nullptr;      // {1, 0} for L = 1
   Workspace ws;
@@ -248,6 +252,31 @@ int upload_weights(npsolve *h) {
       fold_aff(base + 2 * kCConvParams + kAffParams, lvl, aw[lvl * 2 + 1]);
     }
   }
+  if (h->cfg.precision == NPSOLVE_BF16) {
+    // the BF16 form: every folded CConv weight rounded to BF16 (nearest even)
+    auto rnd = [](float f) {
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+      memcpy(&f, &u, 4);
+      return f;
+    };
+    for (auto &c : cw) {
+      for (int a = 0; a < 27; ++a) {
+        for (int l = 0; l < 27; ++l) {
+          c.wf[a][l] = rnd(c.wf[a][l]);
+          c.wa[a][l] = rnd(c.wa[a][l]);
+        }
+        c.bp[a] = rnd(c.bp[a]);
+      }
+    }
+  }
+  {
+    const int wb = umma_weight_bytes(3);
+    std::vector<uint8_t> uw((size_t)(kMaxLevels + 1) * 2 * wb, 0);
+    for (int i = 0; i < (kMaxLevels + 1) * 2; ++i) prepare_umma_weights(cw[i], h->nsplit, uw.data() + (size_t)i * wb);
+    CK(h, cudaMemcpy(h->uw, uw.data(), uw.size(), cudaMemcpyHostToDevice));
+  }
   CK(h, cudaMemcpy(h->cw, cw.data(), cw.size() * sizeof(CConvW), cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(h->aw, aw.data(), aw.size() * sizeof(AffW), cudaMemcpyHostToDevice));
   return NPSOLVE_OK;
@@ -270,9 +299,16 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
            int mask_input, float *out, const SolveState *st, cudaStream_t s) {
   Workspace &w = h->ws;
   const Dims dl = level_dims(d1, lvl);
-  const CConvW *cw = h->cw + lvl * 2 + (type - 1);
-  launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, cw, in, vscale, mask_input,
-                   out, st, s);
+  const int idx = lvl * 2 + (type - 1);
+  if (h->cfg.kernel_path == NPSOLVE_PATH_TENSOR && lvl <= 3) {
+    // image features exact in BF16 up to level 3 (counts <= 64)
+    launch_cconv_umma(h->nsplit, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl,
+                      h->uw + (size_t)idx * umma_weight_bytes(3), in, vscale, mask_input, out, st, h->umma_err,
+                      h->num_sms, s);
+    return;
+  }
+  launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw + idx, in, vscale,
+                   mask_input, out, st, s);
 }
 
 // The network z = P_net(I, r) of Alg. 2 on the prepared pyramid and Aff
@@ -328,6 +364,17 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
   launch_update(recur, n, x, w.r, w.dring, w.qring, w.part, w.st, w.hist, s);
   if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
+}
+
+// A tensor-core kernel that timed out waiting for its MMAs leaves a flag.
+int check_umma_err(npsolve *h) {
+  int e = 0;
+  CK(h, cudaMemcpy(&e, h->umma_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    cudaMemset(h->umma_err, 0, sizeof(int));
+    return fail(h, NPSOLVE_CUDA_ERROR, "tensor-core CConv: MMA completion wait timed out");
+  }
+  return NPSOLVE_OK;
 }
 
 int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x) {
@@ -425,6 +472,8 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
   hs = w.h_st[0];
   *iters = hs.k;
   *rel_residual = rr[0];
+  st = check_umma_err(h);
+  if (st) return st;
   h->last_hist.resize(hs.k + 1);
   CK(h, cudaMemcpy(h->last_hist.data(), w.hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost));
   if (hs.done == kDoneBreakdown) return fail(h, NPSOLVE_BREAKDOWN, "breakdown: d^T A d <= 0 or non-finite at iteration %d", hs.k + 1);
@@ -459,9 +508,13 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
   if (prop.major * 10 + prop.minor != 103)
     return fail(nullptr, NPSOLVE_CUDA_ERROR, "device %s is sm_%d%d; this library is built for sm_103a", prop.name,
                 prop.major, prop.minor);
+  if (cfg->kernel_path != NPSOLVE_PATH_TENSOR && cfg->kernel_path != NPSOLVE_PATH_CUDA_CORE)
+    return fail(nullptr, NPSOLVE_BAD_ARG, "bad kernel_path");
   npsolve *h = new npsolve();
   h->cfg = *cfg;
   h->device = dev;
+  h->nsplit = cfg->precision == NPSOLVE_BF16 ? 1 : 3;
+  h->num_sms = prop.multiProcessorCount;
   h->weights.assign(weights_host, weights_host + n_weights);
   int st = NPSOLVE_OK;
   {
@@ -469,7 +522,11 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
     cudaError_t e2 = cudaMalloc(&h->aw, sizeof(AffW) * (kMaxLevels + 1) * 2);
     cudaError_t e3 = cudaMalloc(&h->unit_c12, 2 * sizeof(double));
     cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
-    if (e1 || e2 || e3 || e4) st = fail(nullptr, NPSOLVE_OOM, "device allocation failed");
+    cudaError_t e5 = cudaMalloc(&h->uw, (size_t)(kMaxLevels + 1) * 2 * umma_weight_bytes(3));
+    cudaError_t e6 = cudaMalloc(&h->umma_err, sizeof(int));
+    if (e1 || e2 || e3 || e4 || e5 || e6) st = fail(nullptr, NPSOLVE_OOM, "device allocation failed");
+    if (!st && cudaMemset(h->umma_err, 0, sizeof(int)) != cudaSuccess)
+      st = fail(nullptr, NPSOLVE_CUDA_ERROR, "cudaMemset failed");
   }
   if (!st) {
     const double one_zero[2] = {1.0, 0.0};
@@ -508,6 +565,8 @@ void npsolve_destroy(npsolve_t h) {
   cudaFree(h->cw);
   cudaFree(h->aw);
   cudaFree(h->unit_c12);
+  cudaFree(h->uw);
+  cudaFree(h->umma_err);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
@@ -593,7 +652,7 @@ int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int
     }
   }
   CK(h, cudaStreamSynchronize(s));
-  return NPSOLVE_OK;
+  return check_umma_err(h);
 }
 
 int npsolve_apply_network(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r, float *z,
@@ -681,6 +740,35 @@ int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const floa
   if (done == kDoneBadInput) return fail(nullptr, NPSOLVE_BAD_ARG, "non-finite b");
   if (done == kDoneBreakdown) return fail(nullptr, NPSOLVE_BREAKDOWN, "PCG breakdown");
   if (done != kDoneConverged) return fail(nullptr, NPSOLVE_NO_CONVERGENCE, "no convergence in %d iterations", k);
+  return NPSOLVE_OK;
+}
+
+int npsolve_selftest_tensor_core(double *max_abs_err) {
+  if (!max_abs_err) return fail(nullptr, NPSOLVE_BAD_ARG, "null argument");
+  int dev = 0;
+  cudaDeviceProp prop;
+  CK(nullptr, cudaGetDevice(&dev));
+  CK(nullptr, cudaGetDeviceProperties(&prop, dev));
+  if (prop.major * 10 + prop.minor != 103)
+    return fail(nullptr, NPSOLVE_CUDA_ERROR, "device is sm_%d%d, not sm_103a", prop.major, prop.minor);
+  float *buf = nullptr;
+  int *err = nullptr;
+  CK(nullptr, cudaMalloc(&buf, 2 * 128 * 32 * sizeof(float)));
+  CK(nullptr, cudaMalloc(&err, sizeof(int)));
+  CK(nullptr, cudaMemset(err, 0, sizeof(int)));
+  launch_umma_selftest(buf, buf + 128 * 32, err, 0);
+  std::vector<float> hb(2 * 128 * 32);
+  int herr = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(hb.data(), buf, hb.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  cudaFree(err);
+  CK(nullptr, e);
+  if (herr) return fail(nullptr, NPSOLVE_CUDA_ERROR, "tensor-core self-test: MMA wait timed out");
+  double m = 0.0;
+  for (int i = 0; i < 128 * 32; ++i) m = fmax(m, fabs((double)hb[i] - (double)hb[128 * 32 + i]));
+  *max_abs_err = m;
   return NPSOLVE_OK;
 }
 
