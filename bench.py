@@ -1,0 +1,368 @@
+"""Benchmark: milliseconds per 256^3 NPSDO solve to 1e-6 relative residual.
+
+One step = one complete solve (setup from the labels, the NPSDO iterations,
+the final FP64 true-residual check) of a seeded 256^3 scene shaped like the
+paper's mixed-boundary examples (solid shell, 10-40 solid spheres/boxes,
+sinusoidal free surface, b ~ N(0,1) on fluid), in the BF16 served form.
+The inputs are resident in HBM when the timed region starts; every 256^3
+vector is 67 MB and one iteration touches about 1.5 GB, so the working set
+is far larger than the 126 MB L2 and no flush is needed between steps.
+
+Also reported on the same line:
+  e2e            the same solve through npsolve_solve_host (pinned host
+                 buffers in, x back to the host, copies inside the timing)
+  fp32_form      ms per solve and iterations of the FP32 form
+  accuracy       true relative residuals (FP64 oracle Laplacian), iterations
+                 of both forms, ||x_bf16 - x_fp32|| / ||x_fp32||
+  roofline       the dominant kernel class of a profiled solve (CUDA events
+                 around each launch on the solve's stream) against the
+                 measured peaks in MEASURED_PEAKS.json
+  cpu_baseline   the FP64 CPU oracle on a bounded sample of the same solve
+  clocks         nvidia-smi samples taken during the timed region
+
+--impl reference times the FP64 CPU oracle instead (the paper ships no code
+to run): each step is one oracle NPSDO iteration of the same 256^3 problem,
+scaled to a whole solve by the oracle's own iteration count for it.
+
+Multi-GPU: the path does not shard (every solve is independent), so N ranks
+run N independent replicas; value = total solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ms per 256^3 solve to 1e-6 rel. residual (BF16 served form)"
+WEIGHTS_FILE = os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32")
+ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
+
+# Algorithmic HBM bytes per fine cell for one launch of each kernel class
+# (inputs read once, outputs written once).
+BYTES_PER_CELL = {
+    "cconv_l1": 4 + 1 + 4,      # v, labels -> out
+    "lap_alpha": 4 + 1 + 4 + 4,  # d, labels, r -> q
+    "update": 8 + 8 + 4 + 4 + 4 + 4,  # x r/w (FP64), r r/w, d, q
+    "ortho_dir": 4 + 4 + 4 + 4,  # z, d1, d2 -> d
+    "combine": 4 + 4 + 4 + 1 + 8,  # x1, x2 -> z, labels, q1, q2 (level 1)
+    "interp": 4 + 0.5,           # fine out, coarse in (level 1 dominates)
+    "pool": 4 + 0.5,
+}
+# Algorithmic tensor flops per fine cell of one level-1 CConv launch:
+# 27 taps x 55 features (54 image features + bias) x 2.
+FLOPS_PER_CELL_CCONV = 2 * 27 * 55
+
+
+def load_weights():
+    from paper_2310_00177_b300 import synth
+
+    if os.path.exists(WEIGHTS_FILE):
+        return np.fromfile(WEIGHTS_FILE, dtype=np.float32), "trained (paper_2310_00177_b300/weights/npsdo_L4.f32)"
+    return synth.init_weights(4, 7).astype(np.float32), "random-init (seed 7)"
+
+
+def workload(n):
+    from paper_2310_00177_b300 import synth
+
+    lab = synth.slosh_scene(n, 3000)
+    rhs = synth.rhs_normal(lab, 3001).astype(np.float32)
+    return lab, rhs
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "src": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "src": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_iteration_ms(lab, rhs, w, iters_sample=1):
+    """Wall time of `iters_sample` FP64 oracle NPSDO iterations on the workload."""
+    import oracle
+
+    t = time.perf_counter()
+    oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-6, max_iter=iters_sample)
+    return (time.perf_counter() - t) * 1e3 / iters_sample
+
+
+def oracle_iterations(weights_desc):
+    if os.path.exists(ORACLE_ITERS_FILE):
+        d = json.load(open(ORACLE_ITERS_FILE))
+        if d.get("weights") == weights_desc:
+            return int(d["iters"]), "oracle FP64 solve of this problem (" + os.path.basename(ORACLE_ITERS_FILE) + ")"
+    return None, None
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle (rank 0 only)."""
+    if rank != 0:
+        return
+    lab, rhs = workload(args.n)
+    w, wdesc = load_weights()
+    cores = os.cpu_count()
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_iteration_ms(lab, rhs, w)
+    times = [cpu_oracle_iteration_ms(lab, rhs, w) for _ in range(args.steps)]
+    per_it = float(np.mean(times))
+    iters, src = oracle_iterations(wdesc)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no stored oracle iteration count for these weights "
+                          "(run oracle/count_iterations.py)"}))
+        return
+    value = per_it * iters
+    sample = f"1 FP64 oracle NPSDO iteration of the 256^3 solve per step, x {iters} iterations ({src})"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": min(args.warmup, 1), "ms_per_step": per_it, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"slosh {args.n}^3 mixed BC, L=4, n_ortho=2, tol 1e-6", "weights": wdesc},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--max-iter", type=int, default=5000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2310_00177_b300 import binding
+
+    lab, rhs = workload(args.n)
+    w, wdesc = load_weights()
+    lab_d = torch.from_numpy(lab).to(dev)
+    rhs_d = torch.from_numpy(rhs).to(dev)
+    x_d = torch.empty(lab.shape, dtype=torch.float64, device=dev)
+    sol = binding.Solver(w, levels=4, n_ortho=2, precision=binding.BF16)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        _, it_bf16, rr_bf16, st = sol.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x_d)
+    torch.cuda.synchronize()
+    # ---- timed region -------------------------------------------------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        launches0 = sol.launch_count()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, it_bf16, rr_bf16, st = sol.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x_d)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches_timed = sol.launch_count() - launches0
+    total_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = total_ms / (args.steps * world)
+    x_bf16 = x_d.cpu().numpy()
+
+    # ---- end to end through the host-buffer C-ABI call -------------------
+    lab_h = torch.from_numpy(lab).pin_memory()
+    rhs_h = torch.from_numpy(rhs).pin_memory()
+    x_h = torch.empty(lab.shape, dtype=torch.float64).pin_memory()
+    sol.solve_host(lab_h.numpy(), rhs_h.numpy(), 1e-6, args.max_iter, x=x_h.numpy())
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        sol.solve_host(lab_h.numpy(), rhs_h.numpy(), 1e-6, args.max_iter, x=x_h.numpy())
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = e2e_ms / world
+
+    # ---- FP32 form -----------------------------------------------------
+    sol32 = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
+    x32 = torch.empty_like(x_d)
+    sol32.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n32 = 2
+    for _ in range(n32):
+        _, it_fp32, rr_fp32, _ = sol32.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp32_ms = e0.elapsed_time(e1) / n32
+    x_fp32 = x32.cpu().numpy()
+
+    # ---- profiled solve: per-kernel-class device time (roofline) -------------
+    sol.set_profiling(True)
+    sol.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x_d)
+    torch.cuda.synchronize()
+    prof = sol.profile()
+    sol.set_profiling(False)
+
+    if rank != 0:
+        return
+    n = lab.size
+    pk = peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    avg_s = dom_ms / max(dom_launches, 1) / 1e3
+    if dom == "cconv_l1":
+        flops = FLOPS_PER_CELL_CCONV * n
+        achieved = flops / avg_s / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_cconv_umma<1> (level-1 CConv, BF16 form)",
+                "algorithmic": f"{FLOPS_PER_CELL_CCONV} flop/cell x {n} cells",
+                "hbm_achieved_gbs": BYTES_PER_CELL["cconv_l1"] * n / avg_s / 1e9,
+                "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"] + " (sustained bf16)"}
+    else:
+        bpc = BYTES_PER_CELL.get(dom, 0.0)
+        achieved = bpc * n / avg_s / 1e9
+        peak = pk["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "algorithmic": f"{bpc} B/cell x {n} cells",
+                "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"]}
+    total_prof = sum(v[0] for v in prof.values())
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total_prof, 4)}
+                 for k, v in prof.items() if v[1]}
+
+    import oracle
+
+    bm = np.where(lab == 1, rhs.astype(np.float64), 0.0)
+    nb = np.linalg.norm(bm)
+
+    def true_rel(x):
+        return float(np.linalg.norm(bm - oracle.lap_apply(lab, x)) / nb)
+
+    accuracy = {
+        "iters_bf16": it_bf16, "iters_fp32": it_fp32,
+        "true_relres_bf16_fp64_oracle": true_rel(x_bf16), "true_relres_fp32_fp64_oracle": true_rel(x_fp32),
+        "x_bf16_vs_fp32_rel": float(np.linalg.norm(x_bf16 - x_fp32) / np.linalg.norm(x_fp32)),
+    }
+    cpu = None
+    if not args.no_cpu:
+        per_it = cpu_oracle_iteration_ms(lab, rhs, w)
+        cpu = {"value": per_it * it_bf16, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"1 FP64 oracle NPSDO iteration of this 256^3 solve ({per_it:.0f} ms), "
+                         f"scaled by the {it_bf16} iterations of the timed solve"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"slosh {args.n}^3 mixed BC (seed 3000), b ~ N(0,1) (seed 3001), L=4, n_ortho=2, "
+                               f"tol 1e-6", "weights": wdesc, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": int(lab.nbytes + rhs.nbytes),
+                "d2h_bytes_per_step": int(n * 8)},
+        "fp32_form": {"ms_per_solve": fp32_ms, "iters": it_fp32},
+        "accuracy": accuracy,
+        "roofline": roof,
+        "kernel_breakdown": breakdown,
+        "gpu_launches": int(launches_timed),
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -168,6 +168,23 @@ int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const f
 int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol, int max_iter,
                        void *stream, double *x, int *iters, double *rel_residual);
 
+/* Optional per-kernel-class timing of solves on a handle.  While profiling
+ * is on, npsolve_solve runs one iteration at a time (no CUDA graph) and
+ * records a CUDA event pair on the solve's stream around every launch of each
+ * kernel class; the totals accumulate until profiling is switched on again.
+ *   npsolve_profile_count()     number of classes
+ *   npsolve_profile_name(c)     name of class c ("cconv_l1", "lap_alpha", ...)
+ *   npsolve_get_profile(h, ms, launches)  per class: total device ms and the
+ *                               number of timed launch groups (host arrays of
+ *                               npsolve_profile_count() entries). */
+int npsolve_profile_count(void);
+/* Number of CUDA kernels this handle has enqueued since it was created
+ * (solves, network evaluations; graph replays count their kernels). */
+long long npsolve_launch_count(npsolve_t h);
+const char *npsolve_profile_name(int cls);
+int npsolve_set_profiling(npsolve_t h, int on);
+int npsolve_get_profile(npsolve_t h, double *ms_host, long long *launches_host);
+
 /* Self-test of the tensor-core data path (tcgen05.mma with the A operand in
  * tensor memory and the B operand in shared memory, as used by CConv): one
  * 128 x 32 x 64 BF16 product of exactly representable values, compared with

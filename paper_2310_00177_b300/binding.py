@@ -56,6 +56,11 @@ SIGNATURES = {
     "npsolve_true_residual": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_jacobi_pcg": ([_vp, _i, _i, _i, _vp, _d, _i, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_d)], _i),
     "npsolve_selftest_tensor_core": ([ctypes.POINTER(_d)], _i),
+    "npsolve_profile_count": ([], _i),
+    "npsolve_launch_count": ([_vp], ctypes.c_longlong),
+    "npsolve_profile_name": ([_i], ctypes.c_char_p),
+    "npsolve_set_profiling": ([_vp, _i], _i),
+    "npsolve_get_profile": ([_vp, _vp, _vp], _i),
 }
 
 
@@ -182,6 +187,22 @@ class Solver:
         if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
             _check(st, self._h)
         return x, it.value, rr.value, st
+
+    def launch_count(self):
+        """Kernels enqueued by this handle since creation."""
+        return int(load_library().npsolve_launch_count(self._h))
+
+    def set_profiling(self, on=True):
+        _check(load_library().npsolve_set_profiling(self._h, int(bool(on))), self._h)
+
+    def profile(self):
+        """Per kernel class: (total device ms, timed launches) of the profiled solves."""
+        lib = load_library()
+        n = lib.npsolve_profile_count()
+        ms = np.zeros(n, np.float64)
+        cnt = np.zeros(n, np.int64)
+        _check(lib.npsolve_get_profile(self._h, ms.ctypes.data_as(_vp), cnt.ctypes.data_as(_vp)), self._h)
+        return {lib.npsolve_profile_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
 
     def residual_history(self, cap=100000):
         out = np.zeros(cap, np.float64)

@@ -71,6 +71,32 @@ struct Workspace {
   int graph_pcg = 0;
 };
 
+// Kernel classes timed by the optional per-class profiling (CUDA events on
+// the solve's stream around each launch of the class).
+enum ProfClass {
+  P_SETUP,          // label check, image pyramid, Aff coefficients, r = b
+  P_CCONV_L1,       // CConv1 / CConv2 of level 1 (one launch each)
+  P_CCONV_COARSE,   // CConv of levels >= 2
+  P_POOL,
+  P_INTERP,
+  P_COMBINE,        // c1 x1 + c2 x2 (level 1: with mask and orthogonalisation dots)
+  P_ORTHO_DIR,      // orthogonalisation coefficients + direction
+  P_LAP,            // q = A d with dots + line search
+  P_UPDATE,         // x, r update + stop test
+  P_FINAL,          // residual replacement check and final true residual
+  P_COUNT
+};
+const char *const kProfNames[P_COUNT] = {"setup",   "cconv_l1",  "cconv_coarse", "pool",   "interp",
+                                         "combine", "ortho_dir", "lap_alpha",    "update", "final"};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> cls;  // class of event pair i (events 2i, 2i+1)
+  double ms[P_COUNT] = {};
+  long long launches[P_COUNT] = {};
+};
+
 }  // namespace
 
 struct npsolve {
@@ -88,6 +114,8 @@ struct npsolve {
   cudaStream_t cap_stream = nullptr;
   std::string err;
   std::vector<double> last_hist;
+  Profiler prof;
+  long long launches = 0;  // kernels enqueued by this handle since creation
 };
 
 namespace {
@@ -110,6 +138,42 @@ int fail(npsolve *h, int code, const char *fmt, ...) {
       return fail((h), e_ == cudaErrorMemoryAllocation ? NPSOLVE_OOM : NPSOLVE_CUDA_ERROR,          \
                   "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);      \
   } while (0)
+
+// Records an event pair around the launches issued in its lifetime when
+// profiling is on.
+struct ProfScope {
+  npsolve *h;
+  int c;
+  cudaStream_t s;
+  ProfScope(npsolve *h_, int c_, cudaStream_t s_) : h(h_), c(c_), s(s_) {
+    if (!h->prof.on) return;
+    const size_t i = h->prof.cls.size();
+    while (h->prof.pool.size() < 2 * i + 2) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      h->prof.pool.push_back(e);
+    }
+    h->prof.cls.push_back(c);
+    cudaEventRecord(h->prof.pool[2 * i], s);
+  }
+  ~ProfScope() {
+    if (!h->prof.on) return;
+    cudaEventRecord(h->prof.pool[2 * (h->prof.cls.size() - 1) + 1], s);
+  }
+};
+
+// Add the recorded pairs into the per-class totals (the stream must be idle).
+void prof_collect(npsolve *h) {
+  if (!h->prof.on) return;
+  for (size_t i = 0; i < h->prof.cls.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->prof.pool[2 * i], h->prof.pool[2 * i + 1]) == cudaSuccess) {
+      h->prof.ms[h->prof.cls[i]] += ms;
+      h->prof.launches[h->prof.cls[i]] += 1;
+    }
+  }
+  h->prof.cls.clear();
+}
 
 template <class T>
 cudaError_t dalloc(T **p, size_t count) {
@@ -300,6 +364,7 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
   Workspace &w = h->ws;
   const Dims dl = level_dims(d1, lvl);
   const int idx = lvl * 2 + (type - 1);
+  ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   if (h->cfg.kernel_path == NPSOLVE_PATH_TENSOR && lvl <= 3) {
     // image features exact in BF16 up to level 3 (counts <= 64)
     launch_cconv_umma(h->nsplit, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl,
@@ -321,17 +386,23 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   const int L = h->cfg.levels;
   for (int l = 1; l < L; ++l) {
     cconv(h, lab, d1, l, 1, l == 1 ? r : w.r1[l], l == 1 ? vscale : nullptr, l == 1, w.x1[l], st, s);
+    ProfScope ps(h, P_POOL, s);
     launch_pool(w.x1[l], level_dims(d1, l), w.r1[l + 1], st, s);
   }
   cconv(h, lab, d1, L, 1, L == 1 ? r : w.r1[L], L == 1 ? vscale : nullptr, L == 1, w.x1[L], st, s);
   if (L == 1) {
+    ProfScope ps(h, P_COMBINE, s);
     launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.part, st, s);
     return;
   }
   for (int l = L - 1; l >= 1; --l) {
     const float *coarse = (l + 1 == L) ? w.x1[L] : w.xc[l + 1];
-    launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+    {
+      ProfScope ps(h, P_INTERP, s);
+      launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+    }
     cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
+    ProfScope ps(h, P_COMBINE, s);
     if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], w.affc + 2 * l, w.xc[l], st, s);
     else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], w.affc + 2, z, w.qring, w.part, st, s);
   }
@@ -353,15 +424,30 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
   return NPSOLVE_OK;
 }
 
+// Kernels enqueued by one network evaluation / one NPSDO iteration.
+int network_kernels(int L) { return L == 1 ? 2 : 5 * L - 4; }
+int iteration_kernels(const npsolve *h) {
+  return network_kernels(h->cfg.levels) + 4 + (h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE ? 2 : 3);
+}
+int setup_kernels(int L) { return 1 + (L - 1) + 2 * (L - 1); }
+
 // Enqueue one NPSDO iteration (Alg. 1 loop body) on stream s.
 void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x, cudaStream_t s) {
   Workspace &w = h->ws;
   const long long n = d1.n();
+  h->launches += iteration_kernels(h);
   run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s);
-  launch_ortho_final(w.part, n, w.st, s);
-  launch_direction(n, w.z, w.dring, w.st, s);
-  launch_lap_ring(lab, d1, w.dring, w.qring, w.r, w.part, w.st, s);
+  {
+    ProfScope ps(h, P_ORTHO_DIR, s);
+    launch_ortho_final(w.part, n, w.st, s);
+    launch_direction(n, w.z, w.dring, w.st, s);
+  }
+  {
+    ProfScope ps(h, P_LAP, s);
+    launch_lap_ring(lab, d1, w.dring, w.qring, w.r, w.part, w.st, s);
+  }
   const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
+  ProfScope ps(h, P_UPDATE, s);
   launch_update(recur, n, x, w.r, w.dring, w.qring, w.part, w.st, w.hist, s);
   if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
 }
@@ -412,17 +498,23 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
   st = ensure_ws(h, d1, max_iter + 1);
   if (st) return st;
   Workspace &w = h->ws;
-  st = setup_image(h, lab, d1, s, true);
-  if (st) return st;
-  launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
+  {
+    ProfScope ps(h, P_SETUP, s);
+    st = setup_image(h, lab, d1, s, true);
+    if (st) return st;
+    launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
+    h->launches += setup_kernels(h->cfg.levels) + 2;
+  }
   CK(h, cudaGetLastError());
   CK(h, cudaMemcpyAsync(w.h_flag, w.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaMemcpyAsync(w.h_st, w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   if (w.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
   if (w.h_st[0].done == kDoneBadInput) return fail(h, NPSOLVE_BAD_ARG, "b has non-finite entries on fluid cells");
-  st = get_graph(h, lab, d1, b, x);
-  if (st) return st;
+  if (!h->prof.on) {  // profiling runs the iterations one at a time, without the graph
+    st = get_graph(h, lab, d1, b, x);
+    if (st) return st;
+  }
   int launched = 0, restarts = 0;
   SolveState hs = w.h_st[0];
   for (;;) {
@@ -431,8 +523,18 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     // has been queued, so the GPU does not wait for the host between batches.
     int nb = 0;
     while (hs.done == kDoneRunning && launched < max_iter) {
+      if (h->prof.on) {  // one iteration at a time, so that no no-op iteration is timed
+        enqueue_iteration(h, lab, d1, b, x, s);
+        CK(h, cudaGetLastError());
+        launched += 1;
+        CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        CK(h, cudaStreamSynchronize(s));
+        hs = w.h_st[0];
+        continue;
+      }
       if (max_iter - launched >= kPollEvery) {
         CK(h, cudaGraphLaunch(w.graph, s));
+        h->launches += (long long)kPollEvery * iteration_kernels(h);
         launched += kPollEvery;
       } else {
         enqueue_iteration(h, lab, d1, b, x, s);
@@ -451,7 +553,9 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     if (nb) hs = w.h_st[(nb - 1) & 1];
     if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&
         restarts < kMaxRestarts) {
+      ProfScope ps(h, P_FINAL, s);
       launch_replace_residual(lab, d1, b, x, w.r, w.part, w.st, w.reopened, s);
+      h->launches += 2;
       CK(h, cudaMemcpyAsync(w.h_flag, w.reopened, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
       CK(h, cudaStreamSynchronize(s));
@@ -464,7 +568,11 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     }
     break;
   }
-  launch_relres(lab, d1, b, x, w.part, w.relres, s);
+  {
+    ProfScope ps(h, P_FINAL, s);
+    launch_relres(lab, d1, b, x, w.part, w.relres, s);
+    h->launches += 2;
+  }
   double rr[2];
   CK(h, cudaMemcpyAsync(rr, w.relres, sizeof(rr), cudaMemcpyDeviceToHost, s));
   CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -472,6 +580,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
   hs = w.h_st[0];
   *iters = hs.k;
   *rel_residual = rr[0];
+  prof_collect(h);
   st = check_umma_err(h);
   if (st) return st;
   h->last_hist.resize(hs.k + 1);
@@ -562,6 +671,7 @@ void npsolve_destroy(npsolve_t h) {
   if (!h) return;
   cudaSetDevice(h->device);
   free_ws(h->ws);
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   cudaFree(h->cw);
   cudaFree(h->aw);
   cudaFree(h->unit_c12);
@@ -740,6 +850,32 @@ int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const floa
   if (done == kDoneBadInput) return fail(nullptr, NPSOLVE_BAD_ARG, "non-finite b");
   if (done == kDoneBreakdown) return fail(nullptr, NPSOLVE_BREAKDOWN, "PCG breakdown");
   if (done != kDoneConverged) return fail(nullptr, NPSOLVE_NO_CONVERGENCE, "no convergence in %d iterations", k);
+  return NPSOLVE_OK;
+}
+
+long long npsolve_launch_count(npsolve_t h) { return h ? h->launches : 0; }
+
+int npsolve_profile_count(void) { return P_COUNT; }
+
+const char *npsolve_profile_name(int cls) { return (cls >= 0 && cls < P_COUNT) ? kProfNames[cls] : ""; }
+
+int npsolve_set_profiling(npsolve_t h, int on) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  h->prof.on = on != 0;
+  for (int i = 0; i < P_COUNT; ++i) {
+    h->prof.ms[i] = 0.0;
+    h->prof.launches[i] = 0;
+  }
+  h->prof.cls.clear();
+  return NPSOLVE_OK;
+}
+
+int npsolve_get_profile(npsolve_t h, double *ms_host, long long *launches_host) {
+  if (!h || !ms_host || !launches_host) return fail(h, NPSOLVE_BAD_ARG, "null argument");
+  for (int i = 0; i < P_COUNT; ++i) {
+    ms_host[i] = h->prof.ms[i];
+    launches_host[i] = h->prof.launches[i];
+  }
   return NPSOLVE_OK;
 }
 
