@@ -1,0 +1,363 @@
+// Bandwidth-oriented versions of the per-iteration vector / stencil kernels
+// of Alg. 1 for grids with nx % 4 == 0 (every grid the network accepts for
+// L >= 3): each thread handles groups of 4 consecutive cells along x with
+// 16-byte loads and stores, 32-bit indexing, and no division per cell.
+//
+// Dot products: each thread sums the 4 products of a group in FP32 and adds
+// the group sum into a double-float (hi + lo FP32 pair, error-free TwoSum)
+// accumulator; the block reduction is FP64.  This keeps FP64 instructions
+// (slow on B300) out of the per-cell path while giving FP64-quality sums.
+//
+// Each reduction kernel ends with a last-block-done step: the block that
+// finishes last (atomic ticket after a memory fence) reduces the per-block
+// partials in a fixed order and updates the solver scalars itself, so no
+// separate single-block kernel is launched and the result is deterministic.
+#include "nps_common.cuh"
+#include "nps_kernels.h"
+
+namespace nps {
+
+namespace {
+
+struct DF {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void df_add(DF &a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b - bb);
+  a.hi = s;
+  a.lo += e;
+}
+__device__ __forceinline__ double df_val(const DF &a) { return (double)a.hi + (double)a.lo; }
+
+// Partials of the grid are reduced by the last block (fixed order, FP64).
+template <int NV>
+__device__ __forceinline__ void reduce_partials_cg(const double *part, int nblocks, double (&tot)[NV]) {
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int j = threadIdx.x; j < nblocks; j += kRedThreads) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __ldcg(part + (size_t)j * NV + i);
+  }
+  __shared__ double res[NV];
+  block_sum_store<NV>(v, res);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) tot[i] = res[i];
+}
+
+// Store this block's partials; the last block to arrive reduces all of them
+// and calls finish(tot) on thread 0, then re-arms the ticket counter.
+template <int NV, class F>
+__device__ __forceinline__ void reduce_and_finish(double (&v)[NV], double *part, unsigned *ticket, F finish) {
+  block_sum_store<NV>(v, part + (size_t)blockIdx.x * NV);
+  __shared__ unsigned s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    double tot[NV];
+    reduce_partials_cg<NV>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      finish(tot);
+      *ticket = 0u;
+    }
+  }
+}
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ uchar4 ldl4(const uint8_t *p) { return *reinterpret_cast<const uchar4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float f4(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ uint8_t u4(const uchar4 &v, int e) {
+  return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+}
+
+constexpr int kThreads = 256;
+inline int grid4(long long n4, int num_sms) {
+  long long b = (n4 + kThreads - 1) / kThreads;
+  long long cap = (long long)num_sms * 8;
+  if (cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // the partials buffer holds kRedMaxBlocks rows
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// r = mask(b), x = 0, ||b||^2 -> initial solver scalars.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ lab, int n, const float *__restrict__ b,
+                                                    float *__restrict__ r, double *__restrict__ x,
+                                                    double *__restrict__ part, unsigned *ticket, double tol,
+                                                    int max_iter, int n_ortho, SolveState *st, double *hist) {
+  DF acc;
+  const int n4 = n >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    const uchar4 l = ldl4(lab + p);
+    const float4 bv = ld4(b + p);
+    const float4 rv = make_float4(l.x == kFluid ? bv.x : 0.f, l.y == kFluid ? bv.y : 0.f, l.z == kFluid ? bv.z : 0.f,
+                                  l.w == kFluid ? bv.w : 0.f);
+    st4(r + p, rv);
+    reinterpret_cast<double2 *>(x + p)[0] = make_double2(0.0, 0.0);
+    reinterpret_cast<double2 *>(x + p)[1] = make_double2(0.0, 0.0);
+    df_add(acc, rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+  }
+  double v[1] = {df_val(acc)};
+  reduce_and_finish<1>(v, part, ticket, [&](const double *t) {
+    SolveState s;
+    s.bnorm2 = t[0];
+    s.eps2 = tol * tol * t[0];
+    s.rnorm2 = t[0];
+    s.alpha = 0.0;
+    for (int i = 0; i < kMaxOrtho; ++i) s.coef[i] = 0.0;
+    for (int i = 0; i < kRing; ++i) s.dAd[i] = 1.0;
+    s.k = 0;
+    s.max_iter = max_iter;
+    s.n_ortho = n_ortho;
+    s.pad_ = 0;
+    s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
+    if (!isfinite(t[0])) s.done = kDoneBadInput;
+    else if (!(t[0] >= s.eps2) || t[0] == 0.0) s.done = kDoneConverged;
+    else s.done = kDoneRunning;
+    *st = s;
+    hist[0] = sqrt(t[0]);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Level-1 combination z = mask_fluid(c1 x1 + c2 x2) with the dot products
+// z . (A d_i) of the previous directions; the last block turns them into the
+// orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i (Alg. 1).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_combine1_4(const uint8_t *__restrict__ lab, int n,
+                                                         const float *__restrict__ x1, const float *__restrict__ x2,
+                                                         const double *__restrict__ c12, float *__restrict__ z,
+                                                         const float *__restrict__ qring, double *__restrict__ part,
+                                                         unsigned *ticket, SolveState *st) {
+  if (st->done) return;
+  const float c1 = (float)c12[0], c2 = (float)c12[1];
+  const int k1 = st->k + 1, no = st->n_ortho;
+  const float *qs[kMaxOrtho] = {qring, qring, qring, qring};
+  int cnt = 0;
+  for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) qs[cnt++] = qring + (size_t)ring_slot(i, no) * n;
+  DF acc[kMaxOrtho];
+  const int n4 = n >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    const uchar4 l = ldl4(lab + p);
+    const float4 a = ld4(x1 + p), b = ld4(x2 + p);
+    const float4 zv = make_float4(l.x == kFluid ? fmaf(c1, a.x, c2 * b.x) : 0.f,
+                                  l.y == kFluid ? fmaf(c1, a.y, c2 * b.y) : 0.f,
+                                  l.z == kFluid ? fmaf(c1, a.z, c2 * b.z) : 0.f,
+                                  l.w == kFluid ? fmaf(c1, a.w, c2 * b.w) : 0.f);
+    st4(z + p, zv);
+#pragma unroll
+    for (int j = 0; j < kMaxOrtho; ++j) {
+      if (j < cnt) {
+        const float4 q = ld4(qs[j] + p);
+        df_add(acc[j], zv.x * q.x + zv.y * q.y + zv.z * q.z + zv.w * q.w);
+      }
+    }
+  }
+  double v[kMaxOrtho];
+#pragma unroll
+  for (int j = 0; j < kMaxOrtho; ++j) v[j] = df_val(acc[j]);
+  reduce_and_finish<kMaxOrtho>(v, part, ticket, [&](const double *t) {
+    for (int j = 0; j < kMaxOrtho; ++j) st->coef[j] = 0.0;
+    for (int i = k1 - no; i < k1; ++i) {
+      if (i < 1) continue;
+      const int j = k1 - 1 - i;
+      st->coef[j] = t[j] / st->dAd[ring_slot(i, no)];
+    }
+  });
+}
+
+// d_k = z - sum_j c_j d_{k-1-j}  (ring slot of iteration k).
+__global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__restrict__ zv, float *__restrict__ dring,
+                                                         const SolveState *st) {
+  if (st->done) return;
+  const int k1 = st->k + 1, no = st->n_ortho;
+  float c[kMaxOrtho] = {0.f, 0.f, 0.f, 0.f};
+  const float *src[kMaxOrtho] = {zv, zv, zv, zv};
+  int cnt = 0;
+  for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) {
+    c[cnt] = (float)st->coef[k1 - 1 - i];
+    src[cnt] = dring + (size_t)ring_slot(i, no) * n;
+    ++cnt;
+  }
+  float *dst = dring + (size_t)ring_slot(k1, no) * n;
+  const int n4 = n >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    float4 v = ld4(zv + p);
+#pragma unroll
+    for (int j = 0; j < kMaxOrtho; ++j) {
+      if (j < cnt) {
+        const float4 s = ld4(src[j] + p);
+        v.x -= c[j] * s.x;
+        v.y -= c[j] * s.y;
+        v.z -= c[j] * s.z;
+        v.w -= c[j] * s.w;
+      }
+    }
+    st4(dst + p, v);
+  }
+}
+
+// q_k = A d_k (masked 7-point Laplacian, difference form) with the dot
+// products d.q and r.d; the last block computes the line search
+// alpha = r^T d / d^T A d and flags breakdown (d^T A d <= 0 or non-finite).
+__global__ void __launch_bounds__(kThreads) k_lap4(const uint8_t *__restrict__ lab, Dims dm,
+                                                   const float *__restrict__ dring, float *__restrict__ qring,
+                                                   const float *__restrict__ r, double *__restrict__ part,
+                                                   unsigned *ticket, SolveState *st) {
+  if (st->done) return;
+  const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
+  const int n = nx * ny * nz, nxy = nx * ny;
+  const int slot = ring_slot(st->k + 1, st->n_ortho);
+  const float *d = dring + (size_t)slot * n;
+  float *q = qring + (size_t)slot * n;
+  DF a0, a1;
+  const int n4 = n >> 2;
+  const uchar4 solid4 = make_uchar4(kSolid, kSolid, kSolid, kSolid);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    const uchar4 lc = ldl4(lab + p);
+    if (lc.x != kFluid && lc.y != kFluid && lc.z != kFluid && lc.w != kFluid) {
+      st4(q + p, zero4);
+      continue;
+    }
+    const int x0 = p % nx;
+    const int yz = p / nx;
+    const int y = yz % ny, z = yz / ny;
+    const float4 dc = ld4(d + p);
+    const float dxl = x0 > 0 ? d[p - 1] : 0.f;
+    const uint8_t lxl = x0 > 0 ? lab[p - 1] : (uint8_t)kSolid;
+    const float dxr = x0 + 4 < nx ? d[p + 4] : 0.f;
+    const uint8_t lxr = x0 + 4 < nx ? lab[p + 4] : (uint8_t)kSolid;
+    const float4 dym = y > 0 ? ld4(d + p - nx) : zero4, dyp = y < ny - 1 ? ld4(d + p + nx) : zero4;
+    const float4 dzm = z > 0 ? ld4(d + p - nxy) : zero4, dzp = z < nz - 1 ? ld4(d + p + nxy) : zero4;
+    const uchar4 lym = y > 0 ? ldl4(lab + p - nx) : solid4, lyp = y < ny - 1 ? ldl4(lab + p + nx) : solid4;
+    const uchar4 lzm = z > 0 ? ldl4(lab + p - nxy) : solid4, lzp = z < nz - 1 ? ldl4(lab + p + nxy) : solid4;
+    float qo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float dp = f4(dc, e);
+      float acc = 0.f;
+      int nair = 0;
+      const float nv[6] = {e == 0 ? dxl : f4(dc, e - 1), e == 3 ? dxr : f4(dc, e + 1), f4(dym, e), f4(dyp, e),
+                           f4(dzm, e), f4(dzp, e)};
+      const uint8_t nl[6] = {e == 0 ? lxl : u4(lc, e - 1), e == 3 ? lxr : u4(lc, e + 1), u4(lym, e), u4(lyp, e),
+                             u4(lzm, e), u4(lzp, e)};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        if (nl[k] == kFluid) acc += dp - nv[k];
+        else if (nl[k] == kAir) nair += 1;
+      }
+      qo[e] = u4(lc, e) == kFluid ? acc + (float)nair * dp : 0.f;
+    }
+    const float4 qv = make_float4(qo[0], qo[1], qo[2], qo[3]);
+    st4(q + p, qv);
+    const float4 rv = ld4(r + p);
+    df_add(a0, dc.x * qv.x + dc.y * qv.y + dc.z * qv.z + dc.w * qv.w);
+    df_add(a1, rv.x * dc.x + rv.y * dc.y + rv.z * dc.z + rv.w * dc.w);
+  }
+  double v[2] = {df_val(a0), df_val(a1)};
+  reduce_and_finish<2>(v, part, ticket, [&](const double *t) {
+    const double dq = t[0], rd = t[1];
+    if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rd)) {
+      st->done = kDoneBreakdown;
+      return;
+    }
+    st->alpha = rd / dq;
+    st->dAd[slot] = dq;
+  });
+}
+
+// x += alpha d (FP64), r -= alpha q (recurrence) with ||r||^2; the last block
+// advances the iteration and applies the stop test ||r_k|| < tol ||b||.
+template <bool RECUR>
+__global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict__ x, float *__restrict__ r,
+                                                      const float *__restrict__ dring, const float *__restrict__ qring,
+                                                      double *__restrict__ part, unsigned *ticket, SolveState *st,
+                                                      double *hist) {
+  if (st->done) return;
+  const int slot = ring_slot(st->k + 1, st->n_ortho);
+  const float *d = dring + (size_t)slot * n;
+  const float *q = qring + (size_t)slot * n;
+  const double a = st->alpha;
+  const float af = (float)a;
+  DF acc;
+  const int n4 = n >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    const float4 dv = ld4(d + p);
+    double2 *xp = reinterpret_cast<double2 *>(x + p);
+    double2 x01 = xp[0], x23 = xp[1];
+    x01.x = fma(a, (double)dv.x, x01.x);
+    x01.y = fma(a, (double)dv.y, x01.y);
+    x23.x = fma(a, (double)dv.z, x23.x);
+    x23.y = fma(a, (double)dv.w, x23.y);
+    xp[0] = x01;
+    xp[1] = x23;
+    if (RECUR) {
+      const float4 qv = ld4(q + p);
+      float4 rv = ld4(r + p);
+      rv.x = fmaf(-af, qv.x, rv.x);
+      rv.y = fmaf(-af, qv.y, rv.y);
+      rv.z = fmaf(-af, qv.z, rv.z);
+      rv.w = fmaf(-af, qv.w, rv.w);
+      st4(r + p, rv);
+      df_add(acc, rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+    }
+  }
+  if (!RECUR) return;
+  double v[1] = {df_val(acc)};
+  reduce_and_finish<1>(v, part, ticket, [&](const double *t) {
+    const double rr = t[0];
+    st->k += 1;
+    st->rnorm2 = rr;
+    hist[st->k] = sqrt(rr);
+    if (!isfinite(rr)) st->done = kDoneBreakdown;
+    else if (rr < st->eps2 || rr == 0.0) st->done = kDoneConverged;
+    else st->rscale = (float)(1.0 / sqrt(rr));
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------
+void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, double *part, unsigned *ticket,
+                  double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms, cudaStream_t s) {
+  k_init4<<<grid4(n / 4, num_sms), kThreads, 0, s>>>(lab, n, b, r, x, part, ticket, tol, max_iter, n_ortho, st, hist);
+}
+void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
+                       const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
+                       cudaStream_t s) {
+  k_combine1_4<<<grid4(n / 4, num_sms), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
+}
+void launch_direction4(int n, const float *z, float *dring, const SolveState *st, int num_sms, cudaStream_t s) {
+  k_direction4<<<grid4(n / 4, num_sms), kThreads, 0, s>>>(n, z, dring, st);
+}
+void launch_lap4(const uint8_t *lab, Dims dm, const float *dring, float *qring, const float *r, double *part,
+                 unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
+  k_lap4<<<grid4(dm.n() / 4, num_sms), kThreads, 0, s>>>(lab, dm, dring, qring, r, part, ticket, st);
+}
+void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
+                    double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s) {
+  if (recurrence)
+    k_update4<true><<<grid4(n / 4, num_sms), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
+  else
+    k_update4<false><<<grid4(n / 4, num_sms), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
+}
+
+}  // namespace nps

@@ -46,6 +46,18 @@ void launch_combine(long long n, const float *x1, const float *x2, const double 
 void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
                      const float *qring, double *part, const SolveState *st, cudaStream_t s);
 
+// kernels_vec4.cu (nx % 4 == 0, n < 2^31)
+void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, double *part, unsigned *ticket,
+                  double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms, cudaStream_t s);
+void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
+                       const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
+                       cudaStream_t s);
+void launch_direction4(int n, const float *z, float *dring, const SolveState *st, int num_sms, cudaStream_t s);
+void launch_lap4(const uint8_t *lab, Dims dm, const float *dring, float *qring, const float *r, double *part,
+                 unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
+void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
+                    double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s);
+
 // kernels_umma.cu
 void prepare_umma_weights(const CConvW &w, int nsplit, uint8_t *out);
 int umma_weight_bytes(int nsplit);

@@ -13,6 +13,7 @@
 //   a final FP64 true-residual check (with residual replacement in the
 //     recurrence mode).
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -51,6 +52,7 @@ struct Workspace {
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
   int hist_cap = 0;
   SolveState *st = nullptr;
+  unsigned *tickets = nullptr;  // last-block-done counters of the fused reduction kernels
   void *pcg_st = nullptr;
   unsigned int *bad = nullptr;
   int *reopened = nullptr;
@@ -200,6 +202,7 @@ void free_ws(Workspace &w) {
   cudaFree(w.relres);
   cudaFree(w.hist);
   cudaFree(w.st);
+  cudaFree(w.tickets);
   cudaFree(w.pcg_st);
   cudaFree(w.bad);
   cudaFree(w.reopened);
@@ -253,6 +256,8 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     CK(h, dalloc(&w.affc, (size_t)(kMaxLevels + 1) * 2));
     CK(h, dalloc(&w.relres, 2));
     CK(h, dalloc(&w.st, 1));
+    CK(h, dalloc(&w.tickets, 8));
+    CK(h, cudaMemset(w.tickets, 0, 8 * sizeof(unsigned)));
     CK(h, cudaMalloc(&w.pcg_st, pcg_state_bytes()));
     CK(h, dalloc(&w.bad, 1));
     CK(h, dalloc(&w.reopened, 1));
@@ -376,12 +381,17 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
                    mask_input, out, st, s);
 }
 
+// Grids with nx % 4 == 0 use the 16-byte vector kernels with fused
+// last-block reductions (kernels_vec4.cu).
+bool vec4_path(Dims d) { return d.nx % 4 == 0 && d.n() <= (long long)INT32_MAX; }
+enum { kTicketInit = 0, kTicketCombine = 1, kTicketLap = 2, kTicketUpdate = 3 };
+
 // The network z = P_net(I, r) of Alg. 2 on the prepared pyramid and Aff
 // coefficients.  Inside a solve (st != null) the level-1 input is scaled by
 // 1/||r|| from the state and the orthogonalisation dots are fused into the
 // last combination.
 void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const float *vscale, float *z,
-                 const SolveState *st, cudaStream_t s) {
+                 SolveState *st, cudaStream_t s) {
   Workspace &w = h->ws;
   const int L = h->cfg.levels;
   for (int l = 1; l < L; ++l) {
@@ -404,6 +414,9 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
     ProfScope ps(h, P_COMBINE, s);
     if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], w.affc + 2 * l, w.xc[l], st, s);
+    else if (st && vec4_path(d1))  // fused: dots and orthogonalisation coefficients in one launch
+      launch_combine1_4(lab, (int)d1.n(), w.x1[1], w.x2[1], w.affc + 2, z, w.qring, w.part,
+                        w.tickets + kTicketCombine, st, h->num_sms, s);
     else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], w.affc + 2, z, w.qring, w.part, st, s);
   }
 }
@@ -426,8 +439,10 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
 
 // Kernels enqueued by one network evaluation / one NPSDO iteration.
 int network_kernels(int L) { return L == 1 ? 2 : 5 * L - 4; }
-int iteration_kernels(const npsolve *h) {
-  return network_kernels(h->cfg.levels) + 4 + (h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE ? 2 : 3);
+int iteration_kernels(const npsolve *h, bool fast) {
+  const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
+  if (fast && h->cfg.levels > 1) return network_kernels(h->cfg.levels) + 2 + (recur ? 1 : 3);
+  return network_kernels(h->cfg.levels) + 4 + (recur ? 2 : 3);
 }
 int setup_kernels(int L) { return 1 + (L - 1) + 2 * (L - 1); }
 
@@ -435,8 +450,25 @@ int setup_kernels(int L) { return 1 + (L - 1) + 2 * (L - 1); }
 void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x, cudaStream_t s) {
   Workspace &w = h->ws;
   const long long n = d1.n();
-  h->launches += iteration_kernels(h);
+  const bool fast = vec4_path(d1) && h->cfg.levels > 1;
+  h->launches += iteration_kernels(h, fast);
   run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s);
+  const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
+  if (fast) {
+    {
+      ProfScope ps(h, P_ORTHO_DIR, s);
+      launch_direction4((int)n, w.z, w.dring, w.st, h->num_sms, s);
+    }
+    {
+      ProfScope ps(h, P_LAP, s);
+      launch_lap4(lab, d1, w.dring, w.qring, w.r, w.part, w.tickets + kTicketLap, w.st, h->num_sms, s);
+    }
+    ProfScope ps(h, P_UPDATE, s);
+    launch_update4(recur, (int)n, x, w.r, w.dring, w.qring, w.part, w.tickets + kTicketUpdate, w.st, w.hist,
+                   h->num_sms, s);
+    if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
+    return;
+  }
   {
     ProfScope ps(h, P_ORTHO_DIR, s);
     launch_ortho_final(w.part, n, w.st, s);
@@ -446,7 +478,6 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
     ProfScope ps(h, P_LAP, s);
     launch_lap_ring(lab, d1, w.dring, w.qring, w.r, w.part, w.st, s);
   }
-  const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
   ProfScope ps(h, P_UPDATE, s);
   launch_update(recur, n, x, w.r, w.dring, w.qring, w.part, w.st, w.hist, s);
   if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
@@ -502,8 +533,14 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     ProfScope ps(h, P_SETUP, s);
     st = setup_image(h, lab, d1, s, true);
     if (st) return st;
-    launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
-    h->launches += setup_kernels(h->cfg.levels) + 2;
+    if (vec4_path(d1)) {
+      launch_init4(lab, (int)d1.n(), b, w.r, x, w.part, w.tickets + kTicketInit, tol, max_iter, h->cfg.n_ortho,
+                   w.st, w.hist, h->num_sms, s);
+      h->launches += setup_kernels(h->cfg.levels) + 1;
+    } else {
+      launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
+      h->launches += setup_kernels(h->cfg.levels) + 2;
+    }
   }
   CK(h, cudaGetLastError());
   CK(h, cudaMemcpyAsync(w.h_flag, w.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -534,7 +571,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       }
       if (max_iter - launched >= kPollEvery) {
         CK(h, cudaGraphLaunch(w.graph, s));
-        h->launches += (long long)kPollEvery * iteration_kernels(h);
+        h->launches += (long long)kPollEvery * iteration_kernels(h, vec4_path(d1) && h->cfg.levels > 1);
         launched += kPollEvery;
       } else {
         enqueue_iteration(h, lab, d1, b, x, s);

@@ -235,3 +235,23 @@ def test_solve_slosh_64_matches_oracle():
         assert abs(iters - ores["iters"]) <= 1
     assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-5
     s.close()
+
+
+@pytest.mark.parametrize("shape,L", [((6, 10, 14), 2), ((9, 7, 11), 1)])
+def test_solve_generic_path_matches_oracle(shape, L):
+    # nx % 4 != 0 takes the general (non-vectorised) kernels
+    b = _binding()
+    lab = _rng_labels(shape, 41, p=(0.15, 0.7, 0.15))
+    rhs = synth.rhs_normal(lab, 42).astype(np.float32)
+    w = synth.init_weights(L, 43).astype(np.float32)
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=L, w=w.astype(np.float64), tol=1e-6, max_iter=2000)
+    s = b.Solver(w, levels=L)
+    x, iters, relres, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-6, max_iter=2000)
+    h = ores["res_hist"] / ores["res_hist"][0]
+    assert st == b.OK and relres < 1e-6
+    if h[-1] < 0.95e-6 and h[-2] > 1.05e-6:
+        assert iters == ores["iters"]
+    else:
+        assert abs(iters - ores["iters"]) <= 1
+    assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-5
+    s.close()
