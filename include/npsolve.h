@@ -59,10 +59,11 @@ enum { NPSOLVE_LABEL_SOLID = 0, NPSOLVE_LABEL_FLUID = 1, NPSOLVE_LABEL_AIR = 2 }
 /* Precision forms of the network evaluation.  Vectors are FP32, dot products
  * and orthogonalisation coefficients FP64 and x FP64 in both forms. */
 enum {
-  NPSOLVE_FP32 = 0, /* per-cell kernels generated to FP32 accuracy (on the tensor cores: the FP32
-                       weights split into three BF16 terms, FP32 accumulation) */
-  NPSOLVE_BF16 = 1  /* CConv weights rounded to BF16 (one tensor-core pass, FP32 accumulation);
-                       vectors, Aff coefficients and the solver as in the FP32 form */
+  NPSOLVE_FP32 = 0, /* per-cell kernels generated and applied to FP32 accuracy (on the tensor cores: the
+                       FP32 weights split into three BF16 terms, FP32 accumulation) */
+  NPSOLVE_BF16 = 1  /* CConv weights rounded to BF16, kernels accumulated in FP32 and stored/used as BF16
+                       values, applied with FP32 accumulation; vectors, Aff coefficients and the solver
+                       as in the FP32 form */
 };
 
 /* Residual update of Alg. 1. */
@@ -73,11 +74,15 @@ enum {
   NPSOLVE_RESIDUAL_EXPLICIT = 1    /* r_k = b - A x_k every iteration, as printed in Alg. 1 */
 };
 
-/* Where the per-cell kernel generation of CConv runs. */
+/* How CConv obtains its per-cell kernels K_a(p) (Sec. 4.2.1). */
 enum {
-  NPSOLVE_PATH_TENSOR = 0,  /* tcgen05 tensor cores on levels 1-3 (image counts exact in BF16),
-                               CUDA cores on coarser levels */
-  NPSOLVE_PATH_CUDA_CORE = 1 /* CUDA cores (FP32 FMA) on every level; the reference path */
+  NPSOLVE_PATH_CACHED = 0,    /* default: once per solve, the kernels of the cells whose 3x3x3 image window
+                                 is not uniform are generated and cached (a uniform window gives the exact
+                                 closed form Bp + nF*SWf + nA*SWa); every iteration then runs a z-marching
+                                 27-point stencil with fused pooling / interpolation / combination */
+  NPSOLVE_PATH_CUDA_CORE = 1, /* every iteration regenerates every kernel with FP32 FMAs; reference path */
+  NPSOLVE_PATH_TENSOR = 2     /* every iteration regenerates every kernel on the tcgen05 tensor cores
+                                 (levels 1-3, BF16 operands, FP32 accumulation), CUDA cores beyond */
 };
 
 typedef struct {
@@ -85,7 +90,7 @@ typedef struct {
   int n_ortho;       /* directions to A-orthogonalise against, 0..4 (paper: 2, Sec. 4.1) */
   int precision;     /* NPSOLVE_FP32 or NPSOLVE_BF16 */
   int residual_mode; /* NPSOLVE_RESIDUAL_RECURRENCE or NPSOLVE_RESIDUAL_EXPLICIT */
-  int kernel_path;   /* NPSOLVE_PATH_TENSOR or NPSOLVE_PATH_CUDA_CORE */
+  int kernel_path;   /* NPSOLVE_PATH_CACHED, NPSOLVE_PATH_CUDA_CORE or NPSOLVE_PATH_TENSOR */
 } npsolve_config;
 
 /* Number of FP32 network parameters for L levels (Alg. 2): for each level
@@ -181,6 +186,10 @@ int npsolve_profile_count(void);
 /* Number of CUDA kernels this handle has enqueued since it was created
  * (solves, network evaluations; graph replays count their kernels). */
 long long npsolve_launch_count(npsolve_t h);
+/* Cells of level `level` whose 3x3x3 image window was not uniform in the last
+ * setup of the cached path (their kernels are generated and cached; all other
+ * cells use the closed form of a uniform window); -1 when not available. */
+long long npsolve_mixed_cells(npsolve_t h, int level);
 const char *npsolve_profile_name(int cls);
 int npsolve_set_profiling(npsolve_t h, int on);
 int npsolve_get_profile(npsolve_t h, double *ms_host, long long *launches_host);

@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(HERE, "libnpsolve.so")
 
 OK, BAD_ARG, BAD_DIMS, BAD_LABELS, NO_CONVERGENCE, BREAKDOWN, OOM, CUDA_ERROR = range(8)
 FP32, BF16 = 0, 1
-PATH_TENSOR, PATH_CUDA_CORE = 0, 1
+PATH_CACHED, PATH_CUDA_CORE, PATH_TENSOR = 0, 1, 2
 RECURRENCE, EXPLICIT = 0, 1
 STATUS_NAMES = ["OK", "BAD_ARG", "BAD_DIMS", "BAD_LABELS", "NO_CONVERGENCE", "BREAKDOWN", "OOM", "CUDA_ERROR"]
 
@@ -58,6 +58,7 @@ SIGNATURES = {
     "npsolve_selftest_tensor_core": ([ctypes.POINTER(_d)], _i),
     "npsolve_profile_count": ([], _i),
     "npsolve_launch_count": ([_vp], ctypes.c_longlong),
+    "npsolve_mixed_cells": ([_vp, _i], ctypes.c_longlong),
     "npsolve_profile_name": ([_i], ctypes.c_char_p),
     "npsolve_set_profiling": ([_vp, _i], _i),
     "npsolve_get_profile": ([_vp, _vp, _vp], _i),
@@ -122,7 +123,7 @@ class Solver:
     """A solver handle: network weights + device workspace (npsolve_t)."""
 
     def __init__(self, weights, levels=4, n_ortho=2, precision=FP32, residual_mode=RECURRENCE,
-                 kernel_path=PATH_TENSOR):
+                 kernel_path=PATH_CACHED):
         lib = load_library()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
         cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path)
@@ -187,6 +188,10 @@ class Solver:
         if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
             _check(st, self._h)
         return x, it.value, rr.value, st
+
+    def mixed_cells(self, level):
+        """Cells of `level` with a non-uniform image window in the last setup (-1 if unknown)."""
+        return int(load_library().npsolve_mixed_cells(self._h, level))
 
     def launch_count(self):
         """Kernels enqueued by this handle since creation."""

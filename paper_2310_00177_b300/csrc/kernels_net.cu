@@ -3,6 +3,8 @@
 // average pooling, x2 trilinear interpolation and the per-level combination
 // x^l = c1 x1^l + c2 x2^l.  These are the FP32 reference kernels of the
 // library; the tensor-core CConv lives in kernels_umma.cu.
+#include <cuda_bf16.h>
+
 #include "nps_common.cuh"
 #include "nps_kernels.h"
 
@@ -109,7 +111,7 @@ __global__ void k_aff_final(const double *part, int nblocks, const AffW *a1, con
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_cconv_f32(ImgSrc im, Dims dm, const CConvW *__restrict__ w,
                                                      const float *__restrict__ v, const float *__restrict__ vscale,
-                                                     int mask_input, float *__restrict__ out,
+                                                     int mask_input, int round_k, float *__restrict__ out,
                                                      const SolveState *st) {
   if (st && st->done) return;
   __shared__ CConvW sw;
@@ -138,16 +140,29 @@ __global__ void __launch_bounds__(128) k_cconv_f32(ImgSrc im, Dims dm, const CCo
       }
       vv[t] = val * sc;
     }
+    // BF16 form: the kernels of mixed-window cells are stored as BF16 values
+    bool mixed = false;
+#pragma unroll
+    for (int t = 0; t < 27; ++t) mixed |= (nf[t] != nf[13]) | (na[t] != na[13]);
+    const bool rk = round_k && mixed;
     float acc = 0.f;
 #pragma unroll 1
     for (int a = 0; a < 27; ++a) {
       float k = sw.bp[a];
 #pragma unroll
       for (int l = 0; l < 27; ++l) k = fmaf(sw.wf[a][l], nf[l], fmaf(sw.wa[a][l], na[l], k));
+      if (rk) k = __bfloat162float(__float2bfloat16_rn(k));
       acc = fmaf(k, vv[a], acc);
     }
     out[p] = acc;
   }
+}
+
+// out = in on fluid cells, 0 elsewhere (the reduced vector padded with zeros).
+__global__ void k_mask_copy(const uint8_t *__restrict__ lab, long long n, const float *__restrict__ in,
+                            float *__restrict__ out) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    out[p] = lab[p] == kFluid ? in[p] : 0.f;
 }
 
 // 2x2x2 average pooling of a vector: out[P] = mean of its 8 children.
@@ -272,10 +287,15 @@ void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *
 }
 
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,
-                      const float *vscale, int mask_input, float *out, const SolveState *st, cudaStream_t s) {
+                      const float *vscale, int mask_input, int round_k, float *out, const SolveState *st,
+                      cudaStream_t s) {
   ImgSrc im{lab, counts};
   if (counts) im.lab = nullptr;
-  k_cconv_f32<<<grid_for(dm.n(), 128), 128, 0, s>>>(im, dm, w, v, vscale, mask_input, out, st);
+  k_cconv_f32<<<grid_for(dm.n(), 128), 128, 0, s>>>(im, dm, w, v, vscale, mask_input, round_k, out, st);
+}
+
+void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s) {
+  k_mask_copy<<<grid_for(n, 256), 256, 0, s>>>(lab, n, in, out);
 }
 
 void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, cudaStream_t s) {

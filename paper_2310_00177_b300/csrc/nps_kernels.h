@@ -38,7 +38,8 @@ void launch_pyramid(const uint8_t *lab, Dims d1, ushort2 *const *counts, int L, 
 void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,
                 double *out, cudaStream_t s);
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,
-                      const float *vscale, int mask_input, float *out, const SolveState *st, cudaStream_t s);
+                      const float *vscale, int mask_input, int round_k, float *out, const SolveState *st,
+                      cudaStream_t s);
 void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, cudaStream_t s);
 void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s);
 void launch_combine(long long n, const float *x1, const float *x2, const double *c12, float *out,
@@ -65,5 +66,23 @@ void launch_cconv_umma(int nsplit, const uint8_t *lab, const ushort2 *counts, Di
                        const float *v, const float *vscale, int mask_input, float *out, const SolveState *st,
                        int *err, int num_sms, cudaStream_t s);
 void launch_umma_selftest(float *d_out, float *d_ref, int *err, cudaStream_t s);
+
+// kernels_cached.cu
+long long cached_columns(Dims d);
+void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t *mask, uint32_t *offset,
+                     unsigned *total, cudaStream_t s);
+void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w,
+                     const uint32_t *mask, const uint32_t *offset, void *cache, cudaStream_t s);
+int cached_entry_bytes(bool bf16);
+void launch_cconv_cached(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims dm, const float *uni_host,
+                         const uint32_t *mask, const uint32_t *offset, const void *cache, const float *v,
+                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12,
+                         const SolveState *st, int num_sms, cudaStream_t s);
+void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
+
+// kernels_march.cu
+void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
+                        const float *v, const float *coarse, const float *vscale, int mask_input, float *out,
+                        float *pooled, const SolveState *st, int *err, int num_sms, cudaStream_t s);
 
 }  // namespace nps

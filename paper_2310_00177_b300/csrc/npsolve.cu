@@ -49,6 +49,12 @@ struct Workspace {
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
   ushort2 *counts[kMaxLevels + 1] = {};
+  // per-solve kernel cache of the mixed-window cells (cached path)
+  uint32_t *kmask[kMaxLevels + 1] = {}, *koff[kMaxLevels + 1] = {};
+  long long kcols[kMaxLevels + 1] = {};  // column chunks kmask / koff can hold
+  void *kcache[(kMaxLevels + 1) * 2] = {};
+  size_t kcap[(kMaxLevels + 1) * 2] = {};
+  unsigned *ktotal = nullptr, *h_ktotal = nullptr;
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
   int hist_cap = 0;
   SolveState *st = nullptr;
@@ -71,6 +77,7 @@ struct Workspace {
   const float *graph_b = nullptr;
   double *graph_x = nullptr;
   int graph_pcg = 0;
+  long long graph_kernels = 0;  // kernels per replay of the graph
 };
 
 // Kernel classes timed by the optional per-class profiling (CUDA events on
@@ -107,6 +114,8 @@ struct npsolve {
   std::vector<float> weights;      // host copy of the flat blob
   CConvW *cw = nullptr;            // [(kMaxLevels+1)*2], index lvl*2 + (type-1)
   uint8_t *uw = nullptr;           // tensor-core W splits, [(kMaxLevels+1)*2][umma_weight_bytes(3)]
+  float *uni = nullptr;            // uniform-window kernel terms Bp, SWf, SWa: [(kMaxLevels+1)*2][81]
+  std::vector<float> uni_host;     // the same on the host (passed as kernel parameters)
   int nsplit = 3;                  // BF16 terms of W on the tensor cores (3: FP32 form, 1: BF16 form)
   int num_sms = 148;
   int *umma_err = nullptr;         // set by a tensor-core kernel whose MMA wait timed out
@@ -196,7 +205,12 @@ void free_ws(Workspace &w) {
     cudaFree(w.x2[l]);
     cudaFree(w.xc[l]);
     cudaFree(w.counts[l]);
+    cudaFree(w.kmask[l]);
+    cudaFree(w.koff[l]);
   }
+  for (int i = 0; i < (kMaxLevels + 1) * 2; ++i) cudaFree(w.kcache[i]);
+  cudaFree(w.ktotal);
+  cudaFreeHost(w.h_ktotal);
   cudaFree(w.part);
   cudaFree(w.affc);
   cudaFree(w.relres);
@@ -215,6 +229,8 @@ void free_ws(Workspace &w) {
   cudaFree(w.stage_x);
   w = Workspace{};
 }
+
+Dims level_dims(Dims d, int lvl) { return Dims{d.nx >> (lvl - 1), d.ny >> (lvl - 1), d.nz >> (lvl - 1)}; }
 
 // Make sure the workspace holds buffers for a grid of dims (L levels).
 int ensure_ws(npsolve *h, Dims d, int hist_cap) {
@@ -257,6 +273,8 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     CK(h, dalloc(&w.relres, 2));
     CK(h, dalloc(&w.st, 1));
     CK(h, dalloc(&w.tickets, 8));
+    CK(h, dalloc(&w.ktotal, kMaxLevels + 1));
+    CK(h, cudaHostAlloc((void **)&w.h_ktotal, sizeof(unsigned) * (kMaxLevels + 1), cudaHostAllocDefault));
     CK(h, cudaMemset(w.tickets, 0, 8 * sizeof(unsigned)));
     CK(h, cudaMalloc(&w.pcg_st, pcg_state_bytes()));
     CK(h, dalloc(&w.bad, 1));
@@ -346,12 +364,28 @@ int upload_weights(npsolve *h) {
     for (int i = 0; i < (kMaxLevels + 1) * 2; ++i) prepare_umma_weights(cw[i], h->nsplit, uw.data() + (size_t)i * wb);
     CK(h, cudaMemcpy(h->uw, uw.data(), uw.size(), cudaMemcpyHostToDevice));
   }
+  {
+    // uniform-window kernels K_a = Bp[a] + nF SWf[a] + nA SWa[a] (row sums in FP64)
+    std::vector<float> uni((size_t)(kMaxLevels + 1) * 2 * 81, 0.f);
+    for (int i = 0; i < (kMaxLevels + 1) * 2; ++i)
+      for (int a = 0; a < 27; ++a) {
+        double sf = 0.0, sa = 0.0;
+        for (int l = 0; l < 27; ++l) {
+          sf += cw[i].wf[a][l];
+          sa += cw[i].wa[a][l];
+        }
+        uni[(size_t)i * 81 + a] = cw[i].bp[a];
+        uni[(size_t)i * 81 + 27 + a] = (float)sf;
+        uni[(size_t)i * 81 + 54 + a] = (float)sa;
+      }
+    CK(h, cudaMemcpy(h->uni, uni.data(), uni.size() * sizeof(float), cudaMemcpyHostToDevice));
+    h->uni_host = uni;
+  }
   CK(h, cudaMemcpy(h->cw, cw.data(), cw.size() * sizeof(CConvW), cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(h->aw, aw.data(), aw.size() * sizeof(AffW), cudaMemcpyHostToDevice));
   return NPSOLVE_OK;
 }
 
-Dims level_dims(Dims d, int lvl) { return Dims{d.nx >> (lvl - 1), d.ny >> (lvl - 1), d.nz >> (lvl - 1)}; }
 
 int check_dims(npsolve *h, int nx, int ny, int nz) {
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
@@ -363,22 +397,51 @@ int check_dims(npsolve *h, int nx, int ny, int nz) {
   return NPSOLVE_OK;
 }
 
-// One CConv block of level lvl (type 1 or 2).
+// Levels whose CConv runs on the tensor cores in the per-iteration
+// recompute path (image counts <= 64 are exact in BF16 up to level 3).
+bool tensor_level(const npsolve *h, int lvl) { return h->cfg.kernel_path == NPSOLVE_PATH_TENSOR && lvl <= 3; }
+bool cached_path(const npsolve *h) { return h->cfg.kernel_path == NPSOLVE_PATH_CACHED; }
+
+// One CConv block of level lvl (type 1 or 2), CUDA-core kernel.
 void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *vscale,
            int mask_input, float *out, const SolveState *st, cudaStream_t s) {
   Workspace &w = h->ws;
   const Dims dl = level_dims(d1, lvl);
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
-  if (h->cfg.kernel_path == NPSOLVE_PATH_TENSOR && lvl <= 3) {
-    // image features exact in BF16 up to level 3 (counts <= 64)
-    launch_cconv_umma(h->nsplit, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl,
-                      h->uw + (size_t)idx * umma_weight_bytes(3), in, vscale, mask_input, out, st, h->umma_err,
-                      h->num_sms, s);
-    return;
-  }
+  h->launches += 1;
   launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw + idx, in, vscale,
-                   mask_input, out, st, s);
+                   mask_input, h->cfg.precision == NPSOLVE_BF16, out, st, s);
+}
+
+// One CConv block on the tensor cores (z-marching kernel), with the input
+// either read (in) or interpolated from the coarser level (coarse), and an
+// optional fused 2x2x2 pooling of the output into `pooled`.
+void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *coarse,
+              const float *vscale, int mask_input, float *out, float *pooled, const SolveState *st,
+              cudaStream_t s) {
+  Workspace &w = h->ws;
+  const int idx = lvl * 2 + (type - 1);
+  ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
+  h->launches += 1;
+  launch_cconv_march(h->nsplit, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], level_dims(d1, lvl),
+                     h->uw + (size_t)idx * umma_weight_bytes(3), in, coarse, vscale, mask_input, out, pooled, st,
+                     h->umma_err, h->num_sms, s);
+}
+
+// One CConv block with the per-solve kernel cache (kernels_cached.cu): input
+// read (in) or interpolated (coarse), optional fused pooling, optional fused
+// combination out = c1 x1 + c2 CConv(...).
+void cconv_cached(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *vscale,
+                  float *out, float *pooled, const float *x1, const double *c12, const SolveState *st,
+                  cudaStream_t s) {
+  Workspace &w = h->ws;
+  const int idx = lvl * 2 + (type - 1);
+  ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
+  h->launches += 1;
+  launch_cconv_cached(h->cfg.precision == NPSOLVE_BF16, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl],
+                      level_dims(d1, lvl), h->uni_host.data() + (size_t)idx * 81, w.kmask[lvl], w.koff[lvl],
+                      w.kcache[idx], in, vscale, out, pooled, x1, c12, st, h->num_sms, s);
 }
 
 // Grids with nx % 4 == 0 use the 16-byte vector kernels with fused
@@ -389,39 +452,90 @@ enum { kTicketInit = 0, kTicketCombine = 1, kTicketLap = 2, kTicketUpdate = 3 };
 // The network z = P_net(I, r) of Alg. 2 on the prepared pyramid and Aff
 // coefficients.  Inside a solve (st != null) the level-1 input is scaled by
 // 1/||r|| from the state and the orthogonalisation dots are fused into the
-// last combination.
+// last combination.  `unfused` materialises every intermediate (r2, x2) for
+// the per-level inspection entry point.
 void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const float *vscale, float *z,
-                 SolveState *st, cudaStream_t s) {
+                 SolveState *st, cudaStream_t s, bool unfused = false) {
   Workspace &w = h->ws;
   const int L = h->cfg.levels;
-  for (int l = 1; l < L; ++l) {
-    cconv(h, lab, d1, l, 1, l == 1 ? r : w.r1[l], l == 1 ? vscale : nullptr, l == 1, w.x1[l], st, s);
-    ProfScope ps(h, P_POOL, s);
-    launch_pool(w.x1[l], level_dims(d1, l), w.r1[l + 1], st, s);
+  const bool cached = cached_path(h);
+  if (cached && !st) {
+    // the cached stencil expects an input that is zero off fluid: inside a solve
+    // r is, for a user-supplied vector zero it here
+    h->launches += 1;
+    launch_mask_copy(lab, d1.n(), r, w.r, s);
+    r = w.r;
   }
-  cconv(h, lab, d1, L, 1, L == 1 ? r : w.r1[L], L == 1 ? vscale : nullptr, L == 1, w.x1[L], st, s);
+  // down pass: x1^l = CConv1^l(r1^l), r1^{l+1} = Pool(x1^l)
+  for (int l = 1; l < L; ++l) {
+    const float *in = l == 1 ? r : w.r1[l];
+    const float *vs = l == 1 ? vscale : nullptr;
+    if (cached) {
+      cconv_cached(h, lab, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s);
+    } else if (tensor_level(h, l)) {
+      cconv_tc(h, lab, d1, l, 1, in, nullptr, vs, l == 1, w.x1[l], w.r1[l + 1], st, s);
+    } else {
+      cconv(h, lab, d1, l, 1, in, vs, l == 1, w.x1[l], st, s);
+      ProfScope ps(h, P_POOL, s);
+      h->launches += 1;
+      launch_pool(w.x1[l], level_dims(d1, l), w.r1[l + 1], st, s);
+    }
+  }
+  // coarsest level: x^L = CConv1^L(r1^L)
+  {
+    const float *in = L == 1 ? r : w.r1[L];
+    const float *vs = L == 1 ? vscale : nullptr;
+    if (cached) cconv_cached(h, lab, d1, L, 1, in, vs, w.x1[L], nullptr, nullptr, nullptr, st, s);
+    else if (tensor_level(h, L)) cconv_tc(h, lab, d1, L, 1, in, nullptr, vs, L == 1, w.x1[L], nullptr, st, s);
+    else cconv(h, lab, d1, L, 1, in, vs, L == 1, w.x1[L], st, s);
+  }
   if (L == 1) {
     ProfScope ps(h, P_COMBINE, s);
+    h->launches += 1;
     launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.part, st, s);
     return;
   }
+  // up pass: r2^l = Interp(x^{l+1}); x2^l = CConv2^l(r2^l); x^l = c1 x1^l + c2 x2^l
   for (int l = L - 1; l >= 1; --l) {
     const float *coarse = (l + 1 == L) ? w.x1[L] : w.xc[l + 1];
-    {
-      ProfScope ps(h, P_INTERP, s);
-      launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+    const double *c12 = w.affc + 2 * l;
+    if (cached && !unfused) {
+      {
+        ProfScope ps(h, P_INTERP, s);
+        h->launches += 1;
+        launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+      }
+      if (l > 1) {  // CConv2 and the combination in one pass
+        cconv_cached(h, lab, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s);
+        continue;
+      }
+      cconv_cached(h, lab, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
+    } else if (tensor_level(h, l) && !unfused) {
+      cconv_tc(h, lab, d1, l, 2, nullptr, coarse, nullptr, 0, w.x2[l], nullptr, st, s);
+    } else {
+      {
+        ProfScope ps(h, P_INTERP, s);
+        h->launches += 1;
+        launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+      }
+      if (cached) cconv_cached(h, lab, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
+      else if (tensor_level(h, l))
+        cconv_tc(h, lab, d1, l, 2, w.r2[l], nullptr, nullptr, 0, w.x2[l], nullptr, st, s);
+      else cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
     }
-    cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
     ProfScope ps(h, P_COMBINE, s);
-    if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], w.affc + 2 * l, w.xc[l], st, s);
+    h->launches += 1;
+    if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], c12, w.xc[l], st, s);
     else if (st && vec4_path(d1))  // fused: dots and orthogonalisation coefficients in one launch
-      launch_combine1_4(lab, (int)d1.n(), w.x1[1], w.x2[1], w.affc + 2, z, w.qring, w.part,
-                        w.tickets + kTicketCombine, st, h->num_sms, s);
-    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], w.affc + 2, z, w.qring, w.part, st, s);
+      launch_combine1_4(lab, (int)d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.part, w.tickets + kTicketCombine, st,
+                        h->num_sms, s);
+    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.part, st, s);
   }
 }
 
-// Label check, pyramid and Aff coefficients for this grid.
+// Label check, pyramid and Aff coefficients for this grid; for the cached
+// path also the classification of every level and the kernel generation of
+// the mixed-window cells (one host synchronisation to size the cache).
 int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool check) {
   Workspace &w = h->ws;
   const int L = h->cfg.levels;
@@ -433,27 +547,62 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
   for (int l = 1; l < L; ++l)
     launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
                h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s);
+  h->launches += 1 + (L - 1) + 2 * (L - 1);
+  if (cached_path(h)) {
+    for (int l = 1; l <= L; ++l) {  // column-chunk arrays sized for this grid's shape
+      const long long nc = cached_columns(level_dims(d1, l));
+      if (nc > w.kcols[l]) {
+        if (w.graph) cudaGraphExecDestroy(w.graph);
+        w.graph = nullptr;
+        CK(h, cudaStreamSynchronize(s));
+        cudaFree(w.kmask[l]);
+        cudaFree(w.koff[l]);
+        w.kmask[l] = w.koff[l] = nullptr;
+        CK(h, dalloc(&w.kmask[l], (size_t)nc));
+        CK(h, dalloc(&w.koff[l], (size_t)nc));
+        w.kcols[l] = nc;
+      }
+    }
+    CK(h, cudaMemsetAsync(w.ktotal, 0, sizeof(unsigned) * (kMaxLevels + 1), s));
+    for (int l = 1; l <= L; ++l)
+      launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), w.kmask[l],
+                      w.koff[l], w.ktotal + l, s);
+    h->launches += L;
+    CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    const bool bf16 = h->cfg.precision == NPSOLVE_BF16;
+    for (int l = 1; l <= L; ++l)
+      for (int t = 1; t <= (l < L ? 2 : 1); ++t) {
+        const int idx = l * 2 + (t - 1);
+        const size_t need = (size_t)w.h_ktotal[l] + 1;
+        if (need > w.kcap[idx]) {
+          if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old cache buffer
+          w.graph = nullptr;
+          CK(h, cudaStreamSynchronize(s));
+          cudaFree(w.kcache[idx]);
+          w.kcache[idx] = nullptr;
+          const size_t cap = need + need / 4;
+          CK(h, cudaMalloc(&w.kcache[idx], cap * cached_entry_bytes(true) * 2));  // room for either form
+          w.kcap[idx] = cap;
+        }
+        launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
+                        h->cw + idx, w.kmask[l], w.koff[l], w.kcache[idx], s);
+        h->launches += 1;
+      }
+  }
   CK(h, cudaGetLastError());
   return NPSOLVE_OK;
 }
 
-// Kernels enqueued by one network evaluation / one NPSDO iteration.
-int network_kernels(int L) { return L == 1 ? 2 : 5 * L - 4; }
-int iteration_kernels(const npsolve *h, bool fast) {
-  const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
-  if (fast && h->cfg.levels > 1) return network_kernels(h->cfg.levels) + 2 + (recur ? 1 : 3);
-  return network_kernels(h->cfg.levels) + 4 + (recur ? 2 : 3);
-}
-int setup_kernels(int L) { return 1 + (L - 1) + 2 * (L - 1); }
 
 // Enqueue one NPSDO iteration (Alg. 1 loop body) on stream s.
 void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x, cudaStream_t s) {
   Workspace &w = h->ws;
   const long long n = d1.n();
   const bool fast = vec4_path(d1) && h->cfg.levels > 1;
-  h->launches += iteration_kernels(h, fast);
   run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s);
   const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
+  h->launches += fast ? (recur ? 3 : 5) : (recur ? 6 : 7);
   if (fast) {
     {
       ProfScope ps(h, P_ORTHO_DIR, s);
@@ -502,9 +651,12 @@ int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x
   if (w.graph) cudaGraphExecDestroy(w.graph);
   w.graph = nullptr;
   cudaGraph_t g;
+  const long long before = h->launches;
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   for (int i = 0; i < kPollEvery; ++i) enqueue_iteration(h, lab, d1, b, x, h->cap_stream);
   CK(h, cudaStreamEndCapture(h->cap_stream, &g));
+  w.graph_kernels = h->launches - before;  // captured, not launched
+  h->launches = before;
   cudaError_t e = cudaGraphInstantiate(&w.graph, g, 0);
   cudaGraphDestroy(g);
   CK(h, e);
@@ -536,10 +688,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     if (vec4_path(d1)) {
       launch_init4(lab, (int)d1.n(), b, w.r, x, w.part, w.tickets + kTicketInit, tol, max_iter, h->cfg.n_ortho,
                    w.st, w.hist, h->num_sms, s);
-      h->launches += setup_kernels(h->cfg.levels) + 1;
+      h->launches += 1;
     } else {
       launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
-      h->launches += setup_kernels(h->cfg.levels) + 2;
+      h->launches += 2;
     }
   }
   CK(h, cudaGetLastError());
@@ -571,7 +723,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       }
       if (max_iter - launched >= kPollEvery) {
         CK(h, cudaGraphLaunch(w.graph, s));
-        h->launches += (long long)kPollEvery * iteration_kernels(h, vec4_path(d1) && h->cfg.levels > 1);
+        h->launches += w.graph_kernels;
         launched += kPollEvery;
       } else {
         enqueue_iteration(h, lab, d1, b, x, s);
@@ -654,7 +806,8 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
   if (prop.major * 10 + prop.minor != 103)
     return fail(nullptr, NPSOLVE_CUDA_ERROR, "device %s is sm_%d%d; this library is built for sm_103a", prop.name,
                 prop.major, prop.minor);
-  if (cfg->kernel_path != NPSOLVE_PATH_TENSOR && cfg->kernel_path != NPSOLVE_PATH_CUDA_CORE)
+  if (cfg->kernel_path != NPSOLVE_PATH_CACHED && cfg->kernel_path != NPSOLVE_PATH_CUDA_CORE &&
+      cfg->kernel_path != NPSOLVE_PATH_TENSOR)
     return fail(nullptr, NPSOLVE_BAD_ARG, "bad kernel_path");
   npsolve *h = new npsolve();
   h->cfg = *cfg;
@@ -670,7 +823,8 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
     cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     cudaError_t e5 = cudaMalloc(&h->uw, (size_t)(kMaxLevels + 1) * 2 * umma_weight_bytes(3));
     cudaError_t e6 = cudaMalloc(&h->umma_err, sizeof(int));
-    if (e1 || e2 || e3 || e4 || e5 || e6) st = fail(nullptr, NPSOLVE_OOM, "device allocation failed");
+    cudaError_t e7 = cudaMalloc(&h->uni, sizeof(float) * (kMaxLevels + 1) * 2 * 81);
+    if (e1 || e2 || e3 || e4 || e5 || e6 || e7) st = fail(nullptr, NPSOLVE_OOM, "device allocation failed");
     if (!st && cudaMemset(h->umma_err, 0, sizeof(int)) != cudaSuccess)
       st = fail(nullptr, NPSOLVE_CUDA_ERROR, "cudaMemset failed");
   }
@@ -713,6 +867,7 @@ void npsolve_destroy(npsolve_t h) {
   cudaFree(h->aw);
   cudaFree(h->unit_c12);
   cudaFree(h->uw);
+  cudaFree(h->uni);
   cudaFree(h->umma_err);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -779,7 +934,7 @@ int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int
   CK(h, cudaMemcpyAsync(w.h_flag, w.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
   CK(h, cudaStreamSynchronize(s));
   if (w.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
-  run_network(h, labels, d1, r, nullptr, w.z, nullptr, s);
+  run_network(h, labels, d1, r, nullptr, w.z, nullptr, s, level > 0);
   CK(h, cudaGetLastError());
   if (level == 0) {  // the network output z
     CK(h, cudaMemcpyAsync(out, w.z, sizeof(float) * d1.n(), cudaMemcpyDeviceToDevice, s));
@@ -891,6 +1046,11 @@ int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const floa
 }
 
 long long npsolve_launch_count(npsolve_t h) { return h ? h->launches : 0; }
+
+long long npsolve_mixed_cells(npsolve_t h, int level) {
+  if (!h || level < 1 || level > h->cfg.levels || !cached_path(h) || !h->ws.h_ktotal) return -1;
+  return (long long)h->ws.h_ktotal[level];
+}
 
 int npsolve_profile_count(void) { return P_COUNT; }
 

@@ -76,7 +76,10 @@ def test_bf16_form_tensor_equals_cuda_core_with_rounded_weights(shape, L):
     sc = b.Solver(w, levels=L, precision=b.BF16, kernel_path=b.PATH_CUDA_CORE)
     zt = st.apply_network(lab_d, r_d).cpu().numpy()
     zc = sc.apply_network(lab_d, r_d).cpu().numpy()
-    assert _rel(zt, zc) <= 1e-5
+    # both round the generated taps of mixed-window cells to BF16; FP32
+    # rounding differences before that rounding can flip a rare tap by one
+    # BF16 ulp (2^-8 relative)
+    assert _rel(zt, zc) <= 1e-4
     zo = oracle.network(lab, L, w.astype(np.float64), r.astype(np.float64))
     e = _rel(zt, zo)
     assert 0 < e <= 2e-2
@@ -104,3 +107,25 @@ def test_tensor_path_solve_config1(precision):
     else:
         assert abs(iters - ores["iters"]) <= 3
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-5)])
+@pytest.mark.parametrize("shape,L", [((32, 32, 32), 4), ((24, 40, 64), 4), ((16, 32, 8), 3), ((64, 16, 32), 5)])
+def test_cached_path_matches_cuda_core_path(shape, L, precision, tol):
+    # the per-solve kernel cache (default path) against per-iteration
+    # regeneration on CUDA cores: identical arithmetic up to FP32 rounding
+    b = _b()
+    lab = _rng_labels(shape, 51) if shape != (32, 32, 32) else synth.pool_scene(32, 1000)
+    w = synth.init_weights(L, 52, spread=0.05).astype(np.float32)
+    r = np.random.default_rng(53).standard_normal(shape).astype(np.float32)
+    lab_d, r_d = _dev(lab, torch.uint8), _dev(r, torch.float32)
+    s0 = b.Solver(w, levels=L, precision=precision, kernel_path=b.PATH_CACHED)
+    s1 = b.Solver(w, levels=L, precision=precision, kernel_path=b.PATH_CUDA_CORE)
+    z0 = s0.apply_network(lab_d, r_d).cpu().numpy()
+    z1 = s1.apply_network(lab_d, r_d).cpu().numpy()
+    assert _rel(z0, z1) <= tol
+    if precision == 0:
+        zo = oracle.network(lab, L, w.astype(np.float64), r.astype(np.float64))
+        assert _rel(z0, zo) <= 1e-5
+    s0.close()
+    s1.close()
