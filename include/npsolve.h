@@ -173,6 +173,30 @@ int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const f
 int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol, int max_iter,
                        void *stream, double *x, int *iters, double *rel_residual);
 
+/* Reverse mode of the network (the hand-written backward of Alg. 2): for the
+ * output cotangent gz of z = P_net(I, r), the gradient of <gz, z> with
+ * respect to the weights (host, npsolve_weight_count(L) floats, raw blob
+ * layout) and, if grad_r != NULL, with respect to r (device, zero off fluid).
+ * Intermediates are stored during the forward pass; the per-cell kernels are
+ * regenerated from the image for each level of the backward pass. */
+int npsolve_network_vjp(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r, const float *gz,
+                        float *grad_w_host, float *grad_r, void *stream);
+
+/* Training loss of Sec. 4.2.3 for one system, Loss = || b - A P_net(I, b) ||_2
+ * (b as given, zeroed off fluid), and its weight gradient (host floats, may
+ * be NULL). */
+int npsolve_loss_grad(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *b, void *stream,
+                      double *loss, float *grad_w_host);
+
+/* One optimisation step on a batch: the mean of the per-system losses of
+ * npsolve_loss_grad over `batch` systems (labels[i], b[i] device pointers,
+ * dims[3i..3i+2] = nx, ny, nz of system i, each divisible by 2^(L-1)), then
+ * an Adam update (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) of the
+ * handle's weights.  *loss receives the mean loss before the update.  Train
+ * with an FP32-form handle; the Adam state lives in the handle. */
+int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, const int *dims, const float *const *b,
+                       float lr, void *stream, double *loss);
+
 /* Optional per-kernel-class timing of solves on a handle.  While profiling
  * is on, npsolve_solve runs one iteration at a time (no CUDA graph) and
  * records a CUDA event pair on the solve's stream around every launch of each

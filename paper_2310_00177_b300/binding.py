@@ -56,6 +56,9 @@ SIGNATURES = {
     "npsolve_true_residual": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_jacobi_pcg": ([_vp, _i, _i, _i, _vp, _d, _i, _vp, _vp, ctypes.POINTER(_i), ctypes.POINTER(_d)], _i),
     "npsolve_selftest_tensor_core": ([ctypes.POINTER(_d)], _i),
+    "npsolve_network_vjp": ([_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
+    "npsolve_loss_grad": ([_vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
+    "npsolve_train_step": ([_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, ctypes.POINTER(_d)], _i),
     "npsolve_profile_count": ([], _i),
     "npsolve_launch_count": ([_vp], ctypes.c_longlong),
     "npsolve_mixed_cells": ([_vp, _i], ctypes.c_longlong),
@@ -197,6 +200,44 @@ class Solver:
         """Kernels enqueued by this handle since creation."""
         return int(load_library().npsolve_launch_count(self._h))
 
+    def network_vjp(self, labels, r, gz, want_grad_r=True):
+        """Backward of z = P_net(I, r) for the cotangent gz: (grad_w numpy, grad_r tensor or None)."""
+        import torch
+
+        nx, ny, nz = _dims(labels)
+        gw = np.zeros(weight_count(self.levels), np.float32)
+        gr = torch.empty(labels.shape, dtype=torch.float32, device=labels.device) if want_grad_r else None
+        _check(load_library().npsolve_network_vjp(
+            self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz, _ptr(r, torch.float32, "r"),
+            _ptr(gz, torch.float32, "gz"), gw.ctypes.data_as(_vp),
+            _ptr(gr, torch.float32, "grad_r") if gr is not None else None, _stream()), self._h)
+        return gw, gr
+
+    def loss_grad(self, labels, b, want_grad=True):
+        """Loss ||b - A P_net(I, b)|| and its weight gradient (numpy) of one system."""
+        import torch
+
+        nx, ny, nz = _dims(labels)
+        loss = ctypes.c_double(0.0)
+        gw = np.zeros(weight_count(self.levels), np.float32) if want_grad else None
+        _check(load_library().npsolve_loss_grad(
+            self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz, _ptr(b, torch.float32, "b"), _stream(),
+            ctypes.byref(loss), gw.ctypes.data_as(_vp) if gw is not None else None), self._h)
+        return loss.value, gw
+
+    def train_step(self, labels_list, b_list, lr=1e-3):
+        """One Adam step on a batch of systems (lists of device tensors); returns the mean loss."""
+        import torch
+
+        n = len(labels_list)
+        labs = (ctypes.c_void_p * n)(*[_ptr(l, torch.uint8, "labels").value for l in labels_list])
+        bs = (ctypes.c_void_p * n)(*[_ptr(x, torch.float32, "b").value for x in b_list])
+        dims = np.ascontiguousarray(np.array([_dims(l) for l in labels_list], np.int32).ravel())
+        loss = ctypes.c_double(0.0)
+        _check(load_library().npsolve_train_step(self._h, n, labs, dims.ctypes.data_as(_vp), bs, float(lr),
+                                                 _stream(), ctypes.byref(loss)), self._h)
+        return loss.value
+
     def set_profiling(self, on=True):
         _check(load_library().npsolve_set_profiling(self._h, int(bool(on))), self._h)
 
@@ -286,3 +327,38 @@ def selftest_tensor_core():
     e = ctypes.c_double(-1.0)
     _check(load_library().npsolve_selftest_tensor_core(ctypes.byref(e)))
     return e.value
+
+
+class NetworkFunction:
+    """torch.autograd.Function of z = P_net(I, r) with respect to the weights
+    and r, whose backward is the library's hand-written kernel
+    (npsolve_network_vjp).  Usage: NetworkFunction.apply(weights, labels, r, solver)."""
+
+    _fn = None
+
+    @staticmethod
+    def get():
+        if NetworkFunction._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, weights, labels, r, solver):
+                    solver.set_weights(weights.detach().cpu().numpy())
+                    ctx.save_for_backward(labels, r)
+                    ctx.solver = solver
+                    return solver.apply_network(labels, r.detach().contiguous().float())
+
+                @staticmethod
+                def backward(ctx, gz):
+                    labels, r = ctx.saved_tensors
+                    gw, gr = ctx.solver.network_vjp(labels, r.detach().contiguous().float(),
+                                                    gz.detach().contiguous().float())
+                    return torch.from_numpy(gw), None, gr, None
+
+            NetworkFunction._fn = _F
+        return NetworkFunction._fn
+
+    @staticmethod
+    def apply(weights, labels, r, solver):
+        return NetworkFunction.get().apply(weights, labels, r, solver)

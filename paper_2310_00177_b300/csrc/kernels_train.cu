@@ -1,0 +1,368 @@
+// Backward kernels of the network (reverse of Alg. 2) and of the training
+// loss of Sec. 4.2.3, Loss = || b - A P_net(I, b) ||_2.
+//
+// CConv backward for an output cotangent g (per level):
+//   input gradient   gv(q) = sum_a K_a(q - a) g(q - a)          (gather form)
+//   kernel gradient  gK_a(p) = g(p) v(p + a)
+//   weight gradient  gW'[a][j] = sum_p gK_a(p) F_j(p),  F = (nF window, nA window, 1)
+// with K materialised per cell (the same FP32 arithmetic as the forward) so
+// the input gradient is a deterministic gather, and the 27 x 55 weight
+// gradient accumulated per block in FP32 over 32-cell batches and reduced
+// across blocks in FP64 in a fixed order.
+#include "nps_common.cuh"
+#include "nps_kernels.h"
+
+namespace nps {
+
+namespace {
+
+__device__ __forceinline__ float2 feat_at(const uint8_t *lab, const ushort2 *counts, const Dims &d, int x, int y,
+                                          int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= d.nx || y >= d.ny || z >= d.nz) return make_float2(0.f, 0.f);
+  const long long p = ((long long)z * d.ny + y) * d.nx + x;
+  if (lab) {
+    const uint8_t l = lab[p];
+    return make_float2(l == kFluid ? 1.f : 0.f, l == kAir ? 1.f : 0.f);
+  }
+  const ushort2 c = counts[p];
+  return make_float2((float)c.x, (float)c.y);
+}
+
+__device__ __forceinline__ float vec_at(const float *v, const Dims &d, int x, int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= d.nx || y >= d.ny || z >= d.nz) return 0.f;
+  return v[((long long)z * d.ny + y) * d.nx + x];
+}
+
+inline int gridn(long long n, int t) {
+  long long b = (n + t - 1) / t;
+  if (b > 148LL * 16) b = 148LL * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// K[p][a] for every cell of a level (27 floats per cell, FP32 generation).
+__global__ void __launch_bounds__(128) k_materialize_K(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                                       Dims d, const CConvW *__restrict__ w, float *__restrict__ K) {
+  __shared__ CConvW sw;
+  {
+    const float *src = (const float *)w;
+    float *dst = (float *)&sw;
+    for (int i = threadIdx.x; i < (int)(sizeof(CConvW) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const long long n = d.n();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, d, x, y, z);
+    float nf[27], na[27];
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      const float2 f = feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
+      nf[l] = f.x;
+      na[l] = f.y;
+    }
+#pragma unroll 1
+    for (int a = 0; a < 27; ++a) {
+      float k = sw.bp[a];
+#pragma unroll
+      for (int l = 0; l < 27; ++l) k = fmaf(sw.wf[a][l], nf[l], fmaf(sw.wa[a][l], na[l], k));
+      K[p * 27 + a] = k;
+    }
+  }
+}
+
+// gv(q) = sum_a K_a(q - a) g(q - a) over neighbours p = q - a inside the grid.
+__global__ void k_cconv_transpose(const float *__restrict__ K, const float *__restrict__ g, Dims d,
+                                  float *__restrict__ gv) {
+  const long long n = d.n();
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(q, d, x, y, z);
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+      const int px = x - (a % 3 - 1), py = y - ((a / 3) % 3 - 1), pz = z - (a / 9 - 1);
+      if (px < 0 || py < 0 || pz < 0 || px >= d.nx || py >= d.ny || pz >= d.nz) continue;
+      const long long p = ((long long)pz * d.ny + py) * d.nx + px;
+      acc = fmaf(K[p * 27 + a], g[p], acc);
+    }
+    gv[q] = acc;
+  }
+}
+
+// Weight gradient of one CConv block: block partials of
+//   G[a][j] = sum_p g(p) v(p + a) F_j(p),  j < 27: nF(p + l_j), j < 54: nA(p + l_{j-27}), j = 54: 1.
+constexpr int kWG = 27 * 55;  // 1485 outputs
+constexpr int kWGBatch = 32;
+__global__ void __launch_bounds__(256) k_cconv_wgrad(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                                     Dims d, const float *__restrict__ v, const float *__restrict__ g,
+                                                     double *__restrict__ part) {
+  __shared__ float sGK[kWGBatch][27];
+  __shared__ float sF[kWGBatch][56];
+  const int tid = threadIdx.x;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // outputs tid, tid+256, ... (< kWG)
+  const long long n = d.n();
+  const long long nb = (n + kWGBatch - 1) / kWGBatch;
+  for (long long bt = blockIdx.x; bt < nb; bt += gridDim.x) {
+    const long long p0 = bt * kWGBatch;
+    // stage gK (27 per cell) and F (55 per cell) of the batch
+    for (int i = tid; i < kWGBatch * 27; i += blockDim.x) {
+      const int c = i / 27, a = i % 27;
+      const long long p = p0 + c;
+      float val = 0.f;
+      if (p < n) {
+        int x, y, z;
+        cell_xyz(p, d, x, y, z);
+        const float gp = g[p];
+        if (gp != 0.f) val = gp * vec_at(v, d, x + a % 3 - 1, y + (a / 3) % 3 - 1, z + a / 9 - 1);
+      }
+      sGK[c][a] = val;
+    }
+    for (int i = tid; i < kWGBatch * 28; i += blockDim.x) {
+      const int c = i / 28, l = i % 28;
+      const long long p = p0 + c;
+      float ff = 0.f, fa = 0.f;
+      if (p < n && l < 27) {
+        int x, y, z;
+        cell_xyz(p, d, x, y, z);
+        const float2 f = feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
+        ff = f.x;
+        fa = f.y;
+      }
+      if (l < 27) {
+        sF[c][l] = ff;
+        sF[c][27 + l] = fa;
+      } else {
+        sF[c][54] = p < n ? 1.f : 0.f;
+        sF[c][55] = 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int o = tid + k * 256;
+      if (o < kWG) {
+        const int a = o / 55, j = o % 55;
+        float s = acc[k];
+#pragma unroll 8
+        for (int c = 0; c < kWGBatch; ++c) s = fmaf(sGK[c][a], sF[c][j], s);
+        acc[k] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int o = tid + k * 256;
+    if (o < kWG) part[(size_t)blockIdx.x * kWG + o] = (double)acc[k];
+  }
+}
+
+// Sum the block partials of k_cconv_wgrad (fixed order) into out[1485].
+__global__ void k_wgrad_final(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < kWG; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * kWG + o];
+    out[o] = s;
+  }
+}
+
+// Adjoint of 2x2x2 average pooling: fine(p) = coarse(parent(p)) / 8, added into gf.
+__global__ void k_pool_adjoint_add(const float *__restrict__ gc, Dims fine, float *__restrict__ gf) {
+  const long long n = fine.n();
+  const int cx = fine.nx / 2, cy = fine.ny / 2;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, fine, x, y, z);
+    gf[p] += 0.125f * gc[((long long)(z >> 1) * cy + (y >> 1)) * cx + (x >> 1)];
+  }
+}
+
+// Weight of coarse index X in the x2 linear upsampling of fine index f (half-
+// pixel centres, edge clamp): the sum of the tap weights of f that hit X.
+__device__ __forceinline__ float up_weight(int f, int X, int nc) {
+  const int j = f >> 1;
+  int i0, i1;
+  float w1;
+  if (f & 1) {
+    i0 = j;
+    i1 = j + 1 < nc ? j + 1 : nc - 1;
+    w1 = 0.25f;
+  } else if (j > 0) {
+    i0 = j - 1;
+    i1 = j;
+    w1 = 0.75f;
+  } else {
+    i0 = 0;
+    i1 = 0;
+    w1 = 0.f;
+  }
+  return (i0 == X ? 1.f - w1 : 0.f) + (i1 == X ? w1 : 0.f);
+}
+
+// Adjoint of the x2 trilinear interpolation (gather over the fine cells whose
+// taps reach each coarse cell), added into gc.
+__global__ void k_interp_adjoint_add(const float *__restrict__ gfine, Dims coarse, float *__restrict__ gc) {
+  const long long n = coarse.n();
+  const int fx = coarse.nx * 2, fy = coarse.ny * 2, fz = coarse.nz * 2;
+  for (long long P = (long long)blockIdx.x * blockDim.x + threadIdx.x; P < n; P += (long long)gridDim.x * blockDim.x) {
+    int X, Y, Z;
+    cell_xyz(P, coarse, X, Y, Z);
+    float acc = 0.f;
+    for (int z = 2 * Z - 1; z <= 2 * Z + 2; ++z) {
+      if (z < 0 || z >= fz) continue;
+      const float wz = up_weight(z, Z, coarse.nz);
+      if (wz == 0.f) continue;
+      for (int y = 2 * Y - 1; y <= 2 * Y + 2; ++y) {
+        if (y < 0 || y >= fy) continue;
+        const float wy = up_weight(y, Y, coarse.ny);
+        if (wy == 0.f) continue;
+        for (int x = 2 * X - 1; x <= 2 * X + 2; ++x) {
+          if (x < 0 || x >= fx) continue;
+          const float wx = up_weight(x, X, coarse.nx);
+          if (wx == 0.f) continue;
+          acc += wz * wy * wx * gfine[((long long)z * fy + y) * fx + x];
+        }
+      }
+    }
+    gc[P] += acc;
+  }
+}
+
+// Aff gradient statistics: S[c][l] = (1/(27 n)) sum_p I_c(p + l) for the
+// channels c = fluid, air (the solid one is 1/27 - S_fluid - S_air, the
+// channels summing to one, padding included); block partials of the 54 sums
+// with a fixed-order reduction (per warp by shuffles, then across warps).
+__global__ void __launch_bounds__(kRedThreads) k_aff_stats(const uint8_t *__restrict__ lab,
+                                                           const ushort2 *__restrict__ counts, Dims d, float inv,
+                                                           double *__restrict__ part) {
+  __shared__ double sm[kRedThreads / 32][54];
+  float acc[54];
+#pragma unroll
+  for (int i = 0; i < 54; ++i) acc[i] = 0.f;
+  const long long n = d.n();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, d, x, y, z);
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      const float2 f = feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
+      acc[l] += f.x;
+      acc[27 + l] += f.y;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 54; ++i) {
+    double v = (double)acc[i] * inv;
+    v = warp_sum(v);
+    if (lane == 0) sm[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 54) {
+    double t = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) t += sm[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 54 + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_aff_stats_final(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
+  const int o = threadIdx.x;
+  if (o >= 54) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * 54 + o];
+  out[o] = s;
+}
+
+// Plain dot product partials (deterministic, FP64 above the thread).
+__global__ void __launch_bounds__(kRedThreads) k_dot2(const float *__restrict__ a, const float *__restrict__ b,
+                                                      const float *__restrict__ c, long long n,
+                                                      double *__restrict__ part) {
+  double v[2] = {0.0, 0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    v[0] += (double)a[p] * b[p];
+    if (c) v[1] += (double)a[p] * c[p];
+  }
+  block_sum_store<2>(v, part + (size_t)blockIdx.x * 2);
+}
+
+__global__ void k_dot2_final(const double *part, int nblocks, double *out) {
+  double t[2];
+  reduce_partials<2>(part, nblocks, t);
+  if (threadIdx.x == 0) {
+    out[0] = t[0];
+    out[1] = t[1];
+  }
+}
+
+// out = alpha * a + beta * b (masked to fluid when lab != null).
+__global__ void k_axpby(const uint8_t *__restrict__ lab, long long n, float alpha, const float *__restrict__ a,
+                        float beta, const float *__restrict__ b, float *__restrict__ out) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    float v = alpha * a[p] + (b ? beta * b[p] : 0.f);
+    if (lab && lab[p] != kFluid) v = 0.f;
+    out[p] = v;
+  }
+}
+
+// out = alpha * a (masked) with a device scalar alpha = scale / sqrt(*norm2) (loss gradient).
+__global__ void k_scale_by_inv_norm(const uint8_t *__restrict__ lab, long long n, float scale,
+                                    const double *__restrict__ norm2, const float *__restrict__ a,
+                                    float *__restrict__ out) {
+  const double nn = *norm2;
+  const float alpha = nn > 0.0 ? (float)(scale / sqrt(nn)) : 0.f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    out[p] = (lab && lab[p] != kFluid) ? 0.f : alpha * a[p];
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+void launch_materialize_K(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, float *K,
+                          cudaStream_t s) {
+  k_materialize_K<<<gridn(d.n(), 128), 128, 0, s>>>(lab, counts, d, w, K);
+}
+void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s) {
+  k_cconv_transpose<<<gridn(d.n(), 256), 256, 0, s>>>(K, g, d, gv);
+}
+int wgrad_blocks(Dims d) {
+  long long nb = (d.n() + kWGBatch - 1) / kWGBatch;
+  if (nb > 148 * 4) nb = 148 * 4;
+  return (int)(nb < 1 ? 1 : nb);
+}
+void launch_cconv_wgrad(const uint8_t *lab, const ushort2 *counts, Dims d, const float *v, const float *g,
+                        double *part, double *out, cudaStream_t s) {
+  const int nb = wgrad_blocks(d);
+  k_cconv_wgrad<<<nb, 256, 0, s>>>(lab, counts, d, v, g, part);
+  k_wgrad_final<<<(kWG + 255) / 256, 256, 0, s>>>(part, nb, out);
+}
+void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s) {
+  k_pool_adjoint_add<<<gridn(fine.n(), 256), 256, 0, s>>>(gc, fine, gf);
+}
+void launch_interp_adjoint_add(const float *gfine, Dims coarse, float *gc, cudaStream_t s) {
+  k_interp_adjoint_add<<<gridn(coarse.n(), 256), 256, 0, s>>>(gfine, coarse, gc);
+}
+void launch_aff_stats(const uint8_t *lab, const ushort2 *counts, Dims d, double feature_scale, double *part,
+                      double *out, cudaStream_t s) {
+  const int nb = red_blocks(d.n());
+  k_aff_stats<<<nb, kRedThreads, 0, s>>>(lab, counts, d, (float)(feature_scale / (27.0 * (double)d.n())), part);
+  k_aff_stats_final<<<1, 64, 0, s>>>(part, nb, out);
+}
+void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
+                 cudaStream_t s) {
+  const int nb = red_blocks(n);
+  k_dot2<<<nb, kRedThreads, 0, s>>>(a, b, c, n, part);
+  k_dot2_final<<<1, kRedThreads, 0, s>>>(part, nb, out);
+}
+void launch_axpby(const uint8_t *lab, long long n, float alpha, const float *a, float beta, const float *b, float *out,
+                  cudaStream_t s) {
+  k_axpby<<<gridn(n, 256), 256, 0, s>>>(lab, n, alpha, a, beta, b, out);
+}
+void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, const double *norm2, const float *a,
+                              float *out, cudaStream_t s) {
+  k_scale_by_inv_norm<<<gridn(n, 256), 256, 0, s>>>(lab, n, scale, norm2, a, out);
+}
+int wgrad_outputs() { return kWG; }
+
+}  // namespace nps

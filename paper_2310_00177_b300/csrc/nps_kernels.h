@@ -80,6 +80,25 @@ void launch_cconv_cached(bool bf16, const uint8_t *lab, const ushort2 *counts, D
                          const SolveState *st, int num_sms, cudaStream_t s);
 void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
 
+// kernels_train.cu
+void launch_materialize_K(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, float *K,
+                          cudaStream_t s);
+void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s);
+int wgrad_blocks(Dims d);
+int wgrad_outputs();
+void launch_cconv_wgrad(const uint8_t *lab, const ushort2 *counts, Dims d, const float *v, const float *g,
+                        double *part, double *out, cudaStream_t s);
+void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s);
+void launch_interp_adjoint_add(const float *gfine, Dims coarse, float *gc, cudaStream_t s);
+void launch_aff_stats(const uint8_t *lab, const ushort2 *counts, Dims d, double feature_scale, double *part,
+                      double *out, cudaStream_t s);
+void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
+                 cudaStream_t s);
+void launch_axpby(const uint8_t *lab, long long n, float alpha, const float *a, float beta, const float *b, float *out,
+                  cudaStream_t s);
+void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, const double *norm2, const float *a,
+                              float *out, cudaStream_t s);
+
 // kernels_march.cu
 void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
                         const float *v, const float *coarse, const float *vscale, int mask_input, float *out,

@@ -19,6 +19,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -127,6 +128,15 @@ struct npsolve {
   std::vector<double> last_hist;
   Profiler prof;
   long long launches = 0;  // kernels enqueued by this handle since creation
+  // training: backward buffers (grown on demand) and Adam state
+  struct {
+    long long cap = 0;
+    float *gx[kMaxLevels + 1] = {}, *gx1[kMaxLevels + 1] = {};
+    float *rm = nullptr, *tmp = nullptr, *tmp2 = nullptr, *res = nullptr, *gz = nullptr, *K = nullptr;
+    double *part = nullptr, *out = nullptr;  // partials, and the reduced results (see train_backward)
+    std::vector<double> m, v;
+    long long t = 0;
+  } tr;
 };
 
 namespace {
@@ -595,6 +605,198 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Training: forward with stored intermediates, hand-written backward of
+// Alg. 2 (kernels_train.cu) and the loss of Sec. 4.2.3.
+// ---------------------------------------------------------------------------
+constexpr int kWGOut = 27 * 55;
+// layout of tr.out (doubles): per level l: [G1 (1485)][G2 (1485)][dots (2)][stats (54)][norm2 (1)]
+constexpr int kTrOutPerLevel = 2 * kWGOut + 2 + 54 + 1;
+
+void free_train(npsolve *h) {
+  auto &t = h->tr;
+  for (int l = 0; l <= kMaxLevels; ++l) {
+    cudaFree(t.gx[l]);
+    cudaFree(t.gx1[l]);
+    t.gx[l] = t.gx1[l] = nullptr;
+  }
+  cudaFree(t.rm);
+  cudaFree(t.tmp);
+  cudaFree(t.tmp2);
+  cudaFree(t.res);
+  cudaFree(t.gz);
+  cudaFree(t.K);
+  cudaFree(t.part);
+  cudaFree(t.out);
+  t.rm = t.tmp = t.tmp2 = t.res = t.gz = t.K = nullptr;
+  t.part = t.out = nullptr;
+  t.cap = 0;
+}
+
+int ensure_train(npsolve *h, Dims d1) {
+  auto &t = h->tr;
+  const long long n = d1.n();
+  if (t.cap >= n) return NPSOLVE_OK;
+  free_train(h);
+  const int L = h->cfg.levels;
+  long long cl = n;
+  for (int l = 1; l <= L; ++l, cl = (cl + 7) / 8) {
+    CK(h, dalloc(&t.gx[l], (size_t)cl));
+    CK(h, dalloc(&t.gx1[l], (size_t)cl));
+  }
+  CK(h, dalloc(&t.rm, (size_t)n));
+  CK(h, dalloc(&t.tmp, (size_t)n));
+  CK(h, dalloc(&t.tmp2, (size_t)n));
+  CK(h, dalloc(&t.res, (size_t)n));
+  CK(h, dalloc(&t.gz, (size_t)n));
+  CK(h, dalloc(&t.K, (size_t)n * 27));
+  CK(h, dalloc(&t.part, (size_t)148 * 4 * kWGOut + (size_t)kRedMaxBlocks * 64));
+  CK(h, dalloc(&t.out, (size_t)(kMaxLevels + 1) * kTrOutPerLevel));
+  t.cap = n;
+  return NPSOLVE_OK;
+}
+
+// Forward of Alg. 2 on r (zeroed off fluid into tr.rm) with every
+// intermediate kept in the workspace; returns z in ws.z.
+int train_forward(npsolve *h, const uint8_t *lab, Dims d1, const float *r, cudaStream_t s) {
+  int st = check_dims(h, d1.nx, d1.ny, d1.nz);
+  if (st) return st;
+  st = ensure_ws(h, d1, 1);
+  if (st) return st;
+  st = ensure_train(h, d1);
+  if (st) return st;
+  st = setup_image(h, lab, d1, s, true);
+  if (st) return st;
+  CK(h, cudaMemcpyAsync(h->ws.h_flag, h->ws.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (h->ws.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
+  launch_mask_copy(lab, d1.n(), r, h->tr.rm, s);
+  run_network(h, lab, d1, h->tr.rm, nullptr, h->ws.z, nullptr, s, true);
+  CK(h, cudaGetLastError());
+  return NPSOLVE_OK;
+}
+
+// Reverse of Alg. 2 for the output cotangent gz (device), after train_forward.
+// Accumulates d<gz, z>/dw (raw blob layout, FP64) into gw; writes
+// d<gz, z>/dr into gr when gr != null.
+int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std::vector<double> &gw, float *gr,
+                   cudaStream_t s) {
+  Workspace &w = h->ws;
+  auto &t = h->tr;
+  const int L = h->cfg.levels;
+  const long long n1 = d1.n();
+  auto lc = [&](int l) { return l == 1 ? nullptr : w.counts[l]; };
+  auto ll = [&](int l) { return l == 1 ? lab : nullptr; };
+  double *out = t.out;
+  auto O = [&](int l) { return out + (size_t)l * kTrOutPerLevel; };
+  // c1, c2 of every level on the host
+  std::vector<double> c12((kMaxLevels + 1) * 2, 0.0);
+  CK(h, cudaMemcpyAsync(c12.data(), w.affc, sizeof(double) * c12.size(), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemsetAsync(out, 0, sizeof(double) * (kMaxLevels + 1) * kTrOutPerLevel, s));
+  CK(h, cudaStreamSynchronize(s));
+  for (int l = 1; l <= L; ++l) {
+    const long long nl = level_dims(d1, l).n();
+    CK(h, cudaMemsetAsync(t.gx[l], 0, sizeof(float) * nl, s));
+    CK(h, cudaMemsetAsync(t.gx1[l], 0, sizeof(float) * nl, s));
+  }
+  launch_axpby(lab, n1, 1.f, gz, 0.f, nullptr, t.gx[1], s);  // output restriction
+  if (L == 1) launch_axpby(nullptr, n1, 1.f, t.gx[1], 0.f, nullptr, t.gx1[1], s);
+  // up pass in reverse: combination, CConv2, interpolation
+  for (int l = 1; l < L; ++l) {
+    const Dims dl = level_dims(d1, l);
+    const long long nl = dl.n();
+    launch_dot2(t.gx[l], w.x1[l], w.x2[l], nl, t.part, O(l) + 2 * kWGOut, s);
+    launch_aff_stats(ll(l), lc(l), dl, 1.0 / pow(8.0, l - 1), t.part, O(l) + 2 * kWGOut + 2, s);
+    launch_axpby(nullptr, nl, (float)c12[2 * l], t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);  // gx1 += c1 gx
+    launch_axpby(nullptr, nl, (float)c12[2 * l + 1], t.gx[l], 0.f, nullptr, t.tmp, s);  // g x2 = c2 gx
+    launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2 + 1, t.K, s);
+    launch_cconv_wgrad(ll(l), lc(l), dl, w.r2[l], t.tmp, t.part, O(l) + kWGOut, s);
+    launch_cconv_transpose(t.K, t.tmp, dl, t.tmp2, s);  // g r2
+    launch_interp_adjoint_add(t.tmp2, level_dims(d1, l + 1), (l + 1 == L) ? t.gx1[L] : t.gx[l + 1], s);
+    h->launches += 11;
+  }
+  // down pass in reverse: CConv1 and pooling
+  for (int l = L; l >= 1; --l) {
+    const Dims dl = level_dims(d1, l);
+    const float *v = l == 1 ? t.rm : w.r1[l];
+    launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2, t.K, s);
+    launch_cconv_wgrad(ll(l), lc(l), dl, v, t.gx1[l], t.part, O(l), s);
+    h->launches += 3;
+    if (l > 1 || gr) {
+      launch_cconv_transpose(t.K, t.gx1[l], dl, t.tmp, s);  // g r1^l
+      h->launches += 1;
+      if (l > 1) {
+        launch_pool_adjoint_add(t.tmp, level_dims(d1, l - 1), t.gx1[l - 1], s);
+        h->launches += 1;
+      } else {
+        launch_axpby(lab, n1, 1.f, t.tmp, 0.f, nullptr, gr, s);  // input padding
+        h->launches += 1;
+      }
+    }
+  }
+  CK(h, cudaGetLastError());
+  std::vector<double> ho((size_t)(kMaxLevels + 1) * kTrOutPerLevel);
+  CK(h, cudaMemcpyAsync(ho.data(), out, sizeof(double) * ho.size(), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  // folded gradients -> raw blob gradients
+  const size_t per = 2 * kCConvParams + 2 * kAffParams;
+  for (int l = 1; l <= L; ++l) {
+    const double sc = 1.0 / pow(8.0, l - 1);
+    const double *Ol = ho.data() + (size_t)l * kTrOutPerLevel;
+    for (int type = 1; type <= (l < L ? 2 : 1); ++type) {
+      const double *G = Ol + (type - 1) * kWGOut;
+      const size_t base = (size_t)(l - 1) * per + (type == 2 ? kCConvParams : 0);
+      for (int a = 0; a < 27; ++a) {
+        for (int lp = 0; lp < 27; ++lp) {
+          const double gf = G[a * 55 + lp], ga = G[a * 55 + 27 + lp];
+          gw[base + (a * 3 + 0) * 27 + lp] += sc * gf;
+          gw[base + (a * 3 + 1) * 27 + lp] += sc * ga;
+          gw[base + (a * 3 + 2) * 27 + lp] += -sc * (gf + ga) + G[a * 55 + 54];
+        }
+        gw[base + 2187 + a] += G[a * 55 + 54];
+      }
+    }
+    if (l < L) {
+      const double *dots = Ol + 2 * kWGOut;
+      const double *S = dots + 2;
+      for (int k = 0; k < 2; ++k) {
+        const size_t base = (size_t)(l - 1) * per + 2 * kCConvParams + (size_t)k * kAffParams;
+        const double gc = dots[k];
+        for (int lp = 0; lp < 27; ++lp) {
+          gw[base + lp] += gc * S[lp];
+          gw[base + 27 + lp] += gc * S[27 + lp];
+          gw[base + 54 + lp] += gc * (1.0 / 27.0 - S[lp] - S[27 + lp]);
+        }
+        gw[base + 81] += gc;
+      }
+    }
+  }
+  return NPSOLVE_OK;
+}
+
+// Loss = || b - A P_net(I, b) || (Sec. 4.2.3) and its weight gradient
+// accumulated into gw (scaled by `weight`).
+int loss_grad_impl(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *loss, std::vector<double> &gw,
+                   double weight, cudaStream_t s) {
+  int st = train_forward(h, lab, d1, b, s);
+  if (st) return st;
+  auto &t = h->tr;
+  const long long n = d1.n();
+  launch_lap(lab, d1, h->ws.z, t.res, s);                      // A z
+  launch_axpby(lab, n, 1.f, t.rm, -1.f, t.res, t.res, s);      // res = b - A z
+  double *nrm = t.out + (size_t)(kMaxLevels + 1) * kTrOutPerLevel - 1;
+  launch_dot2(t.res, t.res, nullptr, n, t.part, nrm - 1, s);   // ||res||^2 (two-slot output)
+  launch_lap(lab, d1, t.res, t.tmp2, s);                       // A res
+  launch_scale_by_inv_norm(lab, n, (float)(-weight), nrm - 1, t.tmp2, t.gz, s);  // gz = -w A res / ||res||
+  h->launches += 7;
+  double r2[2] = {0.0, 0.0};
+  CK(h, cudaMemcpyAsync(r2, nrm - 1, sizeof(r2), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  *loss = sqrt(r2[0]);
+  return train_backward(h, lab, d1, t.gz, gw, nullptr, s);
+}
+
 // Enqueue one NPSDO iteration (Alg. 1 loop body) on stream s.
 void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x, cudaStream_t s) {
   Workspace &w = h->ws;
@@ -862,6 +1064,7 @@ void npsolve_destroy(npsolve_t h) {
   if (!h) return;
   cudaSetDevice(h->device);
   free_ws(h->ws);
+  free_train(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   cudaFree(h->cw);
   cudaFree(h->aw);
@@ -1074,6 +1277,74 @@ int npsolve_get_profile(npsolve_t h, double *ms_host, long long *launches_host) 
     launches_host[i] = h->prof.launches[i];
   }
   return NPSOLVE_OK;
+}
+
+int npsolve_network_vjp(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r, const float *gz,
+                        float *grad_w_host, float *grad_r, void *stream) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!labels || !r || !gz || !grad_w_host) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d1{nx, ny, nz};
+  int st = train_forward(h, labels, d1, r, s);
+  if (st) return st;
+  std::vector<double> gw(h->weights.size(), 0.0);
+  st = train_backward(h, labels, d1, gz, gw, grad_r, s);
+  if (st) return st;
+  for (size_t i = 0; i < gw.size(); ++i) grad_w_host[i] = (float)gw[i];
+  if (grad_r) CK(h, cudaStreamSynchronize(s));
+  return NPSOLVE_OK;
+}
+
+int npsolve_loss_grad(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *b, void *stream,
+                      double *loss, float *grad_w_host) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!labels || !b || !loss) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  CK(h, cudaSetDevice(h->device));
+  std::vector<double> gw(h->weights.size(), 0.0);
+  int st = loss_grad_impl(h, labels, Dims{nx, ny, nz}, b, loss, gw, 1.0, (cudaStream_t)stream);
+  if (st) return st;
+  if (grad_w_host)
+    for (size_t i = 0; i < gw.size(); ++i) grad_w_host[i] = (float)gw[i];
+  return NPSOLVE_OK;
+}
+
+int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, const int *dims, const float *const *b,
+                       float lr, void *stream, double *loss) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (batch < 1 || !labels || !dims || !b || !loss || !(lr > 0.f)) return fail(h, NPSOLVE_BAD_ARG, "bad argument");
+  CK(h, cudaSetDevice(h->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nw = h->weights.size();
+  std::vector<double> gw(nw, 0.0);
+  double total = 0.0;
+  for (int i = 0; i < batch; ++i) {
+    if (!labels[i] || !b[i]) return fail(h, NPSOLVE_BAD_ARG, "null example pointer");
+    double li = 0.0;
+    int st = loss_grad_impl(h, labels[i], Dims{dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]}, b[i], &li, gw,
+                            1.0 / batch, s);
+    if (st) return st;
+    total += li;
+  }
+  // Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the raw weights, FP64 moments
+  auto &t = h->tr;
+  if (t.m.size() != nw) {
+    t.m.assign(nw, 0.0);
+    t.v.assign(nw, 0.0);
+    t.t = 0;
+  }
+  t.t += 1;
+  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+  const double c1 = 1.0 - pow(b1, (double)t.t), c2 = 1.0 - pow(b2, (double)t.t);
+  for (size_t k = 0; k < nw; ++k) {
+    const double g = gw[k];
+    if (!std::isfinite(g)) return fail(h, NPSOLVE_BREAKDOWN, "non-finite gradient");
+    t.m[k] = b1 * t.m[k] + (1.0 - b1) * g;
+    t.v[k] = b2 * t.v[k] + (1.0 - b2) * g * g;
+    h->weights[k] = (float)(h->weights[k] - lr * (t.m[k] / c1) / (sqrt(t.v[k] / c2) + eps));
+  }
+  *loss = total / batch;
+  return upload_weights(h);
 }
 
 int npsolve_selftest_tensor_core(double *max_abs_err) {
