@@ -197,6 +197,17 @@ int npsolve_loss_grad(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz
 int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, const int *dims, const float *const *b,
                        float lr, void *stream, double *loss);
 
+/* Training right-hand sides from Ritz vectors (Sec. 4.2.3): m Lanczos steps
+ * on the masked Laplacian A of the grid from `start` (device, zeroed off
+ * fluid; project out the constant on pure-Neumann components first), with
+ * full reorthogonalisation; the k lowest Ritz vectors; `count` random
+ * normalised combinations of them (coefficients N(0,1) from a 64-bit
+ * Mersenne twister seeded with `seed`) written to out (device, count x n
+ * floats, zero off fluid).  ritz_values_host (may be NULL) receives the k
+ * lowest Ritz values.  2 <= m <= 128, 1 <= k <= m. */
+int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const float *start, int m, int k, int count,
+                        unsigned long long seed, float *out, double *ritz_values_host, void *stream);
+
 /* Optional per-kernel-class timing of solves on a handle.  While profiling
  * is on, npsolve_solve runs one iteration at a time (no CUDA graph) and
  * records a CUDA event pair on the solve's stream around every launch of each

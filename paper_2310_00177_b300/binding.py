@@ -59,6 +59,7 @@ SIGNATURES = {
     "npsolve_network_vjp": ([_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "npsolve_loss_grad": ([_vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_train_step": ([_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, ctypes.POINTER(_d)], _i),
+    "npsolve_lanczos_rhs": ([_vp, _i, _i, _i, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp, _vp, _vp], _i),
     "npsolve_profile_count": ([], _i),
     "npsolve_launch_count": ([_vp], ctypes.c_longlong),
     "npsolve_mixed_cells": ([_vp, _i], ctypes.c_longlong),
@@ -362,3 +363,18 @@ class NetworkFunction:
     @staticmethod
     def apply(weights, labels, r, solver):
         return NetworkFunction.get().apply(weights, labels, r, solver)
+
+
+def lanczos_rhs(labels, start, m=48, k=32, count=4, seed=0):
+    """Random normalised combinations of the k lowest Ritz vectors of A from m
+    Lanczos steps (device tensors); returns (rhs [count, *shape], ritz values)."""
+    import torch
+
+    nx, ny, nz = _dims(labels)
+    out = torch.empty((count,) + tuple(labels.shape), dtype=torch.float32, device=labels.device)
+    vals = np.zeros(k, np.float64)
+    _check(load_library().npsolve_lanczos_rhs(_ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                              _ptr(start, torch.float32, "start"), int(m), int(k), int(count),
+                                              int(seed), _ptr(out, torch.float32, "out"),
+                                              vals.ctypes.data_as(_vp), _stream()))
+    return out, vals

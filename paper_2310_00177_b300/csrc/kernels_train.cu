@@ -366,3 +366,64 @@ void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, cons
 int wgrad_outputs() { return kWG; }
 
 }  // namespace nps
+
+namespace nps {
+
+// ---------------------------------------------------------------------------
+// Lanczos helpers (training right-hand sides): dot products of a vector with
+// the m columns of a basis, and linear combinations of basis columns.
+// ---------------------------------------------------------------------------
+// out[j] partials: sum_p Q[j][p] w[p] for j < m (m <= 128), block partials.
+__global__ void __launch_bounds__(256) k_multidot(const float *__restrict__ Q, long long n, int m,
+                                                  const float *__restrict__ w, double *__restrict__ part) {
+  extern __shared__ double sred[];  // [8 warps][m]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = 0; j < m; ++j) {
+    double acc = 0.0;
+    const float *q = Q + (size_t)j * n;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+      acc += (double)q[p] * w[p];
+    acc = warp_sum(acc);
+    if (lane == 0) sred[warp * m + j] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double t = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) t += sred[w8 * m + j];
+    part[(size_t)blockIdx.x * m + j] = t;
+  }
+}
+
+__global__ void k_multidot_final(const double *__restrict__ part, int nblocks, int m, double *__restrict__ out) {
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += part[(size_t)b * m + j];
+    out[j] = t;
+  }
+}
+
+// out[p] = beta * out[p] + sum_j c[j] Q[j][p]  (c in device memory, FP64).
+__global__ void k_combine_basis(const float *__restrict__ Q, long long n, int m, const double *__restrict__ c,
+                                float beta, float *__restrict__ out) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    double acc = beta != 0.f ? (double)beta * out[p] : 0.0;
+    for (int j = 0; j < m; ++j) acc += c[j] * (double)Q[(size_t)j * n + p];
+    out[p] = (float)acc;
+  }
+}
+
+void launch_multidot(const float *Q, long long n, int m, const float *w, double *part, double *out, cudaStream_t s) {
+  long long nb = (n + 255) / 256;
+  if (nb > 148 * 4) nb = 148 * 4;
+  k_multidot<<<(int)nb, 256, sizeof(double) * 8 * m, s>>>(Q, n, m, w, part);
+  k_multidot_final<<<1, 128, 0, s>>>(part, (int)nb, m, out);
+}
+
+void launch_combine_basis(const float *Q, long long n, int m, const double *c, float beta, float *out,
+                          cudaStream_t s) {
+  long long nb = (n + 255) / 256;
+  if (nb > 148 * 16) nb = 148 * 16;
+  k_combine_basis<<<(int)nb, 256, 0, s>>>(Q, n, m, c, beta, out);
+}
+
+}  // namespace nps

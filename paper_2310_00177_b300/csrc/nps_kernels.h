@@ -99,6 +99,10 @@ void launch_axpby(const uint8_t *lab, long long n, float alpha, const float *a, 
 void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, const double *norm2, const float *a,
                               float *out, cudaStream_t s);
 
+void launch_multidot(const float *Q, long long n, int m, const float *w, double *part, double *out, cudaStream_t s);
+void launch_combine_basis(const float *Q, long long n, int m, const double *c, float beta, float *out,
+                          cudaStream_t s);
+
 // kernels_march.cu
 void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
                         const float *v, const float *coarse, const float *vscale, int mask_input, float *out,

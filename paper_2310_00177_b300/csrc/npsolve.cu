@@ -20,6 +20,8 @@
 #include <string.h>
 
 #include <cmath>
+#include <random>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -1345,6 +1347,141 @@ int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, con
   }
   *loss = total / batch;
   return upload_weights(h);
+}
+
+// Eigen-decomposition of a small dense symmetric matrix by cyclic Jacobi
+// rotations (A is overwritten; V receives the eigenvectors as columns).
+static void jacobi_eigen(std::vector<double> &A, int m, std::vector<double> &V) {
+  V.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[(size_t)p * m + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+        // rotation angle that zeroes A[p][q]: tan(2 phi) = 2 apq / (aqq - app)
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+          A[(size_t)k * m + p] = c * akp - sn * akq;
+          A[(size_t)k * m + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+          A[(size_t)p * m + k] = c * apk - sn * aqk;
+          A[(size_t)q * m + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+          V[(size_t)k * m + p] = c * vkp - sn * vkq;
+          V[(size_t)k * m + q] = sn * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const float *start, int m, int k, int count,
+                        unsigned long long seed, float *out, double *ritz_values_host, void *stream) {
+  if (!labels || !start || !out || m < 2 || m > 128 || k < 1 || k > m || count < 0)
+    return fail(nullptr, NPSOLVE_BAD_ARG, "bad argument");
+  if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
+    return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d{nx, ny, nz};
+  const long long n = d.n();
+  float *Q = nullptr, *wv = nullptr;
+  double *part = nullptr, *dres = nullptr, *coef = nullptr;
+  CK(nullptr, cudaMalloc(&Q, sizeof(float) * (size_t)n * (m + 1)));
+  CK(nullptr, cudaMalloc(&wv, sizeof(float) * (size_t)n));
+  CK(nullptr, cudaMalloc(&part, sizeof(double) * 148 * 4 * (m + 2)));
+  CK(nullptr, cudaMalloc(&dres, sizeof(double) * (m + 2)));
+  CK(nullptr, cudaMalloc(&coef, sizeof(double) * (m + 2)));
+  std::vector<double> alpha(m, 0.0), beta(m, 0.0), hc(m + 2, 0.0);
+  int ret = NPSOLVE_OK;
+  // q_1 = start / ||start|| (zero off fluid)
+  launch_mask_copy(labels, n, start, wv, s);
+  launch_multidot(wv, n, 1, wv, part, dres, s);
+  cudaMemcpyAsync(hc.data(), dres, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (!(hc[0] > 0.0)) ret = fail(nullptr, NPSOLVE_BAD_ARG, "start vector is zero on the fluid cells");
+  int steps = 0;
+  if (!ret) {
+    hc[0] = 1.0 / sqrt(hc[0]);
+    cudaMemcpyAsync(coef, hc.data(), sizeof(double), cudaMemcpyHostToDevice, s);
+    launch_combine_basis(wv, n, 1, coef, 0.f, Q, s);
+    for (int j = 0; j < m; ++j) {
+      float *qj = Q + (size_t)j * n;
+      launch_lap(labels, d, qj, wv, s);  // w = A q_j
+      // full reorthogonalisation, twice: w -= Q (Q^T w)
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_multidot(Q, n, j + 1, wv, part, dres, s);
+        cudaMemcpyAsync(hc.data(), dres, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (pass == 0) alpha[j] = hc[j];
+        else alpha[j] += hc[j];
+        for (int i = 0; i <= j; ++i) hc[i] = -hc[i];
+        cudaMemcpyAsync(coef, hc.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s);
+        launch_combine_basis(Q, n, j + 1, coef, 1.f, wv, s);
+      }
+      launch_multidot(wv, n, 1, wv, part, dres, s);
+      cudaMemcpyAsync(hc.data(), dres, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      steps = j + 1;
+      beta[j] = sqrt(fmax(hc[0], 0.0));
+      if (j + 1 == m || beta[j] < 1e-10) break;
+      hc[0] = 1.0 / beta[j];
+      cudaMemcpyAsync(coef, hc.data(), sizeof(double), cudaMemcpyHostToDevice, s);
+      launch_combine_basis(wv, n, 1, coef, 0.f, Q + (size_t)(j + 1) * n, s);
+    }
+  }
+  if (!ret) {
+    // Ritz pairs of T = tridiag(beta, alpha, beta)
+    const int mm = steps;
+    std::vector<double> T((size_t)mm * mm, 0.0), V;
+    for (int i = 0; i < mm; ++i) {
+      T[(size_t)i * mm + i] = alpha[i];
+      if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[i];
+    }
+    jacobi_eigen(T, mm, V);
+    std::vector<int> order(mm);
+    for (int i = 0; i < mm; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return T[(size_t)a * mm + a] < T[(size_t)b * mm + b]; });
+    const int kk = k < mm ? k : mm;
+    if (ritz_values_host)
+      for (int i = 0; i < kk; ++i) ritz_values_host[i] = T[(size_t)order[i] * mm + order[i]];
+    // count random normalised combinations b = Q Y c, c ~ N(0, 1)
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (int c = 0; c < count && !ret; ++c) {
+      std::vector<double> cc(kk), qc(mm, 0.0);
+      double nrm = 0.0;
+      for (int i = 0; i < kk; ++i) {
+        cc[i] = nd(rng);
+        nrm += cc[i] * cc[i];
+      }
+      nrm = sqrt(nrm);  // Ritz vectors are orthonormal: ||Q Y c|| = ||c||
+      for (int i = 0; i < kk; ++i)
+        for (int r = 0; r < mm; ++r) qc[r] += V[(size_t)r * mm + order[i]] * cc[i] / nrm;
+      cudaMemcpyAsync(coef, qc.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, s);
+      launch_combine_basis(Q, n, mm, coef, 0.f, out + (size_t)c * n, s);
+      cudaStreamSynchronize(s);
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(Q);
+  cudaFree(wv);
+  cudaFree(part);
+  cudaFree(dres);
+  cudaFree(coef);
+  if (!ret && e != cudaSuccess) ret = fail(nullptr, NPSOLVE_CUDA_ERROR, "lanczos: %s", cudaGetErrorString(e));
+  return ret;
 }
 
 int npsolve_selftest_tensor_core(double *max_abs_err) {

@@ -131,3 +131,26 @@ def test_train_step_reduces_the_loss():
     assert losses[-1] < 0.9 * losses[0]
     assert all(np.isfinite(losses))
     s.close()
+
+
+def test_lanczos_ritz_values_match_dense_eigenvalues():
+    # on a small grid the lowest Ritz values of a long Lanczos run converge
+    # to the lowest eigenvalues of the reduced matrix (dense FP64 eigvalsh)
+    b = _b()
+    lab = synth.pool_scene(8, 3)
+    fl = (lab == 1).ravel()
+    n = lab.size
+    M = np.zeros((n, n))
+    e = np.zeros(n)
+    for j in range(n):
+        e[j] = 1.0
+        M[:, j] = oracle.lap_apply(lab, e.reshape(lab.shape)).ravel()
+        e[j] = 0.0
+    ev = np.linalg.eigvalsh(M[np.ix_(fl, fl)])
+    start = synth.rhs_normal(lab, 4).astype(np.float32)
+    rhs, vals = b.lanczos_rhs(_dev(lab, torch.uint8), _dev(start, torch.float32), m=min(120, int(fl.sum())), k=4,
+                              count=3, seed=5)
+    np.testing.assert_allclose(vals, ev[:4], rtol=1e-4)
+    r = rhs.cpu().numpy()
+    assert np.allclose(np.linalg.norm(r.reshape(3, -1), axis=1), 1.0, atol=1e-4)
+    assert not r[:, lab != 1].any()
