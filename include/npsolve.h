@@ -208,6 +208,25 @@ int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, con
 int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const float *start, int m, int k, int count,
                         unsigned long long seed, float *out, double *ritz_values_host, void *stream);
 
+/* npsolve_true_residual without any device allocation (the paper has no
+ * counterpart; this is a library service).  npsolve_true_residual allocates
+ * its reduction scratch on every call; callers that must not allocate device
+ * memory where they check a solution -- for example a simulation loop that
+ * reserves all GPU memory at start-up and forbids allocation inside a frame,
+ * or a plug-in whose host application owns the device memory -- use this
+ * variant, which keeps the scratch in a fixed device array inside the library.
+ * Same arguments and result as npsolve_true_residual (FP64 ||b - A x|| / ||b||
+ * over the fluid cells; labels, b, x device arrays; result on the host).
+ * Limits: grids of at most 16,777,216 cells (one 256^3 grid; the array is
+ * 128 KB per device, held until the process exits); larger grids return
+ * NPSOLVE_BAD_DIMS with a message (npsolve_last_error(NULL)).  All calls on a
+ * device share the array and overwrite what they use, so nothing needs
+ * clearing, but calls that overlap on the GPU (unordered streams) race on
+ * it.  The first call on a device looks the array up with that device
+ * current; make it before any stream capture. */
+int npsolve_true_residual_noalloc(const uint8_t *labels, int nx, int ny, int nz, const float *b, const double *x,
+                                  double *rel_residual, void *stream);
+
 /* Optional per-kernel-class timing of solves on a handle.  While profiling
  * is on, npsolve_solve runs one iteration at a time (no CUDA graph) and
  * records a CUDA event pair on the solve's stream around every launch of each

@@ -60,6 +60,7 @@ SIGNATURES = {
     "npsolve_loss_grad": ([_vp, _vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_train_step": ([_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, ctypes.POINTER(_d)], _i),
     "npsolve_lanczos_rhs": ([_vp, _i, _i, _i, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp, _vp, _vp], _i),
+    "npsolve_true_residual_noalloc": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_profile_count": ([], _i),
     "npsolve_launch_count": ([_vp], ctypes.c_longlong),
     "npsolve_mixed_cells": ([_vp, _i], ctypes.c_longlong),

@@ -8,6 +8,9 @@
 
 namespace nps {
 
+// npsolve.cu: the per-thread message returned by npsolve_last_error(NULL).
+void set_thread_error(const char *msg);
+
 // kernels_vec.cu
 void launch_lap(const uint8_t *lab, Dims dm, const float *d, float *q, cudaStream_t s);
 void launch_check_labels(const uint8_t *lab, long long n, unsigned int *bad, cudaStream_t s);

@@ -986,6 +986,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
 
 }  // namespace
 
+namespace nps {
+void set_thread_error(const char *msg) { g_thread_error = msg; }
+}  // namespace nps
+
 extern "C" {
 
 size_t npsolve_weight_count(int levels) { return weight_count(levels); }
