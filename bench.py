@@ -151,10 +151,15 @@ def cpu_oracle_iteration_ms(lab, rhs, w, iters_sample=1):
     return (time.perf_counter() - t) * 1e3 / iters_sample
 
 
-def oracle_iterations(weights_desc):
-    if os.path.exists(ORACLE_ITERS_FILE):
+def oracle_iterations(n):
+    """The FP64 oracle's own iteration count for this problem, stored by
+    oracle/count_iterations.py for the current weights file."""
+    import hashlib
+
+    if os.path.exists(ORACLE_ITERS_FILE) and os.path.exists(WEIGHTS_FILE):
         d = json.load(open(ORACLE_ITERS_FILE))
-        if d.get("weights") == weights_desc:
+        wid = hashlib.sha256(open(WEIGHTS_FILE, "rb").read()).hexdigest()[:16]
+        if d.get("weights_sha256_16") == wid and d.get("n") == n:
             return int(d["iters"]), "oracle FP64 solve of this problem (" + os.path.basename(ORACLE_ITERS_FILE) + ")"
     return None, None
 
@@ -170,7 +175,7 @@ def run_reference(args, rank, world):
         cpu_oracle_iteration_ms(lab, rhs, w)
     times = [cpu_oracle_iteration_ms(lab, rhs, w) for _ in range(args.steps)]
     per_it = float(np.mean(times))
-    iters, src = oracle_iterations(wdesc)
+    iters, src = oracle_iterations(args.n)
     if iters is None:
         print(json.dumps({"impl": "reference", "unavailable": "no stored oracle iteration count for these weights "
                           "(run oracle/count_iterations.py)"}))

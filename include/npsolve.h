@@ -227,6 +227,42 @@ int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const flo
 int npsolve_true_residual_noalloc(const uint8_t *labels, int nx, int ny, int nz, const float *b, const double *x,
                                   double *rel_residual, void *stream);
 
+/* Continuous-batching solve server (the serving pattern of the deployment
+ * setting; the paper has no serving layer).  Requests are queued as they
+ * arrive and admitted to solver slots as slots and HBM budget become free;
+ * each slot owns a solver handle (workspace, Krylov state and image pyramid
+ * on the device), a non-blocking stream and a worker thread, so solves of
+ * different sizes overlap on the GPU.  A slot's reservation against the
+ * budget is its measured device footprint (an upper estimate of 256 bytes
+ * per cell + 64 MB before its first solve at a size); idle slots keep their
+ * workspace and its reservation.  Admission is first-fit in arrival order.
+ * Results are identical to a solve of the same request on its own.
+ *   npsolve_server_create   config and weights as npsolve_create; hbm_budget_bytes > 0;
+ *                           1 <= max_active <= 64 concurrent solves
+ *   npsolve_server_submit   queues the solve of labels_host / b_host (host memory; pinned
+ *                           memory gives the fastest copies) with x written to x_host
+ *                           (host FP64, may be NULL); the three buffers are the caller's
+ *                           and must stay valid until the request's result has been read;
+ *                           submit and result allocate nothing.  Returns the request id;
+ *                           a request larger than the whole budget fails with NPSOLVE_OOM
+ *   npsolve_server_poll     ids of requests finished since the last poll (non-blocking)
+ *   npsolve_server_result   iterations, FP64 true relative residual, the solve's status,
+ *                           the time spent queued and in service (ms); releases the request
+ *   npsolve_server_stats    reserved and peak reserved bytes, active and queued requests
+ *   npsolve_server_destroy  waits for running solves, drops queued ones, frees everything */
+typedef struct npsolve_server *npsolve_server_t;
+int npsolve_server_create(const npsolve_config *cfg, const float *weights_host, size_t n_weights,
+                          size_t hbm_budget_bytes, int max_active, npsolve_server_t *out);
+int npsolve_server_submit(npsolve_server_t s, const uint8_t *labels_host, int nx, int ny, int nz, const float *b_host,
+                          double *x_host, double tol, int max_iter, long long *request_id);
+int npsolve_server_poll(npsolve_server_t s, long long *ids, int cap, int *count);
+int npsolve_server_result(npsolve_server_t s, long long id, int *iters, double *rel_residual, int *solve_status,
+                          double *queue_ms, double *service_ms);
+int npsolve_server_stats(npsolve_server_t s, size_t *reserved_bytes, size_t *peak_reserved_bytes, int *active,
+                         int *queued);
+void npsolve_server_destroy(npsolve_server_t s);
+const char *npsolve_server_last_error(npsolve_server_t s);
+
 /* Optional per-kernel-class timing of solves on a handle.  While profiling
  * is on, npsolve_solve runs one iteration at a time (no CUDA graph) and
  * records a CUDA event pair on the solve's stream around every launch of each
@@ -240,6 +276,9 @@ int npsolve_profile_count(void);
 /* Number of CUDA kernels this handle has enqueued since it was created
  * (solves, network evaluations; graph replays count their kernels). */
 long long npsolve_launch_count(npsolve_t h);
+/* Device bytes held by the handle's solve workspace (Krylov state, pyramid,
+ * network intermediates, kernel cache, staging buffers). */
+size_t npsolve_workspace_bytes(npsolve_t h);
 /* Cells of level `level` whose 3x3x3 image window was not uniform in the last
  * setup of the cached path (their kernels are generated and cached; all other
  * cells use the closed form of a uniform window); -1 when not available. */

@@ -61,6 +61,17 @@ SIGNATURES = {
     "npsolve_train_step": ([_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, ctypes.POINTER(_d)], _i),
     "npsolve_lanczos_rhs": ([_vp, _i, _i, _i, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp, _vp, _vp], _i),
     "npsolve_true_residual_noalloc": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
+    "npsolve_workspace_bytes": ([_vp], ctypes.c_size_t),
+    "npsolve_server_create": ([ctypes.POINTER(_Config), _vp, ctypes.c_size_t, ctypes.c_size_t, _i,
+                               ctypes.POINTER(_vp)], _i),
+    "npsolve_server_submit": ([_vp, _vp, _i, _i, _i, _vp, _vp, _d, _i, ctypes.POINTER(ctypes.c_longlong)], _i),
+    "npsolve_server_poll": ([_vp, _vp, _i, ctypes.POINTER(_i)], _i),
+    "npsolve_server_result": ([_vp, ctypes.c_longlong, ctypes.POINTER(_i), ctypes.POINTER(_d),
+                               ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_d)], _i),
+    "npsolve_server_stats": ([_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "npsolve_server_destroy": ([_vp], None),
+    "npsolve_server_last_error": ([_vp], ctypes.c_char_p),
     "npsolve_profile_count": ([], _i),
     "npsolve_launch_count": ([_vp], ctypes.c_longlong),
     "npsolve_mixed_cells": ([_vp, _i], ctypes.c_longlong),
@@ -379,3 +390,75 @@ def lanczos_rhs(labels, start, m=48, k=32, count=4, seed=0):
                                               int(seed), _ptr(out, torch.float32, "out"),
                                               vals.ctypes.data_as(_vp), _stream()))
     return out, vals
+
+
+class Server:
+    """Continuous-batching solve server (npsolve_server_*): submit host arrays,
+    poll for finished ids, fetch results."""
+
+    def __init__(self, weights, levels=4, n_ortho=2, precision=BF16, residual_mode=RECURRENCE,
+                 kernel_path=PATH_CACHED, hbm_budget_bytes=150 << 30, max_active=16):
+        lib = load_library()
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
+        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path)
+        h = ctypes.c_void_p()
+        st = lib.npsolve_server_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, int(hbm_budget_bytes),
+                                       int(max_active), ctypes.byref(h))
+        if st != OK:
+            raise NpsolveError(st, lib.npsolve_last_error(None).decode())
+        self._h = h
+        self.levels = levels
+        self._alive = {}
+
+    def _check(self, st):
+        if st != OK:
+            raise NpsolveError(st, load_library().npsolve_server_last_error(self._h).decode())
+
+    def submit(self, labels, b, x=None, tol=1e-6, max_iter=1000):
+        """Queue a solve; labels (uint8), b (float32) and x (float64 output, or
+        None) are host arrays kept alive by the server object until the result
+        is read (pinned arrays give the fastest copies)."""
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        if x is not None:
+            assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"] and x.shape == labels.shape
+        nz, ny, nx = labels.shape
+        rid = ctypes.c_longlong(-1)
+        self._check(load_library().npsolve_server_submit(
+            self._h, labels.ctypes.data_as(_vp), nx, ny, nz, b.ctypes.data_as(_vp),
+            x.ctypes.data_as(_vp) if x is not None else None, float(tol), int(max_iter), ctypes.byref(rid)))
+        self._alive[rid.value] = (labels, b, x)
+        return rid.value
+
+    def poll(self, cap=1024):
+        ids = np.zeros(cap, np.int64)
+        cnt = ctypes.c_int(0)
+        self._check(load_library().npsolve_server_poll(self._h, ids.ctypes.data_as(_vp), cap, ctypes.byref(cnt)))
+        return [int(v) for v in ids[:cnt.value]]
+
+    def result(self, rid):
+        """(x or None, iters, rel_residual, status, queue_ms, service_ms)."""
+        it, st = ctypes.c_int(0), ctypes.c_int(0)
+        rr, qm, sm = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        self._check(load_library().npsolve_server_result(self._h, int(rid), ctypes.byref(it), ctypes.byref(rr),
+                                                         ctypes.byref(st), ctypes.byref(qm), ctypes.byref(sm)))
+        _, _, x = self._alive.pop(int(rid), (None, None, None))
+        return x, it.value, rr.value, st.value, qm.value, sm.value
+
+    def stats(self):
+        r, p = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        a, q = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(load_library().npsolve_server_stats(self._h, ctypes.byref(r), ctypes.byref(p), ctypes.byref(a),
+                                                        ctypes.byref(q)))
+        return {"reserved": r.value, "peak_reserved": p.value, "active": a.value, "queued": q.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().npsolve_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

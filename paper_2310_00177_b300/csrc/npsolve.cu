@@ -48,6 +48,7 @@ size_t weight_count(int L) {
 struct Workspace {
   Dims dims{0, 0, 0};
   long long cap = 0;  // cells of level 1 the buffers were sized for
+  size_t bytes = 0;   // device bytes held by this workspace
   float *r = nullptr, *z = nullptr, *dring = nullptr, *qring = nullptr;
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
@@ -198,9 +199,14 @@ void prof_collect(npsolve *h) {
   h->prof.cls.clear();
 }
 
+// cudaMalloc of `count` elements (+256 bytes of slack), adding the bytes to
+// *counter (the workspace's footprint, used for HBM-budget admission).
 template <class T>
-cudaError_t dalloc(T **p, size_t count) {
-  return cudaMalloc((void **)p, count * sizeof(T) + 256);
+cudaError_t dalloc(size_t *counter, T **p, size_t count) {
+  const size_t bytes = count * sizeof(T) + 256;
+  const cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e == cudaSuccess && counter) *counter += bytes;
+  return e;
 }
 
 void free_ws(Workspace &w) {
@@ -263,34 +269,34 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     free_ws(w);
     const long long cap = n;
     const int R = kRing;
-    CK(h, dalloc(&w.r, cap));
-    CK(h, dalloc(&w.z, cap));
-    CK(h, dalloc(&w.dring, cap * R));
-    CK(h, dalloc(&w.qring, cap * R));
+    CK(h, dalloc(&w.bytes, &w.r, cap));
+    CK(h, dalloc(&w.bytes, &w.z, cap));
+    CK(h, dalloc(&w.bytes, &w.dring, cap * R));
+    CK(h, dalloc(&w.bytes, &w.qring, cap * R));
     long long cl = cap;
     for (int l = 1; l <= L; ++l, cl = (cl + 7) / 8) {
-      CK(h, dalloc(&w.x1[l], cl));
+      CK(h, dalloc(&w.bytes, &w.x1[l], cl));
       if (l >= 2) {
-        CK(h, dalloc(&w.r1[l], cl));
-        CK(h, dalloc(&w.counts[l], cl));
+        CK(h, dalloc(&w.bytes, &w.r1[l], cl));
+        CK(h, dalloc(&w.bytes, &w.counts[l], cl));
       }
       if (l < L) {
-        CK(h, dalloc(&w.r2[l], cl));
-        CK(h, dalloc(&w.x2[l], cl));
-        if (l >= 2) CK(h, dalloc(&w.xc[l], cl));
+        CK(h, dalloc(&w.bytes, &w.r2[l], cl));
+        CK(h, dalloc(&w.bytes, &w.x2[l], cl));
+        if (l >= 2) CK(h, dalloc(&w.bytes, &w.xc[l], cl));
       }
     }
-    CK(h, dalloc(&w.part, (size_t)kRedMaxBlocks * kMaxPartials));
-    CK(h, dalloc(&w.affc, (size_t)(kMaxLevels + 1) * 2));
-    CK(h, dalloc(&w.relres, 2));
-    CK(h, dalloc(&w.st, 1));
-    CK(h, dalloc(&w.tickets, 8));
-    CK(h, dalloc(&w.ktotal, kMaxLevels + 1));
+    CK(h, dalloc(&w.bytes, &w.part, (size_t)kRedMaxBlocks * kMaxPartials));
+    CK(h, dalloc(&w.bytes, &w.affc, (size_t)(kMaxLevels + 1) * 2));
+    CK(h, dalloc(&w.bytes, &w.relres, 2));
+    CK(h, dalloc(&w.bytes, &w.st, 1));
+    CK(h, dalloc(&w.bytes, &w.tickets, 8));
+    CK(h, dalloc(&w.bytes, &w.ktotal, kMaxLevels + 1));
     CK(h, cudaHostAlloc((void **)&w.h_ktotal, sizeof(unsigned) * (kMaxLevels + 1), cudaHostAllocDefault));
     CK(h, cudaMemset(w.tickets, 0, 8 * sizeof(unsigned)));
     CK(h, cudaMalloc(&w.pcg_st, pcg_state_bytes()));
-    CK(h, dalloc(&w.bad, 1));
-    CK(h, dalloc(&w.reopened, 1));
+    CK(h, dalloc(&w.bytes, &w.bad, 1));
+    CK(h, dalloc(&w.bytes, &w.reopened, 1));
     CK(h, cudaHostAlloc((void **)&w.h_st, sizeof(SolveState) * 2, cudaHostAllocDefault));
     CK(h, cudaHostAlloc((void **)&w.h_flag, sizeof(int) * 8, cudaHostAllocDefault));
     for (int i = 0; i < 2; ++i) CK(h, cudaEventCreateWithFlags(&w.ev[i], cudaEventDisableTiming));
@@ -299,9 +305,10 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
   if (hist_cap > w.hist_cap) {
     if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old history buffer
     w.graph = nullptr;
+    if (w.hist) w.bytes -= (size_t)w.hist_cap * sizeof(double) + 256;
     cudaFree(w.hist);
     w.hist = nullptr;
-    CK(h, dalloc(&w.hist, (size_t)hist_cap));
+    CK(h, dalloc(&w.bytes, &w.hist, (size_t)hist_cap));
     w.hist_cap = hist_cap;
   }
   w.dims = d;
@@ -567,11 +574,12 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
         if (w.graph) cudaGraphExecDestroy(w.graph);
         w.graph = nullptr;
         CK(h, cudaStreamSynchronize(s));
+        if (w.kmask[l]) w.bytes -= 2 * ((size_t)w.kcols[l] * sizeof(uint32_t) + 256);
         cudaFree(w.kmask[l]);
         cudaFree(w.koff[l]);
         w.kmask[l] = w.koff[l] = nullptr;
-        CK(h, dalloc(&w.kmask[l], (size_t)nc));
-        CK(h, dalloc(&w.koff[l], (size_t)nc));
+        CK(h, dalloc(&w.bytes, &w.kmask[l], (size_t)nc));
+        CK(h, dalloc(&w.bytes, &w.koff[l], (size_t)nc));
         w.kcols[l] = nc;
       }
     }
@@ -591,10 +599,11 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
           if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old cache buffer
           w.graph = nullptr;
           CK(h, cudaStreamSynchronize(s));
+          if (w.kcache[idx]) w.bytes -= w.kcap[idx] * cached_entry_bytes(bf16) + 256;
           cudaFree(w.kcache[idx]);
           w.kcache[idx] = nullptr;
           const size_t cap = need + need / 4;
-          CK(h, cudaMalloc(&w.kcache[idx], cap * cached_entry_bytes(true) * 2));  // room for either form
+          CK(h, dalloc(&w.bytes, (uint8_t **)&w.kcache[idx], cap * cached_entry_bytes(bf16)));
           w.kcap[idx] = cap;
         }
         launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
@@ -644,17 +653,17 @@ int ensure_train(npsolve *h, Dims d1) {
   const int L = h->cfg.levels;
   long long cl = n;
   for (int l = 1; l <= L; ++l, cl = (cl + 7) / 8) {
-    CK(h, dalloc(&t.gx[l], (size_t)cl));
-    CK(h, dalloc(&t.gx1[l], (size_t)cl));
+    CK(h, dalloc(nullptr, &t.gx[l], (size_t)cl));
+    CK(h, dalloc(nullptr, &t.gx1[l], (size_t)cl));
   }
-  CK(h, dalloc(&t.rm, (size_t)n));
-  CK(h, dalloc(&t.tmp, (size_t)n));
-  CK(h, dalloc(&t.tmp2, (size_t)n));
-  CK(h, dalloc(&t.res, (size_t)n));
-  CK(h, dalloc(&t.gz, (size_t)n));
-  CK(h, dalloc(&t.K, (size_t)n * 27));
-  CK(h, dalloc(&t.part, (size_t)148 * 4 * kWGOut + (size_t)kRedMaxBlocks * 64));
-  CK(h, dalloc(&t.out, (size_t)(kMaxLevels + 1) * kTrOutPerLevel));
+  CK(h, dalloc(nullptr, &t.rm, (size_t)n));
+  CK(h, dalloc(nullptr, &t.tmp, (size_t)n));
+  CK(h, dalloc(nullptr, &t.tmp2, (size_t)n));
+  CK(h, dalloc(nullptr, &t.res, (size_t)n));
+  CK(h, dalloc(nullptr, &t.gz, (size_t)n));
+  CK(h, dalloc(nullptr, &t.K, (size_t)n * 27));
+  CK(h, dalloc(nullptr, &t.part, (size_t)148 * 4 * kWGOut + (size_t)kRedMaxBlocks * 64));
+  CK(h, dalloc(nullptr, &t.out, (size_t)(kMaxLevels + 1) * kTrOutPerLevel));
   t.cap = n;
   return NPSOLVE_OK;
 }
@@ -1102,9 +1111,9 @@ int npsolve_solve_host(npsolve_t h, const uint8_t *labels_host, int nx, int ny, 
   Workspace &w = h->ws;
   const size_t n = (size_t)nx * ny * nz;
   if (!w.stage_lab) {  // staging buffers live as long as the workspace
-    CK(h, dalloc(&w.stage_lab, (size_t)w.cap));
-    CK(h, dalloc(&w.stage_b, (size_t)w.cap));
-    CK(h, dalloc(&w.stage_x, (size_t)w.cap));
+    CK(h, dalloc(&w.bytes, &w.stage_lab, (size_t)w.cap));
+    CK(h, dalloc(&w.bytes, &w.stage_b, (size_t)w.cap));
+    CK(h, dalloc(&w.bytes, &w.stage_x, (size_t)w.cap));
   }
   CK(h, cudaMemcpyAsync(w.stage_lab, labels_host, n, cudaMemcpyHostToDevice, s));
   CK(h, cudaMemcpyAsync(w.stage_b, b_host, n * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -1255,6 +1264,8 @@ int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const floa
 }
 
 long long npsolve_launch_count(npsolve_t h) { return h ? h->launches : 0; }
+
+size_t npsolve_workspace_bytes(npsolve_t h) { return h ? h->ws.bytes : 0; }
 
 long long npsolve_mixed_cells(npsolve_t h, int level) {
   if (!h || level < 1 || level > h->cfg.levels || !cached_path(h) || !h->ws.h_ktotal) return -1;
