@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(" ".join(cmd), flush=True)
         subprocess.check_call(cmd)
         objs.append(obj)
-    cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lcuda"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)

@@ -70,17 +70,21 @@ void launch_cconv_umma(int nsplit, const uint8_t *lab, const ushort2 *counts, Di
                        int *err, int num_sms, cudaStream_t s);
 void launch_umma_selftest(float *d_out, float *d_ref, int *err, cudaStream_t s);
 
-// kernels_cached.cu
-long long cached_columns(Dims d);
-void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t *mask, uint32_t *offset,
-                     unsigned *total, cudaStream_t s);
-void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w,
-                     const uint32_t *mask, const uint32_t *offset, void *cache, cudaStream_t s);
-int cached_entry_bytes(bool bf16);
-void launch_cconv_cached(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims dm, const float *uni_host,
-                         const uint32_t *mask, const uint32_t *offset, const void *cache, const float *v,
-                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12,
-                         const SolveState *st, int num_sms, cudaStream_t s);
+// kernels_cached.cu: per-solve classification and kernel cache, streamed CConv
+bool stream_shape_ok(Dims d);          // the TMA boxes need rows of a multiple of 16 bytes
+long long stream_desc_count(Dims d);   // plane descriptors of a level (tiles x nz)
+size_t stream_desc_bytes();            // bytes of one plane descriptor
+int cached_entry_bytes(bool bf16);     // bytes of one cached kernel
+// totals[0] += cache entries (blocks padded to 4), totals[1] += mixed cells
+void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
+                     int num_sms, cudaStream_t s);
+void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
+                     const void *desc, void *cache0, void *cache1, int num_sms, cudaStream_t s);
+// kfix: the 81 constants K^S, K^F, K^A of the pure windows; returns -1 if a
+// tensor map cannot be encoded
+int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
+                        const float *vscale, float *out, float *pooled, const float *x1, const double *c12,
+                        const SolveState *st, int *err, int num_sms, cudaStream_t s);
 void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
 
 // kernels_train.cu
@@ -109,6 +113,7 @@ void launch_combine_basis(const float *Q, long long n, int m, const double *c, f
 // kernels_march.cu
 void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
                         const float *v, const float *coarse, const float *vscale, int mask_input, float *out,
-                        float *pooled, const SolveState *st, int *err, int num_sms, cudaStream_t s);
+                        float *pooled, const SolveState *st, int *err, uint32_t full, int num_sms,
+                        cudaStream_t s);
 
 }  // namespace nps

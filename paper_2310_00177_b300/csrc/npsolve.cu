@@ -54,10 +54,11 @@ struct Workspace {
         *xc[kMaxLevels + 1] = {};
   ushort2 *counts[kMaxLevels + 1] = {};
   // per-solve kernel cache of the mixed-window cells (cached path)
-  uint32_t *kmask[kMaxLevels + 1] = {}, *koff[kMaxLevels + 1] = {};
-  long long kcols[kMaxLevels + 1] = {};  // column chunks kmask / koff can hold
+  uint8_t *kdesc[kMaxLevels + 1] = {};    // plane descriptors per level
+  long long kdesc_cap[kMaxLevels + 1] = {};  // descriptors kdesc can hold
   void *kcache[(kMaxLevels + 1) * 2] = {};
-  size_t kcap[(kMaxLevels + 1) * 2] = {};
+  size_t kcap[(kMaxLevels + 1) * 2] = {};    // cache entries kcache can hold
+  // per level: [2 l] cache entries (blocks padded to 4), [2 l + 1] mixed cells
   unsigned *ktotal = nullptr, *h_ktotal = nullptr;
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
   int hist_cap = 0;
@@ -119,10 +120,12 @@ struct npsolve {
   CConvW *cw = nullptr;            // [(kMaxLevels+1)*2], index lvl*2 + (type-1)
   uint8_t *uw = nullptr;           // tensor-core W splits, [(kMaxLevels+1)*2][umma_weight_bytes(3)]
   float *uni = nullptr;            // uniform-window kernel terms Bp, SWf, SWa: [(kMaxLevels+1)*2][81]
-  std::vector<float> uni_host;     // the same on the host (passed as kernel parameters)
+  std::vector<float> uni_host;     // the same on the host
+  std::vector<float> kfix_host;    // [(kMaxLevels+1)*2][81]: K^S, K^F, K^A of the pure windows (kernel parameters)
   int nsplit = 3;                  // BF16 terms of W on the tensor cores (3: FP32 form, 1: BF16 form)
   int num_sms = 148;
-  int *umma_err = nullptr;         // set by a tensor-core kernel whose MMA wait timed out
+  int *umma_err = nullptr;         // set by a kernel whose bounded wait (MMA or TMA completion) timed out
+  bool stream_err = false;         // a tensor map of the streamed CConv could not be encoded
   AffW *aw = nullptr;              // [(kMaxLevels+1)*2]
   double *unit_c12 = nullptr;      // {1, 0} for L = 1
   Workspace ws;
@@ -223,8 +226,7 @@ void free_ws(Workspace &w) {
     cudaFree(w.x2[l]);
     cudaFree(w.xc[l]);
     cudaFree(w.counts[l]);
-    cudaFree(w.kmask[l]);
-    cudaFree(w.koff[l]);
+    cudaFree(w.kdesc[l]);
   }
   for (int i = 0; i < (kMaxLevels + 1) * 2; ++i) cudaFree(w.kcache[i]);
   cudaFree(w.ktotal);
@@ -291,8 +293,8 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     CK(h, dalloc(&w.bytes, &w.relres, 2));
     CK(h, dalloc(&w.bytes, &w.st, 1));
     CK(h, dalloc(&w.bytes, &w.tickets, 8));
-    CK(h, dalloc(&w.bytes, &w.ktotal, kMaxLevels + 1));
-    CK(h, cudaHostAlloc((void **)&w.h_ktotal, sizeof(unsigned) * (kMaxLevels + 1), cudaHostAllocDefault));
+    CK(h, dalloc(&w.bytes, &w.ktotal, 2 * (kMaxLevels + 1)));
+    CK(h, cudaHostAlloc((void **)&w.h_ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaHostAllocDefault));
     CK(h, cudaMemset(w.tickets, 0, 8 * sizeof(unsigned)));
     CK(h, cudaMalloc(&w.pcg_st, pcg_state_bytes()));
     CK(h, dalloc(&w.bytes, &w.bad, 1));
@@ -399,6 +401,23 @@ int upload_weights(npsolve *h) {
       }
     CK(h, cudaMemcpy(h->uni, uni.data(), uni.size() * sizeof(float), cudaMemcpyHostToDevice));
     h->uni_host = uni;
+    // kernels of the pure windows of level lvl (F = 8^(lvl-1) fine cells per cell):
+    // K^S = Bp, K^F = Bp + F SWf, K^A = Bp + F SWa
+    std::vector<float> kfix((size_t)(kMaxLevels + 1) * 2 * 81, 0.f);
+    for (int i = 2; i < (kMaxLevels + 1) * 2; ++i) {
+      const double F = pow(8.0, i / 2 - 1);
+      for (int a = 0; a < 27; ++a) {
+        double sf = 0.0, sa = 0.0;
+        for (int l = 0; l < 27; ++l) {
+          sf += cw[i].wf[a][l];
+          sa += cw[i].wa[a][l];
+        }
+        kfix[(size_t)i * 81 + a] = cw[i].bp[a];
+        kfix[(size_t)i * 81 + 27 + a] = (float)((double)cw[i].bp[a] + F * sf);
+        kfix[(size_t)i * 81 + 54 + a] = (float)((double)cw[i].bp[a] + F * sa);
+      }
+    }
+    h->kfix_host = kfix;
   }
   CK(h, cudaMemcpy(h->cw, cw.data(), cw.size() * sizeof(CConvW), cudaMemcpyHostToDevice));
   CK(h, cudaMemcpy(h->aw, aw.data(), aw.size() * sizeof(AffW), cudaMemcpyHostToDevice));
@@ -419,7 +438,14 @@ int check_dims(npsolve *h, int nx, int ny, int nz) {
 // Levels whose CConv runs on the tensor cores in the per-iteration
 // recompute path (image counts <= 64 are exact in BF16 up to level 3).
 bool tensor_level(const npsolve *h, int lvl) { return h->cfg.kernel_path == NPSOLVE_PATH_TENSOR && lvl <= 3; }
-bool cached_path(const npsolve *h) { return h->cfg.kernel_path == NPSOLVE_PATH_CACHED; }
+// The cached path streams vector planes with TMA boxes, whose rows must be a
+// multiple of 16 bytes at every level; other shapes use the CUDA-core kernels.
+bool cached_path(const npsolve *h, Dims d1) {
+  if (h->cfg.kernel_path != NPSOLVE_PATH_CACHED) return false;
+  for (int l = 1; l <= h->cfg.levels; ++l)
+    if (!stream_shape_ok(level_dims(d1, l))) return false;
+  return true;
+}
 
 // One CConv block of level lvl (type 1 or 2), CUDA-core kernel.
 void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *vscale,
@@ -430,7 +456,7 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw + idx, in, vscale,
-                   mask_input, h->cfg.precision == NPSOLVE_BF16, out, st, s);
+                   mask_input, h->cfg.precision == NPSOLVE_BF16 ? 1 << (3 * (lvl - 1)) : 0, out, st, s);
 }
 
 // One CConv block on the tensor cores (z-marching kernel), with the input
@@ -445,22 +471,22 @@ void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const 
   h->launches += 1;
   launch_cconv_march(h->nsplit, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], level_dims(d1, lvl),
                      h->uw + (size_t)idx * umma_weight_bytes(3), in, coarse, vscale, mask_input, out, pooled, st,
-                     h->umma_err, h->num_sms, s);
+                     h->umma_err, 1u << (3 * (lvl - 1)), h->num_sms, s);
 }
 
 // One CConv block with the per-solve kernel cache (kernels_cached.cu): input
 // read (in) or interpolated (coarse), optional fused pooling, optional fused
 // combination out = c1 x1 + c2 CConv(...).
-void cconv_cached(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *vscale,
-                  float *out, float *pooled, const float *x1, const double *c12, const SolveState *st,
-                  cudaStream_t s) {
+void cconv_cached(npsolve *h, Dims d1, int lvl, int type, const float *in, const float *vscale, float *out,
+                  float *pooled, const float *x1, const double *c12, const SolveState *st, cudaStream_t s) {
   Workspace &w = h->ws;
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
-  launch_cconv_cached(h->cfg.precision == NPSOLVE_BF16, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl],
-                      level_dims(d1, lvl), h->uni_host.data() + (size_t)idx * 81, w.kmask[lvl], w.koff[lvl],
-                      w.kcache[idx], in, vscale, out, pooled, x1, c12, st, h->num_sms, s);
+  if (launch_cconv_stream(h->cfg.precision == NPSOLVE_BF16, level_dims(d1, lvl), h->kfix_host.data() + (size_t)idx * 81,
+                          w.kdesc[lvl], w.kcache[idx], in, vscale, out, pooled, x1, c12, st, h->umma_err, h->num_sms,
+                          s))
+    h->stream_err = true;
 }
 
 // Grids with nx % 4 == 0 use the 16-byte vector kernels with fused
@@ -477,7 +503,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
                  SolveState *st, cudaStream_t s, bool unfused = false) {
   Workspace &w = h->ws;
   const int L = h->cfg.levels;
-  const bool cached = cached_path(h);
+  const bool cached = cached_path(h, d1);
   if (cached && !st) {
     // the cached stencil expects an input that is zero off fluid: inside a solve
     // r is, for a user-supplied vector zero it here
@@ -490,7 +516,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     const float *in = l == 1 ? r : w.r1[l];
     const float *vs = l == 1 ? vscale : nullptr;
     if (cached) {
-      cconv_cached(h, lab, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s);
+      cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s);
     } else if (tensor_level(h, l)) {
       cconv_tc(h, lab, d1, l, 1, in, nullptr, vs, l == 1, w.x1[l], w.r1[l + 1], st, s);
     } else {
@@ -504,7 +530,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   {
     const float *in = L == 1 ? r : w.r1[L];
     const float *vs = L == 1 ? vscale : nullptr;
-    if (cached) cconv_cached(h, lab, d1, L, 1, in, vs, w.x1[L], nullptr, nullptr, nullptr, st, s);
+    if (cached) cconv_cached(h, d1, L, 1, in, vs, w.x1[L], nullptr, nullptr, nullptr, st, s);
     else if (tensor_level(h, L)) cconv_tc(h, lab, d1, L, 1, in, nullptr, vs, L == 1, w.x1[L], nullptr, st, s);
     else cconv(h, lab, d1, L, 1, in, vs, L == 1, w.x1[L], st, s);
   }
@@ -525,10 +551,10 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
         launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
       }
       if (l > 1) {  // CConv2 and the combination in one pass
-        cconv_cached(h, lab, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s);
+        cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s);
         continue;
       }
-      cconv_cached(h, lab, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
+      cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
     } else if (tensor_level(h, l) && !unfused) {
       cconv_tc(h, lab, d1, l, 2, nullptr, coarse, nullptr, 0, w.x2[l], nullptr, st, s);
     } else {
@@ -537,7 +563,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
         h->launches += 1;
         launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
       }
-      if (cached) cconv_cached(h, lab, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
+      if (cached) cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
       else if (tensor_level(h, l))
         cconv_tc(h, lab, d1, l, 2, w.r2[l], nullptr, nullptr, 0, w.x2[l], nullptr, st, s);
       else cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
@@ -567,49 +593,49 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
     launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
                h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s);
   h->launches += 1 + (L - 1) + 2 * (L - 1);
-  if (cached_path(h)) {
-    for (int l = 1; l <= L; ++l) {  // column-chunk arrays sized for this grid's shape
-      const long long nc = cached_columns(level_dims(d1, l));
-      if (nc > w.kcols[l]) {
-        if (w.graph) cudaGraphExecDestroy(w.graph);
+  if (cached_path(h, d1)) {
+    const bool bf16 = h->cfg.precision == NPSOLVE_BF16;
+    for (int l = 1; l <= L; ++l) {  // plane descriptors sized for this grid's shape
+      const long long nd = stream_desc_count(level_dims(d1, l));
+      if (nd > w.kdesc_cap[l]) {
+        if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old buffers
         w.graph = nullptr;
         CK(h, cudaStreamSynchronize(s));
-        if (w.kmask[l]) w.bytes -= 2 * ((size_t)w.kcols[l] * sizeof(uint32_t) + 256);
-        cudaFree(w.kmask[l]);
-        cudaFree(w.koff[l]);
-        w.kmask[l] = w.koff[l] = nullptr;
-        CK(h, dalloc(&w.bytes, &w.kmask[l], (size_t)nc));
-        CK(h, dalloc(&w.bytes, &w.koff[l], (size_t)nc));
-        w.kcols[l] = nc;
+        if (w.kdesc[l]) w.bytes -= (size_t)w.kdesc_cap[l] * stream_desc_bytes() + 256;
+        cudaFree(w.kdesc[l]);
+        w.kdesc[l] = nullptr;
+        CK(h, dalloc(&w.bytes, &w.kdesc[l], (size_t)nd * stream_desc_bytes()));
+        w.kdesc_cap[l] = nd;
       }
     }
-    CK(h, cudaMemsetAsync(w.ktotal, 0, sizeof(unsigned) * (kMaxLevels + 1), s));
+    CK(h, cudaMemsetAsync(w.ktotal, 0, sizeof(unsigned) * 2 * (kMaxLevels + 1), s));
     for (int l = 1; l <= L; ++l)
-      launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), w.kmask[l],
-                      w.koff[l], w.ktotal + l, s);
+      launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
+                      1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l, h->num_sms, s);
     h->launches += L;
-    CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
-    const bool bf16 = h->cfg.precision == NPSOLVE_BF16;
-    for (int l = 1; l <= L; ++l)
-      for (int t = 1; t <= (l < L ? 2 : 1); ++t) {
-        const int idx = l * 2 + (t - 1);
-        const size_t need = (size_t)w.h_ktotal[l] + 1;
+    for (int l = 1; l <= L; ++l) {
+      const int nblk = l < L ? 2 : 1;
+      for (int t = 0; t < nblk; ++t) {
+        const int idx = l * 2 + t;
+        const size_t need = (size_t)w.h_ktotal[2 * l] + 4;
         if (need > w.kcap[idx]) {
           if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old cache buffer
           w.graph = nullptr;
           CK(h, cudaStreamSynchronize(s));
-          if (w.kcache[idx]) w.bytes -= w.kcap[idx] * cached_entry_bytes(bf16) + 256;
+          if (w.kcache[idx]) w.bytes -= w.kcap[idx] * (size_t)cached_entry_bytes(bf16) + 256;
           cudaFree(w.kcache[idx]);
           w.kcache[idx] = nullptr;
-          const size_t cap = need + need / 4;
+          const size_t cap = (need + need / 4 + 3) & ~(size_t)3;
           CK(h, dalloc(&w.bytes, (uint8_t **)&w.kcache[idx], cap * cached_entry_bytes(bf16)));
           w.kcap[idx] = cap;
         }
-        launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
-                        h->cw + idx, w.kmask[l], w.koff[l], w.kcache[idx], s);
-        h->launches += 1;
       }
+      launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->cw + l * 2,
+                      nblk, w.kdesc[l], w.kcache[l * 2], nblk > 1 ? w.kcache[l * 2 + 1] : nullptr, h->num_sms, s);
+      h->launches += 1;
+    }
   }
   CK(h, cudaGetLastError());
   return NPSOLVE_OK;
@@ -845,13 +871,18 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
 }
 
-// A tensor-core kernel that timed out waiting for its MMAs leaves a flag.
+// A kernel whose bounded wait (tensor-core MMA or TMA copy completion) timed
+// out leaves a flag; a tensor map that could not be encoded leaves another.
 int check_umma_err(npsolve *h) {
+  if (h->stream_err) {
+    h->stream_err = false;
+    return fail(h, NPSOLVE_CUDA_ERROR, "streamed CConv: a TMA tensor map could not be encoded");
+  }
   int e = 0;
   CK(h, cudaMemcpy(&e, h->umma_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (e) {
     cudaMemset(h->umma_err, 0, sizeof(int));
-    return fail(h, NPSOLVE_CUDA_ERROR, "tensor-core CConv: MMA completion wait timed out");
+    return fail(h, NPSOLVE_CUDA_ERROR, "a bounded device wait (MMA or TMA completion) timed out");
   }
   return NPSOLVE_OK;
 }
@@ -1268,8 +1299,8 @@ long long npsolve_launch_count(npsolve_t h) { return h ? h->launches : 0; }
 size_t npsolve_workspace_bytes(npsolve_t h) { return h ? h->ws.bytes : 0; }
 
 long long npsolve_mixed_cells(npsolve_t h, int level) {
-  if (!h || level < 1 || level > h->cfg.levels || !cached_path(h) || !h->ws.h_ktotal) return -1;
-  return (long long)h->ws.h_ktotal[level];
+  if (!h || level < 1 || level > h->cfg.levels || !h->ws.h_ktotal || !cached_path(h, h->ws.dims)) return -1;
+  return (long long)h->ws.h_ktotal[2 * level + 1];
 }
 
 int npsolve_profile_count(void) { return P_COUNT; }

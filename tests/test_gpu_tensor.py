@@ -110,10 +110,14 @@ def test_tensor_path_solve_config1(precision):
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-5)])
-@pytest.mark.parametrize("shape,L", [((32, 32, 32), 4), ((24, 40, 64), 4), ((16, 32, 8), 3), ((64, 16, 32), 5)])
+@pytest.mark.parametrize("shape,L", [((32, 32, 32), 4), ((96, 40, 72), 3), ((40, 12, 20), 2), ((16, 32, 8), 3),
+                                     ((64, 16, 32), 5), ((24, 40, 64), 4)])
 def test_cached_path_matches_cuda_core_path(shape, L, precision, tol):
     # the per-solve kernel cache (default path) against per-iteration
-    # regeneration on CUDA cores: identical arithmetic up to FP32 rounding
+    # regeneration on CUDA cores: identical arithmetic up to FP32 rounding.
+    # Shapes: ragged x and y tiles and z chunks (96 x 40 x 72, 40 x 12 x 20);
+    # 24 x 40 x 64 at L = 4 has a 6-cell row at level 3 (not a multiple of 16
+    # bytes), which the library runs on the CUDA-core kernels instead.
     b = _b()
     lab = _rng_labels(shape, 51) if shape != (32, 32, 32) else synth.pool_scene(32, 1000)
     w = synth.init_weights(L, 52, spread=0.05).astype(np.float32)
