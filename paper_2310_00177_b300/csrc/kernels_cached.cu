@@ -28,22 +28,23 @@
 // BF16 in the BF16 form).
 //
 // Per iteration: k_cconv_stream.  Each CTA marches units (a tile and a chunk
-// of planes) along z.  Thread 0 is the producer: it keeps RV vector planes in
-// flight (a 40 x 6 TMA tensor box with the one-cell halo, the plane's
-// descriptor and, when the output is combined, the 32 x 4 box of x1), and as
-// soon as a plane's descriptor has arrived it issues the bulk copy of the
-// plane's kernel block into a circular buffer of shared memory, up to NK
-// blocks ahead.  All threads consume: planes z-1 and z of the vector window
-// live in registers, plane z+1 comes from its slot, the kernel of a uniform
-// window is one of the three constants (kernel parameters), that of a mixed
-// window is read from its block.  One CTA barrier per plane frees the slots.
-// Fusions: scaling by the input normalisation (level-1 CConv1), the 2x2x2
-// mean pooling of the output (CConv1), the combination x = c1 x1 + c2 x2
-// (CConv2 at levels >= 2).
+// of planes) along z, two planes per step.  One producer warp (one thread)
+// loads per unit the plane descriptors (bulk copy, three buffers), and per
+// step, into one of RV slots completing on one mbarrier: the 40 x 6 x 2 TMA
+// box of the input planes z+1, z+2 (one-cell halo), the 32 x 4 x 2 box of x1
+// (combination only) and, with a bulk copy into a circular buffer, the two
+// planes' kernel blocks (contiguous in the cache).  Four consumer warps (one
+// per tile row) keep planes z-1, z in registers and compute the centres z and
+// z+1: the kernel of a pure window is one of three constants (kernel
+// parameters), that of a mixed window is read from its block.  Slots and
+// descriptor buffers are released with mbarrier arrivals; there is no CTA-wide
+// barrier in the march.  Fusions: scaling by the input normalisation (level-1
+// CConv1), the 2x2x2 mean pooling of the output (CConv1), the combination
+// x = c1 x1 + c2 x2 (CConv2 at levels >= 2).
 //
-// Every wait on an mbarrier is bounded (1 s of %globaltimer); a timeout sets
-// *err, ends the kernel uniformly at the next CTA barrier and waits (bounded)
-// for the copies still in flight before returning.
+// Every wait on an mbarrier is bounded (1 s of %globaltimer, with the thread
+// suspended in hardware meanwhile); a timeout sets *err, and every warp then
+// leaves; the producer waits (bounded) for its copies in flight first.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -59,7 +60,6 @@ namespace {
 
 using umma::globaltimer;
 using umma::mbar_init;
-using umma::mbar_try_wait;
 using umma::mbar_wait_bounded;
 using umma::smem_u32;
 
@@ -67,29 +67,31 @@ constexpr int TX = 32, TY = 4, NT = TX * TY;  // tile; warp w holds row w
 constexpr int ZCG = 32;                       // planes per unit of the setup kernels
 constexpr int BXW = TX + 8;                   // vector box: x0-4 .. x0+35 (start on a 16-byte boundary)
 constexpr int BYH = TY + 2;                   // rows y0-1 .. y0+4
-constexpr int VBYTES = BXW * BYH * 4;         // 960
-constexpr int X1OFF = 1024;                   // x1 box (32 x 4) in a slot
-constexpr int DOFF = X1OFF + NT * 4;          // plane descriptor in a slot
-constexpr int VSLOT = DOFF + 128;             // 1664 bytes = 13 x 128
-constexpr int RV = 10;                        // vector-plane slots
-constexpr int NK = 8;                         // kernel blocks in flight
-constexpr int kMetaBytes = 768;               // mbarriers, block positions, pooling exchange, abort flag
+constexpr int VPLANE = BXW * BYH * 4;         // 960 bytes per plane of the vector box
+constexpr int X1OFF = 2 * VPLANE;             // x1 box (32 x 4 x 2) in a slot
+constexpr int SLOT = 3072;                    // 1920 + 1024 bytes, 24 x 128
+constexpr int RV = 6;                         // step slots
+constexpr int ND = 3;                         // descriptor buffers (units)
+constexpr int kMetaBytes = 640;               // mbarriers, block positions, pooling exchange, abort flag
 constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
 
+// Plane descriptor: per row w of the tile the masks {mixed window, pure-fluid
+// window, pure-air window, fluid cell} (bit = lane), then the kernel block.
 struct PlaneDesc {
-  uint32_t mixed[TY], fluid[TY], air[TY], self[TY];
-  uint32_t off;    // first cache entry of the plane's kernel block (a multiple of 4)
-  uint32_t cpad;   // entries of the block: the mixed count rounded up to 4
-  uint32_t count;  // mixed cells of the plane
-  uint32_t pad_;
+  uint4 row[TY];     // x: mixed, y: pure fluid, z: pure air, w: the cell is fluid
+  uint32_t off;      // first cache entry of the plane's kernel block (a multiple of 4)
+  uint32_t count;    // mixed cells of the plane
+  uint32_t cpad;     // entries of the block: the mixed count rounded up to 4
+  uint32_t rowbase;  // byte w: mixed cells in rows 0..w-1 (the rank of row w's first one)
 };
 static_assert(sizeof(PlaneDesc) == 80, "plane descriptor is 80 bytes");
+constexpr int DBUF = ZCG * (int)sizeof(PlaneDesc);  // one unit's descriptors
 
 template <bool BF16C>
 struct KCfg {
   static constexpr int EB = BF16C ? 56 : 108;        // bytes per cached kernel
-  static constexpr int CB = BF16C ? 16384 : 28672;   // circular kernel-block buffer
-  static constexpr int SMEM = RV * VSLOT + CB + kMetaBytes;
+  static constexpr int CB = BF16C ? 24576 : 28672;   // circular kernel-block buffer (>= two full planes)
+  static constexpr int SMEM = RV * SLOT + ND * DBUF + CB + kMetaBytes;
 };
 
 // Image key of a cell: fluid count | air count << 16 (0/1 at level 1); zero
@@ -110,6 +112,26 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Wait for an mbarrier phase with the thread suspended in hardware (up to
+// 100 us per try) instead of spinning; gives up after limit_ns of wall time.
+__device__ __forceinline__ bool mbar_sleep_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  constexpr uint32_t kHintNs = 100000u;
+  uint32_t ok;
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kHintNs)
+        : "memory");
+    if (ok) return true;
+    if (it == 0) t0 = globaltimer();
+    else if (globaltimer() - t0 > limit_ns) return false;
+  }
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
@@ -174,23 +196,26 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
       const uint32_t bm = __ballot_sync(0xffffffffu, mixed), bf = __ballot_sync(0xffffffffu, fl);
       const uint32_t ba = __ballot_sync(0xffffffffu, ai), bs = __ballot_sync(0xffffffffu, self);
       if (lane == 0) {
-        sd[j][warp] = bm;
-        sd[j][TY + warp] = bf;
-        sd[j][2 * TY + warp] = ba;
-        sd[j][3 * TY + warp] = bs;
+        sd[j][4 * warp] = bm;
+        sd[j][4 * warp + 1] = bf;
+        sd[j][4 * warp + 2] = ba;
+        sd[j][4 * warp + 3] = bs;
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       uint32_t tot = 0, cnt = 0;
       for (int j = 0; j < nzu; ++j) {
-        uint32_t m = 0;
-        for (int w = 0; w < TY; ++w) m += __popc(sd[j][w]);
+        uint32_t m = 0, rb = 0;
+        for (int w = 0; w < TY; ++w) {
+          rb |= m << (8 * w);
+          m += __popc(sd[j][4 * w]);
+        }
         const uint32_t cp = (m + 3u) & ~3u;
         sd[j][16] = tot;
-        sd[j][17] = cp;
-        sd[j][18] = m;
-        sd[j][19] = 0u;
+        sd[j][17] = m;
+        sd[j][18] = cp;
+        sd[j][19] = rb;
         tot += cp;
         cnt += m;
       }
@@ -242,10 +267,9 @@ __global__ void __launch_bounds__(NT) k_generate(const uint8_t *__restrict__ lab
     __syncthreads();
     for (int j = 0; j < nzu; ++j) {
       const PlaneDesc &pd = sd[j];
-      const uint32_t mw = pd.mixed[warp];
+      const uint32_t mw = pd.row[warp].x;
       if (!((mw >> lane) & 1u)) continue;
-      uint32_t rank = __popc(mw & lanemask_lt());
-      for (int q = 0; q < warp; ++q) rank += __popc(pd.mixed[q]);
+      const uint32_t rank = __popc(mw & lanemask_lt()) + ((pd.rowbase >> (8 * warp)) & 0xFFu);
       const int z = zs + j;
       float nf[27], na[27];
 #pragma unroll
@@ -293,8 +317,8 @@ __global__ void __launch_bounds__(NT) k_generate(const uint8_t *__restrict__ lab
 // Per iteration: the streamed z-marching CConv.
 // ---------------------------------------------------------------------------
 struct StreamParams {
-  CUtensorMap tv;   // input vector of the level: box 40 x 6 x 1 (FP32)
-  CUtensorMap tx1;  // x1 of the level (combination only): box 32 x 4 x 1
+  CUtensorMap tv;   // input vector of the level: box 40 x 6 x 2 (FP32)
+  CUtensorMap tx1;  // x1 of the level (combination only): box 32 x 4 x 2
   Dims dm;
   int ntx, ntiles, zc, units;
   const PlaneDesc *desc;
@@ -336,13 +360,61 @@ __device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9
   return (s0 + s1) + s2;
 }
 
-// Shared memory after the slots and the kernel-block buffer (8-byte aligned):
-// vfull / vempty [RV], kfull / kempty [NK], pfull / pempty [2 pairs][2 buffers]
-// (mbarriers), kstart / kend [NK] (positions of the blocks), poolx [2][2][16]
-// (pooling exchange between the two warps of a row pair), abort flag.
+// One output cell: the classes of the warp's row decide which (warp-uniform)
+// constant-kernel sums are needed; a mixed lane reads its kernel from the block.
+template <bool BF16C>
+__device__ __forceinline__ float cconv_cell(const StreamParams &P, uint4 rw, uint32_t rank, uint32_t cp,
+                                            const uint32_t *kblk, int lane, const float (&vA)[9],
+                                            const float (&vB)[9], const float (&vC)[9]) {
+  const uint32_t cm = rw.x, cf = rw.y, ca = rw.z;
+  if (cf == 0xFFFFFFFFu) return dot27(P.kF, vA, vB, vC);
+  if (ca == 0xFFFFFFFFu) return dot27(P.kA, vA, vB, vC);
+  const uint32_t cs = ~(cm | cf | ca);  // pure-solid windows (and lanes outside the grid)
+  if (cs == 0xFFFFFFFFu) return dot27(P.kS, vA, vB, vC);
+  float acc = 0.f;
+  if (cf) {
+    const float t = dot27(P.kF, vA, vB, vC);
+    if ((cf >> lane) & 1u) acc = t;
+  }
+  if (ca) {
+    const float t = dot27(P.kA, vA, vB, vC);
+    if ((ca >> lane) & 1u) acc = t;
+  }
+  if (cs) {
+    const float t = dot27(P.kS, vA, vB, vC);
+    if ((cs >> lane) & 1u) acc = t;
+  }
+  if ((cm >> lane) & 1u) {
+    const uint32_t *kw = kblk + rank;
+    float K[28];
+    if (BF16C) {
+#pragma unroll
+      for (int q = 0; q < 14; ++q) {
+        const uint32_t wv = kw[q * cp];
+        K[2 * q] = __uint_as_float(wv << 16);
+        K[2 * q + 1] = __uint_as_float(wv & 0xFFFF0000u);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 27; ++a) K[a] = __uint_as_float(kw[a * cp]);
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      s0 = fmaf(K[q], vA[q], s0);
+      s1 = fmaf(K[9 + q], vB[q], s1);
+      s2 = fmaf(K[18 + q], vC[q], s2);
+    }
+    acc = (s0 + s1) + s2;
+  }
+  return acc;
+}
+
+// Shared memory after the slots, descriptor buffers and the kernel-block
+// buffer (8-byte aligned): mbarriers, block positions, pooling exchange.
 struct StreamMeta {
-  uint64_t vfull[RV], vempty[RV], kfull[NK], kempty[NK], pfull[4], pempty[4];
-  uint32_t kstart[NK], kend[NK];
+  uint64_t full[RV], empty[RV], dfull[ND], dempty[ND], pfull[4], pempty[4];
+  uint32_t kstart[RV], kend[RV];
   float poolx[4][16];
   int abort_;
 };
@@ -356,7 +428,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
   if (P.st && P.st->done) return;
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *vs = smem;
-  uint8_t *kb = smem + RV * VSLOT;
+  uint8_t *ds = smem + RV * SLOT;
+  uint8_t *kb = ds + ND * DBUF;
   StreamMeta &M = *(StreamMeta *)(kb + C::CB);
   volatile int *sabort = &M.abort_;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -366,14 +439,14 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
 
   if (tid == 0) {
     for (int i = 0; i < RV; ++i) {
-      mbar_init(&M.vfull[i], 1);
-      mbar_init(&M.vempty[i], TY);
-    }
-    for (int i = 0; i < NK; ++i) {
-      mbar_init(&M.kfull[i], 1);
-      mbar_init(&M.kempty[i], TY);
+      mbar_init(&M.full[i], 1);
+      mbar_init(&M.empty[i], TY);
       M.kstart[i] = 0u;
       M.kend[i] = 0u;
+    }
+    for (int i = 0; i < ND; ++i) {
+      mbar_init(&M.dfull[i], 1);
+      mbar_init(&M.dempty[i], TY);
     }
     for (int i = 0; i < 4; ++i) {
       mbar_init(&M.pfull[i], 1);
@@ -389,141 +462,98 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
     // ------------------------------------------------------------------ producer
     if (lane != 0) return;
     bool fail = false;
-    // V cursor: load vi = plane vu.zs - 1 + vj of the vm-th unit of this CTA
-    int vm = 0, vj = 0;
-    uint32_t vi = 0;
-    Unit vu{};
-    bool vvalid = (int)blockIdx.x < P.units;
-    if (vvalid) vu = unit_at(P, blockIdx.x);
-    // K cursor: block ki = plane ku.zs + kj; its descriptor travels with V load kvbase + kj + 1
-    int km = 0, kj = 0;
-    uint32_t ki = 0, kvbase = 0, kdone = 0;
-    Unit ku = vu;
-    bool kvalid = vvalid;
+    uint32_t vi = 0, vrel = 0;            // loads issued / slots known released
     uint32_t khead = 0, ktail = 0, kpos = 0;
-
-    auto issue_k = [&](bool block) -> bool {
-      if (!kvalid || fail) return false;
-      const uint32_t dv = kvbase + (uint32_t)kj + 1u;
-      if (dv >= vi) return false;
-      const int vslot = (int)(dv % RV);
-      if (block) {
-        if (!mbar_wait_bounded(&M.vfull[vslot], (dv / RV) & 1u, kWaitNs)) {
-          fail = true;
-          return false;
-        }
-      } else if (!mbar_try_wait(&M.vfull[vslot], (dv / RV) & 1u)) {
-        return false;
+    uint32_t di = 0;                      // descriptor loads issued (= units)
+    auto release_next = [&]() {
+      const int sl = (int)(vrel % RV);
+      if (!mbar_sleep_wait(&M.empty[sl], (vrel / RV) & 1u, kWaitNs)) {
+        fail = true;
+        return;
       }
-      const PlaneDesc *d = (const PlaneDesc *)(vs + vslot * VSLOT + DOFF);
-      const uint32_t cp = min(d->cpad, (uint32_t)NT);
-      const uint32_t bytes = cp * (uint32_t)C::EB;
-      const uint32_t waste = (kpos + bytes > (uint32_t)C::CB) ? (uint32_t)C::CB - kpos : 0u;
-      // retire released blocks until a slot and the space are free
-      while (kdone < ki && (ki - kdone >= (uint32_t)NK || (khead - ktail) + waste + bytes > (uint32_t)C::CB)) {
-        const int ds = (int)(kdone % NK);
-        if (block) {
-          if (!mbar_wait_bounded(&M.kempty[ds], (kdone / NK) & 1u, kWaitNs)) {
-            fail = true;
-            return false;
-          }
-        } else if (!mbar_try_wait(&M.kempty[ds], (kdone / NK) & 1u)) {
-          return false;
-        }
-        ktail = M.kend[ds];
-        ++kdone;
-      }
-      const int ks = (int)(ki % NK);
-      if (waste) {
-        khead += waste;
-        kpos = 0;
-      }
-      M.kstart[ks] = kpos;
-      khead += bytes;
-      M.kend[ks] = khead;
-      if (bytes) {
-        mbar_expect_tx(&M.kfull[ks], bytes);
-        bulk_load(kb + kpos, P.cache + (size_t)d->off * C::EB, bytes, &M.kfull[ks]);
-      } else {
-        mbar_arrive(&M.kfull[ks]);
-      }
-      kpos += bytes;
-      ++ki;
-      if (++kj == ku.nzu) {
-        kj = 0;
-        kvbase += (uint32_t)ku.nzu + 2u;
-        ++km;
-        const int u = blockIdx.x + km * G;
-        kvalid = u < P.units;
-        if (kvalid) ku = unit_at(P, u);
-      }
-      return true;
+      ktail = M.kend[sl];
+      ++vrel;
     };
-
-    auto issue_v = [&](bool block) -> bool {
-      if (!vvalid || fail) return false;
-      const int slot = (int)(vi % RV);
-      if (vi >= (uint32_t)RV) {
-        // the descriptor in the load being replaced must have served its block
-        while (kvalid && kvbase + (uint32_t)kj + 1u <= vi - (uint32_t)RV) {
-          if (!issue_k(block)) return false;
-        }
-        if (block) {
-          if (!mbar_wait_bounded(&M.vempty[slot], ((vi / RV) - 1u) & 1u, kWaitNs)) {
-            fail = true;
-            return false;
-          }
-        } else if (!mbar_try_wait(&M.vempty[slot], ((vi / RV) - 1u) & 1u)) {
-          return false;
-        }
+    auto issue_desc = [&](int m) {  // descriptors of this CTA's m-th unit
+      const int u = blockIdx.x + m * G;
+      if (u >= P.units || fail) return;
+      const Unit U = unit_at(P, u);
+      const int b = m % ND;
+      if (m >= ND && !mbar_sleep_wait(&M.dempty[b], ((m / ND) - 1) & 1, kWaitNs)) {
+        fail = true;
+        return;
       }
-      const int z = vu.zs - 1 + vj;
-      const bool hasd = vj >= 1 && vj <= vu.nzu;
-      uint8_t *dst = vs + slot * VSLOT;
-      uint64_t *bar = &M.vfull[slot];
-      mbar_expect_tx(bar, (uint32_t)VBYTES +
-                              (hasd ? (uint32_t)sizeof(PlaneDesc) + (has_x1 ? (uint32_t)(NT * 4) : 0u) : 0u));
-      tma_load_3d(dst, &P.tv, vu.x0 - 4, vu.y0 - 1, z, bar);
-      if (hasd) {
-        bulk_load(dst + DOFF, P.desc + (size_t)vu.t * nz + z, (uint32_t)sizeof(PlaneDesc), bar);
-        if (has_x1) tma_load_3d(dst + X1OFF, &P.tx1, vu.x0, vu.y0, z, bar);
-      }
-      ++vi;
-      if (++vj == vu.nzu + 2) {
-        vj = 0;
-        ++vm;
-        const int u = blockIdx.x + vm * G;
-        vvalid = u < P.units;
-        if (vvalid) vu = unit_at(P, u);
-      }
-      return true;
+      mbar_expect_tx(&M.dfull[b], (uint32_t)(U.nzu * (int)sizeof(PlaneDesc)));
+      bulk_load(ds + b * DBUF, P.desc + (size_t)U.t * nz + U.zs, (uint32_t)(U.nzu * (int)sizeof(PlaneDesc)),
+                &M.dfull[b]);
+      ++di;
     };
-
-    while (!fail && !*sabort && (vvalid || kvalid)) {
-      bool prog = false;
-      while (issue_v(false)) prog = true;
-      while (issue_k(false)) prog = true;
-      if (!prog) {
-        if (vvalid) (void)issue_v(true);
-        else (void)issue_k(true);
+    issue_desc(0);
+    for (int m = 0; !fail && !*sabort; ++m) {
+      const int u = blockIdx.x + m * G;
+      if (u >= P.units) break;
+      const Unit U = unit_at(P, u);
+      issue_desc(m + 1);  // one unit ahead
+      const PlaneDesc *D = (const PlaneDesc *)(ds + (m % ND) * DBUF);
+      bool dready = false;
+      const int T = (U.nzu + 1) >> 1;
+      for (int t = -1; t < T && !fail; ++t) {
+        // slot: planes z0+1, z0+2 (prologue: zs-1, zs), x1 of z0, z0+1 and the kernel blocks of z0, z0+1
+        while (!fail && vrel + RV <= vi) release_next();
+        uint32_t kbytes = 0, koff = 0;
+        if (t >= 0) {
+          if (!dready) {
+            if (!mbar_sleep_wait(&M.dfull[m % ND], (m / ND) & 1, kWaitNs)) {
+              fail = true;
+              break;
+            }
+            dready = true;
+          }
+          const int j0 = 2 * t;
+          const uint32_t cp0 = min(D[j0].cpad, (uint32_t)NT);
+          const uint32_t cp1 = j0 + 1 < U.nzu ? min(D[j0 + 1].cpad, (uint32_t)NT) : 0u;
+          koff = D[j0].off;
+          kbytes = (cp0 + cp1) * (uint32_t)C::EB;
+        }
+        const uint32_t waste = (kpos + kbytes > (uint32_t)C::CB) ? (uint32_t)C::CB - kpos : 0u;
+        while (!fail && vrel < vi && (khead - ktail) + waste + kbytes > (uint32_t)C::CB) release_next();
+        if (fail) break;
+        const int sl = (int)(vi % RV);
+        if (waste) {
+          khead += waste;
+          kpos = 0;
+        }
+        M.kstart[sl] = kpos;
+        khead += kbytes;
+        M.kend[sl] = khead;
+        uint8_t *dst = vs + sl * SLOT;
+        uint64_t *bar = &M.full[sl];
+        const int zv = t < 0 ? U.zs - 1 : U.zs + 2 * t + 1;
+        const bool x1 = has_x1 && t >= 0;
+        mbar_expect_tx(bar, 2u * VPLANE + (x1 ? 2u * NT * 4u : 0u) + kbytes);
+        tma_load_3d(dst, &P.tv, U.x0 - 4, U.y0 - 1, zv, bar);
+        if (x1) tma_load_3d(dst + X1OFF, &P.tx1, U.x0, U.y0, U.zs + 2 * t, bar);
+        if (kbytes) bulk_load(kb + kpos, P.cache + (size_t)koff * C::EB, kbytes, bar);
+        kpos += kbytes;
+        ++vi;
       }
     }
-    if (fail && P.err) {
+    if (fail) {
       *sabort = 1;
-      atomicExch(P.err, 1);
+      if (P.err) atomicExch(P.err, 1);
     }
     // every copy must have landed before the CTA may exit
     for (uint32_t i = vi > (uint32_t)RV ? vi - RV : 0u; i < vi; ++i)
-      (void)mbar_wait_bounded(&M.vfull[i % RV], (i / RV) & 1u, kWaitNs);
-    for (uint32_t i = ki > (uint32_t)NK ? ki - NK : 0u; i < ki; ++i)
-      (void)mbar_wait_bounded(&M.kfull[i % NK], (i / NK) & 1u, kWaitNs);
+      (void)mbar_sleep_wait(&M.full[i % RV], (i / RV) & 1u, kWaitNs);
+    for (uint32_t m = di > (uint32_t)ND ? di - ND : 0u; m < di; ++m)
+      (void)mbar_sleep_wait(&M.dfull[m % ND], (m / ND) & 1u, kWaitNs);
     return;
   }
 
   // -------------------------------------------------------------------- consumers
   bool ok = true;
   auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
-    if (ok && !mbar_wait_bounded(bar, parity, kWaitNs)) {
+    if (ok && !mbar_sleep_wait(bar, parity, kWaitNs)) {
       ok = false;
       *sabort = 1;
       if (P.err) atomicExch(P.err, 1);
@@ -536,10 +566,11 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
   const long long nxy = (long long)P.dm.nx * P.dm.ny;
   const uint32_t below = lanemask_lt();
   const int pair = warp >> 1;
-  uint32_t vc = 0, kc = 0;  // V loads / K blocks consumed
-  uint32_t pround = 0;      // pooling rounds (odd planes) so far
-  // pooling of the even row of a pair: the value of round pend_r waits for the odd row's sum
-  float psum = 0.f, pend_t = 0.f;
+  const int vrow = warp * BXW + lane + 3;  // box index of the cell (x-1, y-1) in a plane (box starts at x0-4, y0-1)
+  uint32_t vc = 0;                         // slots consumed
+  uint32_t pround = 0;                     // pooling rounds so far
+  // pooling of the even row of a pair waits for the odd row's sum of round pend_r
+  float pend_t = 0.f;
   long long pend_idx = -1;
   bool pend = false;
   uint32_t pend_r = 0;
@@ -560,139 +591,97 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
     const Unit U = unit_at(P, u);
     const int gx = U.x0 + lane, gy = U.y0 + warp;
     const bool inside = gx < P.dm.nx && gy < P.dm.ny;
+    const PlaneDesc *D = (const PlaneDesc *)(ds + (m % ND) * DBUF);
+    if (!wait(&M.dfull[m % ND], (m / ND) & 1)) break;
     float vA[9], vB[9];
-    uint32_t cm = 0u, cf = 0u, ca = 0u, crank = 0u, ccp = 0u;
-    float cx1 = 0.f;
-    // unit prologue: planes zs-1 and zs, descriptor (and x1) of plane zs
-    flush_pool();
-    {
-      const uint32_t i0 = vc, i1 = vc + 1u;
-      if (!wait(&M.vfull[i0 % RV], (i0 / RV) & 1u) || !wait(&M.vfull[i1 % RV], (i1 / RV) & 1u)) break;
-      const float *s0 = (const float *)(vs + (i0 % RV) * VSLOT);
-      const uint8_t *slot1 = vs + (i1 % RV) * VSLOT;
-      const float *s1 = (const float *)slot1;
+    {  // prologue slot: planes zs-1, zs
+      const uint32_t sl = vc % RV;
+      if (!wait(&M.full[sl], (vc / RV) & 1u)) break;
+      const float *pl = (const float *)(vs + sl * SLOT);
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const int e = (warp + q / 3) * BXW + lane + 3 + q % 3;
-        vA[q] = s0[e];
-        vB[q] = s1[e];
+        const int e = vrow + (q / 3) * BXW + q % 3;
+        vA[q] = pl[e];
+        vB[q] = pl[BXW * BYH + e];
       }
-      const PlaneDesc *d = (const PlaneDesc *)(slot1 + DOFF);
-      cm = d->mixed[warp];
-      cf = d->fluid[warp];
-      ca = d->air[warp];
-      crank = __popc(cm & below);
-      for (int q = 0; q < warp; ++q) crank += __popc(d->mixed[q]);
-      ccp = min(d->cpad, (uint32_t)NT);
-      if (has_x1) cx1 = ((const float *)(slot1 + X1OFF))[warp * TX + lane];
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&M.vempty[i0 % RV]);
-        mbar_arrive(&M.vempty[i1 % RV]);
-      }
-      vc += 2u;
+      if (lane == 0) mbar_arrive(&M.empty[sl]);
+      ++vc;
     }
-
-    for (int j = 0; j < U.nzu; ++j) {
-      const int z = U.zs + j;
+    const int T = (U.nzu + 1) >> 1;
+    for (int t = 0; t < T; ++t) {
+      const int j0 = 2 * t, z0 = U.zs + j0;
+      const bool two = j0 + 1 < U.nzu;
       flush_pool();
-      const uint32_t iv = vc, ik = kc;
-      if (!wait(&M.vfull[iv % RV], (iv / RV) & 1u)) break;
-      const uint8_t *slot = vs + (iv % RV) * VSLOT;
-      float vC[9];
+      const uint32_t sl = vc % RV;
+      if (!wait(&M.full[sl], (vc / RV) & 1u)) break;
+      const uint8_t *slot = vs + sl * SLOT;
+      const float *pl = (const float *)slot;
+      float vC[9], vD[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) vC[q] = ((const float *)slot)[(warp + q / 3) * BXW + lane + 3 + q % 3];
-      // descriptor and x1 of the next centre plane
-      uint32_t nm = 0u, nf = 0u, na = 0u, nrank = 0u, ncp = 0u;
-      float nx1 = 0.f;
-      if (j + 1 < U.nzu) {
-        const PlaneDesc *d = (const PlaneDesc *)(slot + DOFF);
-        nm = d->mixed[warp];
-        nf = d->fluid[warp];
-        na = d->air[warp];
-        nrank = __popc(nm & below);
-        for (int q = 0; q < warp; ++q) nrank += __popc(d->mixed[q]);
-        ncp = min(d->cpad, (uint32_t)NT);
-        if (has_x1) nx1 = ((const float *)(slot + X1OFF))[warp * TX + lane];
+      for (int q = 0; q < 9; ++q) {
+        const int e = vrow + (q / 3) * BXW + q % 3;
+        vC[q] = pl[e];
+        vD[q] = pl[BXW * BYH + e];
+      }
+      float x1a = 0.f, x1b = 0.f;
+      if (has_x1) {
+        x1a = ((const float *)(slot + X1OFF))[tid];
+        x1b = ((const float *)(slot + X1OFF))[NT + tid];
+      }
+      const uint32_t *kblk = (const uint32_t *)(kb + M.kstart[sl]);
+      const uint4 r0 = D[j0].row[warp];
+      const uint2 c0 = *(const uint2 *)&D[j0].cpad;  // cpad, rowbase
+      const uint32_t cp0 = min(c0.x, (uint32_t)NT);
+      float acc0 = cconv_cell<BF16C>(P, r0, __popc(r0.x & below) + ((c0.y >> (8 * warp)) & 0xFFu), cp0, kblk, lane,
+                                     vA, vB, vC);
+      float acc1 = 0.f;
+      if (two) {
+        const uint4 r1 = D[j0 + 1].row[warp];
+        const uint2 c1d = *(const uint2 *)&D[j0 + 1].cpad;
+        acc1 = cconv_cell<BF16C>(P, r1, __popc(r1.x & below) + ((c1d.y >> (8 * warp)) & 0xFFu),
+                                 min(c1d.x, (uint32_t)NT), kblk + (size_t)cp0 * (C::EB / 4), lane, vB, vC, vD);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&M.vempty[iv % RV]);
-      vc += 1u;
-      if (!wait(&M.kfull[ik % NK], (ik / NK) & 1u)) break;
-      float acc;
-      if (cm == 0u && cf == 0xFFFFFFFFu) {
-        acc = dot27(P.kF, vA, vB, vC);
-      } else if (cm == 0u && ca == 0xFFFFFFFFu) {
-        acc = dot27(P.kA, vA, vB, vC);
-      } else if ((cm | cf | ca) == 0u) {
-        acc = dot27(P.kS, vA, vB, vC);
-      } else {
-        const float sS = dot27(P.kS, vA, vB, vC), sF = dot27(P.kF, vA, vB, vC), sA = dot27(P.kA, vA, vB, vC);
-        acc = ((cf >> lane) & 1u) ? sF : (((ca >> lane) & 1u) ? sA : sS);
-        if ((cm >> lane) & 1u) {
-          const uint32_t *kw = (const uint32_t *)(kb + M.kstart[ik % NK]) + crank;
-          float K[28];
-          if (BF16C) {
-#pragma unroll
-            for (int q = 0; q < 14; ++q) {
-              const uint32_t wv = kw[q * ccp];
-              K[2 * q] = __uint_as_float(wv << 16);
-              K[2 * q + 1] = __uint_as_float(wv & 0xFFFF0000u);
-            }
-          } else {
-#pragma unroll
-            for (int a = 0; a < 27; ++a) K[a] = __uint_as_float(kw[a * ccp]);
-          }
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) {
-            s0 = fmaf(K[q], vA[q], s0);
-            s1 = fmaf(K[9 + q], vB[q], s1);
-            s2 = fmaf(K[18 + q], vC[q], s2);
-          }
-          acc = (s0 + s1) + s2;
-        }
+      if (lane == 0) mbar_arrive(&M.empty[sl]);
+      ++vc;
+      acc0 *= sc;
+      acc1 *= sc;
+      if (has_x1) {
+        acc0 = fmaf(c1, x1a, c2 * acc0);
+        acc1 = fmaf(c1, x1b, c2 * acc1);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&M.kempty[ik % NK]);
-      kc += 1u;
-      acc *= sc;
-      if (has_x1) acc = fmaf(c1, cx1, c2 * acc);
-      if (inside) P.out[(long long)z * nxy + (long long)gy * P.dm.nx + gx] = acc;
-      if (P.pooled) {
-        if ((z & 1) == 0) {
-          psum = acc;
+      if (inside) {
+        float *o = P.out + (long long)z0 * nxy + (long long)gy * P.dm.nx + gx;
+        o[0] = acc0;
+        if (two) o[nxy] = acc1;
+      }
+      if (P.pooled) {  // z0 is even: the step holds a z pair
+        float tp = acc0 + acc1;
+        tp += __shfl_xor_sync(0xffffffffu, tp, 1);
+        const int buf = (int)(pround & 1u);
+        if (warp & 1) {
+          // odd row: hand the x/z-pooled sums to the even row of the pair
+          if (pround >= 2u && !wait(&M.pempty[pair * 2 + buf], ((pround >> 1) - 1u) & 1u)) break;
+          if (!(lane & 1)) M.poolx[pair * 2 + buf][lane >> 1] = tp;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&M.pfull[pair * 2 + buf]);
         } else {
-          float t = psum + acc;
-          t += __shfl_xor_sync(0xffffffffu, t, 1);
-          const int buf = (int)(pround & 1u);
-          if (warp & 1) {
-            // odd row: hand the x/z-pooled sums to the even row of the pair
-            if (pround >= 2u && !wait(&M.pempty[pair * 2 + buf], ((pround >> 1) - 1u) & 1u)) break;
-            if (!(lane & 1)) M.poolx[pair * 2 + buf][lane >> 1] = t;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&M.pfull[pair * 2 + buf]);
-          } else {
-            pend = true;
-            pend_r = pround;
-            pend_t = t;
-            pend_idx = (inside && !(lane & 1)) ? ((long long)(z >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1) : -1;
-          }
-          ++pround;
+          pend = true;
+          pend_r = pround;
+          pend_t = tp;
+          pend_idx = (inside && !(lane & 1)) ? ((long long)(z0 >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1) : -1;
         }
+        ++pround;
       }
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        vA[q] = vB[q];
-        vB[q] = vC[q];
+        vA[q] = vC[q];
+        vB[q] = vD[q];
       }
-      cm = nm;
-      cf = nf;
-      ca = na;
-      crank = nrank;
-      ccp = ncp;
-      cx1 = nx1;
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&M.dempty[m % ND]);
   }
   if (ok) flush_pool();
 }
@@ -709,14 +698,18 @@ int grid_for_units(long long units, int cap) {
 
 template <bool BF16C>
 int stream_occupancy() {
-  static int occ = 0;
-  if (!occ) {
+  // per device: the dynamic shared-memory opt-in is a per-device function attribute
+  static int occ[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!occ[dev]) {
     int o = 0;
     cudaFuncSetAttribute(k_cconv_stream<BF16C>, cudaFuncAttributeMaxDynamicSharedMemorySize, KCfg<BF16C>::SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C>, NTHREADS, KCfg<BF16C>::SMEM);
-    occ = o < 1 ? 1 : o;
+    occ[dev] = o < 1 ? 1 : o;
   }
-  return occ;
+  return occ[dev];
 }
 
 // cuTensorMapEncodeTiled, looked up through the runtime so that the library
@@ -738,12 +731,12 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool encode_map(CUtensorMap *m, const float *base, Dims d, int bw, int bh) {
+bool encode_map(CUtensorMap *m, const float *base, Dims d, int bw, int bh, int bd) {
   const EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
   cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4u, (cuuint64_t)d.nx * (cuuint64_t)d.ny * 4u};
-  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
+  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bd};
   cuuint32_t es[3] = {1u, 1u, 1u};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -787,8 +780,8 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s) {
   StreamParams P;
   memset(&P, 0, sizeof(P));
-  if (!encode_map(&P.tv, v, dm, BXW, BYH)) return -1;
-  if (c12 && !encode_map(&P.tx1, x1, dm, TX, TY)) return -1;
+  if (!encode_map(&P.tv, v, dm, BXW, BYH, 2)) return -1;
+  if (c12 && !encode_map(&P.tx1, x1, dm, TX, TY, 2)) return -1;
   P.dm = dm;
   P.ntx = (dm.nx + TX - 1) / TX;
   P.ntiles = P.ntx * ((dm.ny + TY - 1) / TY);

@@ -70,36 +70,94 @@ __device__ __forceinline__ float2 img_at(const ImgSrc &im, const Dims &dm, int x
 }
 
 // ---------------------------------------------------------------------------
-// Aff (Sec. 4.2.1): partial sums of sum_l (wf[l] nF(p+l) + wa[l] nA(p+l)) for
-// the two Aff blocks of a level, in FP64 per block.
+// Aff (Sec. 4.2.1) through exact window sums.  The image outside the grid is
+// solid, I = (0, 0, 1), so for the fluid and air channels
+//   sum_p I_c(p + l) = sum of I_c(q) over the cells q of the grid with q - l
+//                      also inside, i.e. all cells except the face plane that
+//                      the offset l pushes out of the grid.
+// The whole reduction therefore needs, per channel, the counts over the 4x4x4
+// boundary classes of a cell (per axis: interior, first plane, last plane,
+// both when the axis has one plane); the 27 window sums follow by inclusion.
+// The counts are exact integers, so their summation order does not matter;
+// the final 27-term sums are FP64.  The solid channel is folded into the
+// weights (AffW).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRedThreads) k_aff_partial(ImgSrc im, Dims dm, const AffW *__restrict__ a1,
-                                                               const AffW *__restrict__ a2, double *__restrict__ part) {
-  const long long n = dm.n();
-  double v[2] = {0.0, 0.0};
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(p, dm, x, y, z);
-    float s1 = 0.f, s2 = 0.f;
-#pragma unroll
-    for (int l = 0; l < 27; ++l) {
-      const float2 f = img_at(im, dm, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
-      s1 += a1->wf[l] * f.x + a1->wa[l] * f.y;
-      s2 += a2->wf[l] * f.x + a2->wa[l] * f.y;
+__device__ __forceinline__ int edge_class(int q, int n) { return (q == 0 ? 1 : 0) | (q == n - 1 ? 2 : 0); }
+
+__global__ void __launch_bounds__(256) k_aff_counts(ImgSrc im, Dims dm, unsigned long long *__restrict__ cnt) {
+  __shared__ unsigned long long sc[128];  // [boundary class 64][channel 2]
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) sc[i] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long rows = (long long)dm.ny * dm.nz;
+  unsigned long long inf = 0ull, ina = 0ull;  // interior cells of this thread
+  for (long long r = (long long)blockIdx.x * nw + warp; r < rows; r += (long long)gridDim.x * nw) {
+    const int y = (int)(r % dm.ny), z = (int)(r / dm.ny);
+    const int cyz = 4 * edge_class(y, dm.ny) + 16 * edge_class(z, dm.nz);
+    const long long base = r * dm.nx;
+    for (int x = lane; x < dm.nx; x += 32) {
+      uint32_t f, a;
+      if (im.lab) {
+        const uint8_t l = im.lab[base + x];
+        f = l == kFluid;
+        a = l == kAir;
+      } else {
+        const ushort2 c = im.counts[base + x];
+        f = c.x;
+        a = c.y;
+      }
+      const int cls = cyz + edge_class(x, dm.nx);
+      if (cls == 0) {
+        inf += f;
+        ina += a;
+      } else {
+        if (f) atomicAdd(&sc[2 * cls], (unsigned long long)f);
+        if (a) atomicAdd(&sc[2 * cls + 1], (unsigned long long)a);
+      }
     }
-    v[0] += s1;
-    v[1] += s2;
   }
-  block_sum_store<2>(v, part + (size_t)blockIdx.x * 2);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    inf += __shfl_down_sync(0xffffffffu, inf, o);
+    ina += __shfl_down_sync(0xffffffffu, ina, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&sc[0], inf);
+    atomicAdd(&sc[1], ina);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 128; i += blockDim.x)
+    if (sc[i]) atomicAdd(&cnt[i], sc[i]);
 }
 
-__global__ void k_aff_final(const double *part, int nblocks, const AffW *a1, const AffW *a2, long long n,
-                            double *out) {
-  double t[2];
-  reduce_partials<2>(part, nblocks, t);
+// A cell of boundary class c (bit 0: first plane, bit 1: last plane) along an
+// axis stays inside the window sum of offset o unless o pushes it out.
+__device__ __forceinline__ bool keeps(int c, int o) { return !((o == 1 && (c & 1)) || (o == -1 && (c & 2))); }
+
+__global__ void k_aff_from_counts(const unsigned long long *__restrict__ cnt, const AffW *a1, const AffW *a2,
+                                  long long n, double *out) {
+  __shared__ double t1[27], t2[27];
+  const int l = threadIdx.x;
+  if (l < 27) {
+    const int ox = l % 3 - 1, oy = (l / 3) % 3 - 1, oz = l / 9 - 1;
+    double sf = 0.0, sa = 0.0;  // exact: integer counts below 2^53
+    for (int c = 0; c < 64; ++c) {
+      if (!(keeps(c & 3, ox) && keeps((c >> 2) & 3, oy) && keeps(c >> 4, oz))) continue;
+      sf += (double)cnt[2 * c];
+      sa += (double)cnt[2 * c + 1];
+    }
+    t1[l] = (double)a1->wf[l] * sf + (double)a1->wa[l] * sa;
+    t2[l] = (double)a2->wf[l] * sf + (double)a2->wa[l] * sa;
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
-  out[0] = a1->bconst + t[0] / (27.0 * (double)n);
-  out[1] = a2->bconst + t[1] / (27.0 * (double)n);
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = 0; i < 27; ++i) {
+    s1 += t1[i];
+    s2 += t2[i];
+  }
+  out[0] = a1->bconst + s1 / (27.0 * (double)n);
+  out[1] = a2->bconst + s2 / (27.0 * (double)n);
 }
 
 // ---------------------------------------------------------------------------
@@ -285,9 +343,13 @@ void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *
                 double *out, cudaStream_t s) {
   ImgSrc im{lab, counts};
   if (counts) im.lab = nullptr;
-  const int nb = red_blocks(dm.n());
-  k_aff_partial<<<nb, kRedThreads, 0, s>>>(im, dm, a1, a2, part);
-  k_aff_final<<<1, kRedThreads, 0, s>>>(part, nb, a1, a2, dm.n(), out);
+  unsigned long long *cnt = (unsigned long long *)part;  // 128 counters in the reduction scratch
+  cudaMemsetAsync(cnt, 0, 128 * sizeof(unsigned long long), s);
+  const long long rows = (long long)dm.ny * dm.nz;
+  long long g = (rows + 7) / 8;
+  if (g > 148LL * 8) g = 148LL * 8;
+  k_aff_counts<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(im, dm, cnt);
+  k_aff_from_counts<<<1, 32, 0, s>>>(cnt, a1, a2, dm.n(), out);
 }
 
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,

@@ -126,11 +126,13 @@ struct Dims {
   __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
 };
 
+// Grids hold fewer than 2^31 cells, so the index arithmetic is 32-bit.
 __device__ __forceinline__ void cell_xyz(long long p, const Dims &d, int &x, int &y, int &z) {
-  x = (int)(p % d.nx);
-  long long t = p / d.nx;
-  y = (int)(t % d.ny);
-  z = (int)(t / d.ny);
+  const unsigned q = (unsigned)p, nx = (unsigned)d.nx, ny = (unsigned)d.ny;
+  const unsigned t = q / nx;
+  x = (int)(q - t * nx);
+  y = (int)(t % ny);
+  z = (int)(t / ny);
 }
 
 }  // namespace nps
