@@ -314,6 +314,177 @@ __global__ void __launch_bounds__(NT) k_generate(const uint8_t *__restrict__ lab
 }
 
 // ---------------------------------------------------------------------------
+// Setup 2 on the tensor cores (levels whose image counts are exact in BF16):
+// the kernels of the mixed cells of a unit, 128 cells per tcgen05 MMA
+//   D[128 cells x 32 taps] = F[128 x 64 features] . W^T[64 x 32]  (FP32 in TMEM),
+// the feature rows F = (fluid counts of the 27 window cells, air counts, 1)
+// written into TMEM by the threads, W (folded CConv weights and bias, K-major
+// in shared memory, NSPLIT BF16 terms: 1 in the BF16 form, 3 in the FP32
+// form) from the host.  Thread i owns TMEM lane i and mixed cell i of the
+// chunk; it reads its 32 results back and writes them tap-major into the
+// plane's block, rounded to BF16 in the BF16 form.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t image_code_bf16(const uint8_t *lab, const ushort2 *counts, const Dims &d, int x,
+                                                    int y, int z) {
+  if (x < 0 || y < 0 || z < 0 || x >= d.nx || y >= d.ny || z >= d.nz) return 0u;
+  const long long p = ((long long)z * d.ny + y) * d.nx + x;
+  if (lab) {
+    const uint8_t l = __ldg(lab + p);
+    return l == kFluid ? 0x00003F80u : (l == kAir ? 0x3F800000u : 0u);
+  }
+  const ushort2 c = counts[p];
+  return umma::bf16_bits_small(c.x) | (umma::bf16_bits_small(c.y) << 16);
+}
+
+constexpr int kGenTmemCols = 64;  // A: columns [0, 32), D: [32, 64)
+
+template <int NSPLIT, bool BF16>
+__global__ void __launch_bounds__(NT) k_generate_tc(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                                    Dims d, const uint8_t *__restrict__ w0,
+                                                    const uint8_t *__restrict__ w1, int nblk,
+                                                    const PlaneDesc *__restrict__ desc, uint32_t *__restrict__ cache0,
+                                                    uint32_t *__restrict__ cache1, int *err) {
+  using namespace umma;
+  constexpr int KW = BF16 ? 14 : 27;
+  __shared__ __align__(1024) uint8_t sW[2][NSPLIT * kBBytes];
+  __shared__ PlaneDesc sd[ZCG];
+  __shared__ uint16_t cell_of[ZCG * NT];  // unit-local cache entry -> plane << 7 | cell (0xFFFF: padding)
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    const uint4 *src0 = (const uint4 *)w0;
+    const uint4 *src1 = (const uint4 *)w1;
+    uint4 *dst0 = (uint4 *)sW[0];
+    uint4 *dst1 = (uint4 *)sW[1];
+    for (int i = tid; i < NSPLIT * kBBytes / 16; i += NT) {
+      dst0[i] = src0[i];
+      if (nblk > 1) dst1[i] = src1[i];
+    }
+  }
+  if (warp == 0) {
+    tmem_alloc(&s_tmem, kGenTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
+  fence_proxy_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t idesc = idesc_bf16(kTileM, kN);
+  uint32_t phase = 0u;
+  bool aborted = false;
+  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + ZCG - 1) / ZCG;
+  const int ntiles = ntx * nty;
+  const long long units = (long long)ntiles * nch;
+  const uint32_t below = lanemask_lt();
+  for (long long u = blockIdx.x; u < units && !aborted; u += gridDim.x) {
+    const int t = (int)(u % ntiles), c = (int)(u / ntiles);
+    const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
+    const int zs = c * ZCG, nzu = min(ZCG, d.nz - zs);
+    {
+      const uint32_t *src = (const uint32_t *)(desc + (size_t)t * d.nz + zs);
+      uint32_t *dsd = (uint32_t *)sd;
+      for (int i = tid; i < nzu * 20; i += NT) dsd[i] = src[i];
+    }
+    __syncthreads();
+    const uint32_t base = sd[0].off;
+    const int total = (int)(sd[nzu - 1].off + sd[nzu - 1].cpad - base);  // entries of the unit, padding included
+    if (total > 0) {
+      for (int i = tid; i < total; i += NT) cell_of[i] = 0xFFFFu;
+      __syncthreads();
+      for (int j = 0; j < nzu; ++j) {
+        const uint32_t m = sd[j].row[warp].x;
+        if ((m >> lane) & 1u) {
+          const uint32_t rank = __popc(m & below) + ((sd[j].rowbase >> (8 * warp)) & 0xFFu);
+          cell_of[sd[j].off - base + rank] = (uint16_t)((j << 7) | tid);
+        }
+      }
+      __syncthreads();
+      for (int c0 = 0; c0 < total && !aborted; c0 += NT) {
+        const int li = c0 + tid;
+        const uint32_t e = li < total ? cell_of[li] : 0xFFFFu;
+        const bool valid = e != 0xFFFFu;
+        uint32_t fw[32];
+        int j = 0;
+        if (valid) {
+          j = (int)(e >> 7);
+          const int cell = (int)(e & 127u);
+          const int x = x0 + (cell & 31), y = y0 + (cell >> 5), z = zs + j;
+          uint32_t win[27];
+#pragma unroll
+          for (int l = 0; l < 27; ++l)
+            win[l] = image_code_bf16(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
+          build_feature_words(win, fw);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) fw[q] = 0u;
+        }
+        tmem_st32(tmem + lane_off, fw);
+        tmem_wait_st();
+        for (int b = 0; b < nblk; ++b) {
+          fence_before_sync();
+          __syncthreads();
+          if (tid == 0) {
+            fence_after_sync();
+#pragma unroll
+            for (int sp = 0; sp < NSPLIT; ++sp)
+#pragma unroll
+              for (int kk = 0; kk < kK / 16; ++kk) {
+                const uint64_t bd = smem_desc_kmajor(smem_u32(sW[b] + sp * kBBytes + kk * 2 * kLBO), kLBO, kSBO);
+                mma_bf16_ts(tmem + 32, tmem + kk * 8, bd, idesc, (sp | kk) != 0);
+              }
+            umma_commit(&mbar);
+          }
+          const bool ok = mbar_wait_bounded(&mbar, phase, umma::kWaitNs);
+          phase ^= 1u;
+          if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+          }
+          fence_after_sync();
+          uint32_t kr[32];
+          tmem_ld32(tmem + 32 + lane_off, kr);
+          tmem_wait_ld();
+          if (valid) {
+            const PlaneDesc &pd = sd[j];
+            const uint32_t rank = (uint32_t)li - (pd.off - base);
+            uint32_t *dst = (b == 0 ? cache0 : cache1) + (size_t)pd.off * KW + rank;
+            if (BF16) {
+#pragma unroll
+              for (int jj = 0; jj < 14; ++jj) {
+                const float k0 = __uint_as_float(kr[2 * jj]);
+                const float k1 = 2 * jj + 1 < 27 ? __uint_as_float(kr[2 * jj + 1]) : 0.f;
+                dst[(size_t)jj * pd.cpad] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(k0)) |
+                                            ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(k1)) << 16);
+              }
+            } else {
+#pragma unroll
+              for (int a = 0; a < 27; ++a) dst[(size_t)a * pd.cpad] = kr[a];
+            }
+          }
+        }
+        fence_before_sync();
+        __syncthreads();  // the next chunk overwrites A and D
+      }
+    }
+    __syncthreads();  // sd and cell_of are reloaded for the next unit
+  }
+  if (aborted) {
+    if (tid == 0 && err) atomicExch(err, 1);
+    (void)mbar_wait_bounded(&mbar, phase, umma::kWaitNs);  // an MMA batch possibly still in flight
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kGenTmemCols);
+}
+
+// ---------------------------------------------------------------------------
 // Per iteration: the streamed z-marching CConv.
 // ---------------------------------------------------------------------------
 struct StreamParams {
@@ -329,6 +500,7 @@ struct StreamParams {
   const double *c12;    // non-null: out = c1 x1 + c2 CConv(v)
   const SolveState *st;
   int *err;
+  int mode;             // which outputs are computed (STREAM_MODE_*)
   float kS[27], kF[27], kA[27];  // kernels of the pure-solid, pure-fluid, pure-air windows
 };
 
@@ -361,16 +533,23 @@ __device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9
 }
 
 // One output cell: the classes of the warp's row decide which (warp-uniform)
-// constant-kernel sums are needed; a mixed lane reads its kernel from the block.
+// constant-kernel sums are needed; a mixed lane reads its kernel from the
+// block.  Lanes that need no output (mode) get 0: with a zero input off fluid
+// (level-1 CConv1) a pure-air or pure-solid window sums to exactly 0, and the
+// level-1 CConv2 output is used on fluid cells only (Sec. 4.2 restriction).
 template <bool BF16C>
 __device__ __forceinline__ float cconv_cell(const StreamParams &P, uint4 rw, uint32_t rank, uint32_t cp,
                                             const uint32_t *kblk, int lane, const float (&vA)[9],
                                             const float (&vB)[9], const float (&vC)[9]) {
-  const uint32_t cm = rw.x, cf = rw.y, ca = rw.z;
+  uint32_t need = 0xFFFFFFFFu;
+  if (P.mode == STREAM_MODE_ZERO_PURE) need = rw.x | rw.y;
+  else if (P.mode == STREAM_MODE_FLUID_ONLY) need = rw.w;
+  const uint32_t cm = rw.x & need, cf = rw.y & need, ca = rw.z & need;
+  const uint32_t cs = ~(rw.x | rw.y | rw.z) & need;  // pure-solid windows (and lanes outside the grid)
   if (cf == 0xFFFFFFFFu) return dot27(P.kF, vA, vB, vC);
   if (ca == 0xFFFFFFFFu) return dot27(P.kA, vA, vB, vC);
-  const uint32_t cs = ~(cm | cf | ca);  // pure-solid windows (and lanes outside the grid)
   if (cs == 0xFFFFFFFFu) return dot27(P.kS, vA, vB, vC);
+  if ((cm | cf | ca | cs) == 0u) return 0.f;
   float acc = 0.f;
   if (cf) {
     const float t = dot27(P.kF, vA, vB, vC);
@@ -567,7 +746,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
   const uint32_t below = lanemask_lt();
   const int pair = warp >> 1;
   const int vrow = warp * BXW + lane + 3;  // box index of the cell (x-1, y-1) in a plane (box starts at x0-4, y0-1)
-  uint32_t vc = 0;                         // slots consumed
+  uint32_t sl = 0, sph = 0;                // next slot and the parity of its phase
   uint32_t pround = 0;                     // pooling rounds so far
   // pooling of the even row of a pair waits for the odd row's sum of round pend_r
   float pend_t = 0.f;
@@ -595,8 +774,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
     if (!wait(&M.dfull[m % ND], (m / ND) & 1)) break;
     float vA[9], vB[9];
     {  // prologue slot: planes zs-1, zs
-      const uint32_t sl = vc % RV;
-      if (!wait(&M.full[sl], (vc / RV) & 1u)) break;
+      if (!wait(&M.full[sl], sph)) break;
       const float *pl = (const float *)(vs + sl * SLOT);
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
@@ -606,15 +784,21 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
-      ++vc;
+      if (++sl == RV) {
+        sl = 0;
+        sph ^= 1u;
+      }
     }
+    float *op = P.out + (long long)U.zs * nxy + (long long)gy * P.dm.nx + gx;
+    long long pidx = ((long long)(U.zs >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1);
+    const long long pstep = (long long)cxn * cyn;
+    const bool pown = inside && !(lane & 1);  // even lane of an even row writes the pooled value
     const int T = (U.nzu + 1) >> 1;
     for (int t = 0; t < T; ++t) {
-      const int j0 = 2 * t, z0 = U.zs + j0;
+      const int j0 = 2 * t;
       const bool two = j0 + 1 < U.nzu;
       flush_pool();
-      const uint32_t sl = vc % RV;
-      if (!wait(&M.full[sl], (vc / RV) & 1u)) break;
+      if (!wait(&M.full[sl], sph)) break;
       const uint8_t *slot = vs + sl * SLOT;
       const float *pl = (const float *)slot;
       float vC[9], vD[9];
@@ -644,7 +828,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
-      ++vc;
+      if (++sl == RV) {
+        sl = 0;
+        sph ^= 1u;
+      }
       acc0 *= sc;
       acc1 *= sc;
       if (has_x1) {
@@ -652,10 +839,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
         acc1 = fmaf(c1, x1b, c2 * acc1);
       }
       if (inside) {
-        float *o = P.out + (long long)z0 * nxy + (long long)gy * P.dm.nx + gx;
-        o[0] = acc0;
-        if (two) o[nxy] = acc1;
+        op[0] = acc0;
+        if (two) op[nxy] = acc1;
       }
+      op += 2 * nxy;
       if (P.pooled) {  // z0 is even: the step holds a z pair
         float tp = acc0 + acc1;
         tp += __shfl_xor_sync(0xffffffffu, tp, 1);
@@ -670,9 +857,10 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
           pend = true;
           pend_r = pround;
           pend_t = tp;
-          pend_idx = (inside && !(lane & 1)) ? ((long long)(z0 >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1) : -1;
+          pend_idx = pown ? pidx : -1;
         }
         ++pround;
+        pidx += pstep;
       }
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
@@ -764,22 +952,36 @@ void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t
 }
 
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
-                     const void *desc, void *cache0, void *cache1, int num_sms, cudaStream_t s) {
+                     const void *desc, void *cache0, void *cache1, const uint8_t *wsplit0, const uint8_t *wsplit1,
+                     int nsplit, int *err, int num_sms, cudaStream_t s) {
   const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + ZCG - 1) / ZCG);
+  const PlaneDesc *pd = (const PlaneDesc *)desc;
+  if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3)
+    const int g = grid_for_units(units, num_sms * 4);
+    if (nsplit == 1)
+      k_generate_tc<1, true><<<g, NT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+                                              (uint32_t *)cache1, err);
+    else if (bf16)
+      k_generate_tc<3, true><<<g, NT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+                                              (uint32_t *)cache1, err);
+    else
+      k_generate_tc<3, false><<<g, NT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+                                               (uint32_t *)cache1, err);
+    return;
+  }
   const int g = grid_for_units(units, num_sms * 8);
   if (bf16)
-    k_generate<true><<<g, NT, 0, s>>>(lab, counts, d, w, nblk, (const PlaneDesc *)desc, (uint32_t *)cache0,
-                                      (uint32_t *)cache1);
+    k_generate<true><<<g, NT, 0, s>>>(lab, counts, d, w, nblk, pd, (uint32_t *)cache0, (uint32_t *)cache1);
   else
-    k_generate<false><<<g, NT, 0, s>>>(lab, counts, d, w, nblk, (const PlaneDesc *)desc, (uint32_t *)cache0,
-                                       (uint32_t *)cache1);
+    k_generate<false><<<g, NT, 0, s>>>(lab, counts, d, w, nblk, pd, (uint32_t *)cache0, (uint32_t *)cache1);
 }
 
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
-                        const float *vscale, float *out, float *pooled, const float *x1, const double *c12,
+                        const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s) {
   StreamParams P;
   memset(&P, 0, sizeof(P));
+  P.mode = mode;
   if (!encode_map(&P.tv, v, dm, BXW, BYH, 2)) return -1;
   if (c12 && !encode_map(&P.tx1, x1, dm, TX, TY, 2)) return -1;
   P.dm = dm;

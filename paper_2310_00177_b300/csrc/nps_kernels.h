@@ -78,12 +78,20 @@ int cached_entry_bytes(bool bf16);     // bytes of one cached kernel
 // totals[0] += cache entries (blocks padded to 4), totals[1] += mixed cells
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
                      int num_sms, cudaStream_t s);
+// wsplit0/1: the tensor-core weight splits of the two blocks (nsplit BF16
+// terms each) to generate on the tensor cores, or null for CUDA cores
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
-                     const void *desc, void *cache0, void *cache1, int num_sms, cudaStream_t s);
-// kfix: the 81 constants K^S, K^F, K^A of the pure windows; returns -1 if a
-// tensor map cannot be encoded
+                     const void *desc, void *cache0, void *cache1, const uint8_t *wsplit0, const uint8_t *wsplit1,
+                     int nsplit, int *err, int num_sms, cudaStream_t s);
+// kfix: the 81 constants K^S, K^F, K^A of the pure windows.  mode: which
+// outputs are computed, the others written as 0: STREAM_MODE_ALL; _ZERO_PURE
+// (the input is zero off fluid, so pure-air and pure-solid windows give
+// exactly 0: level-1 CConv1); _FLUID_ONLY (only fluid cells are used: the
+// level-1 CConv2 inside the network).  Returns -1 if a tensor map cannot be
+// encoded.
+enum { STREAM_MODE_ALL = 0, STREAM_MODE_ZERO_PURE = 1, STREAM_MODE_FLUID_ONLY = 2 };
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
-                        const float *vscale, float *out, float *pooled, const float *x1, const double *c12,
+                        const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s);
 void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
 

@@ -478,14 +478,15 @@ void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const 
 // read (in) or interpolated (coarse), optional fused pooling, optional fused
 // combination out = c1 x1 + c2 CConv(...).
 void cconv_cached(npsolve *h, Dims d1, int lvl, int type, const float *in, const float *vscale, float *out,
-                  float *pooled, const float *x1, const double *c12, const SolveState *st, cudaStream_t s) {
+                  float *pooled, const float *x1, const double *c12, const SolveState *st, cudaStream_t s,
+                  int mode = STREAM_MODE_ALL) {
   Workspace &w = h->ws;
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   if (launch_cconv_stream(h->cfg.precision == NPSOLVE_BF16, level_dims(d1, lvl), h->kfix_host.data() + (size_t)idx * 81,
-                          w.kdesc[lvl], w.kcache[idx], in, vscale, out, pooled, x1, c12, st, h->umma_err, h->num_sms,
-                          s))
+                          w.kdesc[lvl], w.kcache[idx], in, vscale, out, pooled, x1, c12, mode, st, h->umma_err,
+                          h->num_sms, s))
     h->stream_err = true;
 }
 
@@ -516,7 +517,8 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     const float *in = l == 1 ? r : w.r1[l];
     const float *vs = l == 1 ? vscale : nullptr;
     if (cached) {
-      cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s);
+      cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s,
+                   l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL);
     } else if (tensor_level(h, l)) {
       cconv_tc(h, lab, d1, l, 1, in, nullptr, vs, l == 1, w.x1[l], w.r1[l + 1], st, s);
     } else {
@@ -530,7 +532,9 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   {
     const float *in = L == 1 ? r : w.r1[L];
     const float *vs = L == 1 ? vscale : nullptr;
-    if (cached) cconv_cached(h, d1, L, 1, in, vs, w.x1[L], nullptr, nullptr, nullptr, st, s);
+    if (cached)
+      cconv_cached(h, d1, L, 1, in, vs, w.x1[L], nullptr, nullptr, nullptr, st, s,
+                   L == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL);
     else if (tensor_level(h, L)) cconv_tc(h, lab, d1, L, 1, in, nullptr, vs, L == 1, w.x1[L], nullptr, st, s);
     else cconv(h, lab, d1, L, 1, in, vs, L == 1, w.x1[L], st, s);
   }
@@ -554,7 +558,9 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
         cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s);
         continue;
       }
-      cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
+      // level 1: only the fluid cells of x2 enter z (the output restriction)
+      cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s,
+                   STREAM_MODE_FLUID_ONLY);
     } else if (tensor_level(h, l) && !unfused) {
       cconv_tc(h, lab, d1, l, 2, nullptr, coarse, nullptr, 0, w.x2[l], nullptr, st, s);
     } else {
@@ -632,8 +638,13 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
           w.kcap[idx] = cap;
         }
       }
+      // kernel generation on the tensor cores where the image counts are exact in BF16 (<= 64 fine cells)
+      const bool tc = l <= 3;
+      const size_t wb = (size_t)umma_weight_bytes(3);
       launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->cw + l * 2,
-                      nblk, w.kdesc[l], w.kcache[l * 2], nblk > 1 ? w.kcache[l * 2 + 1] : nullptr, h->num_sms, s);
+                      nblk, w.kdesc[l], w.kcache[l * 2], nblk > 1 ? w.kcache[l * 2 + 1] : nullptr,
+                      tc ? h->uw + (size_t)(l * 2) * wb : nullptr, tc ? h->uw + (size_t)(l * 2 + 1) * wb : nullptr,
+                      h->nsplit, h->umma_err, h->num_sms, s);
       h->launches += 1;
     }
   }

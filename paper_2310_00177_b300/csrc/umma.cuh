@@ -146,6 +146,21 @@ __device__ __forceinline__ uint32_t bf16_bits_small(unsigned n) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)n));
 }
 
+// 32 packed BF16 pairs of the feature row F[0..63] of a cell from its 27
+// window codes w[l] (l = 9(dz+1) + 3(dy+1) + (dx+1)):
+//   F[j] = fluid(l = j) for j < 27, air(l = j - 27) for 27 <= j < 54,
+//   F[54] = 1 (bias), F[55..63] = 0.
+__device__ __forceinline__ void build_feature_words(const uint32_t (&w)[27], uint32_t (&fw)[32]) {
+#pragma unroll
+  for (int c = 0; c < 13; ++c) fw[c] = __byte_perm(w[2 * c], w[2 * c + 1], 0x5410);  // fluid pairs
+  fw[13] = __byte_perm(w[26], w[0], 0x7610);                                          // fluid(26), air(0)
+#pragma unroll
+  for (int c = 14; c < 27; ++c) fw[c] = __byte_perm(w[2 * c - 27], w[2 * c - 26], 0x7632);  // air pairs
+  fw[27] = 0x00003F80u;  // F[54] = 1.0, F[55] = 0
+#pragma unroll
+  for (int c = 28; c < 32; ++c) fw[c] = 0u;
+}
+
 }  // namespace umma
 
 }  // namespace nps
