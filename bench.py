@@ -48,10 +48,16 @@ METRIC = "ms per 256^3 solve to 1e-6 rel. residual (BF16 served form)"
 WEIGHTS_FILE = os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32")
 ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
 
+# DRAM bytes (read + write) per level-1 CConv launch of the 256^3 workload,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
+# CConv1 and CConv2 launches of one iteration; profiles/); None when the
+# kernel has changed since the counters were taken.
+TRAFFIC_L1 = None
+
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
 # (inputs read once, outputs written once).
 BYTES_PER_CELL = {
-    "cconv_l1": 4 + 1 + 4,      # v, labels -> out
+    "cconv_l1": 4 + 0.625 + 4,  # v, descriptors -> out (+ cached kernels, see below)
     "lap_alpha": 4 + 1 + 4 + 4,  # d, labels, r -> q
     "update": 8 + 8 + 4 + 4 + 4 + 4,  # x r/w (FP64), r r/w, d, q
     "ortho_dir": 4 + 4 + 4 + 4,  # z, d1, d2 -> d
@@ -308,18 +314,18 @@ def main():
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms / max(dom_launches, 1) / 1e3
     if dom == "cconv_l1":
-        # the level-1 CConv of the cached path is a 27-point stencil: per cell it
-        # reads the input (4 B) and the label (1 B), writes the output (4 B) and,
-        # for the cells with a mixed image window, reads the cached kernel
-        # (64 B BF16); the pooled output (CConv1) or interpolated input (CConv2)
-        # adds 0.5 B.  Averaged over the two launches of an iteration.
+        # the level-1 CConv (TMA-streamed z-march): per cell it reads the input
+        # (4 B) and the plane descriptors (80 B per 128 cells), for the cells
+        # with a mixed image window the cached kernel (56 B, BF16), and writes
+        # the output (4 B); CConv1 also writes the pooled output (0.5 B).
+        # Averaged over the two launches of an iteration.
         mixed = sol.mixed_cells(1)
         frac = mixed / n if mixed >= 0 else 0.0
-        bpc = 9.5 + 64.0 * frac
+        bpc = 4 + 80 / 128 + 56.0 * frac + 4 + 0.25
         achieved = bpc * n / avg_s / 1e9
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_cconv_stencil<bf16> (level-1 CConv, cached kernels)",
+                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1 + CConv2, TMA-streamed)",
                 "algorithmic": f"{bpc:.2f} B/cell x {n} cells (mixed-window fraction {frac:.4f})",
                 "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"] + " (hbm_gbs)"}
     else:

@@ -11,34 +11,41 @@
 // own kernel, generated once per solve and cached in HBM.
 //
 // Layout of one level:
-//   tiles of 32 (x) x 4 (y) cells; warp w of a CTA holds row w of a tile;
-//   one plane descriptor per (tile, z): one word per row of each of the bit
-//   masks "mixed window", "pure-fluid window", "pure-air window" and "the cell
-//   is fluid", and the place of the plane's kernel block in the cache;
+//   tiles of 32 (x) x 8 (y) cells;
+//   one plane descriptor per (tile, z): for each row of the tile the bit masks
+//   "mixed window", "pure-fluid window", "pure-air window" and "the cell is
+//   fluid" (bit = x within the tile), and the place of the plane's kernel
+//   block in the cache;
 //   a kernel block holds the kernels of the plane's mixed cells in the order of
-//   their bit index, tap-major: word (j, i) of a block with stride cpad is
-//   tap pair j of mixed cell i (BF16 form: taps 2j and 2j+1 as a BF16 pair,
-//   14 words per cell) or tap j of mixed cell i (FP32 form: 27 words per cell);
-//   cpad is the mixed count rounded up to 4, so that every block starts and
-//   ends on a 16-byte boundary.
+//   their bit index (row-major), tap-major: word (j, i) of a block with stride
+//   cpad is tap pair j of mixed cell i (BF16 form: taps 2j and 2j+1 as a BF16
+//   pair, 14 words per cell) or tap j of mixed cell i (FP32 form: 27 words per
+//   cell); cpad is the mixed count rounded up to 4, so that every block starts
+//   and ends on a 16-byte boundary.
 //
 // Per solve: k_classify (masks, block sizes, block offsets by one atomic per
-// unit of 32 planes) and k_generate (the FP32 contraction of the 54 image
-// features of a mixed cell, the arithmetic of the CUDA-core CConv, rounded to
-// BF16 in the BF16 form).
+// unit of 32 planes) and k_generate_tc / k_generate (the contraction of the 54
+// image features and the bias of each mixed cell with the folded weights, on
+// the tensor cores where the counts are exact in BF16, else on CUDA cores).
+// The BF16 form rounds every kernel value to BF16, the three constant ones
+// included.
 //
 // Per iteration: k_cconv_stream.  Each CTA marches units (a tile and a chunk
 // of planes) along z, two planes per step.  One producer warp (one thread)
 // loads per unit the plane descriptors (bulk copy, three buffers), and per
-// step, into one of RV slots completing on one mbarrier: the 40 x 6 x 2 TMA
-// box of the input planes z+1, z+2 (one-cell halo), the 32 x 4 x 2 box of x1
+// step, into one of RV slots completing on one mbarrier: the 40 x 10 x 2 TMA
+// box of the input planes z+1, z+2 (one-cell halo), the 32 x 8 x 2 box of x1
 // (combination only) and, with a bulk copy into a circular buffer, the two
-// planes' kernel blocks (contiguous in the cache).  Four consumer warps (one
-// per tile row) keep planes z-1, z in registers and compute the centres z and
-// z+1: the kernel of a pure window is one of three constants (kernel
-// parameters), that of a mixed window is read from its block.  Slots and
-// descriptor buffers are released with mbarrier arrivals; there is no CTA-wide
-// barrier in the march.  Fusions: scaling by the input normalisation (level-1
+// planes' kernel blocks (contiguous in the cache).  Four consumer warps each
+// own two rows of the tile: a thread keeps the 4-row x 3-column window
+// columns of planes z-1, z in registers and computes the 2 x 2 cells (rows y,
+// y+1; planes z, z+1) of its column, so a 2x2x2 pooling block is a pair of
+// adjacent lanes.  A row whose 32 windows are all pure takes a constant
+// kernel from the kernel parameters; any other row reads each lane's kernel
+// from shared memory (the class tables of the three constant kernels or the
+// cell's cached block), one code path for all lanes.  Slots and descriptor
+// buffers are released with mbarrier arrivals; there is no CTA-wide barrier
+// in the march.  Fusions: scaling by the input normalisation (level-1
 // CConv1), the 2x2x2 mean pooling of the output (CConv1), the combination
 // x = c1 x1 + c2 x2 (CConv2 at levels >= 2).
 //
@@ -63,34 +70,38 @@ using umma::mbar_init;
 using umma::mbar_wait_bounded;
 using umma::smem_u32;
 
-constexpr int TX = 32, TY = 4, NT = TX * TY;  // tile; warp w holds row w
+constexpr int TX = 32, TY = 8, NT = TX * TY;  // tile (x, y)
 constexpr int ZCG = 32;                       // planes per unit of the setup kernels
 constexpr int BXW = TX + 8;                   // vector box: x0-4 .. x0+35 (start on a 16-byte boundary)
 constexpr int BYH = TY + 2;                   // rows y0-1 .. y0+4
-constexpr int VPLANE = BXW * BYH * 4;         // 960 bytes per plane of the vector box
-constexpr int X1OFF = 2 * VPLANE;             // x1 box (32 x 4 x 2) in a slot
-constexpr int SLOT = 3072;                    // 1920 + 1024 bytes, 24 x 128
-constexpr int RV = 6;                         // step slots
+constexpr int VPLANE = BXW * BYH * 4;         // 1600 bytes per plane of the vector box
+constexpr int X1OFF = 2 * VPLANE;             // x1 box (32 x 8 x 2) in a slot
+constexpr int SLOT = 5376;                    // 3200 + 2048 bytes, 42 x 128
+constexpr int RV = 4;                         // step slots
 constexpr int ND = 3;                         // descriptor buffers (units)
-constexpr int kMetaBytes = 640;               // mbarriers, block positions, pooling exchange, abort flag
+constexpr int kMetaBytes = 640;               // mbarriers, block positions, class tables, abort flag
 constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s
 
 // Plane descriptor: per row w of the tile the masks {mixed window, pure-fluid
-// window, pure-air window, fluid cell} (bit = lane), then the kernel block.
+// window, pure-air window, fluid cell} (bit = x within the tile), then the
+// kernel block.
 struct PlaneDesc {
   uint4 row[TY];     // x: mixed, y: pure fluid, z: pure air, w: the cell is fluid
   uint32_t off;      // first cache entry of the plane's kernel block (a multiple of 4)
   uint32_t count;    // mixed cells of the plane
   uint32_t cpad;     // entries of the block: the mixed count rounded up to 4
-  uint32_t rowbase;  // byte w: mixed cells in rows 0..w-1 (the rank of row w's first one)
+  uint32_t pad0;
+  uint32_t rowbase[2];  // byte w: mixed cells in rows 0..w-1 (the rank of row w's first one)
+  uint32_t pad1[2];
 };
-static_assert(sizeof(PlaneDesc) == 80, "plane descriptor is 80 bytes");
+static_assert(sizeof(PlaneDesc) == 160, "plane descriptor is 160 bytes");
+constexpr int DWORDS = (int)sizeof(PlaneDesc) / 4;  // 40
 constexpr int DBUF = ZCG * (int)sizeof(PlaneDesc);  // one unit's descriptors
 
 template <bool BF16C>
 struct KCfg {
   static constexpr int EB = BF16C ? 56 : 108;        // bytes per cached kernel
-  static constexpr int CB = BF16C ? 24576 : 28672;   // circular kernel-block buffer (>= two full planes)
+  static constexpr int CB = BF16C ? 28672 : 55296;   // circular kernel-block buffer (>= two full planes)
   static constexpr int SMEM = RV * SLOT + ND * DBUF + CB + kMetaBytes;
 };
 
@@ -106,6 +117,11 @@ __device__ __forceinline__ uint32_t image_key(const uint8_t *lab, const ushort2 
   }
   const ushort2 c = counts[p];
   return (uint32_t)c.x | ((uint32_t)c.y << 16);
+}
+
+// Rank of row w's first mixed cell within the plane's block.
+__device__ __forceinline__ uint32_t row_base(const PlaneDesc &d, int w) {
+  return (d.rowbase[w >> 2] >> (8 * (w & 3))) & 0xFFu;
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -164,7 +180,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
                                                  Dims d, uint32_t full, PlaneDesc *__restrict__ desc,
                                                  unsigned *__restrict__ totals) {
-  __shared__ uint32_t sd[ZCG][20];
+  __shared__ uint32_t sd[ZCG][DWORDS];
   __shared__ uint32_t sbase;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + ZCG - 1) / ZCG;
@@ -206,16 +222,20 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
     if (threadIdx.x == 0) {
       uint32_t tot = 0, cnt = 0;
       for (int j = 0; j < nzu; ++j) {
-        uint32_t m = 0, rb = 0;
+        uint32_t m = 0, rb[2] = {0u, 0u};
         for (int w = 0; w < TY; ++w) {
-          rb |= m << (8 * w);
+          rb[w >> 2] |= m << (8 * (w & 3));
           m += __popc(sd[j][4 * w]);
         }
         const uint32_t cp = (m + 3u) & ~3u;
-        sd[j][16] = tot;
-        sd[j][17] = m;
-        sd[j][18] = cp;
-        sd[j][19] = rb;
+        sd[j][4 * TY] = tot;
+        sd[j][4 * TY + 1] = m;
+        sd[j][4 * TY + 2] = cp;
+        sd[j][4 * TY + 3] = 0u;
+        sd[j][4 * TY + 4] = rb[0];
+        sd[j][4 * TY + 5] = rb[1];
+        sd[j][4 * TY + 6] = 0u;
+        sd[j][4 * TY + 7] = 0u;
         tot += cp;
         cnt += m;
       }
@@ -224,9 +244,9 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
     }
     __syncthreads();
     uint32_t *dst = (uint32_t *)(desc + (size_t)t * d.nz + zs);
-    for (int i = threadIdx.x; i < nzu * 20; i += NT) {
-      uint32_t v = sd[i / 20][i % 20];
-      if (i % 20 == 16) v += sbase;
+    for (int i = threadIdx.x; i < nzu * DWORDS; i += NT) {
+      uint32_t v = sd[i / DWORDS][i % DWORDS];
+      if (i % DWORDS == 4 * TY) v += sbase;
       dst[i] = v;
     }
     __syncthreads();
@@ -262,14 +282,14 @@ __global__ void __launch_bounds__(NT) k_generate(const uint8_t *__restrict__ lab
     {
       const uint32_t *src = (const uint32_t *)(desc + (size_t)t * d.nz + zs);
       uint32_t *dsd = (uint32_t *)sd;
-      for (int i = threadIdx.x; i < nzu * 20; i += NT) dsd[i] = src[i];
+      for (int i = threadIdx.x; i < nzu * DWORDS; i += NT) dsd[i] = src[i];
     }
     __syncthreads();
     for (int j = 0; j < nzu; ++j) {
       const PlaneDesc &pd = sd[j];
       const uint32_t mw = pd.row[warp].x;
       if (!((mw >> lane) & 1u)) continue;
-      const uint32_t rank = __popc(mw & lanemask_lt()) + ((pd.rowbase >> (8 * warp)) & 0xFFu);
+      const uint32_t rank = __popc(mw & lanemask_lt()) + row_base(pd, warp);
       const int z = zs + j;
       float nf[27], na[27];
 #pragma unroll
@@ -337,9 +357,10 @@ __device__ __forceinline__ uint32_t image_code_bf16(const uint8_t *lab, const us
 }
 
 constexpr int kGenTmemCols = 64;  // A: columns [0, 32), D: [32, 64)
+constexpr int GT = 128;           // threads of the tensor-core generator: one per TMEM lane / MMA row
 
 template <int NSPLIT, bool BF16>
-__global__ void __launch_bounds__(NT) k_generate_tc(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+__global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
                                                     Dims d, const uint8_t *__restrict__ w0,
                                                     const uint8_t *__restrict__ w1, int nblk,
                                                     const PlaneDesc *__restrict__ desc, uint32_t *__restrict__ cache0,
@@ -348,16 +369,16 @@ __global__ void __launch_bounds__(NT) k_generate_tc(const uint8_t *__restrict__ 
   constexpr int KW = BF16 ? 14 : 27;
   __shared__ __align__(1024) uint8_t sW[2][NSPLIT * kBBytes];
   __shared__ PlaneDesc sd[ZCG];
-  __shared__ uint16_t cell_of[ZCG * NT];  // unit-local cache entry -> plane << 7 | cell (0xFFFF: padding)
+  __shared__ uint16_t cell_of[ZCG * NT];  // unit-local cache entry -> plane << 8 | cell (0xFFFF: padding)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   {
     const uint4 *src0 = (const uint4 *)w0;
     const uint4 *src1 = (const uint4 *)w1;
     uint4 *dst0 = (uint4 *)sW[0];
     uint4 *dst1 = (uint4 *)sW[1];
-    for (int i = tid; i < NSPLIT * kBBytes / 16; i += NT) {
+    for (int i = tid; i < NSPLIT * kBBytes / 16; i += GT) {
       dst0[i] = src0[i];
       if (nblk > 1) dst1[i] = src1[i];
     }
@@ -382,7 +403,6 @@ __global__ void __launch_bounds__(NT) k_generate_tc(const uint8_t *__restrict__ 
   const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + ZCG - 1) / ZCG;
   const int ntiles = ntx * nty;
   const long long units = (long long)ntiles * nch;
-  const uint32_t below = lanemask_lt();
   for (long long u = blockIdx.x; u < units && !aborted; u += gridDim.x) {
     const int t = (int)(u % ntiles), c = (int)(u / ntiles);
     const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
@@ -390,31 +410,34 @@ __global__ void __launch_bounds__(NT) k_generate_tc(const uint8_t *__restrict__ 
     {
       const uint32_t *src = (const uint32_t *)(desc + (size_t)t * d.nz + zs);
       uint32_t *dsd = (uint32_t *)sd;
-      for (int i = tid; i < nzu * 20; i += NT) dsd[i] = src[i];
+      for (int i = tid; i < nzu * DWORDS; i += GT) dsd[i] = src[i];
     }
     __syncthreads();
     const uint32_t base = sd[0].off;
     const int total = (int)(sd[nzu - 1].off + sd[nzu - 1].cpad - base);  // entries of the unit, padding included
     if (total > 0) {
-      for (int i = tid; i < total; i += NT) cell_of[i] = 0xFFFFu;
+      for (int i = tid; i < total; i += GT) cell_of[i] = 0xFFFFu;
       __syncthreads();
       for (int j = 0; j < nzu; ++j) {
-        const uint32_t m = sd[j].row[warp].x;
-        if ((m >> lane) & 1u) {
-          const uint32_t rank = __popc(m & below) + ((sd[j].rowbase >> (8 * warp)) & 0xFFu);
-          cell_of[sd[j].off - base + rank] = (uint16_t)((j << 7) | tid);
+        for (int cc = tid; cc < NT; cc += GT) {  // cell cc = row * 32 + x of the tile
+          const int row = cc >> 5, xb = cc & 31;
+          const uint32_t m = sd[j].row[row].x;
+          if ((m >> xb) & 1u) {
+            const uint32_t rank = __popc(m & ((1u << xb) - 1u)) + row_base(sd[j], row);
+            cell_of[sd[j].off - base + rank] = (uint16_t)((j << 8) | cc);
+          }
         }
       }
       __syncthreads();
-      for (int c0 = 0; c0 < total && !aborted; c0 += NT) {
+      for (int c0 = 0; c0 < total && !aborted; c0 += GT) {
         const int li = c0 + tid;
         const uint32_t e = li < total ? cell_of[li] : 0xFFFFu;
         const bool valid = e != 0xFFFFu;
         uint32_t fw[32];
         int j = 0;
         if (valid) {
-          j = (int)(e >> 7);
-          const int cell = (int)(e & 127u);
+          j = (int)(e >> 8);
+          const int cell = (int)(e & 255u);
           const int x = x0 + (cell & 31), y = y0 + (cell >> 5), z = zs + j;
           uint32_t win[27];
 #pragma unroll
@@ -488,8 +511,8 @@ __global__ void __launch_bounds__(NT) k_generate_tc(const uint8_t *__restrict__ 
 // Per iteration: the streamed z-marching CConv.
 // ---------------------------------------------------------------------------
 struct StreamParams {
-  CUtensorMap tv;   // input vector of the level: box 40 x 6 x 2 (FP32)
-  CUtensorMap tx1;  // x1 of the level (combination only): box 32 x 4 x 2
+  CUtensorMap tv;   // input vector of the level: box 40 x 10 x 2 (FP32)
+  CUtensorMap tx1;  // x1 of the level (combination only): box 32 x 8 x 2
   Dims dm;
   int ntx, ntiles, zc, units;
   const PlaneDesc *desc;
@@ -502,6 +525,7 @@ struct StreamParams {
   int *err;
   int mode;             // which outputs are computed (STREAM_MODE_*)
   float kS[27], kF[27], kA[27];  // kernels of the pure-solid, pure-fluid, pure-air windows
+  uint32_t ktab[3][27];          // the same as stored in the class tables (BF16 pairs or FP32 words)
 };
 
 struct Unit {
@@ -519,6 +543,15 @@ __device__ __forceinline__ Unit unit_at(const StreamParams &P, int u) {
   return U;
 }
 
+// A thread's window column of one plane: rows y-1 .. y+2 x columns x-1 .. x+1
+// (row-major), so rows 0..2 are the 3x3 window of cell y and rows 1..3 that of
+// cell y+1.
+using Col = float[12];
+template <int R>
+__device__ __forceinline__ const float (&rows3(const Col &c))[9] {
+  return *reinterpret_cast<const float(*)[9]>(&c[3 * R]);
+}
+
 // sum_a k[a] v[a] over the window held as three 3x3 planes.
 __device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9], const float (&vB)[9],
                                        const float (&vC)[9]) {
@@ -532,77 +565,74 @@ __device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9
   return (s0 + s1) + s2;
 }
 
-// One output cell: the classes of the warp's row decide which (warp-uniform)
-// constant-kernel sums are needed; a mixed lane reads its kernel from the
-// block.  Lanes that need no output (mode) get 0: with a zero input off fluid
-// (level-1 CConv1) a pure-air or pure-solid window sums to exactly 0, and the
-// level-1 CConv2 output is used on fluid cells only (Sec. 4.2 restriction).
+// One output cell.  A row whose windows are all of one pure class (among the
+// cells whose output is needed) uses that class's constant kernel from the
+// kernel parameters; any other row reads each lane's kernel from shared
+// memory: the class table of its pure class (stride 1) or its mixed block
+// (stride cpad).  Lanes whose output is not needed get 0: with a zero input
+// off fluid (level-1 CConv1) a pure-air or pure-solid window sums to exactly
+// 0, and the level-1 CConv2 output is used on fluid cells only.
 template <bool BF16C>
 __device__ __forceinline__ float cconv_cell(const StreamParams &P, uint4 rw, uint32_t rank, uint32_t cp,
-                                            const uint32_t *kblk, int lane, const float (&vA)[9],
-                                            const float (&vB)[9], const float (&vC)[9]) {
+                                            const uint32_t *kblk, const uint32_t *ktab, int xb,
+                                            const float (&vA)[9], const float (&vB)[9], const float (&vC)[9]) {
   uint32_t need = 0xFFFFFFFFu;
   if (P.mode == STREAM_MODE_ZERO_PURE) need = rw.x | rw.y;
   else if (P.mode == STREAM_MODE_FLUID_ONLY) need = rw.w;
   const uint32_t cm = rw.x & need, cf = rw.y & need, ca = rw.z & need;
-  const uint32_t cs = ~(rw.x | rw.y | rw.z) & need;  // pure-solid windows (and lanes outside the grid)
-  if (cf == 0xFFFFFFFFu) return dot27(P.kF, vA, vB, vC);
-  if (ca == 0xFFFFFFFFu) return dot27(P.kA, vA, vB, vC);
-  if (cs == 0xFFFFFFFFu) return dot27(P.kS, vA, vB, vC);
-  if ((cm | cf | ca | cs) == 0u) return 0.f;
-  float acc = 0.f;
-  if (cf) {
-    const float t = dot27(P.kF, vA, vB, vC);
-    if ((cf >> lane) & 1u) acc = t;
+  const uint32_t cs = ~(rw.x | rw.y | rw.z) & need;  // pure-solid windows (and cells outside the grid)
+  // (lanes outside `need` may then carry any value: their output is unused or exactly 0 anyway)
+  if (need == 0u) return 0.f;
+  if (cf == need) return dot27(P.kF, vA, vB, vC);
+  if (ca == need) return dot27(P.kA, vA, vB, vC);
+  if (cs == need) return dot27(P.kS, vA, vB, vC);
+  const uint32_t bit = 1u << xb;
+  const uint32_t *src;
+  uint32_t stride = 1;
+  if (cm & bit) {
+    src = kblk + rank;
+    stride = cp;
+  } else {
+    src = ktab + (cf & bit ? 1 : (ca & bit ? 2 : 0)) * 27;
   }
-  if (ca) {
-    const float t = dot27(P.kA, vA, vB, vC);
-    if ((ca >> lane) & 1u) acc = t;
-  }
-  if (cs) {
-    const float t = dot27(P.kS, vA, vB, vC);
-    if ((cs >> lane) & 1u) acc = t;
-  }
-  if ((cm >> lane) & 1u) {
-    const uint32_t *kw = kblk + rank;
-    float K[28];
-    if (BF16C) {
+  float K[28];
+  if (BF16C) {
 #pragma unroll
-      for (int q = 0; q < 14; ++q) {
-        const uint32_t wv = kw[q * cp];
-        K[2 * q] = __uint_as_float(wv << 16);
-        K[2 * q + 1] = __uint_as_float(wv & 0xFFFF0000u);
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < 27; ++a) K[a] = __uint_as_float(kw[a * cp]);
+    for (int q = 0; q < 14; ++q) {
+      const uint32_t wv = src[q * stride];
+      K[2 * q] = __uint_as_float(wv << 16);
+      K[2 * q + 1] = __uint_as_float(wv & 0xFFFF0000u);
     }
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  } else {
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      s0 = fmaf(K[q], vA[q], s0);
-      s1 = fmaf(K[9 + q], vB[q], s1);
-      s2 = fmaf(K[18 + q], vC[q], s2);
-    }
-    acc = (s0 + s1) + s2;
+    for (int a = 0; a < 27; ++a) K[a] = __uint_as_float(src[a * stride]);
   }
-  return acc;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    s0 = fmaf(K[q], vA[q], s0);
+    s1 = fmaf(K[9 + q], vB[q], s1);
+    s2 = fmaf(K[18 + q], vC[q], s2);
+  }
+  const float acc = (s0 + s1) + s2;
+  return (need & bit) ? acc : 0.f;
 }
 
 // Shared memory after the slots, descriptor buffers and the kernel-block
-// buffer (8-byte aligned): mbarriers, block positions, pooling exchange.
+// buffer (16-byte aligned): mbarriers, block positions, class tables.
 struct StreamMeta {
-  uint64_t full[RV], empty[RV], dfull[ND], dempty[ND], pfull[4], pempty[4];
+  uint64_t full[RV], empty[RV], dfull[ND], dempty[ND];
   uint32_t kstart[RV], kend[RV];
-  float poolx[4][16];
+  uint32_t ktab[3 * 27];
   int abort_;
 };
 static_assert(sizeof(StreamMeta) <= kMetaBytes, "stream metadata fits");
 
-constexpr int NTHREADS = NT + 32;  // four consumer warps (tile rows) and one producer warp
+constexpr int NCW = 4;                    // consumer warps: two tile rows each
+constexpr int NTHREADS = NCW * 32 + 32;   // and one producer warp
 
 template <bool BF16C>
-__global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_constant__ StreamParams P) {
+__global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_constant__ StreamParams P) {
   using C = KCfg<BF16C>;
   if (P.st && P.st->done) return;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -619,31 +649,28 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
   if (tid == 0) {
     for (int i = 0; i < RV; ++i) {
       mbar_init(&M.full[i], 1);
-      mbar_init(&M.empty[i], TY);
+      mbar_init(&M.empty[i], NCW);
       M.kstart[i] = 0u;
       M.kend[i] = 0u;
     }
     for (int i = 0; i < ND; ++i) {
       mbar_init(&M.dfull[i], 1);
-      mbar_init(&M.dempty[i], TY);
-    }
-    for (int i = 0; i < 4; ++i) {
-      mbar_init(&M.pfull[i], 1);
-      mbar_init(&M.pempty[i], 1);
+      mbar_init(&M.dempty[i], NCW);
     }
     *sabort = 0;
     umma::fence_mbar_init();
     umma::fence_proxy_async_smem();
   }
+  for (int i = tid; i < 3 * 27; i += NTHREADS) M.ktab[i] = (&P.ktab[0][0])[i];
   __syncthreads();  // the only CTA-wide barrier
 
-  if (warp == TY) {
+  if (warp == NCW) {
     // ------------------------------------------------------------------ producer
     if (lane != 0) return;
     bool fail = false;
-    uint32_t vi = 0, vrel = 0;            // loads issued / slots known released
+    uint32_t vi = 0, vrel = 0;  // loads issued / slots known released
     uint32_t khead = 0, ktail = 0, kpos = 0;
-    uint32_t di = 0;                      // descriptor loads issued (= units)
+    uint32_t di = 0;            // descriptor loads issued (= units)
     auto release_next = [&]() {
       const int sl = (int)(vrel % RV);
       if (!mbar_sleep_wait(&M.empty[sl], (vrel / RV) & 1u, kWaitNs)) {
@@ -694,11 +721,14 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
           koff = D[j0].off;
           kbytes = (cp0 + cp1) * (uint32_t)C::EB;
         }
-        const uint32_t waste = (kpos + kbytes > (uint32_t)C::CB) ? (uint32_t)C::CB - kpos : 0u;
+        // the block must not cross the end of the buffer: if it would, it starts at 0
+        // and the bytes left at the end count as used until this slot is released
+        const bool wrap = kpos + kbytes > (uint32_t)C::CB;
+        const uint32_t waste = wrap ? (uint32_t)C::CB - kpos : 0u;
         while (!fail && vrel < vi && (khead - ktail) + waste + kbytes > (uint32_t)C::CB) release_next();
         if (fail) break;
         const int sl = (int)(vi % RV);
-        if (waste) {
+        if (wrap) {
           khead += waste;
           kpos = 0;
         }
@@ -744,43 +774,29 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
   const int cxn = P.dm.nx >> 1, cyn = P.dm.ny >> 1;
   const long long nxy = (long long)P.dm.nx * P.dm.ny;
   const uint32_t below = lanemask_lt();
-  const int pair = warp >> 1;
-  const int vrow = warp * BXW + lane + 3;  // box index of the cell (x-1, y-1) in a plane (box starts at x0-4, y0-1)
-  uint32_t sl = 0, sph = 0;                // next slot and the parity of its phase
-  uint32_t pround = 0;                     // pooling rounds so far
-  // pooling of the even row of a pair waits for the odd row's sum of round pend_r
-  float pend_t = 0.f;
-  long long pend_idx = -1;
-  bool pend = false;
-  uint32_t pend_r = 0;
-  auto flush_pool = [&]() {
-    if (!pend) return;
-    pend = false;
-    const int buf = (int)(pend_r & 1u);
-    if (!wait(&M.pfull[pair * 2 + buf], (pend_r >> 1) & 1u)) return;
-    const float o = M.poolx[pair * 2 + buf][lane >> 1];
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&M.pempty[pair * 2 + buf]);
-    if (pend_idx >= 0) P.pooled[pend_idx] = 0.125f * (pend_t + o);
-  };
+  const int ra = 2 * warp;  // this thread's rows ra, ra+1 of the tile
+  // box index of the cell (x-1, y-1) of row ra in a plane (the box starts at x0-4, y0-1)
+  const int vbase = ra * BXW + lane + 3;
+  uint32_t sl = 0, sph = 0;  // next slot and the parity of its phase
 
   for (int m = 0; ok; ++m) {
     const int u = blockIdx.x + m * G;
     if (u >= P.units) break;
     const Unit U = unit_at(P, u);
-    const int gx = U.x0 + lane, gy = U.y0 + warp;
-    const bool inside = gx < P.dm.nx && gy < P.dm.ny;
+    const int gx = U.x0 + lane, gy = U.y0 + ra;
+    const bool in_x = gx < P.dm.nx;
+    const bool in_a = in_x && gy < P.dm.ny, in_b = in_x && gy + 1 < P.dm.ny;
     const PlaneDesc *D = (const PlaneDesc *)(ds + (m % ND) * DBUF);
     if (!wait(&M.dfull[m % ND], (m / ND) & 1)) break;
-    float vA[9], vB[9];
-    {  // prologue slot: planes zs-1, zs
+    Col pA, pB;  // planes zs-1, zs
+    {
       if (!wait(&M.full[sl], sph)) break;
       const float *pl = (const float *)(vs + sl * SLOT);
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const int e = vrow + (q / 3) * BXW + q % 3;
-        vA[q] = pl[e];
-        vB[q] = pl[BXW * BYH + e];
+      for (int q = 0; q < 12; ++q) {
+        const int e = vbase + (q / 3) * BXW + q % 3;
+        pA[q] = pl[e];
+        pB[q] = pl[BXW * BYH + e];
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
@@ -790,41 +806,55 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
       }
     }
     float *op = P.out + (long long)U.zs * nxy + (long long)gy * P.dm.nx + gx;
-    long long pidx = ((long long)(U.zs >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1);
+    float *pp = P.pooled ? P.pooled + ((long long)(U.zs >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1) : nullptr;
     const long long pstep = (long long)cxn * cyn;
-    const bool pown = inside && !(lane & 1);  // even lane of an even row writes the pooled value
+    const bool pown = in_a && !(lane & 1);  // even lane writes the 2x2x2 block's mean
     const int T = (U.nzu + 1) >> 1;
     for (int t = 0; t < T; ++t) {
       const int j0 = 2 * t;
       const bool two = j0 + 1 < U.nzu;
-      flush_pool();
       if (!wait(&M.full[sl], sph)) break;
       const uint8_t *slot = vs + sl * SLOT;
       const float *pl = (const float *)slot;
-      float vC[9], vD[9];
+      Col pC, pD;  // planes z0+1, z0+2
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const int e = vrow + (q / 3) * BXW + q % 3;
-        vC[q] = pl[e];
-        vD[q] = pl[BXW * BYH + e];
+      for (int q = 0; q < 12; ++q) {
+        const int e = vbase + (q / 3) * BXW + q % 3;
+        pC[q] = pl[e];
+        pD[q] = pl[BXW * BYH + e];
       }
-      float x1a = 0.f, x1b = 0.f;
+      float x1v[4] = {0.f, 0.f, 0.f, 0.f};  // (row a, z0), (row b, z0), (row a, z1), (row b, z1)
       if (has_x1) {
-        x1a = ((const float *)(slot + X1OFF))[tid];
-        x1b = ((const float *)(slot + X1OFF))[NT + tid];
+        const float *xb = (const float *)(slot + X1OFF) + ra * TX + lane;
+        x1v[0] = xb[0];
+        x1v[1] = xb[TX];
+        x1v[2] = xb[NT];
+        x1v[3] = xb[NT + TX];
       }
       const uint32_t *kblk = (const uint32_t *)(kb + M.kstart[sl]);
-      const uint4 r0 = D[j0].row[warp];
-      const uint2 c0 = *(const uint2 *)&D[j0].cpad;  // cpad, rowbase
-      const uint32_t cp0 = min(c0.x, (uint32_t)NT);
-      float acc0 = cconv_cell<BF16C>(P, r0, __popc(r0.x & below) + ((c0.y >> (8 * warp)) & 0xFFu), cp0, kblk, lane,
-                                     vA, vB, vC);
-      float acc1 = 0.f;
-      if (two) {
-        const uint4 r1 = D[j0 + 1].row[warp];
-        const uint2 c1d = *(const uint2 *)&D[j0 + 1].cpad;
-        acc1 = cconv_cell<BF16C>(P, r1, __popc(r1.x & below) + ((c1d.y >> (8 * warp)) & 0xFFu),
-                                 min(c1d.x, (uint32_t)NT), kblk + (size_t)cp0 * (C::EB / 4), lane, vB, vC, vD);
+      float acc[4];
+      {
+        const PlaneDesc &d0 = D[j0];
+        const uint4 wa = d0.row[ra], wb = d0.row[ra + 1];
+        const uint32_t rb = d0.rowbase[ra >> 2] >> (8 * (ra & 3));
+        const uint32_t cp0 = min(d0.cpad, (uint32_t)NT);
+        acc[0] = cconv_cell<BF16C>(P, wa, __popc(wa.x & below) + (rb & 0xFFu), cp0, kblk, M.ktab, lane,
+                                   rows3<0>(pA), rows3<0>(pB), rows3<0>(pC));
+        acc[1] = cconv_cell<BF16C>(P, wb, __popc(wb.x & below) + ((rb >> 8) & 0xFFu), cp0, kblk, M.ktab, lane,
+                                   rows3<1>(pA), rows3<1>(pB), rows3<1>(pC));
+        acc[2] = 0.f;
+        acc[3] = 0.f;
+        if (two) {
+          const PlaneDesc &d1 = D[j0 + 1];
+          const uint4 va = d1.row[ra], vb = d1.row[ra + 1];
+          const uint32_t rb1 = d1.rowbase[ra >> 2] >> (8 * (ra & 3));
+          const uint32_t cp1 = min(d1.cpad, (uint32_t)NT);
+          const uint32_t *kblk1 = kblk + (size_t)cp0 * (C::EB / 4);
+          acc[2] = cconv_cell<BF16C>(P, va, __popc(va.x & below) + (rb1 & 0xFFu), cp1, kblk1, M.ktab, lane,
+                                     rows3<0>(pB), rows3<0>(pC), rows3<0>(pD));
+          acc[3] = cconv_cell<BF16C>(P, vb, __popc(vb.x & below) + ((rb1 >> 8) & 0xFFu), cp1, kblk1, M.ktab,
+                                     lane, rows3<1>(pB), rows3<1>(pC), rows3<1>(pD));
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
@@ -832,46 +862,33 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_cconv_stream(const __grid_const
         sl = 0;
         sph ^= 1u;
       }
-      acc0 *= sc;
-      acc1 *= sc;
-      if (has_x1) {
-        acc0 = fmaf(c1, x1a, c2 * acc0);
-        acc1 = fmaf(c1, x1b, c2 * acc1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i] *= sc;
+        if (has_x1) acc[i] = fmaf(c1, x1v[i], c2 * acc[i]);
       }
-      if (inside) {
-        op[0] = acc0;
-        if (two) op[nxy] = acc1;
+      if (in_a) op[0] = acc[0];
+      if (in_b) op[P.dm.nx] = acc[1];
+      if (two) {
+        if (in_a) op[nxy] = acc[2];
+        if (in_b) op[nxy + P.dm.nx] = acc[3];
       }
       op += 2 * nxy;
-      if (P.pooled) {  // z0 is even: the step holds a z pair
-        float tp = acc0 + acc1;
+      if (pp) {  // z0 even, rows ra, ra+1: the thread holds half of a 2x2x2 block, the odd lane the other half
+        float tp = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         tp += __shfl_xor_sync(0xffffffffu, tp, 1);
-        const int buf = (int)(pround & 1u);
-        if (warp & 1) {
-          // odd row: hand the x/z-pooled sums to the even row of the pair
-          if (pround >= 2u && !wait(&M.pempty[pair * 2 + buf], ((pround >> 1) - 1u) & 1u)) break;
-          if (!(lane & 1)) M.poolx[pair * 2 + buf][lane >> 1] = tp;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&M.pfull[pair * 2 + buf]);
-        } else {
-          pend = true;
-          pend_r = pround;
-          pend_t = tp;
-          pend_idx = pown ? pidx : -1;
-        }
-        ++pround;
-        pidx += pstep;
+        if (pown) *pp = 0.125f * tp;
+        pp += pstep;
       }
 #pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        vA[q] = vC[q];
-        vB[q] = vD[q];
+      for (int q = 0; q < 12; ++q) {
+        pA[q] = pC[q];
+        pB[q] = pD[q];
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&M.dempty[m % ND]);
   }
-  if (ok) flush_pool();
 }
 
 // ---------------------------------------------------------------------------
@@ -959,13 +976,13 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
   if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3)
     const int g = grid_for_units(units, num_sms * 4);
     if (nsplit == 1)
-      k_generate_tc<1, true><<<g, NT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+      k_generate_tc<1, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
                                               (uint32_t *)cache1, err);
     else if (bf16)
-      k_generate_tc<3, true><<<g, NT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+      k_generate_tc<3, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
                                               (uint32_t *)cache1, err);
     else
-      k_generate_tc<3, false><<<g, NT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+      k_generate_tc<3, false><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
                                                (uint32_t *)cache1, err);
     return;
   }
@@ -984,6 +1001,22 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
   P.mode = mode;
   if (!encode_map(&P.tv, v, dm, BXW, BYH, 2)) return -1;
   if (c12 && !encode_map(&P.tx1, x1, dm, TX, TY, 2)) return -1;
+  // class tables in the stored format: BF16 pairs (the constants are BF16 values in that form) or FP32 words
+  for (int c = 0; c < 3; ++c) {
+    const float *k = kfix + 27 * c;
+    for (int a = 0; a < 27; ++a) {
+      uint32_t u;
+      memcpy(&u, &k[a], 4);
+      P.ktab[c][a] = u;
+    }
+    if (bf16)
+      for (int j = 0; j < 14; ++j) {
+        uint32_t lo, hi = 0u;
+        memcpy(&lo, &k[2 * j], 4);
+        if (2 * j + 1 < 27) memcpy(&hi, &k[2 * j + 1], 4);
+        P.ktab[c][j] = (lo >> 16) | (hi & 0xFFFF0000u);
+      }
+  }
   P.dm = dm;
   P.ntx = (dm.nx + TX - 1) / TX;
   P.ntiles = P.ntx * ((dm.ny + TY - 1) / TY);

@@ -56,7 +56,6 @@ struct MarchParams {
   float *pooled;           // optional 2x2x2 mean of the output (dims / 2)
   const SolveState *st;
   int *err;
-  uint32_t pure_f;         // image code of a pure-fluid cell (BF16 bits of 8^(lvl-1)); << 16: pure air
 };
 
 // Packed image code of one cell: BF16 bits of the air count in the high half,
@@ -194,7 +193,6 @@ __global__ void __launch_bounds__(128, 4) k_cconv_march(MarchParams P) {
       vB[j] = sV[(zs - 1 + RING) % RING][e];
     }
     float psum = 0.f;
-    bool mixed_prev = false, mixed_cur = false;  // window of plane z-1 / z not uniform
 
     for (int z = zs; z <= ze; ++z) {
       const bool do_feat = z < ze, do_apply = z > zs;
@@ -222,12 +220,6 @@ __global__ void __launch_bounds__(128, 4) k_cconv_march(MarchParams P) {
         }
         uint32_t fw[32];
         build_feature_words(win, fw);
-        bool mx = false;
-#pragma unroll
-        for (int j = 0; j < 27; ++j) mx |= win[j] != win[13];
-        // BF16 form: all but the pure windows (pure fluid, air or solid) are rounded
-        mx |= !(win[13] == 0u || win[13] == P.pure_f || win[13] == (P.pure_f << 16));
-        mixed_cur = mx;
         tmem_st32(tmem + 32 * b + lane_off, fw);
         tmem_wait_st();
       }
@@ -261,7 +253,7 @@ __global__ void __launch_bounds__(128, 4) k_cconv_march(MarchParams P) {
           uint32_t kr[32];
           tmem_ld32(tmem + 64 + 32 * pb + lane_off, kr);
           tmem_wait_ld();
-          if (NSPLIT == 1 && mixed_prev) {  // BF16 form: kernels of non-pure windows as BF16 values
+          if (NSPLIT == 1) {  // BF16 form: every kernel value rounded to BF16
 #pragma unroll
             for (int j = 0; j < 27; ++j)
               kr[j] = __float_as_uint(__bfloat162float(__float2bfloat16_rn(__uint_as_float(kr[j]))));
@@ -312,7 +304,6 @@ __global__ void __launch_bounds__(128, 4) k_cconv_march(MarchParams P) {
         vA[j] = vB[j];
         vB[j] = vC[j];
       }
-      mixed_prev = mixed_cur;
     }
   }
   if (aborted) {
@@ -344,7 +335,7 @@ static void launch_march_t(const MarchParams &P, int num_sms, cudaStream_t s) {
 
 void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
                         const float *v, const float *coarse, const float *vscale, int mask_input, float *out,
-                        float *pooled, const SolveState *st, int *err, uint32_t full, int num_sms, cudaStream_t s) {
+                        float *pooled, const SolveState *st, int *err, int num_sms, cudaStream_t s) {
   MarchParams P;
   P.dm = dm;
   P.lab = lab;
@@ -358,12 +349,6 @@ void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, D
   P.pooled = pooled;
   P.st = st;
   P.err = err;
-  {  // BF16 bits of the fine-cell count F of a pure cell (F <= 256: exact)
-    const float f = (float)full;
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    P.pure_f = u >> 16;
-  }
   const bool interp = coarse != nullptr;
   if (nsplit == 1) {
     if (interp) launch_march_t<1, true>(P, num_sms, s);

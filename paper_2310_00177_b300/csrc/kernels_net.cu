@@ -166,7 +166,7 @@ __global__ void k_aff_from_counts(const unsigned long long *__restrict__ cnt, co
 //   out_p  = sum_a K_a(p) v(p+a) * vscale,  v zero outside the grid.
 // When mask_input is set (level-1 CConv1), v is also zeroed off fluid (the
 // reduced input vector padded with zeros, Sec. 4.2).  round_k = 0: FP32
-// kernels; round_k = F = 8^(lvl-1): the BF16 form (see below).
+// kernels; nonzero: the BF16 form (kernel values rounded to BF16).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_cconv_f32(ImgSrc im, Dims dm, const CConvW *__restrict__ w,
                                                      const float *__restrict__ v, const float *__restrict__ vscale,
@@ -199,14 +199,8 @@ __global__ void __launch_bounds__(128) k_cconv_f32(ImgSrc im, Dims dm, const CCo
       }
       vv[t] = val * sc;
     }
-    // BF16 form: every kernel except those of pure windows (all 27 cells pure
-    // fluid, pure air or pure solid) is stored as BF16 values
-    bool mixed = false;
-#pragma unroll
-    for (int t = 0; t < 27; ++t) mixed |= (nf[t] != nf[13]) | (na[t] != na[13]);
-    const float full = (float)round_k;
-    const bool pure = (na[13] == 0.f && (nf[13] == 0.f || nf[13] == full)) || (nf[13] == 0.f && na[13] == full);
-    const bool rk = round_k && (mixed || !pure);
+    // BF16 form: every per-cell kernel value is rounded to BF16 (nearest even)
+    const bool rk = round_k != 0;
     float acc = 0.f;
 #pragma unroll 1
     for (int a = 0; a < 27; ++a) {

@@ -121,7 +121,6 @@ void launch_combine_basis(const float *Q, long long n, int m, const double *c, f
 // kernels_march.cu
 void launch_cconv_march(int nsplit, const uint8_t *lab, const ushort2 *counts, Dims dm, const uint8_t *wsplit,
                         const float *v, const float *coarse, const float *vscale, int mask_input, float *out,
-                        float *pooled, const SolveState *st, int *err, uint32_t full, int num_sms,
-                        cudaStream_t s);
+                        float *pooled, const SolveState *st, int *err, int num_sms, cudaStream_t s);
 
 }  // namespace nps

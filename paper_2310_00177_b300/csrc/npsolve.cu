@@ -317,6 +317,15 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
   return NPSOLVE_OK;
 }
 
+// Round to the nearest BF16 value (ties to even), kept as FP32.
+float bf16_round_host(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
 // Fold the blob into the device form of every CConv / Aff block (Sec. 4.2.1
 // with the channel-sum-to-one identity; see CConvW / AffW).
 int upload_weights(npsolve *h) {
@@ -362,13 +371,7 @@ int upload_weights(npsolve *h) {
   }
   if (h->cfg.precision == NPSOLVE_BF16) {
     // the BF16 form: every folded CConv weight rounded to BF16 (nearest even)
-    auto rnd = [](float f) {
-      uint32_t u;
-      memcpy(&u, &f, 4);
-      if ((u & 0x7F800000u) != 0x7F800000u) u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
-      memcpy(&f, &u, 4);
-      return f;
-    };
+    auto rnd = bf16_round_host;
     for (auto &c : cw) {
       for (int a = 0; a < 27; ++a) {
         for (int l = 0; l < 27; ++l) {
@@ -417,6 +420,8 @@ int upload_weights(npsolve *h) {
         kfix[(size_t)i * 81 + 54 + a] = (float)((double)cw[i].bp[a] + F * sa);
       }
     }
+    if (h->cfg.precision == NPSOLVE_BF16)  // the BF16 form rounds every kernel value, these included
+      for (float &f : kfix) f = bf16_round_host(f);
     h->kfix_host = kfix;
   }
   CK(h, cudaMemcpy(h->cw, cw.data(), cw.size() * sizeof(CConvW), cudaMemcpyHostToDevice));
@@ -456,7 +461,7 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw + idx, in, vscale,
-                   mask_input, h->cfg.precision == NPSOLVE_BF16 ? 1 << (3 * (lvl - 1)) : 0, out, st, s);
+                   mask_input, h->cfg.precision == NPSOLVE_BF16 ? 1 : 0, out, st, s);
 }
 
 // One CConv block on the tensor cores (z-marching kernel), with the input
@@ -471,7 +476,7 @@ void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const 
   h->launches += 1;
   launch_cconv_march(h->nsplit, lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], level_dims(d1, lvl),
                      h->uw + (size_t)idx * umma_weight_bytes(3), in, coarse, vscale, mask_input, out, pooled, st,
-                     h->umma_err, 1u << (3 * (lvl - 1)), h->num_sms, s);
+                     h->umma_err, h->num_sms, s);
 }
 
 // One CConv block with the per-solve kernel cache (kernels_cached.cu): input
