@@ -72,11 +72,14 @@ using umma::smem_u32;
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;  // tile (x, y)
 constexpr int ZCG = 32;                       // planes per unit of the setup kernels
-constexpr int BXW = TX + 8;                   // vector box: x0-4 .. x0+35 (start on a 16-byte boundary)
+constexpr int BXW = TX + 12;                  // vector box: x0-4 .. x0+39 (start on a 16-byte boundary; the
+                                              // width 44 keeps the 8x8-patch reads free of bank conflicts)
 constexpr int BYH = TY + 2;                   // rows y0-1 .. y0+4
-constexpr int VPLANE = BXW * BYH * 4;         // 1600 bytes per plane of the vector box
-constexpr int X1OFF = 2 * VPLANE;             // x1 box (32 x 8 x 2) in a slot
-constexpr int SLOT = 5376;                    // 3200 + 2048 bytes, 42 x 128
+constexpr int VPLANE = BXW * BYH * 4;         // 1760 bytes per plane of the vector box
+constexpr int X1OFF = 3584;                   // x1 box (32 x 8 x 2) in a slot (128-byte aligned, after 3520)
+constexpr int SLOT = 5632;                    // 3584 + 2048 bytes, 44 x 128
+static_assert(X1OFF >= 2 * VPLANE && X1OFF % 128 == 0 && SLOT % 128 == 0 && X1OFF + 2048 <= SLOT, "slot layout");
+constexpr int PW = 8;                         // patch width: consumer warp w covers x in [8w, 8w+8) x 8 rows
 constexpr int RV = 4;                         // step slots
 constexpr int ND = 3;                         // descriptor buffers (units)
 constexpr int kMetaBytes = 640;               // mbarriers, block positions, class tables, abort flag
@@ -90,7 +93,8 @@ struct PlaneDesc {
   uint32_t off;      // first cache entry of the plane's kernel block (a multiple of 4)
   uint32_t count;    // mixed cells of the plane
   uint32_t cpad;     // entries of the block: the mixed count rounded up to 4
-  uint32_t pad0;
+  uint32_t patch;    // bits 2p, 2p+1: class of the 8x8 patch p (x in [8p, 8p+8)): 0 all pure solid,
+                     // 1 all pure fluid, 2 all pure air, 3 anything else
   uint32_t rowbase[2];  // byte w: mixed cells in rows 0..w-1 (the rank of row w's first one)
   uint32_t pad1[2];
 };
@@ -228,10 +232,22 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
           m += __popc(sd[j][4 * w]);
         }
         const uint32_t cp = (m + 3u) & ~3u;
+        uint32_t pc = 0u;
+        for (int q = 0; q < TX / PW; ++q) {
+          const uint32_t pm = ((1u << PW) - 1u) << (PW * q);
+          bool allf = true, alla = true, alls = true;
+          for (int w = 0; w < TY; ++w) {
+            const uint32_t mx = sd[j][4 * w] & pm, fl = sd[j][4 * w + 1] & pm, ai = sd[j][4 * w + 2] & pm;
+            allf &= fl == pm;
+            alla &= ai == pm;
+            alls &= (mx | fl | ai) == 0u;
+          }
+          pc |= (allf ? 1u : alla ? 2u : alls ? 0u : 3u) << (2 * q);
+        }
         sd[j][4 * TY] = tot;
         sd[j][4 * TY + 1] = m;
         sd[j][4 * TY + 2] = cp;
-        sd[j][4 * TY + 3] = 0u;
+        sd[j][4 * TY + 3] = pc;
         sd[j][4 * TY + 4] = rb[0];
         sd[j][4 * TY + 5] = rb[1];
         sd[j][4 * TY + 6] = 0u;
@@ -565,35 +581,25 @@ __device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9
   return (s0 + s1) + s2;
 }
 
-// One output cell.  A row whose windows are all of one pure class (among the
-// cells whose output is needed) uses that class's constant kernel from the
-// kernel parameters; any other row reads each lane's kernel from shared
-// memory: the class table of its pure class (stride 1) or its mixed block
-// (stride cpad).  Lanes whose output is not needed get 0: with a zero input
-// off fluid (level-1 CConv1) a pure-air or pure-solid window sums to exactly
-// 0, and the level-1 CConv2 output is used on fluid cells only.
+// A cell of a patch that is not all one pure class: its kernel is read from
+// shared memory, the class table of its pure class (stride 1) or the cell's
+// mixed block (stride cpad), one code path for all lanes.  Cells whose output
+// is not needed get 0: with a zero input off fluid (level-1 CConv1) a
+// pure-air or pure-solid window sums to exactly 0, and the level-1 CConv2
+// output is used on fluid cells only.
 template <bool BF16C>
-__device__ __forceinline__ float cconv_cell(const StreamParams &P, uint4 rw, uint32_t rank, uint32_t cp,
-                                            const uint32_t *kblk, const uint32_t *ktab, int xb,
-                                            const float (&vA)[9], const float (&vB)[9], const float (&vC)[9]) {
-  uint32_t need = 0xFFFFFFFFu;
-  if (P.mode == STREAM_MODE_ZERO_PURE) need = rw.x | rw.y;
-  else if (P.mode == STREAM_MODE_FLUID_ONLY) need = rw.w;
-  const uint32_t cm = rw.x & need, cf = rw.y & need, ca = rw.z & need;
-  const uint32_t cs = ~(rw.x | rw.y | rw.z) & need;  // pure-solid windows (and cells outside the grid)
-  // (lanes outside `need` may then carry any value: their output is unused or exactly 0 anyway)
-  if (need == 0u) return 0.f;
-  if (cf == need) return dot27(P.kF, vA, vB, vC);
-  if (ca == need) return dot27(P.kA, vA, vB, vC);
-  if (cs == need) return dot27(P.kS, vA, vB, vC);
-  const uint32_t bit = 1u << xb;
-  const uint32_t *src;
+__device__ __forceinline__ float cconv_generic(const StreamParams &P, uint4 rw, uint32_t rank, uint32_t cp,
+                                               const uint32_t *kblk, const uint32_t *ktab, uint32_t bit,
+                                               const float (&vA)[9], const float (&vB)[9], const float (&vC)[9]) {
+  const bool mixed = (rw.x & bit) != 0u, fl = (rw.y & bit) != 0u, ai = (rw.z & bit) != 0u;
+  bool need = true;
+  if (P.mode == STREAM_MODE_ZERO_PURE) need = mixed || fl;
+  else if (P.mode == STREAM_MODE_FLUID_ONLY) need = (rw.w & bit) != 0u;
+  const uint32_t *src = ktab + (fl ? 27 : (ai ? 54 : 0));
   uint32_t stride = 1;
-  if (cm & bit) {
+  if (mixed) {
     src = kblk + rank;
     stride = cp;
-  } else {
-    src = ktab + (cf & bit ? 1 : (ca & bit ? 2 : 0)) * 27;
   }
   float K[28];
   if (BF16C) {
@@ -615,7 +621,43 @@ __device__ __forceinline__ float cconv_cell(const StreamParams &P, uint4 rw, uin
     s2 = fmaf(K[18 + q], vC[q], s2);
   }
   const float acc = (s0 + s1) + s2;
-  return (need & bit) ? acc : 0.f;
+  return need ? acc : 0.f;
+}
+
+// The two cells (rows y, y+1) of one plane for a patch of one pure class cls
+// (0 solid, 1 fluid, 2 air): the class's constant kernel from the kernel
+// parameters, or 0 where the mode says the output is exactly 0 or unused.
+__device__ __forceinline__ void cconv_pure_pair(const StreamParams &P, int cls, const Col &p0, const Col &p1,
+                                                const Col &p2, float &oa, float &ob) {
+  if (P.mode != STREAM_MODE_ALL && cls != 1) {
+    oa = 0.f;
+    ob = 0.f;
+  } else if (cls == 1) {
+    oa = dot27(P.kF, rows3<0>(p0), rows3<0>(p1), rows3<0>(p2));
+    ob = dot27(P.kF, rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+  } else if (cls == 2) {
+    oa = dot27(P.kA, rows3<0>(p0), rows3<0>(p1), rows3<0>(p2));
+    ob = dot27(P.kA, rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+  } else {
+    oa = dot27(P.kS, rows3<0>(p0), rows3<0>(p1), rows3<0>(p2));
+    ob = dot27(P.kS, rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+  }
+}
+
+// The two cells of one plane (rows ra, ra+1, bit b of the row masks) of a
+// patch that is not all one pure class.
+template <bool BF16C>
+__device__ __forceinline__ void cconv_generic_pair(const StreamParams &P, const PlaneDesc &d, int ra, int b,
+                                                   const uint32_t *kblk, const uint32_t *ktab, const Col &p0,
+                                                   const Col &p1, const Col &p2, float &oa, float &ob) {
+  const uint4 wa = d.row[ra], wb = d.row[ra + 1];
+  const uint32_t rb = d.rowbase[ra >> 2] >> (8 * (ra & 3));
+  const uint32_t cp = min(d.cpad, (uint32_t)NT);
+  const uint32_t bit = 1u << b, below = bit - 1u;
+  oa = cconv_generic<BF16C>(P, wa, __popc(wa.x & below) + (rb & 0xFFu), cp, kblk, ktab, bit, rows3<0>(p0),
+                            rows3<0>(p1), rows3<0>(p2));
+  ob = cconv_generic<BF16C>(P, wb, __popc(wb.x & below) + ((rb >> 8) & 0xFFu), cp, kblk, ktab, bit,
+                            rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
 }
 
 // Shared memory after the slots, descriptor buffers and the kernel-block
@@ -760,6 +802,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   }
 
   // -------------------------------------------------------------------- consumers
+  // warp w owns the 8x8 patch x in [8w, 8w+8) of the tile; a thread owns
+  // column xi = lane % 8 and rows ra = 2 (lane / 8), ra + 1
   bool ok = true;
   auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
     if (ok && !mbar_sleep_wait(bar, parity, kWaitNs)) {
@@ -773,17 +817,17 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   const float c1 = has_x1 ? (float)P.c12[0] : 0.f, c2 = has_x1 ? (float)P.c12[1] : 1.f;
   const int cxn = P.dm.nx >> 1, cyn = P.dm.ny >> 1;
   const long long nxy = (long long)P.dm.nx * P.dm.ny;
-  const uint32_t below = lanemask_lt();
-  const int ra = 2 * warp;  // this thread's rows ra, ra+1 of the tile
+  const int xi = lane & 7, ra = 2 * (lane >> 3);
+  const int xb = PW * warp + xi;  // x within the tile = bit of the row masks
   // box index of the cell (x-1, y-1) of row ra in a plane (the box starts at x0-4, y0-1)
-  const int vbase = ra * BXW + lane + 3;
+  const int vbase = ra * BXW + xb + 3;
   uint32_t sl = 0, sph = 0;  // next slot and the parity of its phase
 
   for (int m = 0; ok; ++m) {
     const int u = blockIdx.x + m * G;
     if (u >= P.units) break;
     const Unit U = unit_at(P, u);
-    const int gx = U.x0 + lane, gy = U.y0 + ra;
+    const int gx = U.x0 + xb, gy = U.y0 + ra;
     const bool in_x = gx < P.dm.nx;
     const bool in_a = in_x && gy < P.dm.ny, in_b = in_x && gy + 1 < P.dm.ny;
     const PlaneDesc *D = (const PlaneDesc *)(ds + (m % ND) * DBUF);
@@ -808,7 +852,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
     float *op = P.out + (long long)U.zs * nxy + (long long)gy * P.dm.nx + gx;
     float *pp = P.pooled ? P.pooled + ((long long)(U.zs >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1) : nullptr;
     const long long pstep = (long long)cxn * cyn;
-    const bool pown = in_a && !(lane & 1);  // even lane writes the 2x2x2 block's mean
+    const bool pown = in_a && !(xi & 1);  // even column writes the 2x2x2 block's mean
     const int T = (U.nzu + 1) >> 1;
     for (int t = 0; t < T; ++t) {
       const int j0 = 2 * t;
@@ -825,35 +869,28 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       }
       float x1v[4] = {0.f, 0.f, 0.f, 0.f};  // (row a, z0), (row b, z0), (row a, z1), (row b, z1)
       if (has_x1) {
-        const float *xb = (const float *)(slot + X1OFF) + ra * TX + lane;
-        x1v[0] = xb[0];
-        x1v[1] = xb[TX];
-        x1v[2] = xb[NT];
-        x1v[3] = xb[NT + TX];
+        const float *xs = (const float *)(slot + X1OFF) + ra * TX + xb;
+        x1v[0] = xs[0];
+        x1v[1] = xs[TX];
+        x1v[2] = xs[NT];
+        x1v[3] = xs[NT + TX];
       }
       const uint32_t *kblk = (const uint32_t *)(kb + M.kstart[sl]);
-      float acc[4];
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
       {
         const PlaneDesc &d0 = D[j0];
-        const uint4 wa = d0.row[ra], wb = d0.row[ra + 1];
-        const uint32_t rb = d0.rowbase[ra >> 2] >> (8 * (ra & 3));
-        const uint32_t cp0 = min(d0.cpad, (uint32_t)NT);
-        acc[0] = cconv_cell<BF16C>(P, wa, __popc(wa.x & below) + (rb & 0xFFu), cp0, kblk, M.ktab, lane,
-                                   rows3<0>(pA), rows3<0>(pB), rows3<0>(pC));
-        acc[1] = cconv_cell<BF16C>(P, wb, __popc(wb.x & below) + ((rb >> 8) & 0xFFu), cp0, kblk, M.ktab, lane,
-                                   rows3<1>(pA), rows3<1>(pB), rows3<1>(pC));
-        acc[2] = 0.f;
-        acc[3] = 0.f;
+        const int cl0 = (int)((d0.patch >> (2 * warp)) & 3u);
+        if (cl0 != 3) cconv_pure_pair(P, cl0, pA, pB, pC, acc[0], acc[1]);
+        else cconv_generic_pair<BF16C>(P, d0, ra, xb, kblk, M.ktab, pA, pB, pC, acc[0], acc[1]);
         if (two) {
           const PlaneDesc &d1 = D[j0 + 1];
-          const uint4 va = d1.row[ra], vb = d1.row[ra + 1];
-          const uint32_t rb1 = d1.rowbase[ra >> 2] >> (8 * (ra & 3));
-          const uint32_t cp1 = min(d1.cpad, (uint32_t)NT);
-          const uint32_t *kblk1 = kblk + (size_t)cp0 * (C::EB / 4);
-          acc[2] = cconv_cell<BF16C>(P, va, __popc(va.x & below) + (rb1 & 0xFFu), cp1, kblk1, M.ktab, lane,
-                                     rows3<0>(pB), rows3<0>(pC), rows3<0>(pD));
-          acc[3] = cconv_cell<BF16C>(P, vb, __popc(vb.x & below) + ((rb1 >> 8) & 0xFFu), cp1, kblk1, M.ktab,
-                                     lane, rows3<1>(pB), rows3<1>(pC), rows3<1>(pD));
+          const int cl1 = (int)((d1.patch >> (2 * warp)) & 3u);
+          if (cl1 != 3) {
+            cconv_pure_pair(P, cl1, pB, pC, pD, acc[2], acc[3]);
+          } else {
+            const uint32_t *kblk1 = kblk + (size_t)min(d0.cpad, (uint32_t)NT) * (C::EB / 4);
+            cconv_generic_pair<BF16C>(P, d1, ra, xb, kblk1, M.ktab, pB, pC, pD, acc[2], acc[3]);
+          }
         }
       }
       __syncwarp();
@@ -874,7 +911,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         if (in_b) op[nxy + P.dm.nx] = acc[3];
       }
       op += 2 * nxy;
-      if (pp) {  // z0 even, rows ra, ra+1: the thread holds half of a 2x2x2 block, the odd lane the other half
+      if (pp) {  // z0 even, rows ra, ra+1: the thread holds half of a 2x2x2 block, its neighbour lane the rest
         float tp = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         tp += __shfl_xor_sync(0xffffffffu, tp, 1);
         if (pown) *pp = 0.125f * tp;
