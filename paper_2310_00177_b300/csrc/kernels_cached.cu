@@ -287,14 +287,14 @@ __global__ void __launch_bounds__(NT) k_generate(const uint8_t *__restrict__ lab
     for (int i = threadIdx.x; i < nblk * (int)(sizeof(CConvW) / 4); i += NT) dstw[i] = src[i];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + ZCG - 1) / ZCG;
+  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY;
   const int ntiles = ntx * nty;
-  const long long units = (long long)ntiles * nch;
-  for (long long u = blockIdx.x; u < units; u += gridDim.x) {
-    const int t = (int)(u % ntiles), c = (int)(u / ntiles);
+  // one work item per (tile, plane): the coarse levels that run here are small
+  const long long items = (long long)ntiles * d.nz;
+  for (long long u = blockIdx.x; u < items; u += gridDim.x) {
+    const int t = (int)(u % ntiles), zs = (int)(u / ntiles), nzu = 1;
     const int x = (t % ntx) * TX + lane, y = (t / ntx) * TY + warp;
-    const int zs = c * ZCG, nzu = min(ZCG, d.nz - zs);
-    __syncthreads();  // previous unit done with sd (and the weights are in place)
+    __syncthreads();  // previous item done with sd (and the weights are in place)
     {
       const uint32_t *src = (const uint32_t *)(desc + (size_t)t * d.nz + zs);
       uint32_t *dsd = (uint32_t *)sd;
@@ -1023,7 +1023,7 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
                                                (uint32_t *)cache1, err);
     return;
   }
-  const int g = grid_for_units(units, num_sms * 8);
+  const int g = grid_for_units((long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * d.nz, num_sms * 8);
   if (bf16)
     k_generate<true><<<g, NT, 0, s>>>(lab, counts, d, w, nblk, pd, (uint32_t *)cache0, (uint32_t *)cache1);
   else

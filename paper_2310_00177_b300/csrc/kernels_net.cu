@@ -280,49 +280,68 @@ __global__ void k_interp(const float *__restrict__ in, Dims coarse, float *__res
   }
 }
 
-// The same interpolation, four consecutive fine cells of a row per thread
-// (fine nx % 4 == 0): fine x = 4q .. 4q+3 use coarse columns 2q-1 .. 2q+2
-// (clamped), each fine value is the x-, then y-, then z-lerp of k_interp
-// with the same weights, and the four values go out as one 16-byte store.
-// One grid row of threads per (y, z) pair: no division per cell.
-__global__ void __launch_bounds__(256) k_interp4(const float *__restrict__ in, Dims coarse, float *__restrict__ out,
-                                                 const SolveState *st) {
+// The same interpolation for grids whose coarse dims are all even... and any
+// nz: each thread produces a 4 (x) x 2 (y) x 2 (z) block of fine cells from
+// the 3 x 3 coarse rows around it, sharing the x- and then y-interpolated
+// values between the fine rows and planes of the block (about 12 operations
+// per fine cell), and writes four 16-byte rows.  Per axis, fine 2j uses
+// 0.25 c[j-1] + 0.75 c[j] (c[0] at j = 0) and fine 2j+1 uses
+// 0.75 c[j] + 0.25 c[j+1] (c[n-1] at the end), as in k_interp.
+__device__ __forceinline__ float lerp_lo(float a, float b) { return 0.25f * a + 0.75f * b; }  // fine 2j from c[j-1], c[j]
+__device__ __forceinline__ float lerp_hi(float b, float c) { return 0.75f * b + 0.25f * c; }  // fine 2j+1 from c[j], c[j+1]
+
+__global__ void __launch_bounds__(256) k_interp_blk(const float *__restrict__ in, Dims coarse, float *__restrict__ out,
+                                                    const SolveState *st) {
   if (st && st->done) return;
-  const int fx = coarse.nx * 2, fy = coarse.ny * 2, fz = coarse.nz * 2;
-  const int nq = fx >> 2;
-  const long long rows = (long long)fy * fz;
-  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int y = (int)(r % fy), z = (int)(r / fy);
-    int y0, y1, z0, z1;
-    float wy, wz;
-    up_taps(y, coarse.ny, y0, y1, wy);
-    up_taps(z, coarse.nz, z0, z1, wz);
-    const float *rows4[4] = {in + ((long long)z0 * coarse.ny + y0) * coarse.nx, in + ((long long)z0 * coarse.ny + y1) * coarse.nx,
-                             in + ((long long)z1 * coarse.ny + y0) * coarse.nx, in + ((long long)z1 * coarse.ny + y1) * coarse.nx};
-    float4 *orow = (float4 *)(out + r * fx);
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-      const int cm = max(2 * q - 1, 0), c0 = 2 * q, c1 = 2 * q + 1, cp = min(2 * q + 2, coarse.nx - 1);
-      float xl[4][4];  // x-lerped values of the 4 coarse rows at the 4 fine columns
+  const int cx = coarse.nx, cy = coarse.ny, cz = coarse.nz;
+  const int fx = 2 * cx, fy = 2 * cy;
+  const int nq = fx >> 2;  // x groups of 4 fine cells (cx / 2)
+  const long long nthr = (long long)nq * cy * cz;
+  const long long fxy = (long long)fx * fy;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nthr;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t % nq);
+    const long long r = t / nq;
+    const int jy = (int)(r % cy), kz = (int)(r / cy);  // fine rows 2jy, 2jy+1; fine planes 2kz, 2kz+1
+    const int xm = max(2 * q - 1, 0), x0 = 2 * q, x1 = 2 * q + 1, xp = min(2 * q + 2, cx - 1);
+    const int ym = max(jy - 1, 0), yp = min(jy + 1, cy - 1);
+    const int zm = max(kz - 1, 0), zp = min(kz + 1, cz - 1);
+    const int ys[3] = {ym, jy, yp}, zs[3] = {zm, kz, zp};
+    // x-interpolated values of the 3 x 3 coarse rows at the 4 fine columns
+    float xl[3][3][4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float a = __ldg(rows4[k] + cm), b = __ldg(rows4[k] + c0), c = __ldg(rows4[k] + c1),
-                    d = __ldg(rows4[k] + cp);
-        // fine 4q: j = 2q even (0.25 c[j-1] + 0.75 c[j]; c[0] at j = 0); 4q+1: 0.75 c[j] + 0.25 c[j+1];
-        // 4q+2: 0.25 c[j] + 0.75 c[j+1]; 4q+3: 0.75 c[j+1] + 0.25 c[min(j+2, n-1)]
-        xl[k][0] = q > 0 ? (1.f - 0.75f) * a + 0.75f * b : (1.f - 0.f) * b + 0.f * b;
-        xl[k][1] = (1.f - 0.25f) * b + 0.25f * c;
-        xl[k][2] = (1.f - 0.75f) * b + 0.75f * c;
-        xl[k][3] = (1.f - 0.25f) * c + 0.25f * d;
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float *row = in + ((long long)zs[a] * cy + ys[b]) * cx;
+        const float vm = __ldg(row + xm), v0 = __ldg(row + x0), v1 = __ldg(row + x1), vp = __ldg(row + xp);
+        xl[a][b][0] = q > 0 ? lerp_lo(vm, v0) : v0;
+        xl[a][b][1] = lerp_hi(v0, v1);
+        xl[a][b][2] = lerp_lo(v0, v1);
+        xl[a][b][3] = lerp_hi(v1, vp);
       }
-      float o[4];
+    // then y: fine rows 2jy (from coarse rows jy-1, jy) and 2jy+1 (jy, jy+1)
+    float yl[3][2][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float cz0 = (1.f - wy) * xl[0][i] + wy * xl[1][i];
-        const float cz1 = (1.f - wy) * xl[2][i] + wy * xl[3][i];
-        o[i] = (1.f - wz) * cz0 + wz * cz1;
+        yl[a][0][i] = jy > 0 ? lerp_lo(xl[a][0][i], xl[a][1][i]) : xl[a][1][i];
+        yl[a][1][i] = lerp_hi(xl[a][1][i], xl[a][2][i]);
       }
-      orow[q] = make_float4(o[0], o[1], o[2], o[3]);
-    }
+    // then z, and the four 16-byte rows of the block
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy) {
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          o[i] = dz == 0 ? (kz > 0 ? lerp_lo(yl[0][dy][i], yl[1][dy][i]) : yl[1][dy][i])
+                         : lerp_hi(yl[1][dy][i], yl[2][dy][i]);
+        const long long p = (long long)(2 * kz + dz) * fxy + (long long)(2 * jy + dy) * fx + 4 * q;
+        *reinterpret_cast<float4 *>(out + p) = make_float4(o[0], o[1], o[2], o[3]);
+      }
   }
 }
 
@@ -411,10 +430,7 @@ void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, c
 
 void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s) {
   if (coarse.nx % 2 == 0) {  // fine rows of a multiple of 4 cells: 16-byte stores
-    const long long rows = (long long)coarse.ny * 2 * coarse.nz * 2;
-    const int threads = coarse.nx * 2 / 4 >= 256 ? 256 : (coarse.nx * 2 / 4 >= 128 ? 128 : 64);
-    long long g = rows < 148LL * 32 ? rows : 148LL * 32;
-    k_interp4<<<(int)g, threads, 0, s>>>(in, coarse, out, st);
+    k_interp_blk<<<grid_for((long long)(coarse.nx / 2) * coarse.ny * coarse.nz, 256), 256, 0, s>>>(in, coarse, out, st);
     return;
   }
   k_interp<<<grid_for(coarse.n() * 8, 256), 256, 0, s>>>(in, coarse, out, st);
