@@ -75,17 +75,26 @@ __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast
 __device__ __forceinline__ uchar4 ldl4(const uint8_t *p) { return *reinterpret_cast<const uchar4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float f4(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-__device__ __forceinline__ uint8_t u4(const uchar4 &v, int e) {
-  return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-}
 
 constexpr int kThreads = 256;
-inline int grid4(long long n4, int num_sms) {
+inline int grid4(long long n4, int num_sms, int per_sm = 8) {
   long long b = (n4 + kThreads - 1) / kThreads;
-  long long cap = (long long)num_sms * 8;
+  long long cap = (long long)num_sms * per_sm;  // one wave: the loops are grid-strided
   if (cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // the partials buffer holds kRedMaxBlocks rows
   if (b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
+}
+
+// Resident blocks per SM of a kernel (looked up once per kernel).
+template <auto F>
+int resident_blocks() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, F, kThreads, 0);
+    per_sm = b < 1 ? 1 : b;
+  }
+  return per_sm;
 }
 
 }  // namespace
@@ -145,28 +154,40 @@ __global__ void __launch_bounds__(kThreads) k_combine1_4(const uint8_t *__restri
   if (st->done) return;
   const float c1 = (float)c12[0], c2 = (float)c12[1];
   const int k1 = st->k + 1, no = st->n_ortho;
-  const float *qs[kMaxOrtho] = {qring, qring, qring, qring};
-  int cnt = 0;
-  for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) qs[cnt++] = qring + (size_t)ring_slot(i, no) * n;
+  // q of the previous directions i = k1-1-j (j < no, i >= 1), each without dynamic indexing
+  const int cnt = min(no, k1 - 1);
+  const float *q0 = qring + (size_t)ring_slot(max(k1 - 1, 1), no) * n;
+  const float *q1 = qring + (size_t)ring_slot(max(k1 - 2, 1), no) * n;
+  const float *q2 = qring + (size_t)ring_slot(max(k1 - 3, 1), no) * n;
+  const float *q3 = qring + (size_t)ring_slot(max(k1 - 4, 1), no) * n;
   DF acc[kMaxOrtho];
   const int n4 = n >> 2;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  auto group = [&](int g) {
     const int p = g << 2;
     const uchar4 l = ldl4(lab + p);
     const float4 a = ld4(x1 + p), b = ld4(x2 + p);
+    float4 qv[kMaxOrtho];
+    qv[0] = cnt > 0 ? ld4(q0 + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    qv[1] = cnt > 1 ? ld4(q1 + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    qv[2] = cnt > 2 ? ld4(q2 + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    qv[3] = cnt > 3 ? ld4(q3 + p) : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 zv = make_float4(l.x == kFluid ? fmaf(c1, a.x, c2 * b.x) : 0.f,
                                   l.y == kFluid ? fmaf(c1, a.y, c2 * b.y) : 0.f,
                                   l.z == kFluid ? fmaf(c1, a.z, c2 * b.z) : 0.f,
                                   l.w == kFluid ? fmaf(c1, a.w, c2 * b.w) : 0.f);
     st4(z + p, zv);
 #pragma unroll
-    for (int j = 0; j < kMaxOrtho; ++j) {
-      if (j < cnt) {
-        const float4 q = ld4(qs[j] + p);
-        df_add(acc[j], zv.x * q.x + zv.y * q.y + zv.z * q.z + zv.w * q.w);
-      }
-    }
+    for (int j = 0; j < kMaxOrtho; ++j)
+      if (j < cnt) df_add(acc[j], zv.x * qv[j].x + zv.y * qv[j].y + zv.z * qv[j].z + zv.w * qv[j].w);
+  };
+  // two groups per iteration: twice the loads in flight per thread
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + stride < n4; g += 2 * stride) {
+    group(g);
+    group(g + stride);
   }
+  if (g < n4) group(g);
   double v[kMaxOrtho];
 #pragma unroll
   for (int j = 0; j < kMaxOrtho; ++j) v[j] = df_val(acc[j]);
@@ -185,37 +206,76 @@ __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__r
                                                          const SolveState *st) {
   if (st->done) return;
   const int k1 = st->k + 1, no = st->n_ortho;
-  float c[kMaxOrtho] = {0.f, 0.f, 0.f, 0.f};
-  const float *src[kMaxOrtho] = {zv, zv, zv, zv};
-  int cnt = 0;
-  for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) {
-    c[cnt] = (float)st->coef[k1 - 1 - i];
-    src[cnt] = dring + (size_t)ring_slot(i, no) * n;
-    ++cnt;
-  }
+  const int cnt = min(no, k1 - 1);
+  float c[kMaxOrtho];
+#pragma unroll
+  for (int j = 0; j < kMaxOrtho; ++j) c[j] = j < cnt ? (float)st->coef[j] : 0.f;
+  const float *s0 = dring + (size_t)ring_slot(max(k1 - 1, 1), no) * n;
+  const float *s1 = dring + (size_t)ring_slot(max(k1 - 2, 1), no) * n;
+  const float *s2 = dring + (size_t)ring_slot(max(k1 - 3, 1), no) * n;
+  const float *s3 = dring + (size_t)ring_slot(max(k1 - 4, 1), no) * n;
   float *dst = dring + (size_t)ring_slot(k1, no) * n;
   const int n4 = n >> 2;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  auto group = [&](int g) {
     const int p = g << 2;
     float4 v = ld4(zv + p);
+    const float *src[kMaxOrtho] = {s0, s1, s2, s3};
 #pragma unroll
     for (int j = 0; j < kMaxOrtho; ++j) {
       if (j < cnt) {
-        const float4 s = ld4(src[j] + p);
-        v.x -= c[j] * s.x;
-        v.y -= c[j] * s.y;
-        v.z -= c[j] * s.z;
-        v.w -= c[j] * s.w;
+        const float4 sv = ld4(src[j] + p);
+        v.x -= c[j] * sv.x;
+        v.y -= c[j] * sv.y;
+        v.z -= c[j] * sv.z;
+        v.w -= c[j] * sv.w;
       }
     }
     st4(dst + p, v);
+  };
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + stride < n4; g += 2 * stride) {
+    group(g);
+    group(g + stride);
+  }
+  if (g < n4) group(g);
+}
+
+// Per-cell stencil code of the masked 7-point Laplacian (Sec. 3.2), built once
+// per solve from the labels: bits 0-5 = the neighbour -x, +x, -y, +y, -z, +z
+// is fluid (inside the grid), bits 8-10 = number of air neighbours, bit 15 =
+// the cell itself is fluid.
+__global__ void __launch_bounds__(kThreads) k_lap_codes(const uint8_t *__restrict__ lab, Dims dm,
+                                                        uint16_t *__restrict__ code) {
+  const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
+  const long long n = dm.n();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(p, dm, x, y, z);
+    uint32_t c = 0;
+    if (lab[p] == kFluid) {
+      c = 0x8000u;
+      const long long nb[6] = {p - 1, p + 1, p - nx, p + nx, p - (long long)nx * ny, p + (long long)nx * ny};
+      const bool in[6] = {x > 0, x < nx - 1, y > 0, y < ny - 1, z > 0, z < nz - 1};
+      uint32_t nair = 0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        if (!in[k]) continue;
+        const uint8_t l = lab[nb[k]];
+        if (l == kFluid) c |= 1u << k;
+        else if (l == kAir) nair += 1;
+      }
+      c |= nair << 8;
+    }
+    code[p] = (uint16_t)c;
   }
 }
 
-// q_k = A d_k (masked 7-point Laplacian, difference form) with the dot
-// products d.q and r.d; the last block computes the line search
+// q_k = A d_k (masked 7-point Laplacian, difference form: sum over the fluid
+// neighbours n of (d_p - d_n), plus d_p per air neighbour, 0 off fluid) with
+// the dot products d.q and r.d; the last block computes the line search
 // alpha = r^T d / d^T A d and flags breakdown (d^T A d <= 0 or non-finite).
-__global__ void __launch_bounds__(kThreads) k_lap4(const uint8_t *__restrict__ lab, Dims dm,
+__global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ code, Dims dm,
                                                    const float *__restrict__ dring, float *__restrict__ qring,
                                                    const float *__restrict__ r, double *__restrict__ part,
                                                    unsigned *ticket, SolveState *st) {
@@ -227,12 +287,11 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint8_t *__restrict__ l
   float *q = qring + (size_t)slot * n;
   DF a0, a1;
   const int n4 = n >> 2;
-  const uchar4 solid4 = make_uchar4(kSolid, kSolid, kSolid, kSolid);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
     const int p = g << 2;
-    const uchar4 lc = ldl4(lab + p);
-    if (lc.x != kFluid && lc.y != kFluid && lc.z != kFluid && lc.w != kFluid) {
+    const ushort4 cc = *reinterpret_cast<const ushort4 *>(code + p);
+    if (((cc.x | cc.y | cc.z | cc.w) & 0x8000u) == 0u) {
       st4(q + p, zero4);
       continue;
     }
@@ -241,29 +300,22 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint8_t *__restrict__ l
     const int y = yz % ny, z = yz / ny;
     const float4 dc = ld4(d + p);
     const float dxl = x0 > 0 ? d[p - 1] : 0.f;
-    const uint8_t lxl = x0 > 0 ? lab[p - 1] : (uint8_t)kSolid;
     const float dxr = x0 + 4 < nx ? d[p + 4] : 0.f;
-    const uint8_t lxr = x0 + 4 < nx ? lab[p + 4] : (uint8_t)kSolid;
     const float4 dym = y > 0 ? ld4(d + p - nx) : zero4, dyp = y < ny - 1 ? ld4(d + p + nx) : zero4;
     const float4 dzm = z > 0 ? ld4(d + p - nxy) : zero4, dzp = z < nz - 1 ? ld4(d + p + nxy) : zero4;
-    const uchar4 lym = y > 0 ? ldl4(lab + p - nx) : solid4, lyp = y < ny - 1 ? ldl4(lab + p + nx) : solid4;
-    const uchar4 lzm = z > 0 ? ldl4(lab + p - nxy) : solid4, lzp = z < nz - 1 ? ldl4(lab + p + nxy) : solid4;
+    const uint16_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
     float qo[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
+      const uint32_t c = cs[e];
       const float dp = f4(dc, e);
-      float acc = 0.f;
-      int nair = 0;
       const float nv[6] = {e == 0 ? dxl : f4(dc, e - 1), e == 3 ? dxr : f4(dc, e + 1), f4(dym, e), f4(dyp, e),
                            f4(dzm, e), f4(dzp, e)};
-      const uint8_t nl[6] = {e == 0 ? lxl : u4(lc, e - 1), e == 3 ? lxr : u4(lc, e + 1), u4(lym, e), u4(lyp, e),
-                             u4(lzm, e), u4(lzp, e)};
+      float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        if (nl[k] == kFluid) acc += dp - nv[k];
-        else if (nl[k] == kAir) nair += 1;
-      }
-      qo[e] = u4(lc, e) == kFluid ? acc + (float)nair * dp : 0.f;
+      for (int k = 0; k < 6; ++k)
+        if (c & (1u << k)) acc += dp - nv[k];
+      qo[e] = (c & 0x8000u) ? acc + (float)((c >> 8) & 7u) * dp : 0.f;
     }
     const float4 qv = make_float4(qo[0], qo[1], qo[2], qo[3]);
     st4(q + p, qv);
@@ -338,26 +390,31 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
 // ---------------------------------------------------------------------------
 void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, double *part, unsigned *ticket,
                   double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms, cudaStream_t s) {
-  k_init4<<<grid4(n / 4, num_sms), kThreads, 0, s>>>(lab, n, b, r, x, part, ticket, tol, max_iter, n_ortho, st, hist);
+  k_init4<<<grid4(n / 4, num_sms, resident_blocks<k_init4>()), kThreads, 0, s>>>(lab, n, b, r, x, part, ticket, tol, max_iter, n_ortho, st, hist);
 }
 void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
                        const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
                        cudaStream_t s) {
-  k_combine1_4<<<grid4(n / 4, num_sms), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
+  k_combine1_4<<<grid4(n / 4, num_sms, resident_blocks<k_combine1_4>()), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
 }
 void launch_direction4(int n, const float *z, float *dring, const SolveState *st, int num_sms, cudaStream_t s) {
-  k_direction4<<<grid4(n / 4, num_sms), kThreads, 0, s>>>(n, z, dring, st);
+  k_direction4<<<grid4(n / 4, num_sms, resident_blocks<k_direction4>()), kThreads, 0, s>>>(n, z, dring, st);
 }
-void launch_lap4(const uint8_t *lab, Dims dm, const float *dring, float *qring, const float *r, double *part,
+void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s) {
+  long long b = (dm.n() + kThreads - 1) / kThreads;
+  if (b > 148LL * 16) b = 148LL * 16;
+  k_lap_codes<<<(int)(b < 1 ? 1 : b), kThreads, 0, s>>>(lab, dm, code);
+}
+void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
                  unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
-  k_lap4<<<grid4(dm.n() / 4, num_sms), kThreads, 0, s>>>(lab, dm, dring, qring, r, part, ticket, st);
+  k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(code, dm, dring, qring, r, part, ticket, st);
 }
 void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s) {
   if (recurrence)
-    k_update4<true><<<grid4(n / 4, num_sms), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
+    k_update4<true><<<grid4(n / 4, num_sms, resident_blocks<k_update4<true>>()), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
   else
-    k_update4<false><<<grid4(n / 4, num_sms), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
+    k_update4<false><<<grid4(n / 4, num_sms, resident_blocks<k_update4<false>>()), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
 }
 
 }  // namespace nps

@@ -57,7 +57,9 @@ void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *
                        const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
                        cudaStream_t s);
 void launch_direction4(int n, const float *z, float *dring, const SolveState *st, int num_sms, cudaStream_t s);
-void launch_lap4(const uint8_t *lab, Dims dm, const float *dring, float *qring, const float *r, double *part,
+// per-cell stencil codes of the masked Laplacian (once per solve) and q = A d with them
+void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s);
+void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
                  unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
 void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s);

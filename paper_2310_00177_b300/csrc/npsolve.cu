@@ -50,6 +50,7 @@ struct Workspace {
   long long cap = 0;  // cells of level 1 the buffers were sized for
   size_t bytes = 0;   // device bytes held by this workspace
   float *r = nullptr, *z = nullptr, *dring = nullptr, *qring = nullptr;
+  uint16_t *lapcode = nullptr;  // per-cell stencil codes of the masked Laplacian (vec4 path)
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
   ushort2 *counts[kMaxLevels + 1] = {};
@@ -217,6 +218,7 @@ void free_ws(Workspace &w) {
   w.graph = nullptr;
   cudaFree(w.r);
   cudaFree(w.z);
+  cudaFree(w.lapcode);
   cudaFree(w.dring);
   cudaFree(w.qring);
   for (int l = 0; l <= kMaxLevels; ++l) {
@@ -273,6 +275,7 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     const int R = kRing;
     CK(h, dalloc(&w.bytes, &w.r, cap));
     CK(h, dalloc(&w.bytes, &w.z, cap));
+    CK(h, dalloc(&w.bytes, &w.lapcode, cap));
     CK(h, dalloc(&w.bytes, &w.dring, cap * R));
     CK(h, dalloc(&w.bytes, &w.qring, cap * R));
     long long cl = cap;
@@ -600,6 +603,10 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
     launch_check_labels(lab, d1.n(), w.bad, s);
   }
   launch_pyramid(lab, d1, w.counts, L, s);
+  if (vec4_path(d1)) {
+    launch_lap_codes(lab, d1, w.lapcode, s);
+    h->launches += 1;
+  }
   for (int l = 1; l < L; ++l)
     launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
                h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s);
@@ -865,7 +872,7 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
     }
     {
       ProfScope ps(h, P_LAP, s);
-      launch_lap4(lab, d1, w.dring, w.qring, w.r, w.part, w.tickets + kTicketLap, w.st, h->num_sms, s);
+      launch_lap4(w.lapcode, d1, w.dring, w.qring, w.r, w.part, w.tickets + kTicketLap, w.st, h->num_sms, s);
     }
     ProfScope ps(h, P_UPDATE, s);
     launch_update4(recur, (int)n, x, w.r, w.dring, w.qring, w.part, w.tickets + kTicketUpdate, w.st, w.hist,
