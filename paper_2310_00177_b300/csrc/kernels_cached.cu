@@ -102,11 +102,19 @@ static_assert(sizeof(PlaneDesc) == 160, "plane descriptor is 160 bytes");
 constexpr int DWORDS = (int)sizeof(PlaneDesc) / 4;  // 40
 constexpr int DBUF = ZCG * (int)sizeof(PlaneDesc);  // one unit's descriptors
 
-template <bool BF16C>
+// Slots of the fused level-1 CConv2 (+ combination and orthogonalisation dots):
+// the vector box, x1 and up to two q boxes of the previous directions.
+constexpr int QOFF = SLOT;                    // q box j (32 x 8 x 2) at QOFF + 2048 j
+constexpr int SLOT_F = SLOT + 2 * 2048;       // 9728 bytes, 76 x 128
+constexpr int kMaxFusedOrtho = 2;
+
+template <bool BF16C, bool FUSE = false>
 struct KCfg {
   static constexpr int EB = BF16C ? 56 : 108;        // bytes per cached kernel
   static constexpr int CB = BF16C ? 28672 : 55296;   // circular kernel-block buffer (>= two full planes)
-  static constexpr int SMEM = RV * SLOT + ND * DBUF + CB + kMetaBytes;
+  static constexpr int NRV = FUSE ? 3 : RV;          // step slots
+  static constexpr int SL = FUSE ? SLOT_F : SLOT;    // bytes per slot
+  static constexpr int SMEM = NRV * SL + ND * DBUF + CB + kMetaBytes;
 };
 
 // Image key of a cell: fluid count | air count << 16 (0/1 at level 1); zero
@@ -166,6 +174,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// 4-D tiled TMA load (the fourth coordinate picks a vector of a ring).
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
       : "memory");
 }
 // Bulk (untiled) copy global -> shared; both addresses and the size multiples of 16 bytes.
@@ -540,6 +557,11 @@ struct StreamParams {
   const SolveState *st;
   int *err;
   int mode;             // which outputs are computed (STREAM_MODE_*)
+  // fused level-1 combination: z = mask_fluid(c1 x1 + c2 CConv2) and the dots z . q_i
+  CUtensorMap tq;       // q ring: dims (nx, ny, nz, ring), box 32 x 8 x 2 x 1
+  double *part;         // per-CTA partial dots
+  unsigned *ticket;     // last-CTA-done counter
+  SolveState *stw;      // the solve state (orthogonalisation coefficients are written)
   float kS[27], kF[27], kA[27];  // kernels of the pure-solid, pure-fluid, pure-air windows
   uint32_t ktab[3][27];          // the same as stored in the class tables (BF16 pairs or FP32 words)
 };
@@ -664,22 +686,90 @@ __device__ __forceinline__ void cconv_generic_pair(const StreamParams &P, const 
 // buffer (16-byte aligned): mbarriers, block positions, class tables.
 struct StreamMeta {
   uint64_t full[RV], empty[RV], dfull[ND], dempty[ND];
+  double fsum[4][kMaxFusedOrtho];  // fused dots: per consumer warp
   uint32_t kstart[RV], kend[RV];
   uint32_t ktab[3 * 27];
   int abort_;
+  int last_;
 };
 static_assert(sizeof(StreamMeta) <= kMetaBytes, "stream metadata fits");
+
+namespace {
+
+// Double-float accumulator (error-free TwoSum into a (hi, lo) FP32 pair).
+struct DF {
+  float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void df_add(DF &a, float b) {
+  const float s = a.hi + b;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b - bb);
+  a.hi = s;
+  a.lo += e;
+}
+
+// Consumer-only barrier (named barrier 1): the producer warp has left.
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// End of the fused level-1 CConv2: the CTA's dots z . q_i (fixed order) go to
+// its row of partials; the last CTA to arrive reduces all rows in a fixed
+// order and sets the orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i
+// (Alg. 1), then re-arms the counter.  Deterministic.
+__device__ __noinline__ void fused_finish(const StreamParams &P, StreamMeta &M, DF (&fdot)[kMaxFusedOrtho], int cnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double v[kMaxFusedOrtho];
+#pragma unroll
+  for (int j = 0; j < kMaxFusedOrtho; ++j) {
+    v[j] = (double)fdot[j].hi + (double)fdot[j].lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    if (lane == 0) M.fsum[warp][j] = v[j];
+  }
+  consumers_sync();
+  if (tid == 0) {
+    for (int j = 0; j < kMaxFusedOrtho; ++j)
+      P.part[(size_t)blockIdx.x * kMaxFusedOrtho + j] = ((M.fsum[0][j] + M.fsum[1][j]) + M.fsum[2][j]) + M.fsum[3][j];
+    __threadfence();
+    const unsigned t = atomicAdd(P.ticket, 1u);
+    M.last_ = t == gridDim.x - 1 ? 1 : 0;
+  }
+  consumers_sync();
+  if (!M.last_) return;
+  __threadfence();
+#pragma unroll
+  for (int j = 0; j < kMaxFusedOrtho; ++j) {
+    double a = 0.0;
+    for (int i = tid; i < (int)gridDim.x; i += 128) a += __ldcg(P.part + (size_t)i * kMaxFusedOrtho + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) M.fsum[warp][j] = a;
+  }
+  consumers_sync();
+  if (tid == 0) {
+    SolveState *st = P.stw;
+    const int k1 = st->k + 1, no = st->n_ortho;
+    for (int j = 0; j < kMaxOrtho; ++j) st->coef[j] = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+      const double t = ((M.fsum[0][j] + M.fsum[1][j]) + M.fsum[2][j]) + M.fsum[3][j];
+      st->coef[j] = t / st->dAd[ring_slot(k1 - 1 - j, no)];
+    }
+    *P.ticket = 0u;
+  }
+}
+
+}  // namespace
 
 constexpr int NCW = 4;                    // consumer warps: two tile rows each
 constexpr int NTHREADS = NCW * 32 + 32;   // and one producer warp
 
-template <bool BF16C>
+template <bool BF16C, bool FUSE>
 __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_constant__ StreamParams P) {
-  using C = KCfg<BF16C>;
+  using C = KCfg<BF16C, FUSE>;
+  constexpr int NRV = C::NRV;
   if (P.st && P.st->done) return;
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t *vs = smem;
-  uint8_t *ds = smem + RV * SLOT;
+  uint8_t *ds = smem + NRV * C::SL;
   uint8_t *kb = ds + ND * DBUF;
   StreamMeta &M = *(StreamMeta *)(kb + C::CB);
   volatile int *sabort = &M.abort_;
@@ -689,7 +779,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   const bool has_x1 = P.c12 != nullptr;
 
   if (tid == 0) {
-    for (int i = 0; i < RV; ++i) {
+    for (int i = 0; i < NRV; ++i) {
       mbar_init(&M.full[i], 1);
       mbar_init(&M.empty[i], NCW);
       M.kstart[i] = 0u;
@@ -700,6 +790,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       mbar_init(&M.dempty[i], NCW);
     }
     *sabort = 0;
+    M.last_ = 0;
     umma::fence_mbar_init();
     umma::fence_proxy_async_smem();
   }
@@ -713,9 +804,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
     uint32_t vi = 0, vrel = 0;  // loads issued / slots known released
     uint32_t khead = 0, ktail = 0, kpos = 0;
     uint32_t di = 0;            // descriptor loads issued (= units)
+    // fused: q of the previous directions i = k1-1-j (j < qcnt, i >= 1) of Alg. 1
+    int qcnt = 0, qslot[kMaxFusedOrtho] = {0, 0};
+    if (FUSE) {
+      const int k1 = P.st->k + 1, no = P.st->n_ortho;
+      qcnt = min(min(no, k1 - 1), kMaxFusedOrtho);
+      for (int j = 0; j < kMaxFusedOrtho; ++j) qslot[j] = ring_slot(max(k1 - 1 - j, 1), no);
+    }
     auto release_next = [&]() {
-      const int sl = (int)(vrel % RV);
-      if (!mbar_sleep_wait(&M.empty[sl], (vrel / RV) & 1u, kWaitNs)) {
+      const int sl = (int)(vrel % NRV);
+      if (!mbar_sleep_wait(&M.empty[sl], (vrel / NRV) & 1u, kWaitNs)) {
         fail = true;
         return;
       }
@@ -747,7 +845,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       const int T = (U.nzu + 1) >> 1;
       for (int t = -1; t < T && !fail; ++t) {
         // slot: planes z0+1, z0+2 (prologue: zs-1, zs), x1 of z0, z0+1 and the kernel blocks of z0, z0+1
-        while (!fail && vrel + RV <= vi) release_next();
+        while (!fail && vrel + NRV <= vi) release_next();
         uint32_t kbytes = 0, koff = 0;
         if (t >= 0) {
           if (!dready) {
@@ -769,7 +867,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         const uint32_t waste = wrap ? (uint32_t)C::CB - kpos : 0u;
         while (!fail && vrel < vi && (khead - ktail) + waste + kbytes > (uint32_t)C::CB) release_next();
         if (fail) break;
-        const int sl = (int)(vi % RV);
+        const int sl = (int)(vi % NRV);
         if (wrap) {
           khead += waste;
           kpos = 0;
@@ -777,13 +875,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         M.kstart[sl] = kpos;
         khead += kbytes;
         M.kend[sl] = khead;
-        uint8_t *dst = vs + sl * SLOT;
+        uint8_t *dst = vs + sl * C::SL;
         uint64_t *bar = &M.full[sl];
         const int zv = t < 0 ? U.zs - 1 : U.zs + 2 * t + 1;
         const bool x1 = has_x1 && t >= 0;
-        mbar_expect_tx(bar, 2u * VPLANE + (x1 ? 2u * NT * 4u : 0u) + kbytes);
+        const int nq = (FUSE && t >= 0) ? qcnt : 0;
+        mbar_expect_tx(bar, 2u * VPLANE + (x1 ? 2u * NT * 4u : 0u) + (uint32_t)nq * 2u * NT * 4u + kbytes);
         tma_load_3d(dst, &P.tv, U.x0 - 4, U.y0 - 1, zv, bar);
         if (x1) tma_load_3d(dst + X1OFF, &P.tx1, U.x0, U.y0, U.zs + 2 * t, bar);
+        if (FUSE)
+          for (int j = 0; j < nq; ++j) tma_load_4d(dst + QOFF + 2 * NT * 4 * j, &P.tq, U.x0, U.y0, U.zs + 2 * t, qslot[j], bar);
         if (kbytes) bulk_load(kb + kpos, P.cache + (size_t)koff * C::EB, kbytes, bar);
         kpos += kbytes;
         ++vi;
@@ -794,8 +895,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       if (P.err) atomicExch(P.err, 1);
     }
     // every copy must have landed before the CTA may exit
-    for (uint32_t i = vi > (uint32_t)RV ? vi - RV : 0u; i < vi; ++i)
-      (void)mbar_sleep_wait(&M.full[i % RV], (i / RV) & 1u, kWaitNs);
+    for (uint32_t i = vi > (uint32_t)NRV ? vi - NRV : 0u; i < vi; ++i)
+      (void)mbar_sleep_wait(&M.full[i % NRV], (i / NRV) & 1u, kWaitNs);
     for (uint32_t m = di > (uint32_t)ND ? di - ND : 0u; m < di; ++m)
       (void)mbar_sleep_wait(&M.dfull[m % ND], (m / ND) & 1u, kWaitNs);
     return;
@@ -822,6 +923,9 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   // box index of the cell (x-1, y-1) of row ra in a plane (the box starts at x0-4, y0-1)
   const int vbase = ra * BXW + xb + 3;
   uint32_t sl = 0, sph = 0;  // next slot and the parity of its phase
+  DF fdot[kMaxFusedOrtho];   // fused: per-thread double-float dots z . q_i
+  int fqcnt = 0;
+  if (FUSE) fqcnt = min(min(P.st->n_ortho, P.st->k), kMaxFusedOrtho);
 
   for (int m = 0; ok; ++m) {
     const int u = blockIdx.x + m * G;
@@ -835,7 +939,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
     Col pA, pB;  // planes zs-1, zs
     {
       if (!wait(&M.full[sl], sph)) break;
-      const float *pl = (const float *)(vs + sl * SLOT);
+      const float *pl = (const float *)(vs + sl * C::SL);
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         const int e = vbase + (q / 3) * BXW + q % 3;
@@ -844,7 +948,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
-      if (++sl == RV) {
+      if (++sl == NRV) {
         sl = 0;
         sph ^= 1u;
       }
@@ -858,7 +962,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       const int j0 = 2 * t;
       const bool two = j0 + 1 < U.nzu;
       if (!wait(&M.full[sl], sph)) break;
-      const uint8_t *slot = vs + sl * SLOT;
+      const uint8_t *slot = vs + sl * C::SL;
       const float *pl = (const float *)slot;
       Col pC, pD;  // planes z0+1, z0+2
 #pragma unroll
@@ -893,16 +997,37 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
           }
         }
       }
+      if (FUSE) {
+        // z = mask_fluid(c1 x1 + c2 x2) (Sec. 4.2 output restriction) and the dots z . q_i
+        const uint32_t bit = 1u << xb;
+        const PlaneDesc &d0 = D[j0];
+        bool fl[4];
+        fl[0] = (d0.row[ra].w & bit) != 0u;
+        fl[1] = (d0.row[ra + 1].w & bit) != 0u;
+        fl[2] = two && (D[j0 + 1].row[ra].w & bit) != 0u;
+        fl[3] = two && (D[j0 + 1].row[ra + 1].w & bit) != 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] = fl[i] ? fmaf(c1, x1v[i], c2 * acc[i]) : 0.f;
+#pragma unroll
+        for (int j = 0; j < kMaxFusedOrtho; ++j) {
+          if (j < fqcnt) {
+            const float *qs = (const float *)(slot + QOFF + 2 * NT * 4 * j) + ra * TX + xb;
+            df_add(fdot[j], (acc[0] * qs[0] + acc[1] * qs[TX]) + (acc[2] * qs[NT] + acc[3] * qs[NT + TX]));
+          }
+        }
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
-      if (++sl == RV) {
+      if (++sl == NRV) {
         sl = 0;
         sph ^= 1u;
       }
+      if (!FUSE) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        acc[i] *= sc;
-        if (has_x1) acc[i] = fmaf(c1, x1v[i], c2 * acc[i]);
+        for (int i = 0; i < 4; ++i) {
+          acc[i] *= sc;
+          if (has_x1) acc[i] = fmaf(c1, x1v[i], c2 * acc[i]);
+        }
       }
       if (in_a) op[0] = acc[0];
       if (in_b) op[P.dm.nx] = acc[1];
@@ -926,6 +1051,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
     __syncwarp();
     if (lane == 0) mbar_arrive(&M.dempty[m % ND]);
   }
+  if (FUSE) fused_finish(P, M, fdot, fqcnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -938,7 +1064,7 @@ int grid_for_units(long long units, int cap) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <bool BF16C>
+template <bool BF16C, bool FUSE>
 int stream_occupancy() {
   // per device: the dynamic shared-memory opt-in is a per-device function attribute
   static int occ[64] = {};
@@ -947,8 +1073,9 @@ int stream_occupancy() {
   if (dev < 0 || dev >= 64) dev = 0;
   if (!occ[dev]) {
     int o = 0;
-    cudaFuncSetAttribute(k_cconv_stream<BF16C>, cudaFuncAttributeMaxDynamicSharedMemorySize, KCfg<BF16C>::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C>, NTHREADS, KCfg<BF16C>::SMEM);
+    using C = KCfg<BF16C, FUSE>;
+    cudaFuncSetAttribute(k_cconv_stream<BF16C, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C, FUSE>, NTHREADS, C::SMEM);
     occ[dev] = o < 1 ? 1 : o;
   }
   return occ[dev];
@@ -986,6 +1113,18 @@ bool encode_map(CUtensorMap *m, const float *base, Dims d, int bw, int bh, int b
   return r == CUDA_SUCCESS;
 }
 
+CUresult encode_map_4d(CUtensorMap *m, const float *base, Dims d, int nring) {
+  const EncodeTiledFn fn = encode_fn();
+  if (!fn) return CUDA_ERROR_NOT_SUPPORTED;
+  cuuint64_t dims[4] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)nring};
+  const cuuint64_t rowb = (cuuint64_t)d.nx * 4u;
+  cuuint64_t strides[3] = {rowb, rowb * (cuuint64_t)d.ny, rowb * (cuuint64_t)d.ny * (cuuint64_t)d.nz};
+  cuuint32_t box[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 2u, 1u};
+  cuuint32_t es[4] = {1u, 1u, 1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
 }  // namespace
 
 bool stream_shape_ok(Dims d) { return d.nx % 4 == 0 && d.nx >= 4; }
@@ -998,6 +1137,8 @@ long long stream_desc_count(Dims d) {
 size_t stream_desc_bytes() { return sizeof(PlaneDesc); }
 
 int cached_entry_bytes(bool bf16) { return bf16 ? KCfg<true>::EB : KCfg<false>::EB; }
+
+bool stream_fusion_ok(int n_ortho) { return n_ortho <= kMaxFusedOrtho; }
 
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
                      int num_sms, cudaStream_t s) {
@@ -1032,10 +1173,18 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
 
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
-                        const SolveState *st, int *err, int num_sms, cudaStream_t s) {
+                        const SolveState *st, int *err, int num_sms, cudaStream_t s, const StreamFusion *fuse) {
   StreamParams P;
   memset(&P, 0, sizeof(P));
-  P.mode = mode;
+  P.mode = fuse ? STREAM_MODE_FLUID_ONLY : mode;
+  if (fuse) {
+    // the q ring as a 4-D tensor (nx, ny, nz, slot); slot stride = one grid
+    const CUresult r = encode_map_4d(&P.tq, fuse->qring, dm, fuse->nring);
+    if (r != CUDA_SUCCESS) return -1;
+    P.part = fuse->part;
+    P.ticket = fuse->ticket;
+    P.stw = fuse->st;
+  }
   if (!encode_map(&P.tv, v, dm, BXW, BYH, 2)) return -1;
   if (c12 && !encode_map(&P.tx1, x1, dm, TX, TY, 2)) return -1;
   // class tables in the stored format: BF16 pairs (the constants are BF16 values in that form) or FP32 words
@@ -1070,15 +1219,23 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
     P.kF[a] = kfix[27 + a];
     P.kA[a] = kfix[54 + a];
   }
-  const int cap = num_sms * (bf16 ? stream_occupancy<true>() : stream_occupancy<false>());
+  const int occ = fuse ? (bf16 ? stream_occupancy<true, true>() : stream_occupancy<false, true>())
+                       : (bf16 ? stream_occupancy<true, false>() : stream_occupancy<false, false>());
+  int cap = num_sms * occ;
+  if (fuse && cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // one row of partials per CTA
   // the longest even chunk of planes that still gives every resident CTA a unit
   int zc = 32;
   while (zc > 2 && (long long)P.ntiles * ((dm.nz + zc - 1) / zc) < cap) zc >>= 1;
   P.zc = zc;
   P.units = P.ntiles * ((dm.nz + zc - 1) / zc);
   const int grid = grid_for_units(P.units, cap);
-  if (bf16) k_cconv_stream<true><<<grid, NTHREADS, KCfg<true>::SMEM, s>>>(P);
-  else k_cconv_stream<false><<<grid, NTHREADS, KCfg<false>::SMEM, s>>>(P);
+  if (fuse) {
+    if (bf16) k_cconv_stream<true, true><<<grid, NTHREADS, KCfg<true, true>::SMEM, s>>>(P);
+    else k_cconv_stream<false, true><<<grid, NTHREADS, KCfg<false, true>::SMEM, s>>>(P);
+  } else {
+    if (bf16) k_cconv_stream<true, false><<<grid, NTHREADS, KCfg<true, false>::SMEM, s>>>(P);
+    else k_cconv_stream<false, false><<<grid, NTHREADS, KCfg<false, false>::SMEM, s>>>(P);
+  }
   return 0;
 }
 

@@ -92,9 +92,22 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
 // level-1 CConv2 inside the network).  Returns -1 if a tensor map cannot be
 // encoded.
 enum { STREAM_MODE_ALL = 0, STREAM_MODE_ZERO_PURE = 1, STREAM_MODE_FLUID_ONLY = 2 };
+// Fusion of the level-1 combination into the level-1 CConv2 inside a solve:
+// out = z = mask_fluid(c1 x1 + c2 CConv2(v)) and the orthogonalisation dots
+// z . q_i of the previous directions (ring of nring vectors of one grid each),
+// finished by the last CTA into st->coef (as launch_combine1_4).
+struct StreamFusion {
+  const float *qring;
+  int nring;
+  double *part;
+  unsigned *ticket;
+  SolveState *st;
+};
+bool stream_fusion_ok(int n_ortho);  // the fused kernel loads up to two previous directions
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
-                        const SolveState *st, int *err, int num_sms, cudaStream_t s);
+                        const SolveState *st, int *err, int num_sms, cudaStream_t s,
+                        const StreamFusion *fuse = nullptr);
 void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
 
 // kernels_train.cu

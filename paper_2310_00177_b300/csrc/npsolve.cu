@@ -487,14 +487,14 @@ void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const 
 // combination out = c1 x1 + c2 CConv(...).
 void cconv_cached(npsolve *h, Dims d1, int lvl, int type, const float *in, const float *vscale, float *out,
                   float *pooled, const float *x1, const double *c12, const SolveState *st, cudaStream_t s,
-                  int mode = STREAM_MODE_ALL) {
+                  int mode = STREAM_MODE_ALL, const StreamFusion *fuse = nullptr) {
   Workspace &w = h->ws;
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   if (launch_cconv_stream(h->cfg.precision == NPSOLVE_BF16, level_dims(d1, lvl), h->kfix_host.data() + (size_t)idx * 81,
                           w.kdesc[lvl], w.kcache[idx], in, vscale, out, pooled, x1, c12, mode, st, h->umma_err,
-                          h->num_sms, s))
+                          h->num_sms, s, fuse))
     h->stream_err = true;
 }
 
@@ -564,6 +564,12 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       }
       if (l > 1) {  // CConv2 and the combination in one pass
         cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s);
+        continue;
+      }
+      if (st && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
+        // level-1 CConv2, z = mask_fluid(c1 x1 + c2 x2) and the orthogonalisation dots in one pass
+        const StreamFusion fu{w.qring, kRing, w.part, w.tickets + kTicketCombine, st};
+        cconv_cached(h, d1, 1, 2, w.r2[1], nullptr, z, nullptr, w.x1[1], c12, st, s, STREAM_MODE_FLUID_ONLY, &fu);
         continue;
       }
       // level 1: only the fluid cells of x2 enter z (the output restriction)
