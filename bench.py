@@ -61,7 +61,7 @@ BYTES_PER_CELL = {
     "lap_alpha": 4 + 1 + 4 + 4,  # d, labels, r -> q
     "update": 8 + 8 + 4 + 4 + 4 + 4,  # x r/w (FP64), r r/w, d, q
     "ortho_dir": 4 + 4 + 4 + 4,  # z, d1, d2 -> d
-    "combine": 4 + 4 + 4 + 1 + 8,  # x1, x2 -> z, labels, q1, q2 (level 1)
+    "combine": 4 + 4 + 4 + 1 + 8,  # x1, x2 -> z, labels, q1, q2 (level 1, unfused)
     "interp": 4 + 0.5,           # fine out, coarse in (level 1 dominates)
     "pool": 4 + 0.5,
 }
@@ -314,18 +314,21 @@ def main():
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms / max(dom_launches, 1) / 1e3
     if dom == "cconv_l1":
-        # the level-1 CConv (TMA-streamed z-march): per cell it reads the input
-        # (4 B) and the plane descriptors (80 B per 128 cells), for the cells
-        # with a mixed image window the cached kernel (56 B, BF16), and writes
-        # the output (4 B); CConv1 also writes the pooled output (0.5 B).
-        # Averaged over the two launches of an iteration.
+        # the level-1 CConv launches (TMA-streamed z-march) per cell: the input
+        # (4 B), the plane descriptors (160 B per 256 cells), the cached kernels
+        # of the mixed-window cells (56 B BF16 each), the output (4 B); CConv1
+        # adds the pooled output (0.5 B); the CConv2 fused with the level-1
+        # combination adds x1 (4 B) and the two previous q (8 B).  Averaged over
+        # the two launches of an iteration.
         mixed = sol.mixed_cells(1)
         frac = mixed / n if mixed >= 0 else 0.0
-        bpc = 4 + 80 / 128 + 56.0 * frac + 4 + 0.25
+        common = 4 + 160 / 256 + 56.0 * frac + 4
+        bpc = ((common + 0.5) + (common + 4 + 8)) / 2
         achieved = bpc * n / avg_s / 1e9
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1 + CConv2, TMA-streamed)",
+                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1; CConv2 fused with the "
+                "combination and orthogonalisation dots)",
                 "algorithmic": f"{bpc:.2f} B/cell x {n} cells (mixed-window fraction {frac:.4f})",
                 "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"] + " (hbm_gbs)"}
     else:

@@ -559,7 +559,7 @@ struct StreamParams {
   int mode;             // which outputs are computed (STREAM_MODE_*)
   // fused level-1 combination: z = mask_fluid(c1 x1 + c2 CConv2) and the dots z . q_i
   CUtensorMap tq;       // q ring: dims (nx, ny, nz, ring), box 32 x 8 x 2 x 1
-  double *part;         // per-CTA partial dots
+  double *part;         // partial dots, one row per CTA
   unsigned *ticket;     // last-CTA-done counter
   SolveState *stw;      // the solve state (orthogonalisation coefficients are written)
   float kS[27], kF[27], kA[27];  // kernels of the pure-solid, pure-fluid, pure-air windows
@@ -686,7 +686,8 @@ __device__ __forceinline__ void cconv_generic_pair(const StreamParams &P, const 
 // buffer (16-byte aligned): mbarriers, block positions, class tables.
 struct StreamMeta {
   uint64_t full[RV], empty[RV], dfull[ND], dempty[ND];
-  double fsum[4][kMaxFusedOrtho];  // fused dots: per consumer warp
+  double fsum[4][kMaxFusedOrtho];  // fused dots: per consumer warp (final reduction)
+  int unit[ND];                       // the unit of each descriptor buffer (-1: no more units)
   uint32_t kstart[RV], kend[RV];
   uint32_t ktab[3 * 27];
   int abort_;
@@ -711,19 +712,20 @@ __device__ __forceinline__ void df_add(DF &a, float b) {
 // Consumer-only barrier (named barrier 1): the producer warp has left.
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// End of the fused level-1 CConv2: the CTA's dots z . q_i (fixed order) go to
-// its row of partials; the last CTA to arrive reduces all rows in a fixed
-// order and sets the orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i
-// (Alg. 1), then re-arms the counter.  Deterministic.
+// End of the fused level-1 CConv2: each consumer warp's dots z . q_i (its
+// patch in all of the CTA's units; the units of a CTA are fixed by the grid,
+// blockIdx.x + m gridDim.x) go to the CTA's row of partials in a fixed order;
+// the last CTA to arrive reduces the rows in a fixed order and sets the
+// orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i (Alg. 1), then
+// re-arms the counter.  Deterministic for a given grid.
 __device__ __noinline__ void fused_finish(const StreamParams &P, StreamMeta &M, DF (&fdot)[kMaxFusedOrtho], int cnt) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double v[kMaxFusedOrtho];
 #pragma unroll
   for (int j = 0; j < kMaxFusedOrtho; ++j) {
-    v[j] = (double)fdot[j].hi + (double)fdot[j].lo;
+    double v = (double)fdot[j].hi + (double)fdot[j].lo;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
-    if (lane == 0) M.fsum[warp][j] = v[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) M.fsum[warp][j] = v;
   }
   consumers_sync();
   if (tid == 0) {
@@ -820,26 +822,34 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       ktail = M.kend[sl];
       ++vrel;
     };
-    auto issue_desc = [&](int m) {  // descriptors of this CTA's m-th unit
-      const int u = blockIdx.x + m * G;
-      if (u >= P.units || fail) return;
-      const Unit U = unit_at(P, u);
+    // units blockIdx.x + m G: the CTAs sweep the units in order together, so
+    // neighbouring tiles are streamed at about the same time and their halo
+    // rows are read from HBM once (L2); handing units out dynamically was
+    // measured 10-20% slower for that reason.
+    // descriptors of this CTA's m-th unit u (u < 0: tell the consumers there is none)
+    auto issue_desc = [&](int m, int u) {
+      if (fail) return;
       const int b = m % ND;
       if (m >= ND && !mbar_sleep_wait(&M.dempty[b], ((m / ND) - 1) & 1, kWaitNs)) {
         fail = true;
         return;
       }
-      mbar_expect_tx(&M.dfull[b], (uint32_t)(U.nzu * (int)sizeof(PlaneDesc)));
-      bulk_load(ds + b * DBUF, P.desc + (size_t)U.t * nz + U.zs, (uint32_t)(U.nzu * (int)sizeof(PlaneDesc)),
-                &M.dfull[b]);
+      M.unit[b] = u;
+      if (u < 0) {
+        mbar_arrive(&M.dfull[b]);
+      } else {
+        const Unit U = unit_at(P, u);
+        mbar_expect_tx(&M.dfull[b], (uint32_t)(U.nzu * (int)sizeof(PlaneDesc)));
+        bulk_load(ds + b * DBUF, P.desc + (size_t)U.t * nz + U.zs, (uint32_t)(U.nzu * (int)sizeof(PlaneDesc)),
+                  &M.dfull[b]);
+      }
       ++di;
     };
-    issue_desc(0);
-    for (int m = 0; !fail && !*sabort; ++m) {
-      const int u = blockIdx.x + m * G;
-      if (u >= P.units) break;
+    int u = (int)blockIdx.x < P.units ? (int)blockIdx.x : -1;
+    issue_desc(0, u);
+    for (int m = 0; u >= 0 && !fail && !*sabort; ++m) {
       const Unit U = unit_at(P, u);
-      issue_desc(m + 1);  // one unit ahead
+      const int un = u + G < P.units ? u + G : -1;
       const PlaneDesc *D = (const PlaneDesc *)(ds + (m % ND) * DBUF);
       bool dready = false;
       const int T = (U.nzu + 1) >> 1;
@@ -888,7 +898,10 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         if (kbytes) bulk_load(kb + kpos, P.cache + (size_t)koff * C::EB, kbytes, bar);
         kpos += kbytes;
         ++vi;
+        if (t == 0) issue_desc(m + 1, un);  // one unit ahead
       }
+      if (fail) break;
+      u = un;
     }
     if (fail) {
       *sabort = 1;
@@ -928,14 +941,14 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   if (FUSE) fqcnt = min(min(P.st->n_ortho, P.st->k), kMaxFusedOrtho);
 
   for (int m = 0; ok; ++m) {
-    const int u = blockIdx.x + m * G;
-    if (u >= P.units) break;
+    if (!wait(&M.dfull[m % ND], (m / ND) & 1)) break;
+    const int u = M.unit[m % ND];
+    if (u < 0) break;
     const Unit U = unit_at(P, u);
     const int gx = U.x0 + xb, gy = U.y0 + ra;
     const bool in_x = gx < P.dm.nx;
     const bool in_a = in_x && gy < P.dm.ny, in_b = in_x && gy + 1 < P.dm.ny;
     const PlaneDesc *D = (const PlaneDesc *)(ds + (m % ND) * DBUF);
-    if (!wait(&M.dfull[m % ND], (m / ND) & 1)) break;
     Col pA, pB;  // planes zs-1, zs
     {
       if (!wait(&M.full[sl], sph)) break;
@@ -1173,7 +1186,8 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
 
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
-                        const SolveState *st, int *err, int num_sms, cudaStream_t s, const StreamFusion *fuse) {
+                        const SolveState *st, int *err, int num_sms, cudaStream_t s,
+                        const StreamFusion *fuse) {
   StreamParams P;
   memset(&P, 0, sizeof(P));
   P.mode = fuse ? STREAM_MODE_FLUID_ONLY : mode;
@@ -1223,11 +1237,22 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
                        : (bf16 ? stream_occupancy<true, false>() : stream_occupancy<false, false>());
   int cap = num_sms * occ;
   if (fuse && cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // one row of partials per CTA
-  // the longest even chunk of planes that still gives every resident CTA a unit
+  // the chunk of planes (even) that minimises the slots on the critical path:
+  // units per CTA (rounded up) x (steps per unit + the prologue slot)
   int zc = 32;
-  while (zc > 2 && (long long)P.ntiles * ((dm.nz + zc - 1) / zc) < cap) zc >>= 1;
+  long long best = -1;
+  for (int c = 32; c >= 2; c >>= 1) {
+    const long long units = (long long)P.ntiles * ((dm.nz + c - 1) / c);
+    const long long per_cta = (units + cap - 1) / cap;
+    const long long cost = per_cta * ((c + 1) / 2 + 1);
+    if (best < 0 || cost < best) {
+      best = cost;
+      zc = c;
+    }
+  }
   P.zc = zc;
   P.units = P.ntiles * ((dm.nz + zc - 1) / zc);
+  if (fuse && (size_t)cap * kMaxFusedOrtho > fuse->part_cap) return -1;  // partials do not fit
   const int grid = grid_for_units(P.units, cap);
   if (fuse) {
     if (bf16) k_cconv_stream<true, true><<<grid, NTHREADS, KCfg<true, true>::SMEM, s>>>(P);

@@ -132,6 +132,9 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
     s.max_iter = max_iter;
     s.n_ortho = n_ortho;
     s.pad_ = 0;
+    s.x_pend = 0;
+    s.alpha_pend = 0.0;
+    s.pend_slot = 0;
     s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
     if (!isfinite(t[0])) s.done = kDoneBadInput;
     else if (!(t[0] >= s.eps2) || t[0] == 0.0) s.done = kDoneConverged;
@@ -337,6 +340,11 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
 
 // x += alpha d (FP64), r -= alpha q (recurrence) with ||r||^2; the last block
 // advances the iteration and applies the stop test ||r_k|| < tol ||b||.
+// In the recurrence mode x is not read during the iterations, so with a ring
+// of at least two directions the steps of two iterations go into x together,
+// x += alpha_{k-1} d_{k-1} + alpha_k d_k in that order (the same FP64
+// arithmetic as two separate updates, one pass over x instead of two); a
+// step left pending at the end is added by k_flush_x.
 template <bool RECUR>
 __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict__ x, float *__restrict__ r,
                                                       const float *__restrict__ dring, const float *__restrict__ qring,
@@ -348,19 +356,33 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
   const float *q = qring + (size_t)slot * n;
   const double a = st->alpha;
   const float af = (float)a;
+  const bool defer_ok = RECUR && st->n_ortho >= 1;
+  const bool pend = st->x_pend != 0;
+  const bool skip_x = defer_ok && !pend;  // this step waits for the next one
+  const double ap = st->alpha_pend;
+  const float *dp = dring + (size_t)st->pend_slot * n;
   DF acc;
   const int n4 = n >> 2;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
     const int p = g << 2;
-    const float4 dv = ld4(d + p);
-    double2 *xp = reinterpret_cast<double2 *>(x + p);
-    double2 x01 = xp[0], x23 = xp[1];
-    x01.x = fma(a, (double)dv.x, x01.x);
-    x01.y = fma(a, (double)dv.y, x01.y);
-    x23.x = fma(a, (double)dv.z, x23.x);
-    x23.y = fma(a, (double)dv.w, x23.y);
-    xp[0] = x01;
-    xp[1] = x23;
+    if (!skip_x) {
+      const float4 dv = ld4(d + p);
+      double2 *xp = reinterpret_cast<double2 *>(x + p);
+      double2 x01 = xp[0], x23 = xp[1];
+      if (pend) {
+        const float4 pv = ld4(dp + p);
+        x01.x = fma(ap, (double)pv.x, x01.x);
+        x01.y = fma(ap, (double)pv.y, x01.y);
+        x23.x = fma(ap, (double)pv.z, x23.x);
+        x23.y = fma(ap, (double)pv.w, x23.y);
+      }
+      x01.x = fma(a, (double)dv.x, x01.x);
+      x01.y = fma(a, (double)dv.y, x01.y);
+      x23.x = fma(a, (double)dv.z, x23.x);
+      x23.y = fma(a, (double)dv.w, x23.y);
+      xp[0] = x01;
+      xp[1] = x23;
+    }
     if (RECUR) {
       const float4 qv = ld4(q + p);
       float4 rv = ld4(r + p);
@@ -376,6 +398,13 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
   double v[1] = {df_val(acc)};
   reduce_and_finish<1>(v, part, ticket, [&](const double *t) {
     const double rr = t[0];
+    if (skip_x) {
+      st->x_pend = 1;
+      st->alpha_pend = a;
+      st->pend_slot = slot;
+    } else {
+      st->x_pend = 0;
+    }
     st->k += 1;
     st->rnorm2 = rr;
     hist[st->k] = sqrt(rr);
@@ -384,6 +413,17 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
     else st->rscale = (float)(1.0 / sqrt(rr));
   });
 }
+
+// Adds a step left pending by k_update4 (x += alpha_pend d_pend); the flag is
+// cleared by k_clear_pend afterwards.
+__global__ void __launch_bounds__(kThreads) k_flush_x(int n, double *__restrict__ x, const float *__restrict__ dring,
+                                                      const SolveState *st) {
+  if (!st->x_pend) return;
+  const double a = st->alpha_pend;
+  const float *d = dring + (size_t)st->pend_slot * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = fma(a, (double)d[i], x[i]);
+}
+__global__ void k_clear_pend(SolveState *st) { st->x_pend = 0; }
 
 // ---------------------------------------------------------------------------
 // Host-side launchers.
@@ -408,6 +448,10 @@ void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t 
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
                  unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
   k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(code, dm, dring, qring, r, part, ticket, st);
+}
+void launch_flush_x(int n, double *x, const float *dring, SolveState *st, int num_sms, cudaStream_t s) {
+  k_flush_x<<<num_sms * 8, kThreads, 0, s>>>(n, x, dring, st);
+  k_clear_pend<<<1, 1, 0, s>>>(st);
 }
 void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s) {

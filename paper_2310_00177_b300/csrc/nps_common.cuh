@@ -57,6 +57,9 @@ struct SolveState {
   int done;             // 0 running, 1 converged, 2 breakdown, 3 non-finite input
   int max_iter;
   int n_ortho;
+  int x_pend;           // 1: alpha_pend d (ring slot pend_slot) is not yet added to x
+  double alpha_pend;    // (the recurrence mode adds the steps of two iterations to x at once)
+  int pend_slot;
   int pad_;
 };
 

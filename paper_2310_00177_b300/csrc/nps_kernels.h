@@ -61,6 +61,8 @@ void launch_direction4(int n, const float *z, float *dring, const SolveState *st
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s);
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
                  unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
+// adds a step of x left pending by the recurrence-mode update (no-op if none)
+void launch_flush_x(int n, double *x, const float *dring, SolveState *st, int num_sms, cudaStream_t s);
 void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s);
 
@@ -99,7 +101,8 @@ enum { STREAM_MODE_ALL = 0, STREAM_MODE_ZERO_PURE = 1, STREAM_MODE_FLUID_ONLY = 
 struct StreamFusion {
   const float *qring;
   int nring;
-  double *part;
+  double *part;     // partial dots: one row of 2 per (unit, consumer warp)
+  size_t part_cap;  // doubles part can hold
   unsigned *ticket;
   SolveState *st;
 };

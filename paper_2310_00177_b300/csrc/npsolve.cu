@@ -61,6 +61,7 @@ struct Workspace {
   size_t kcap[(kMaxLevels + 1) * 2] = {};    // cache entries kcache can hold
   // per level: [2 l] cache entries (blocks padded to 4), [2 l + 1] mixed cells
   unsigned *ktotal = nullptr, *h_ktotal = nullptr;
+  size_t part_cap = 0;        // doubles of part
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
   int hist_cap = 0;
   SolveState *st = nullptr;
@@ -291,7 +292,9 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
         if (l >= 2) CK(h, dalloc(&w.bytes, &w.xc[l], cl));
       }
     }
-    CK(h, dalloc(&w.bytes, &w.part, (size_t)kRedMaxBlocks * kMaxPartials));
+    // reduction partials: per block of the reduction kernels, or per (unit, warp) of the fused CConv
+    w.part_cap = (size_t)kRedMaxBlocks * kMaxPartials + (size_t)(cap / 64) + 64;
+    CK(h, dalloc(&w.bytes, &w.part, w.part_cap));
     CK(h, dalloc(&w.bytes, &w.affc, (size_t)(kMaxLevels + 1) * 2));
     CK(h, dalloc(&w.bytes, &w.relres, 2));
     CK(h, dalloc(&w.bytes, &w.st, 1));
@@ -568,7 +571,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       }
       if (st && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
         // level-1 CConv2, z = mask_fluid(c1 x1 + c2 x2) and the orthogonalisation dots in one pass
-        const StreamFusion fu{w.qring, kRing, w.part, w.tickets + kTicketCombine, st};
+        const StreamFusion fu{w.qring, kRing, w.part, w.part_cap, w.tickets + kTicketCombine, st};
         cconv_cached(h, d1, 1, 2, w.r2[1], nullptr, z, nullptr, w.x1[1], c12, st, s, STREAM_MODE_FLUID_ONLY, &fu);
         continue;
       }
@@ -1013,6 +1016,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     }
     CK(h, cudaStreamSynchronize(s));
     if (nb) hs = w.h_st[(nb - 1) & 1];
+    if (vec4_path(d1)) {  // the recurrence-mode update may leave the last step pending in x
+      launch_flush_x((int)d1.n(), x, w.dring, w.st, h->num_sms, s);
+      h->launches += 2;
+    }
     if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&
         restarts < kMaxRestarts) {
       ProfScope ps(h, P_FINAL, s);
