@@ -50,12 +50,12 @@ ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
 
 # DRAM bytes (read + write) per level-1 CConv launch of the 256^3 workload,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
-# CConv1 and CConv2 launches of one iteration; profiles/); None when the
-# kernel has changed since the counters were taken.
-TRAFFIC_L1 = None
+# CConv1 and CConv2 launches of one iteration, the summary kept in profiles/);
+# None when the kernel has changed since the counters were taken.
+TRAFFIC_L1 = (197.6e6 + 337.8e6) / 2  # ncu: level-1 CConv1 and the fused level-1 CConv2 of one iteration
 
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
-# (inputs read once, outputs written once; see DESIGN.md "Roofline").
+# (inputs read once, outputs written once).
 BYTES_PER_CELL = {
     "cconv_l1": 4 + 0.625 + 4,  # v, descriptors -> out (+ cached kernels, see below)
     "lap_alpha": 4 + 1 + 4 + 4,  # d, labels, r -> q
@@ -93,7 +93,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 200 ms while running."""
+    """nvidia-smi clock / throttle samples every 50 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -108,7 +108,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except OSError:
@@ -201,7 +201,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)

@@ -291,12 +291,12 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
   DF a0, a1;
   const int n4 = n >> 2;
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+  auto group = [&](int g) {
     const int p = g << 2;
     const ushort4 cc = *reinterpret_cast<const ushort4 *>(code + p);
     if (((cc.x | cc.y | cc.z | cc.w) & 0x8000u) == 0u) {
       st4(q + p, zero4);
-      continue;
+      return;
     }
     const int x0 = p % nx;
     const int yz = p / nx;
@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
     const float dxr = x0 + 4 < nx ? d[p + 4] : 0.f;
     const float4 dym = y > 0 ? ld4(d + p - nx) : zero4, dyp = y < ny - 1 ? ld4(d + p + nx) : zero4;
     const float4 dzm = z > 0 ? ld4(d + p - nxy) : zero4, dzp = z < nz - 1 ? ld4(d + p + nxy) : zero4;
+    const float4 rv = ld4(r + p);
     const uint16_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
     float qo[4];
 #pragma unroll
@@ -322,10 +323,16 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
     }
     const float4 qv = make_float4(qo[0], qo[1], qo[2], qo[3]);
     st4(q + p, qv);
-    const float4 rv = ld4(r + p);
     df_add(a0, dc.x * qv.x + dc.y * qv.y + dc.z * qv.z + dc.w * qv.w);
     df_add(a1, rv.x * dc.x + rv.y * dc.y + rv.z * dc.z + rv.w * dc.w);
+  };
+  const int stride = gridDim.x * blockDim.x;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + stride < n4; g += 2 * stride) {
+    group(g);
+    group(g + stride);
   }
+  if (g < n4) group(g);
   double v[2] = {df_val(a0), df_val(a1)};
   reduce_and_finish<2>(v, part, ticket, [&](const double *t) {
     const double dq = t[0], rd = t[1];
