@@ -199,19 +199,19 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // Setup 1: classification.  One CTA (a 32 x 4 tile) per unit of ZCG planes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
-                                                 Dims d, uint32_t full, PlaneDesc *__restrict__ desc,
+                                                 Dims d, uint32_t full, int zcc, PlaneDesc *__restrict__ desc,
                                                  unsigned *__restrict__ totals) {
   __shared__ uint32_t sd[ZCG][DWORDS];
   __shared__ uint32_t sbase;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + ZCG - 1) / ZCG;
+  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + zcc - 1) / zcc;
   const int ntiles = ntx * nty;
   const long long units = (long long)ntiles * nch;
   const uint32_t kF = full, kA = full << 16;
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
     const int t = (int)(u % ntiles), c = (int)(u / ntiles);
     const int x = (t % ntx) * TX + lane, y = (t / ntx) * TY + warp;
-    const int zs = c * ZCG, nzu = min(ZCG, d.nz - zs);
+    const int zs = c * zcc, nzu = min(zcc, d.nz - zs);
     const bool inside = x < d.nx && y < d.ny;
     for (int j = 0; j < nzu; ++j) {
       const int z = zs + j;
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ 
                                                     Dims d, const uint8_t *__restrict__ w0,
                                                     const uint8_t *__restrict__ w1, int nblk,
                                                     const PlaneDesc *__restrict__ desc, uint32_t *__restrict__ cache0,
-                                                    uint32_t *__restrict__ cache1, int *err) {
+                                                    uint32_t *__restrict__ cache1, int zcc, int *err) {
   using namespace umma;
   constexpr int KW = BF16 ? 14 : 27;
   __shared__ __align__(1024) uint8_t sW[2][NSPLIT * kBBytes];
@@ -433,13 +433,13 @@ __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ 
   const uint32_t idesc = idesc_bf16(kTileM, kN);
   uint32_t phase = 0u;
   bool aborted = false;
-  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + ZCG - 1) / ZCG;
+  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + zcc - 1) / zcc;
   const int ntiles = ntx * nty;
   const long long units = (long long)ntiles * nch;
   for (long long u = blockIdx.x; u < units && !aborted; u += gridDim.x) {
     const int t = (int)(u % ntiles), c = (int)(u / ntiles);
     const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-    const int zs = c * ZCG, nzu = min(ZCG, d.nz - zs);
+    const int zs = c * zcc, nzu = min(zcc, d.nz - zs);
     {
       const uint32_t *src = (const uint32_t *)(desc + (size_t)t * d.nz + zs);
       uint32_t *dsd = (uint32_t *)sd;
@@ -1153,28 +1153,40 @@ int cached_entry_bytes(bool bf16) { return bf16 ? KCfg<true>::EB : KCfg<false>::
 
 bool stream_fusion_ok(int n_ortho) { return n_ortho <= kMaxFusedOrtho; }
 
+// Planes per unit of the setup kernels at a level: up to 32 (a unit's kernel
+// blocks are contiguous in the cache, so the chunks must be even), fewer when
+// the level is too small to give every SM a few units.
+static int setup_chunk(Dims d, int num_sms) {
+  const long long ntiles = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+  int zc = ZCG;
+  while (zc > 2 && ntiles * ((d.nz + zc - 1) / zc) < 4LL * num_sms) zc >>= 1;
+  return zc;
+}
+
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
                      int num_sms, cudaStream_t s) {
-  const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + ZCG - 1) / ZCG);
-  k_classify<<<grid_for_units(units, num_sms * 8), NT, 0, s>>>(lab, counts, d, full, (PlaneDesc *)desc, totals);
+  const int zc = setup_chunk(d, num_sms);
+  const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
+  k_classify<<<grid_for_units(units, num_sms * 8), NT, 0, s>>>(lab, counts, d, full, zc, (PlaneDesc *)desc, totals);
 }
 
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
                      const void *desc, void *cache0, void *cache1, const uint8_t *wsplit0, const uint8_t *wsplit1,
                      int nsplit, int *err, int num_sms, cudaStream_t s) {
-  const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + ZCG - 1) / ZCG);
   const PlaneDesc *pd = (const PlaneDesc *)desc;
-  if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3)
+  if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3); units within the classification's
+    const int zc = setup_chunk(d, num_sms);
+    const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
     const int g = grid_for_units(units, num_sms * 4);
     if (nsplit == 1)
       k_generate_tc<1, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
-                                              (uint32_t *)cache1, err);
+                                              (uint32_t *)cache1, zc, err);
     else if (bf16)
       k_generate_tc<3, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
-                                              (uint32_t *)cache1, err);
+                                              (uint32_t *)cache1, zc, err);
     else
       k_generate_tc<3, false><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
-                                               (uint32_t *)cache1, err);
+                                               (uint32_t *)cache1, zc, err);
     return;
   }
   const int g = grid_for_units((long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * d.nz, num_sms * 8);
