@@ -17,6 +17,10 @@ Also reported on the same line:
   roofline       the dominant kernel class of a profiled solve (CUDA events
                  around each launch on the solve's stream) against the
                  measured peaks in MEASURED_PEAKS.json
+  served         p50 / p99 latency and solves per second of the serving
+                 workload: 512 requests, Poisson arrivals at 200/s, sizes
+                 64^3, 128^3, 192^3, 256^3, frames of evolving scenes, HBM
+                 budget 150 GB (rank 0 only; --no-serve skips it)
   cpu_baseline   the FP64 CPU oracle on a bounded sample of the same solve
   clocks         nvidia-smi samples taken during the timed region
 
@@ -206,6 +210,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-latency workload")
     ap.add_argument("--max-iter", type=int, default=5000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
@@ -342,6 +347,18 @@ def main():
     breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total_prof, 4)}
                  for k, v in prof.items() if v[1]}
 
+    # ---- served latency: 512 requests, Poisson arrivals at 200/s, sizes
+    # 64^3..256^3, evolving frames, BF16, tol 1e-6, 150 GB admission budget;
+    # latency from nominal arrival to x on the host
+    served = None
+    if not args.no_serve:
+        from paper_2310_00177_b300 import serve
+
+        served = serve.serve_workload(w)
+        served = {k: served[k] for k in ("requests", "rate_per_s", "sizes", "p50_ms", "p99_ms", "mean_ms",
+                                         "solves_per_s", "all_converged", "peak_reserved_gb", "budget_gb",
+                                         "max_active", "per_size")}
+
     import oracle
 
     bm = np.where(lab == 1, rhs.astype(np.float64), 0.0)
@@ -371,6 +388,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": int(lab.nbytes + rhs.nbytes),
                 "d2h_bytes_per_step": int(n * 8)},
         "fp32_form": {"ms_per_solve": fp32_ms, "iters": it_fp32},
+        "served": served,
         "accuracy": accuracy,
         "roofline": roof,
         "kernel_breakdown": breakdown,

@@ -543,6 +543,20 @@ __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ 
 // ---------------------------------------------------------------------------
 // Per iteration: the streamed z-marching CConv.
 // ---------------------------------------------------------------------------
+// The constant kernel of one pure class laid out for packed FP32 FMAs
+// (fma.rn.f32x2: two independent, correctly rounded FP32 FMAs).  A thread
+// holds a window column of 4 rows x 3 columns per plane as six register
+// pairs c(0,1) .. c(10,11) (row-major) and computes the cell of row y (window
+// rows 0..2, tap j of a plane is c_j) and of row y+1 (rows 1..3, tap j is
+// c_{j+3}).  Per plane dz: the upper cell pairs taps (0,1) (2,3) (4,5) (6,7)
+// with c(0,1) .. c(6,7) and takes tap 8 alone; the lower cell pairs taps
+// (1,2) (3,4) (5,6) (7,8) with c(4,5) .. c(10,11) and takes tap 0 alone.
+struct PairKernel {
+  float2 up[3][4];  // per plane: (k0,k1) (k2,k3) (k4,k5) (k6,k7)
+  float2 lo[3][4];  // per plane: (k1,k2) (k3,k4) (k5,k6) (k7,k8)
+  float up8[3], lo0[3];
+};
+
 struct StreamParams {
   CUtensorMap tv;   // input vector of the level: box 40 x 10 x 2 (FP32)
   CUtensorMap tx1;  // x1 of the level (combination only): box 32 x 8 x 2
@@ -562,7 +576,7 @@ struct StreamParams {
   double *part;         // partial dots, one row per CTA
   unsigned *ticket;     // last-CTA-done counter
   SolveState *stw;      // the solve state (orthogonalisation coefficients are written)
-  float kS[27], kF[27], kA[27];  // kernels of the pure-solid, pure-fluid, pure-air windows
+  PairKernel kp[3];              // kernels of the pure-solid, pure-fluid, pure-air windows, paired
   uint32_t ktab[3][27];          // the same as stored in the class tables (BF16 pairs or FP32 words)
 };
 
@@ -582,25 +596,39 @@ __device__ __forceinline__ Unit unit_at(const StreamParams &P, int u) {
 }
 
 // A thread's window column of one plane: rows y-1 .. y+2 x columns x-1 .. x+1
-// (row-major), so rows 0..2 are the 3x3 window of cell y and rows 1..3 that of
-// cell y+1.
-using Col = float[12];
-template <int R>
-__device__ __forceinline__ const float (&rows3(const Col &c))[9] {
-  return *reinterpret_cast<const float(*)[9]>(&c[3 * R]);
-}
-
-// sum_a k[a] v[a] over the window held as three 3x3 planes.
-__device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9], const float (&vB)[9],
-                                       const float (&vC)[9]) {
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-#pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    s0 = fmaf(k[j], vA[j], s0);
-    s1 = fmaf(k[9 + j], vB[j], s1);
-    s2 = fmaf(k[18 + j], vC[j], s2);
+// (row-major, 12 values) in six register pairs, so that rows 0..2 are the 3x3
+// window of cell y and rows 1..3 that of cell y+1.
+struct Col {
+  float2 v[6];
+  __device__ __forceinline__ float at(int i) const { return (i & 1) ? v[i >> 1].y : v[i >> 1].x; }
+  __device__ __forceinline__ void set(int i, float f) {
+    if (i & 1) v[i >> 1].y = f;
+    else v[i >> 1].x = f;
   }
-  return (s0 + s1) + s2;
+};
+
+// sum_a k[a] v[a] of the two cells of a thread's column pair (rows y, y+1) of
+// one pure class, over the planes p0, p1, p2 (Alg. 2's CConv with a constant
+// kernel): 24 packed FMAs and 6 scalar ones for the two cells.
+__device__ __forceinline__ void dot27_pair(const PairKernel &K, const Col &p0, const Col &p1, const Col &p2,
+                                           float &oa, float &ob) {
+  float2 a02 = make_float2(0.f, 0.f), a1 = a02, b02 = a02, b1 = a02;
+  float sa = 0.f, sb = 0.f;
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz) {
+    const Col &c = dz == 0 ? p0 : (dz == 1 ? p1 : p2);
+    float2 &A = dz == 1 ? a1 : a02;
+    float2 &B = dz == 1 ? b1 : b02;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      A = __ffma2_rn(c.v[i], K.up[dz][i], A);
+      B = __ffma2_rn(c.v[i + 2], K.lo[dz][i], B);
+    }
+    sa = fmaf(c.v[4].x, K.up8[dz], sa);
+    sb = fmaf(c.v[1].y, K.lo0[dz], sb);
+  }
+  oa = ((a02.x + a02.y) + (a1.x + a1.y)) + sa;
+  ob = ((b02.x + b02.y) + (b1.x + b1.y)) + sb;
 }
 
 // A cell of a patch that is not all one pure class: its kernel is read from
@@ -609,14 +637,14 @@ __device__ __forceinline__ float dot27(const float (&k)[27], const float (&vA)[9
 // is not needed get 0: with a zero input off fluid (level-1 CConv1) a
 // pure-air or pure-solid window sums to exactly 0, and the level-1 CConv2
 // output is used on fluid cells only.
-template <bool BF16C>
-__device__ __forceinline__ float cconv_generic(const StreamParams &P, uint4 rw, uint32_t rank, uint32_t cp,
-                                               const uint32_t *kblk, const uint32_t *ktab, uint32_t bit,
-                                               const float (&vA)[9], const float (&vB)[9], const float (&vC)[9]) {
+template <bool BF16C, int MODE, int R>
+__device__ __forceinline__ float cconv_generic(uint4 rw, uint32_t rank, uint32_t cp, const uint32_t *kblk,
+                                               const uint32_t *ktab, uint32_t bit, const Col &pA, const Col &pB,
+                                               const Col &pC) {
   const bool mixed = (rw.x & bit) != 0u, fl = (rw.y & bit) != 0u, ai = (rw.z & bit) != 0u;
   bool need = true;
-  if (P.mode == STREAM_MODE_ZERO_PURE) need = mixed || fl;
-  else if (P.mode == STREAM_MODE_FLUID_ONLY) need = (rw.w & bit) != 0u;
+  if (MODE == STREAM_MODE_ZERO_PURE) need = mixed || fl;
+  else if (MODE == STREAM_MODE_FLUID_ONLY) need = (rw.w & bit) != 0u;
   const uint32_t *src = ktab + (fl ? 27 : (ai ? 54 : 0));
   uint32_t stride = 1;
   if (mixed) {
@@ -638,9 +666,9 @@ __device__ __forceinline__ float cconv_generic(const StreamParams &P, uint4 rw, 
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    s0 = fmaf(K[q], vA[q], s0);
-    s1 = fmaf(K[9 + q], vB[q], s1);
-    s2 = fmaf(K[18 + q], vC[q], s2);
+    s0 = fmaf(K[q], pA.at(3 * R + q), s0);
+    s1 = fmaf(K[9 + q], pB.at(3 * R + q), s1);
+    s2 = fmaf(K[18 + q], pC.at(3 * R + q), s2);
   }
   const float acc = (s0 + s1) + s2;
   return need ? acc : 0.f;
@@ -649,37 +677,34 @@ __device__ __forceinline__ float cconv_generic(const StreamParams &P, uint4 rw, 
 // The two cells (rows y, y+1) of one plane for a patch of one pure class cls
 // (0 solid, 1 fluid, 2 air): the class's constant kernel from the kernel
 // parameters, or 0 where the mode says the output is exactly 0 or unused.
+template <int MODE>
 __device__ __forceinline__ void cconv_pure_pair(const StreamParams &P, int cls, const Col &p0, const Col &p1,
                                                 const Col &p2, float &oa, float &ob) {
-  if (P.mode != STREAM_MODE_ALL && cls != 1) {
+  if (MODE != STREAM_MODE_ALL && cls != 1) {
     oa = 0.f;
     ob = 0.f;
   } else if (cls == 1) {
-    oa = dot27(P.kF, rows3<0>(p0), rows3<0>(p1), rows3<0>(p2));
-    ob = dot27(P.kF, rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+    dot27_pair(P.kp[1], p0, p1, p2, oa, ob);
   } else if (cls == 2) {
-    oa = dot27(P.kA, rows3<0>(p0), rows3<0>(p1), rows3<0>(p2));
-    ob = dot27(P.kA, rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+    dot27_pair(P.kp[2], p0, p1, p2, oa, ob);
   } else {
-    oa = dot27(P.kS, rows3<0>(p0), rows3<0>(p1), rows3<0>(p2));
-    ob = dot27(P.kS, rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+    dot27_pair(P.kp[0], p0, p1, p2, oa, ob);
   }
 }
 
 // The two cells of one plane (rows ra, ra+1, bit b of the row masks) of a
 // patch that is not all one pure class.
-template <bool BF16C>
-__device__ __forceinline__ void cconv_generic_pair(const StreamParams &P, const PlaneDesc &d, int ra, int b,
+template <bool BF16C, int MODE>
+__device__ __forceinline__ void cconv_generic_pair(const PlaneDesc &d, int ra, int b,
                                                    const uint32_t *kblk, const uint32_t *ktab, const Col &p0,
                                                    const Col &p1, const Col &p2, float &oa, float &ob) {
   const uint4 wa = d.row[ra], wb = d.row[ra + 1];
   const uint32_t rb = d.rowbase[ra >> 2] >> (8 * (ra & 3));
   const uint32_t cp = min(d.cpad, (uint32_t)NT);
   const uint32_t bit = 1u << b, below = bit - 1u;
-  oa = cconv_generic<BF16C>(P, wa, __popc(wa.x & below) + (rb & 0xFFu), cp, kblk, ktab, bit, rows3<0>(p0),
-                            rows3<0>(p1), rows3<0>(p2));
-  ob = cconv_generic<BF16C>(P, wb, __popc(wb.x & below) + ((rb >> 8) & 0xFFu), cp, kblk, ktab, bit,
-                            rows3<1>(p0), rows3<1>(p1), rows3<1>(p2));
+  oa = cconv_generic<BF16C, MODE, 0>(wa, __popc(wa.x & below) + (rb & 0xFFu), cp, kblk, ktab, bit, p0, p1, p2);
+  ob = cconv_generic<BF16C, MODE, 1>(wb, __popc(wb.x & below) + ((rb >> 8) & 0xFFu), cp, kblk, ktab, bit, p0, p1,
+                                     p2);
 }
 
 // Shared memory after the slots, descriptor buffers and the kernel-block
@@ -764,8 +789,9 @@ __device__ __noinline__ void fused_finish(const StreamParams &P, StreamMeta &M, 
 constexpr int NCW = 4;                    // consumer warps: two tile rows each
 constexpr int NTHREADS = NCW * 32 + 32;   // and one producer warp
 
-template <bool BF16C, bool FUSE>
+template <bool BF16C, bool FUSE, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_constant__ StreamParams P) {
+  static_assert(!FUSE || MODE == STREAM_MODE_FLUID_ONLY, "the fused CConv2 computes fluid outputs only");
   using C = KCfg<BF16C, FUSE>;
   constexpr int NRV = C::NRV;
   if (P.st && P.st->done) return;
@@ -956,8 +982,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         const int e = vbase + (q / 3) * BXW + q % 3;
-        pA[q] = pl[e];
-        pB[q] = pl[BXW * BYH + e];
+        pA.set(q, pl[e]);
+        pB.set(q, pl[BXW * BYH + e]);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
@@ -981,8 +1007,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         const int e = vbase + (q / 3) * BXW + q % 3;
-        pC[q] = pl[e];
-        pD[q] = pl[BXW * BYH + e];
+        pC.set(q, pl[e]);
+        pD.set(q, pl[BXW * BYH + e]);
       }
       float x1v[4] = {0.f, 0.f, 0.f, 0.f};  // (row a, z0), (row b, z0), (row a, z1), (row b, z1)
       if (has_x1) {
@@ -997,16 +1023,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       {
         const PlaneDesc &d0 = D[j0];
         const int cl0 = (int)((d0.patch >> (2 * warp)) & 3u);
-        if (cl0 != 3) cconv_pure_pair(P, cl0, pA, pB, pC, acc[0], acc[1]);
-        else cconv_generic_pair<BF16C>(P, d0, ra, xb, kblk, M.ktab, pA, pB, pC, acc[0], acc[1]);
+        if (cl0 != 3) cconv_pure_pair<MODE>(P, cl0, pA, pB, pC, acc[0], acc[1]);
+        else cconv_generic_pair<BF16C, MODE>(d0, ra, xb, kblk, M.ktab, pA, pB, pC, acc[0], acc[1]);
         if (two) {
           const PlaneDesc &d1 = D[j0 + 1];
           const int cl1 = (int)((d1.patch >> (2 * warp)) & 3u);
           if (cl1 != 3) {
-            cconv_pure_pair(P, cl1, pB, pC, pD, acc[2], acc[3]);
+            cconv_pure_pair<MODE>(P, cl1, pB, pC, pD, acc[2], acc[3]);
           } else {
             const uint32_t *kblk1 = kblk + (size_t)min(d0.cpad, (uint32_t)NT) * (C::EB / 4);
-            cconv_generic_pair<BF16C>(P, d1, ra, xb, kblk1, M.ktab, pB, pC, pD, acc[2], acc[3]);
+            cconv_generic_pair<BF16C, MODE>(d1, ra, xb, kblk1, M.ktab, pB, pC, pD, acc[2], acc[3]);
           }
         }
       }
@@ -1055,11 +1081,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         if (pown) *pp = 0.125f * tp;
         pp += pstep;
       }
-#pragma unroll
-      for (int q = 0; q < 12; ++q) {
-        pA[q] = pC[q];
-        pB[q] = pD[q];
-      }
+      pA = pC;
+      pB = pD;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&M.dempty[m % ND]);
@@ -1077,7 +1100,7 @@ int grid_for_units(long long units, int cap) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <bool BF16C, bool FUSE>
+template <bool BF16C, bool FUSE, int MODE>
 int stream_occupancy() {
   // per device: the dynamic shared-memory opt-in is a per-device function attribute
   static int occ[64] = {};
@@ -1087,11 +1110,34 @@ int stream_occupancy() {
   if (!occ[dev]) {
     int o = 0;
     using C = KCfg<BF16C, FUSE>;
-    cudaFuncSetAttribute(k_cconv_stream<BF16C, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C, FUSE>, NTHREADS, C::SMEM);
+    cudaFuncSetAttribute(k_cconv_stream<BF16C, FUSE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C, FUSE, MODE>, NTHREADS, C::SMEM);
     occ[dev] = o < 1 ? 1 : o;
   }
   return occ[dev];
+}
+
+// The instantiation for a (fused, mode) pair: the mode is a template argument
+// so that the level-1 launches carry only the fluid kernel's code.
+template <bool BF16C>
+int stream_occupancy_of(bool fused, int mode) {
+  if (fused) return stream_occupancy<BF16C, true, STREAM_MODE_FLUID_ONLY>();
+  if (mode == STREAM_MODE_ZERO_PURE) return stream_occupancy<BF16C, false, STREAM_MODE_ZERO_PURE>();
+  if (mode == STREAM_MODE_FLUID_ONLY) return stream_occupancy<BF16C, false, STREAM_MODE_FLUID_ONLY>();
+  return stream_occupancy<BF16C, false, STREAM_MODE_ALL>();
+}
+
+template <bool BF16C>
+void launch_stream_of(bool fused, const StreamParams &P, int grid, cudaStream_t s) {
+  if (fused) {
+    k_cconv_stream<BF16C, true, STREAM_MODE_FLUID_ONLY><<<grid, NTHREADS, KCfg<BF16C, true>::SMEM, s>>>(P);
+  } else if (P.mode == STREAM_MODE_ZERO_PURE) {
+    k_cconv_stream<BF16C, false, STREAM_MODE_ZERO_PURE><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
+  } else if (P.mode == STREAM_MODE_FLUID_ONLY) {
+    k_cconv_stream<BF16C, false, STREAM_MODE_FLUID_ONLY><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
+  } else {
+    k_cconv_stream<BF16C, false, STREAM_MODE_ALL><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
+  }
 }
 
 // cuTensorMapEncodeTiled, looked up through the runtime so that the library
@@ -1240,13 +1286,21 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
   P.c12 = c12;
   P.st = st;
   P.err = err;
-  for (int a = 0; a < 27; ++a) {
-    P.kS[a] = kfix[a];
-    P.kF[a] = kfix[27 + a];
-    P.kA[a] = kfix[54 + a];
+  for (int c = 0; c < 3; ++c) {
+    const float *k = kfix + 27 * c;
+    PairKernel &K = P.kp[c];
+    for (int dz = 0; dz < 3; ++dz) {
+      const float *kz = k + 9 * dz;
+      for (int i = 0; i < 4; ++i) {
+        K.up[dz][i] = make_float2(kz[2 * i], kz[2 * i + 1]);
+        K.lo[dz][i] = make_float2(kz[2 * i + 1], kz[2 * i + 2]);
+      }
+      K.up8[dz] = kz[8];
+      K.lo0[dz] = kz[0];
+    }
   }
-  const int occ = fuse ? (bf16 ? stream_occupancy<true, true>() : stream_occupancy<false, true>())
-                       : (bf16 ? stream_occupancy<true, false>() : stream_occupancy<false, false>());
+  const int occ = bf16 ? stream_occupancy_of<true>(fuse != nullptr, P.mode)
+                       : stream_occupancy_of<false>(fuse != nullptr, P.mode);
   int cap = num_sms * occ;
   if (fuse && cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // one row of partials per CTA
   // the chunk of planes (even) that minimises the slots on the critical path:
@@ -1266,13 +1320,8 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
   P.units = P.ntiles * ((dm.nz + zc - 1) / zc);
   if (fuse && (size_t)cap * kMaxFusedOrtho > fuse->part_cap) return -1;  // partials do not fit
   const int grid = grid_for_units(P.units, cap);
-  if (fuse) {
-    if (bf16) k_cconv_stream<true, true><<<grid, NTHREADS, KCfg<true, true>::SMEM, s>>>(P);
-    else k_cconv_stream<false, true><<<grid, NTHREADS, KCfg<false, true>::SMEM, s>>>(P);
-  } else {
-    if (bf16) k_cconv_stream<true, false><<<grid, NTHREADS, KCfg<true, false>::SMEM, s>>>(P);
-    else k_cconv_stream<false, false><<<grid, NTHREADS, KCfg<false, false>::SMEM, s>>>(P);
-  }
+  if (bf16) launch_stream_of<true>(fuse != nullptr, P, grid, s);
+  else launch_stream_of<false>(fuse != nullptr, P, grid, s);
   return 0;
 }
 

@@ -123,6 +123,37 @@ def summarize(recs):
     }
 
 
+def serve_workload(w, requests=512, rate=200.0, sizes=(64, 128, 192, 256), frames=6, budget_gb=150.0,
+                   max_active=16):
+    """Run the serving workload (seeded Poisson arrivals, mixed sizes, evolving
+    frames, BF16 network, tol 1e-6, HBM-budget admission) on a fresh server
+    and return the summary: p50 / p99 latency, solves per second, convergence
+    of every request, peak reserved HBM."""
+    from paper_2310_00177_b300 import binding, synth
+
+    sizes = tuple(sizes)
+    fr = build_frames(sizes, frames, pinned=True)
+    reqs = synth.serving_requests(requests, rate, sizes=sizes)
+    # every request returns its x to the host (a pinned array per request)
+    x_pool = [pinned_like((r["n"],) * 3, np.float64) for r in reqs]
+    srv = binding.Server(w, precision=binding.BF16, hbm_budget_bytes=int(budget_gb * (1 << 30)),
+                         max_active=max_active)
+    try:
+        # grow every slot to the largest size once so that workspace growth is not timed
+        warm = run(srv, [{"t_arrival": 0.0, "n": max(sizes), "frame": 0} for _ in range(max_active)], fr)
+        recs = run(srv, reqs, fr, x_pool=x_pool)
+        out = summarize(recs)
+        out["peak_reserved_gb"] = srv.stats()["peak_reserved"] / (1 << 30)
+    finally:
+        srv.close()
+    out["rate_per_s"] = rate
+    out["sizes"] = list(sizes)
+    out["budget_gb"] = budget_gb
+    out["max_active"] = max_active
+    out["warmup_requests"] = len(warm)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--requests", type=int, default=512)
@@ -132,26 +163,12 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-active", type=int, default=16)
     args = ap.parse_args()
-    from paper_2310_00177_b300 import binding, synth
+    from paper_2310_00177_b300 import synth
 
-    sizes = tuple(int(s) for s in args.sizes.split(","))
     wfile = os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32")
     w = np.fromfile(wfile, dtype=np.float32) if os.path.exists(wfile) else synth.init_weights(4, 7)
-    frames = build_frames(sizes, args.frames, pinned=True)
-    reqs = synth.serving_requests(args.requests, args.rate, sizes=sizes)
-    # every request returns its x to the host (a pinned array per request)
-    x_pool = [pinned_like((r["n"],) * 3, np.float64) for r in reqs]
-    srv = binding.Server(w, precision=binding.BF16, hbm_budget_bytes=int(args.budget_gb * (1 << 30)),
-                         max_active=args.max_active)
-    # grow every slot to the largest size once so that workspace growth is not timed
-    warm = run(srv, [{"t_arrival": 0.0, "n": max(sizes), "frame": 0} for _ in range(args.max_active)], frames)
-    recs = run(srv, reqs, frames, x_pool=x_pool)
-    out = summarize(recs)
-    out["peak_reserved_gb"] = srv.stats()["peak_reserved"] / (1 << 30)
-    out["budget_gb"] = args.budget_gb
-    out["max_active"] = args.max_active
-    out["warmup_requests"] = len(warm)
-    srv.close()
+    out = serve_workload(w, args.requests, args.rate, tuple(int(s) for s in args.sizes.split(",")), args.frames,
+                         args.budget_gb, args.max_active)
     print(json.dumps(out))
 
 
