@@ -86,9 +86,8 @@ __global__ void k_init_final(const double *part, int nblocks, double tol, int ma
   s.max_iter = max_iter;
   s.n_ortho = n_ortho;
   s.pad_ = 0;
-  s.x_pend = 0;
-  s.alpha_pend = 0.0;
-  s.pend_slot = 0;
+  s.x_upto = 0;
+  for (int i = 0; i < kRing; ++i) s.alpha_slot[i] = 0.0;
   s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
   if (!isfinite(t[0])) s.done = kDoneBadInput;
   else if (!(t[0] >= s.eps2) || t[0] == 0.0) s.done = kDoneConverged;  // ||r_0|| < tol ||b|| or b = 0

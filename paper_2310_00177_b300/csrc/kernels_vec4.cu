@@ -104,6 +104,7 @@ int resident_blocks() {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ lab, int n, const float *__restrict__ b,
                                                     float *__restrict__ r, double *__restrict__ x,
+                                                    float *__restrict__ xhi, float *__restrict__ xlo,
                                                     double *__restrict__ part, unsigned *ticket, double tol,
                                                     int max_iter, int n_ortho, SolveState *st, double *hist) {
   DF acc;
@@ -115,8 +116,13 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
     const float4 rv = make_float4(l.x == kFluid ? bv.x : 0.f, l.y == kFluid ? bv.y : 0.f, l.z == kFluid ? bv.z : 0.f,
                                   l.w == kFluid ? bv.w : 0.f);
     st4(r + p, rv);
-    reinterpret_cast<double2 *>(x + p)[0] = make_double2(0.0, 0.0);
-    reinterpret_cast<double2 *>(x + p)[1] = make_double2(0.0, 0.0);
+    if (xhi) {
+      st4(xhi + p, make_float4(0.f, 0.f, 0.f, 0.f));
+      st4(xlo + p, make_float4(0.f, 0.f, 0.f, 0.f));
+    } else {
+      reinterpret_cast<double2 *>(x + p)[0] = make_double2(0.0, 0.0);
+      reinterpret_cast<double2 *>(x + p)[1] = make_double2(0.0, 0.0);
+    }
     df_add(acc, rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
   }
   double v[1] = {df_val(acc)};
@@ -132,9 +138,8 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
     s.max_iter = max_iter;
     s.n_ortho = n_ortho;
     s.pad_ = 0;
-    s.x_pend = 0;
-    s.alpha_pend = 0.0;
-    s.pend_slot = 0;
+    s.x_upto = 0;
+    for (int i = 0; i < kRing; ++i) s.alpha_slot[i] = 0.0;
     s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
     if (!isfinite(t[0])) s.done = kDoneBadInput;
     else if (!(t[0] >= s.eps2) || t[0] == 0.0) s.done = kDoneConverged;
@@ -204,15 +209,61 @@ __global__ void __launch_bounds__(kThreads) k_combine1_4(const uint8_t *__restri
   });
 }
 
-// d_k = z - sum_j c_j d_{k-1-j}  (ring slot of iteration k).
+// x += a d for x held as a double-float pair (hi, lo) (|lo| <= ulp(hi) / 2,
+// about 48 significant bits) and a = ah + al split into two floats: the
+// product by the exact FMA product error, the sum by TwoSum, then one
+// renormalisation (Dekker / Knuth).  B300 runs FP32 at 64 times its FP64
+// rate, so this keeps the per-cell FP64 arithmetic off the iteration.
+// (The _rn intrinsics keep the compiler from contracting a product into the
+// error-free sums, which would break them.)
+__device__ __forceinline__ void df_axpy(float &hi, float &lo, float ah, float al, float d) {
+  const float ph = __fmul_rn(ah, d);
+  const float pl = fmaf(al, d, fmaf(ah, d, -ph));
+  const float s = __fadd_rn(hi, ph);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb)), __fadd_rn(lo, pl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+__device__ __forceinline__ void df_axpy4(float4 &hi, float4 &lo, float ah, float al, const float4 &d) {
+  df_axpy(hi.x, lo.x, ah, al, d.x);
+  df_axpy(hi.y, lo.y, ah, al, d.y);
+  df_axpy(hi.z, lo.z, ah, al, d.z);
+  df_axpy(hi.w, lo.w, ah, al, d.w);
+}
+
+__device__ __forceinline__ void split_alpha(double a, float &ah, float &al) {
+  ah = (float)a;
+  al = (float)(a - (double)ah);
+}
+
+// d_k = z - sum_j c_j d_{k-1-j} (Alg. 1's A-orthogonalisation against the last
+// n_ortho directions).  DEFER (recurrence mode): x is not read during the
+// iterations, so the steps alpha_i d_i are added to x (a double-float pair)
+// here, R = n_ortho + 1 of them at once, when the ring slot that d_k
+// overwrites still holds a pending step: x += alpha_{k-R} d_{k-R} + ... +
+// alpha_{k-1} d_{k-1}, oldest first.  The directions d_{k-1} .. d_{k-n_ortho}
+// are read for the orthogonalisation anyway and d_{k-R} is the old content
+// of the slot being written, so the steps cost x's read and write once every
+// R iterations.  The lap kernel's last block records the flush (x_upto)
+// after every block here has read the state.
+template <bool DEFER>
 __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__restrict__ zv, float *__restrict__ dring,
+                                                         float *__restrict__ xhi, float *__restrict__ xlo,
                                                          const SolveState *st) {
   if (st->done) return;
   const int k1 = st->k + 1, no = st->n_ortho;
   const int cnt = min(no, k1 - 1);
-  float c[kMaxOrtho];
+  const bool flush = DEFER && (k1 - 1) - st->x_upto == no + 1;  // then cnt == no
+  float c[kMaxOrtho], ah[kMaxOrtho], al[kMaxOrtho];
 #pragma unroll
-  for (int j = 0; j < kMaxOrtho; ++j) c[j] = j < cnt ? (float)st->coef[j] : 0.f;
+  for (int j = 0; j < kMaxOrtho; ++j) {
+    c[j] = j < cnt ? (float)st->coef[j] : 0.f;
+    split_alpha(flush && j < cnt ? st->alpha_slot[ring_slot(k1 - 1 - j, no)] : 0.0, ah[j], al[j]);
+  }
+  float oh, ol;  // step k - R, whose direction is in d_k's slot
+  split_alpha(flush ? st->alpha_slot[ring_slot(k1, no)] : 0.0, oh, ol);
   const float *s0 = dring + (size_t)ring_slot(max(k1 - 1, 1), no) * n;
   const float *s1 = dring + (size_t)ring_slot(max(k1 - 2, 1), no) * n;
   const float *s2 = dring + (size_t)ring_slot(max(k1 - 3, 1), no) * n;
@@ -224,15 +275,26 @@ __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__r
     const int p = g << 2;
     float4 v = ld4(zv + p);
     const float *src[kMaxOrtho] = {s0, s1, s2, s3};
+    float4 sv[kMaxOrtho];
 #pragma unroll
     for (int j = 0; j < kMaxOrtho; ++j) {
       if (j < cnt) {
-        const float4 sv = ld4(src[j] + p);
-        v.x -= c[j] * sv.x;
-        v.y -= c[j] * sv.y;
-        v.z -= c[j] * sv.z;
-        v.w -= c[j] * sv.w;
+        sv[j] = ld4(src[j] + p);
+        v.x -= c[j] * sv[j].x;
+        v.y -= c[j] * sv[j].y;
+        v.z -= c[j] * sv[j].z;
+        v.w -= c[j] * sv[j].w;
       }
+    }
+    if (DEFER && flush) {
+      const float4 dold = ld4(dst + p);
+      float4 h = ld4(xhi + p), l = ld4(xlo + p);
+      df_axpy4(h, l, oh, ol, dold);
+#pragma unroll
+      for (int j = kMaxOrtho - 1; j >= 0; --j)
+        if (j < cnt) df_axpy4(h, l, ah[j], al[j], sv[j]);
+      st4(xhi + p, h);
+      st4(xlo + p, l);
     }
     st4(dst + p, v);
   };
@@ -336,22 +398,22 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
   double v[2] = {df_val(a0), df_val(a1)};
   reduce_and_finish<2>(v, part, ticket, [&](const double *t) {
     const double dq = t[0], rd = t[1];
+    const int k1 = st->k + 1;
+    if ((k1 - 1) - st->x_upto == st->n_ortho + 1) st->x_upto = k1 - 1;  // k_direction4 added those steps
     if (!(dq > 0.0) || !isfinite(dq) || !isfinite(rd)) {
       st->done = kDoneBreakdown;
       return;
     }
     st->alpha = rd / dq;
+    st->alpha_slot[slot] = st->alpha;
     st->dAd[slot] = dq;
   });
 }
 
-// x += alpha d (FP64), r -= alpha q (recurrence) with ||r||^2; the last block
-// advances the iteration and applies the stop test ||r_k|| < tol ||b||.
-// In the recurrence mode x is not read during the iterations, so with a ring
-// of at least two directions the steps of two iterations go into x together,
-// x += alpha_{k-1} d_{k-1} + alpha_k d_k in that order (the same FP64
-// arithmetic as two separate updates, one pass over x instead of two); a
-// step left pending at the end is added by k_flush_x.
+// Recurrence mode: r -= alpha q with ||r||^2; the last block advances the
+// iteration and applies the stop test ||r_k|| < tol ||b|| (the step's
+// alpha d goes into x later, in k_direction4 or k_flush_x).  Explicit mode:
+// x += alpha d in FP64 (the residual is then recomputed from x).
 template <bool RECUR>
 __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict__ x, float *__restrict__ r,
                                                       const float *__restrict__ dring, const float *__restrict__ qring,
@@ -359,30 +421,16 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
                                                       double *hist) {
   if (st->done) return;
   const int slot = ring_slot(st->k + 1, st->n_ortho);
-  const float *d = dring + (size_t)slot * n;
-  const float *q = qring + (size_t)slot * n;
   const double a = st->alpha;
-  const float af = (float)a;
-  const bool defer_ok = RECUR && st->n_ortho >= 1;
-  const bool pend = st->x_pend != 0;
-  const bool skip_x = defer_ok && !pend;  // this step waits for the next one
-  const double ap = st->alpha_pend;
-  const float *dp = dring + (size_t)st->pend_slot * n;
-  DF acc;
   const int n4 = n >> 2;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
-    const int p = g << 2;
-    if (!skip_x) {
+  const int stride = gridDim.x * blockDim.x;
+  if (!RECUR) {
+    const float *d = dring + (size_t)slot * n;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += stride) {
+      const int p = g << 2;
       const float4 dv = ld4(d + p);
       double2 *xp = reinterpret_cast<double2 *>(x + p);
       double2 x01 = xp[0], x23 = xp[1];
-      if (pend) {
-        const float4 pv = ld4(dp + p);
-        x01.x = fma(ap, (double)pv.x, x01.x);
-        x01.y = fma(ap, (double)pv.y, x01.y);
-        x23.x = fma(ap, (double)pv.z, x23.x);
-        x23.y = fma(ap, (double)pv.w, x23.y);
-      }
       x01.x = fma(a, (double)dv.x, x01.x);
       x01.y = fma(a, (double)dv.y, x01.y);
       x23.x = fma(a, (double)dv.z, x23.x);
@@ -390,28 +438,31 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
       xp[0] = x01;
       xp[1] = x23;
     }
-    if (RECUR) {
-      const float4 qv = ld4(q + p);
-      float4 rv = ld4(r + p);
-      rv.x = fmaf(-af, qv.x, rv.x);
-      rv.y = fmaf(-af, qv.y, rv.y);
-      rv.z = fmaf(-af, qv.z, rv.z);
-      rv.w = fmaf(-af, qv.w, rv.w);
-      st4(r + p, rv);
-      df_add(acc, rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
-    }
+    return;
   }
-  if (!RECUR) return;
+  const float *q = qring + (size_t)slot * n;
+  const float af = (float)a;
+  DF acc;
+  auto group = [&](int g) {
+    const int p = g << 2;
+    const float4 qv = ld4(q + p);
+    float4 rv = ld4(r + p);
+    rv.x = fmaf(-af, qv.x, rv.x);
+    rv.y = fmaf(-af, qv.y, rv.y);
+    rv.z = fmaf(-af, qv.z, rv.z);
+    rv.w = fmaf(-af, qv.w, rv.w);
+    st4(r + p, rv);
+    df_add(acc, rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+  };
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; g + stride < n4; g += 2 * stride) {
+    group(g);
+    group(g + stride);
+  }
+  if (g < n4) group(g);
   double v[1] = {df_val(acc)};
   reduce_and_finish<1>(v, part, ticket, [&](const double *t) {
     const double rr = t[0];
-    if (skip_x) {
-      st->x_pend = 1;
-      st->alpha_pend = a;
-      st->pend_slot = slot;
-    } else {
-      st->x_pend = 0;
-    }
     st->k += 1;
     st->rnorm2 = rr;
     hist[st->k] = sqrt(rr);
@@ -421,31 +472,54 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
   });
 }
 
-// Adds a step left pending by k_update4 (x += alpha_pend d_pend); the flag is
-// cleared by k_clear_pend afterwards.
-__global__ void __launch_bounds__(kThreads) k_flush_x(int n, double *__restrict__ x, const float *__restrict__ dring,
+// Adds the steps not yet in x (x_upto < i <= k, at most n_ortho + 1 of them,
+// their directions still in the ring) to the double-float pair, oldest
+// first, and writes x = xhi + xlo in FP64; k_clear_pend then marks them
+// added.
+__global__ void __launch_bounds__(kThreads) k_flush_x(int n, float *__restrict__ xhi, float *__restrict__ xlo,
+                                                      double *__restrict__ x, const float *__restrict__ dring,
                                                       const SolveState *st) {
-  if (!st->x_pend) return;
-  const double a = st->alpha_pend;
-  const float *d = dring + (size_t)st->pend_slot * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = fma(a, (double)d[i], x[i]);
+  const int k = st->k, from = st->x_upto + 1, no = st->n_ortho;
+  const int n4 = n >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    float4 h = ld4(xhi + p), l = ld4(xlo + p);
+    if (from <= k) {
+      for (int it = from; it <= k; ++it) {
+        const int sl = ring_slot(it, no);
+        float ah, al;
+        split_alpha(st->alpha_slot[sl], ah, al);
+        df_axpy4(h, l, ah, al, ld4(dring + (size_t)sl * n + p));
+      }
+      st4(xhi + p, h);
+      st4(xlo + p, l);
+    }
+    double2 *xp = reinterpret_cast<double2 *>(x + p);
+    xp[0] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    xp[1] = make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w);
+  }
 }
-__global__ void k_clear_pend(SolveState *st) { st->x_pend = 0; }
+__global__ void k_clear_pend(SolveState *st) { st->x_upto = st->k; }
 
 // ---------------------------------------------------------------------------
 // Host-side launchers.
 // ---------------------------------------------------------------------------
-void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, double *part, unsigned *ticket,
-                  double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms, cudaStream_t s) {
-  k_init4<<<grid4(n / 4, num_sms, resident_blocks<k_init4>()), kThreads, 0, s>>>(lab, n, b, r, x, part, ticket, tol, max_iter, n_ortho, st, hist);
+void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, float *xhi, float *xlo, double *part,
+                  unsigned *ticket, double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms,
+                  cudaStream_t s) {
+  k_init4<<<grid4(n / 4, num_sms, resident_blocks<k_init4>()), kThreads, 0, s>>>(lab, n, b, r, x, xhi, xlo, part, ticket, tol, max_iter, n_ortho, st, hist);
 }
 void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
                        const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
                        cudaStream_t s) {
   k_combine1_4<<<grid4(n / 4, num_sms, resident_blocks<k_combine1_4>()), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
 }
-void launch_direction4(int n, const float *z, float *dring, const SolveState *st, int num_sms, cudaStream_t s) {
-  k_direction4<<<grid4(n / 4, num_sms, resident_blocks<k_direction4>()), kThreads, 0, s>>>(n, z, dring, st);
+void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const SolveState *st,
+                       int num_sms, cudaStream_t s) {
+  if (defer_x)
+    k_direction4<true><<<grid4(n / 4, num_sms, resident_blocks<k_direction4<true>>()), kThreads, 0, s>>>(n, z, dring, xhi, xlo, st);
+  else
+    k_direction4<false><<<grid4(n / 4, num_sms, resident_blocks<k_direction4<false>>()), kThreads, 0, s>>>(n, z, dring, xhi, xlo, st);
 }
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s) {
   long long b = (dm.n() + kThreads - 1) / kThreads;
@@ -456,8 +530,9 @@ void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring
                  unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
   k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(code, dm, dring, qring, r, part, ticket, st);
 }
-void launch_flush_x(int n, double *x, const float *dring, SolveState *st, int num_sms, cudaStream_t s) {
-  k_flush_x<<<num_sms * 8, kThreads, 0, s>>>(n, x, dring, st);
+void launch_flush_x(int n, float *xhi, float *xlo, double *x, const float *dring, SolveState *st, int num_sms,
+                    cudaStream_t s) {
+  k_flush_x<<<grid4(n / 4, num_sms, resident_blocks<k_flush_x>()), kThreads, 0, s>>>(n, xhi, xlo, x, dring, st);
   k_clear_pend<<<1, 1, 0, s>>>(st);
 }
 void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,

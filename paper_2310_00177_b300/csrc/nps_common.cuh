@@ -57,10 +57,9 @@ struct SolveState {
   int done;             // 0 running, 1 converged, 2 breakdown, 3 non-finite input
   int max_iter;
   int n_ortho;
-  int x_pend;           // 1: alpha_pend d (ring slot pend_slot) is not yet added to x
-  double alpha_pend;    // (the recurrence mode adds the steps of two iterations to x at once)
-  int pend_slot;
+  int x_upto;           // steps 1..x_upto are in x (the recurrence mode adds several steps to x at once)
   int pad_;
+  double alpha_slot[kRing];  // alpha of the step whose direction is in each ring slot
 };
 
 enum { kDoneRunning = 0, kDoneConverged = 1, kDoneBreakdown = 2, kDoneBadInput = 3 };

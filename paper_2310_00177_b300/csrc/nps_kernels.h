@@ -51,18 +51,23 @@ void launch_combine1(const uint8_t *lab, long long n, const float *x1, const flo
                      const float *qring, double *part, const SolveState *st, cudaStream_t s);
 
 // kernels_vec4.cu (nx % 4 == 0, n < 2^31)
-void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, double *part, unsigned *ticket,
-                  double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms, cudaStream_t s);
+// r = mask(b), ||b||^2 -> the solver state; x = 0, or (xhi, xlo) = 0 when
+// xhi is non-null (x is then written by launch_flush_x at the end).
+void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, float *xhi, float *xlo, double *part,
+                  unsigned *ticket, double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms,
+                  cudaStream_t s);
 void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
                        const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
                        cudaStream_t s);
-void launch_direction4(int n, const float *z, float *dring, const SolveState *st, int num_sms, cudaStream_t s);
+void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const SolveState *st,
+                       int num_sms, cudaStream_t s);
 // per-cell stencil codes of the masked Laplacian (once per solve) and q = A d with them
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s);
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
                  unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
-// adds a step of x left pending by the recurrence-mode update (no-op if none)
-void launch_flush_x(int n, double *x, const float *dring, SolveState *st, int num_sms, cudaStream_t s);
+// Adds the pending steps to (xhi, xlo) and writes x = xhi + xlo in FP64.
+void launch_flush_x(int n, float *xhi, float *xlo, double *x, const float *dring, SolveState *st, int num_sms,
+                    cudaStream_t s);
 void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s);
 

@@ -50,6 +50,7 @@ struct Workspace {
   long long cap = 0;  // cells of level 1 the buffers were sized for
   size_t bytes = 0;   // device bytes held by this workspace
   float *r = nullptr, *z = nullptr, *dring = nullptr, *qring = nullptr;
+  float *xhi = nullptr, *xlo = nullptr;  // x as a double-float pair during recurrence-mode iterations
   uint16_t *lapcode = nullptr;  // per-cell stencil codes of the masked Laplacian (vec4 path)
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
@@ -219,6 +220,8 @@ void free_ws(Workspace &w) {
   w.graph = nullptr;
   cudaFree(w.r);
   cudaFree(w.z);
+  cudaFree(w.xhi);
+  cudaFree(w.xlo);
   cudaFree(w.lapcode);
   cudaFree(w.dring);
   cudaFree(w.qring);
@@ -276,6 +279,8 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     const int R = kRing;
     CK(h, dalloc(&w.bytes, &w.r, cap));
     CK(h, dalloc(&w.bytes, &w.z, cap));
+    CK(h, dalloc(&w.bytes, &w.xhi, cap));
+    CK(h, dalloc(&w.bytes, &w.xlo, cap));
     CK(h, dalloc(&w.bytes, &w.lapcode, cap));
     CK(h, dalloc(&w.bytes, &w.dring, cap * R));
     CK(h, dalloc(&w.bytes, &w.qring, cap * R));
@@ -877,7 +882,7 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   if (fast) {
     {
       ProfScope ps(h, P_ORTHO_DIR, s);
-      launch_direction4((int)n, w.z, w.dring, w.st, h->num_sms, s);
+      launch_direction4(recur, (int)n, w.z, w.dring, w.xhi, w.xlo, w.st, h->num_sms, s);
     }
     {
       ProfScope ps(h, P_LAP, s);
@@ -962,8 +967,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     st = setup_image(h, lab, d1, s, true);
     if (st) return st;
     if (vec4_path(d1)) {
-      launch_init4(lab, (int)d1.n(), b, w.r, x, w.part, w.tickets + kTicketInit, tol, max_iter, h->cfg.n_ortho,
-                   w.st, w.hist, h->num_sms, s);
+      // the recurrence mode of the multilevel path keeps x as a double-float pair until the end
+      const bool xdf = h->cfg.levels > 1 && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
+      launch_init4(lab, (int)d1.n(), b, w.r, x, xdf ? w.xhi : nullptr, xdf ? w.xlo : nullptr, w.part,
+                   w.tickets + kTicketInit, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, h->num_sms, s);
       h->launches += 1;
     } else {
       launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
@@ -1016,8 +1023,9 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     }
     CK(h, cudaStreamSynchronize(s));
     if (nb) hs = w.h_st[(nb - 1) & 1];
-    if (vec4_path(d1)) {  // the recurrence-mode update may leave the last step pending in x
-      launch_flush_x((int)d1.n(), x, w.dring, w.st, h->num_sms, s);
+    if (vec4_path(d1) && h->cfg.levels > 1 &&
+        h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE) {  // the last steps may still be pending
+      launch_flush_x((int)d1.n(), w.xhi, w.xlo, x, w.dring, w.st, h->num_sms, s);
       h->launches += 2;
     }
     if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&

@@ -148,6 +148,27 @@ def test_solve_variants_match_oracle(n_ortho, L, tol):
     s.close()
 
 
+@pytest.mark.parametrize("n_ortho", [0, 2, 3])
+def test_truncated_solve_x_matches_oracle(n_ortho):
+    """x after a fixed number of iterations (no convergence): the recurrence
+    mode adds the steps of n_ortho + 1 iterations to x at once, so every
+    residue of max_iter modulo n_ortho + 1 ends with a different number of
+    steps still pending; each must reach x."""
+    b = _binding()
+    lab = synth.slosh_scene(32, 81)
+    rhs = synth.rhs_normal(lab, 82).astype(np.float32)
+    w = synth.init_weights(4, 83).astype(np.float32)
+    s = b.Solver(w, levels=4, n_ortho=n_ortho)
+    for m in range(1, n_ortho + 3):
+        ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-12, max_iter=m,
+                            n_ortho=n_ortho)
+        x, iters, relres, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-12, max_iter=m)
+        assert st == b.NO_CONVERGENCE and iters == ores["iters"] == m
+        assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 2e-5
+        assert abs(relres - ores["relres"]) <= 1e-4 * ores["relres"]
+    s.close()
+
+
 def test_solve_host_equals_device_solve():
     b = _binding()
     lab, rhs, w = _config1()
