@@ -1129,15 +1129,14 @@ int stream_occupancy_of(bool fused, int mode) {
 
 template <bool BF16C>
 void launch_stream_of(bool fused, const StreamParams &P, int grid, cudaStream_t s) {
-  if (fused) {
+  if (fused)
     k_cconv_stream<BF16C, true, STREAM_MODE_FLUID_ONLY><<<grid, NTHREADS, KCfg<BF16C, true>::SMEM, s>>>(P);
-  } else if (P.mode == STREAM_MODE_ZERO_PURE) {
+  else if (P.mode == STREAM_MODE_ZERO_PURE)
     k_cconv_stream<BF16C, false, STREAM_MODE_ZERO_PURE><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
-  } else if (P.mode == STREAM_MODE_FLUID_ONLY) {
+  else if (P.mode == STREAM_MODE_FLUID_ONLY)
     k_cconv_stream<BF16C, false, STREAM_MODE_FLUID_ONLY><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
-  } else {
+  else
     k_cconv_stream<BF16C, false, STREAM_MODE_ALL><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
-  }
 }
 
 // cuTensorMapEncodeTiled, looked up through the runtime so that the library

@@ -298,11 +298,11 @@ __global__ void __launch_bounds__(256) k_interp_blk(const float *__restrict__ in
   const int nq = fx >> 2;  // x groups of 4 fine cells (cx / 2)
   const long long nthr = (long long)nq * cy * cz;
   const long long fxy = (long long)fx * fy;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nthr;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(t % nq);
-    const long long r = t / nq;
-    const int jy = (int)(r % cy), kz = (int)(r / cy);  // fine rows 2jy, 2jy+1; fine planes 2kz, 2kz+1
+  // 32-bit index arithmetic (a fine grid below 2^31 cells has nthr < 2^27)
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (unsigned)nthr; t += gridDim.x * blockDim.x) {
+    const int q = (int)(t % (unsigned)nq);
+    const unsigned r = t / (unsigned)nq;
+    const int jy = (int)(r % (unsigned)cy), kz = (int)(r / (unsigned)cy);  // fine rows 2jy, 2jy+1; planes 2kz, 2kz+1
     const int xm = max(2 * q - 1, 0), x0 = 2 * q, x1 = 2 * q + 1, xp = min(2 * q + 2, cx - 1);
     const int ym = max(jy - 1, 0), yp = min(jy + 1, cy - 1);
     const int zm = max(kz - 1, 0), zp = min(kz + 1, cz - 1);

@@ -199,22 +199,28 @@ __global__ void __launch_bounds__(kRedThreads) k_true_residual(const uint8_t *__
     cell_xyz(p, dm, xx, yy, zz);
     double res = 0.0;
     if (lab[p] == kFluid) {
-      const double xp = x[p];
-      double acc = 0.0;
-      int nair = 0;
+      // (A x)_p = (fluid + air neighbours) x_p - sum of the fluid neighbours' x
+      // (Sec. 3.2): one FP64 add per fluid neighbour and one FMA, since B300's
+      // FP64 rate bounds this kernel
       const long long nb[6] = {p - 1, p + 1, p - dm.nx, p + dm.nx, p - sxy, p + sxy};
       const bool ok[6] = {xx > 0, xx < dm.nx - 1, yy > 0, yy < dm.ny - 1, zz > 0, zz < dm.nz - 1};
+      double sum = 0.0;
+      int diag = 0;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         if (!ok[k]) continue;
         const uint8_t ln = lab[nb[k]];
-        if (ln == kFluid) acc += xp - x[nb[k]];
-        else if (ln == kAir) nair += 1;
+        if (ln == kFluid) {
+          sum += x[nb[k]];
+          diag += 1;
+        } else if (ln == kAir) {
+          diag += 1;
+        }
       }
       const double bp = (double)b[p];
-      res = bp - (acc + (double)nair * xp);
-      v[0] += res * res;
-      v[1] += bp * bp;
+      res = bp - fma((double)diag, x[p], -sum);
+      v[0] = fma(res, res, v[0]);
+      v[1] = fma(bp, bp, v[1]);
     }
     if (r) r[p] = (float)res;
   }
@@ -246,11 +252,14 @@ __global__ void k_converge_final(const double *part, int nblocks, int part_strid
 
 // After a residual replacement: take ||r||^2 from k_true_residual partials,
 // re-open the iteration if it is still above tolerance.
-__global__ void k_restart_final(const double *part, int nblocks, SolveState *st, int *reopened) {
+__global__ void k_restart_final(const double *part, int nblocks, SolveState *st, int *reopened, double *relres) {
   double t[2];
   reduce_partials<2>(part, nblocks, t);
   if (threadIdx.x != 0) return;
   const double rr = t[0];
+  // the same figures as k_relres_final: the final check when nothing re-opens
+  relres[0] = t[1] > 0.0 ? sqrt(t[0] / t[1]) : 0.0;
+  relres[1] = sqrt(t[1]);
   *reopened = 0;
   if (st->done != kDoneConverged) return;
   if (rr >= st->eps2 && rr > 0.0 && isfinite(rr)) {
@@ -513,10 +522,10 @@ void launch_explicit_residual(const uint8_t *lab, Dims dm, const float *b, const
   k_converge_final<<<1, kRedThreads, 0, s>>>(part, nb, 2, st, hist);
 }
 void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, double *part,
-                             SolveState *st, int *reopened, cudaStream_t s) {
+                             SolveState *st, int *reopened, double *relres, cudaStream_t s) {
   const int nb = red_blocks(dm.n());
   k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, r, part, nullptr);
-  k_restart_final<<<1, kRedThreads, 0, s>>>(part, nb, st, reopened);
+  k_restart_final<<<1, kRedThreads, 0, s>>>(part, nb, st, reopened, relres);
 }
 void launch_relres(const uint8_t *lab, Dims dm, const float *b, const double *x, double *part, double *out,
                    cudaStream_t s) {

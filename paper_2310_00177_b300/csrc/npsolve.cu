@@ -988,6 +988,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     if (st) return st;
   }
   int launched = 0, restarts = 0;
+  bool have_relres = false;  // the last residual replacement check left the final figures
   SolveState hs = w.h_st[0];
   for (;;) {
     // Replay the captured iterations until the device flags completion or the
@@ -1031,7 +1032,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&
         restarts < kMaxRestarts) {
       ProfScope ps(h, P_FINAL, s);
-      launch_replace_residual(lab, d1, b, x, w.r, w.part, w.st, w.reopened, s);
+      launch_replace_residual(lab, d1, b, x, w.r, w.part, w.st, w.reopened, w.relres, s);
       h->launches += 2;
       CK(h, cudaMemcpyAsync(w.h_flag, w.reopened, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -1042,10 +1043,11 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
         launched = hs.k;
         continue;
       }
+      have_relres = true;
     }
     break;
   }
-  {
+  if (!have_relres) {
     ProfScope ps(h, P_FINAL, s);
     launch_relres(lab, d1, b, x, w.part, w.relres, s);
     h->launches += 2;
