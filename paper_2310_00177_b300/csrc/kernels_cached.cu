@@ -33,8 +33,8 @@
 // Per iteration: k_cconv_stream.  Each CTA marches units (a tile and a chunk
 // of planes) along z, two planes per step.  One producer warp (one thread)
 // loads per unit the plane descriptors (bulk copy, three buffers), and per
-// step, into one of RV slots completing on one mbarrier: the 40 x 10 x 2 TMA
-// box of the input planes z+1, z+2 (one-cell halo), the 32 x 8 x 2 box of x1
+// step, into one of RV slots completing on one mbarrier: the 44 x 10 x 2 TMA
+// box of the input planes z+1, z+2 (one-cell halo), the 36 x 8 x 2 box of x1
 // (combination only) and, with a bulk copy into a circular buffer, the two
 // planes' kernel blocks (contiguous in the cache).  Four consumer warps each
 // own two rows of the tile: a thread keeps the 4-row x 3-column window
@@ -76,9 +76,12 @@ constexpr int BXW = TX + 12;                  // vector box: x0-4 .. x0+39 (star
                                               // width 44 keeps the 8x8-patch reads free of bank conflicts)
 constexpr int BYH = TY + 2;                   // rows y0-1 .. y0+4
 constexpr int VPLANE = BXW * BYH * 4;         // 1760 bytes per plane of the vector box
-constexpr int X1OFF = 3584;                   // x1 box (32 x 8 x 2) in a slot (128-byte aligned, after 3520)
-constexpr int SLOT = 5632;                    // 3584 + 2048 bytes, 44 x 128
-static_assert(X1OFF >= 2 * VPLANE && X1OFF % 128 == 0 && SLOT % 128 == 0 && X1OFF + 2048 <= SLOT, "slot layout");
+constexpr int XBW = TX + 4;                   // x1 / q box width: rows 36 words apart, so that the four
+                                              // rows a warp reads of an 8x8 patch fall in distinct banks
+constexpr int XBOX = XBW * TY * 2 * 4;        // 2304 bytes per x1 / q box (36 x 8 x 2)
+constexpr int X1OFF = 3584;                   // x1 box in a slot (128-byte aligned, after 3520)
+constexpr int SLOT = X1OFF + XBOX;            // 5888 bytes, 46 x 128
+static_assert(X1OFF >= 2 * VPLANE && X1OFF % 128 == 0 && SLOT % 128 == 0 && XBOX % 128 == 0, "slot layout");
 constexpr int PW = 8;                         // patch width: consumer warp w covers x in [8w, 8w+8) x 8 rows
 constexpr int RV = 4;                         // step slots
 constexpr int ND = 3;                         // descriptor buffers (units)
@@ -104,8 +107,8 @@ constexpr int DBUF = ZCG * (int)sizeof(PlaneDesc);  // one unit's descriptors
 
 // Slots of the fused level-1 CConv2 (+ combination and orthogonalisation dots):
 // the vector box, x1 and up to two q boxes of the previous directions.
-constexpr int QOFF = SLOT;                    // q box j (32 x 8 x 2) at QOFF + 2048 j
-constexpr int SLOT_F = SLOT + 2 * 2048;       // 9728 bytes, 76 x 128
+constexpr int QOFF = SLOT;                    // q box j (36 x 8 x 2) at QOFF + XBOX j
+constexpr int SLOT_F = SLOT + 2 * XBOX;       // 10496 bytes, 82 x 128
 constexpr int kMaxFusedOrtho = 2;
 
 template <bool BF16C, bool FUSE = false>
@@ -116,6 +119,8 @@ struct KCfg {
   static constexpr int SL = FUSE ? SLOT_F : SLOT;    // bytes per slot
   static constexpr int SMEM = NRV * SL + ND * DBUF + CB + kMetaBytes;
 };
+// three CTAs per SM (1 KB of shared memory reserved per CTA, 228 KB per SM) for the BF16 form
+static_assert(3 * (KCfg<true, true>::SMEM + 1024) <= 228 * 1024, "three fused BF16 CTAs per SM");
 
 // Image key of a cell: fluid count | air count << 16 (0/1 at level 1); zero
 // outside the grid (solid padding).
@@ -558,8 +563,8 @@ struct PairKernel {
 };
 
 struct StreamParams {
-  CUtensorMap tv;   // input vector of the level: box 40 x 10 x 2 (FP32)
-  CUtensorMap tx1;  // x1 of the level (combination only): box 32 x 8 x 2
+  CUtensorMap tv;   // input vector of the level: box 44 x 10 x 2 (FP32)
+  CUtensorMap tx1;  // x1 of the level (combination only): box 36 x 8 x 2
   Dims dm;
   int ntx, ntiles, zc, units;
   const PlaneDesc *desc;
@@ -572,7 +577,7 @@ struct StreamParams {
   int *err;
   int mode;             // which outputs are computed (STREAM_MODE_*)
   // fused level-1 combination: z = mask_fluid(c1 x1 + c2 CConv2) and the dots z . q_i
-  CUtensorMap tq;       // q ring: dims (nx, ny, nz, ring), box 32 x 8 x 2 x 1
+  CUtensorMap tq;       // q ring: dims (nx, ny, nz, ring), box 36 x 8 x 2 x 1
   double *part;         // partial dots, one row per CTA
   unsigned *ticket;     // last-CTA-done counter
   SolveState *stw;      // the solve state (orthogonalisation coefficients are written)
@@ -916,11 +921,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         const int zv = t < 0 ? U.zs - 1 : U.zs + 2 * t + 1;
         const bool x1 = has_x1 && t >= 0;
         const int nq = (FUSE && t >= 0) ? qcnt : 0;
-        mbar_expect_tx(bar, 2u * VPLANE + (x1 ? 2u * NT * 4u : 0u) + (uint32_t)nq * 2u * NT * 4u + kbytes);
+        mbar_expect_tx(bar, 2u * VPLANE + (x1 ? (uint32_t)XBOX : 0u) + (uint32_t)nq * (uint32_t)XBOX + kbytes);
         tma_load_3d(dst, &P.tv, U.x0 - 4, U.y0 - 1, zv, bar);
         if (x1) tma_load_3d(dst + X1OFF, &P.tx1, U.x0, U.y0, U.zs + 2 * t, bar);
         if (FUSE)
-          for (int j = 0; j < nq; ++j) tma_load_4d(dst + QOFF + 2 * NT * 4 * j, &P.tq, U.x0, U.y0, U.zs + 2 * t, qslot[j], bar);
+          for (int j = 0; j < nq; ++j) tma_load_4d(dst + QOFF + XBOX * j, &P.tq, U.x0, U.y0, U.zs + 2 * t, qslot[j], bar);
         if (kbytes) bulk_load(kb + kpos, P.cache + (size_t)koff * C::EB, kbytes, bar);
         kpos += kbytes;
         ++vi;
@@ -1012,11 +1017,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       }
       float x1v[4] = {0.f, 0.f, 0.f, 0.f};  // (row a, z0), (row b, z0), (row a, z1), (row b, z1)
       if (has_x1) {
-        const float *xs = (const float *)(slot + X1OFF) + ra * TX + xb;
+        const float *xs = (const float *)(slot + X1OFF) + ra * XBW + xb;
         x1v[0] = xs[0];
-        x1v[1] = xs[TX];
-        x1v[2] = xs[NT];
-        x1v[3] = xs[NT + TX];
+        x1v[1] = xs[XBW];
+        x1v[2] = xs[XBW * TY];
+        x1v[3] = xs[XBW * TY + XBW];
       }
       const uint32_t *kblk = (const uint32_t *)(kb + M.kstart[sl]);
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1050,8 +1055,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
 #pragma unroll
         for (int j = 0; j < kMaxFusedOrtho; ++j) {
           if (j < fqcnt) {
-            const float *qs = (const float *)(slot + QOFF + 2 * NT * 4 * j) + ra * TX + xb;
-            df_add(fdot[j], (acc[0] * qs[0] + acc[1] * qs[TX]) + (acc[2] * qs[NT] + acc[3] * qs[NT + TX]));
+            const float *qs = (const float *)(slot + QOFF + XBOX * j) + ra * XBW + xb;
+            df_add(fdot[j], (acc[0] * qs[0] + acc[1] * qs[XBW]) + (acc[2] * qs[XBW * TY] + acc[3] * qs[XBW * TY + XBW]));
           }
         }
       }
@@ -1177,7 +1182,7 @@ CUresult encode_map_4d(CUtensorMap *m, const float *base, Dims d, int nring) {
   cuuint64_t dims[4] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)nring};
   const cuuint64_t rowb = (cuuint64_t)d.nx * 4u;
   cuuint64_t strides[3] = {rowb, rowb * (cuuint64_t)d.ny, rowb * (cuuint64_t)d.ny * (cuuint64_t)d.nz};
-  cuuint32_t box[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 2u, 1u};
+  cuuint32_t box[4] = {(cuuint32_t)XBW, (cuuint32_t)TY, 2u, 1u};
   cuuint32_t es[4] = {1u, 1u, 1u, 1u};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1257,7 +1262,7 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
     P.stw = fuse->st;
   }
   if (!encode_map(&P.tv, v, dm, BXW, BYH, 2)) return -1;
-  if (c12 && !encode_map(&P.tx1, x1, dm, TX, TY, 2)) return -1;
+  if (c12 && !encode_map(&P.tx1, x1, dm, XBW, TY, 2)) return -1;
   // class tables in the stored format: BF16 pairs (the constants are BF16 values in that form) or FP32 words
   for (int c = 0; c < 3; ++c) {
     const float *k = kfix + 27 * c;
