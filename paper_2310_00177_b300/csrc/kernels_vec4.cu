@@ -248,36 +248,29 @@ __device__ __forceinline__ void split_alpha(double a, float &ah, float &al) {
 // of the slot being written, so the steps cost x's read and write once every
 // R iterations.  The lap kernel's last block records the flush (x_upto)
 // after every block here has read the state.
-template <bool DEFER>
+template <bool DEFER, int NO>
 __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__restrict__ zv, float *__restrict__ dring,
                                                          float *__restrict__ xhi, float *__restrict__ xlo,
                                                          const SolveState *st) {
   if (st->done) return;
-  const int k1 = st->k + 1, no = st->n_ortho;
+  constexpr int NA = NO > 0 ? NO : 1;  // array extents (n_ortho is a template argument)
+  const int k1 = st->k + 1, no = NO;
   const int cnt = min(no, k1 - 1);
   const bool flush = DEFER && (k1 - 1) - st->x_upto == no + 1;  // then cnt == no
-  float c[kMaxOrtho], ah[kMaxOrtho], al[kMaxOrtho];
+  float c[NA];
+  const float *src[NA];
 #pragma unroll
-  for (int j = 0; j < kMaxOrtho; ++j) {
+  for (int j = 0; j < NA; ++j) {
     c[j] = j < cnt ? (float)st->coef[j] : 0.f;
-    split_alpha(flush && j < cnt ? st->alpha_slot[ring_slot(k1 - 1 - j, no)] : 0.0, ah[j], al[j]);
+    src[j] = dring + (size_t)ring_slot(max(k1 - 1 - j, 1), no) * n;
   }
-  float oh, ol;  // step k - R, whose direction is in d_k's slot
-  split_alpha(flush ? st->alpha_slot[ring_slot(k1, no)] : 0.0, oh, ol);
-  const float *s0 = dring + (size_t)ring_slot(max(k1 - 1, 1), no) * n;
-  const float *s1 = dring + (size_t)ring_slot(max(k1 - 2, 1), no) * n;
-  const float *s2 = dring + (size_t)ring_slot(max(k1 - 3, 1), no) * n;
-  const float *s3 = dring + (size_t)ring_slot(max(k1 - 4, 1), no) * n;
   float *dst = dring + (size_t)ring_slot(k1, no) * n;
   const int n4 = n >> 2;
   const int stride = gridDim.x * blockDim.x;
-  auto group = [&](int g) {
-    const int p = g << 2;
+  auto ortho = [&](int p, float4 (&sv)[NA]) {
     float4 v = ld4(zv + p);
-    const float *src[kMaxOrtho] = {s0, s1, s2, s3};
-    float4 sv[kMaxOrtho];
 #pragma unroll
-    for (int j = 0; j < kMaxOrtho; ++j) {
+    for (int j = 0; j < NA; ++j) {
       if (j < cnt) {
         sv[j] = ld4(src[j] + p);
         v.x -= c[j] * sv[j].x;
@@ -286,17 +279,35 @@ __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__r
         v.w -= c[j] * sv[j].w;
       }
     }
-    if (DEFER && flush) {
+    return v;
+  };
+  if (DEFER && flush) {
+    // one group at a time, so that the flush path does not raise the
+    // kernel's register count (the common path keeps two groups in flight)
+    float ah[NA], al[NA], oh, ol;  // oh, ol: step k - R, whose direction is in d_k's slot
+#pragma unroll
+    for (int j = 0; j < NA; ++j) split_alpha(j < cnt ? st->alpha_slot[ring_slot(k1 - 1 - j, no)] : 0.0, ah[j], al[j]);
+    split_alpha(st->alpha_slot[ring_slot(k1, no)], oh, ol);
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += stride) {
+      const int p = g << 2;
+      float4 sv[NA];
+      const float4 v = ortho(p, sv);
       const float4 dold = ld4(dst + p);
       float4 h = ld4(xhi + p), l = ld4(xlo + p);
       df_axpy4(h, l, oh, ol, dold);
 #pragma unroll
-      for (int j = kMaxOrtho - 1; j >= 0; --j)
+      for (int j = NA - 1; j >= 0; --j)
         if (j < cnt) df_axpy4(h, l, ah[j], al[j], sv[j]);
       st4(xhi + p, h);
       st4(xlo + p, l);
+      st4(dst + p, v);
     }
-    st4(dst + p, v);
+    return;
+  }
+  auto group = [&](int g) {
+    const int p = g << 2;
+    float4 sv[NA];
+    st4(dst + p, ortho(p, sv));
   };
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   for (; g + stride < n4; g += 2 * stride) {
@@ -515,11 +526,27 @@ void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *
   k_combine1_4<<<grid4(n / 4, num_sms, resident_blocks<k_combine1_4>()), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
 }
 void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const SolveState *st,
-                       int num_sms, cudaStream_t s) {
-  if (defer_x)
-    k_direction4<true><<<grid4(n / 4, num_sms, resident_blocks<k_direction4<true>>()), kThreads, 0, s>>>(n, z, dring, xhi, xlo, st);
-  else
-    k_direction4<false><<<grid4(n / 4, num_sms, resident_blocks<k_direction4<false>>()), kThreads, 0, s>>>(n, z, dring, xhi, xlo, st);
+                       int n_ortho, int num_sms, cudaStream_t s) {
+  switch ((defer_x ? 8 : 0) + n_ortho) {
+#define NPS_DIR_CASE(D, NO)                                                                                        \
+  case (D ? 8 : 0) + NO:                                                                                           \
+    k_direction4<D, NO><<<grid4(n / 4, num_sms, resident_blocks<k_direction4<D, NO>>()), kThreads, 0, s>>>(       \
+        n, z, dring, xhi, xlo, st);                                                                                \
+    break;
+    NPS_DIR_CASE(false, 0)
+    NPS_DIR_CASE(false, 1)
+    NPS_DIR_CASE(false, 2)
+    NPS_DIR_CASE(false, 3)
+    NPS_DIR_CASE(false, 4)
+    NPS_DIR_CASE(true, 0)
+    NPS_DIR_CASE(true, 1)
+    NPS_DIR_CASE(true, 2)
+    NPS_DIR_CASE(true, 3)
+    NPS_DIR_CASE(true, 4)
+#undef NPS_DIR_CASE
+    default:
+      break;
+  }
 }
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s) {
   long long b = (dm.n() + kThreads - 1) / kThreads;

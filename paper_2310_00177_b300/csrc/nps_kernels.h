@@ -62,7 +62,7 @@ void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *
                        const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
                        cudaStream_t s);
 void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const SolveState *st,
-                       int num_sms, cudaStream_t s);
+                       int n_ortho, int num_sms, cudaStream_t s);
 // per-cell stencil codes of the masked Laplacian (once per solve) and q = A d with them
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s);
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,

@@ -882,7 +882,7 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   if (fast) {
     {
       ProfScope ps(h, P_ORTHO_DIR, s);
-      launch_direction4(recur, (int)n, w.z, w.dring, w.xhi, w.xlo, w.st, h->num_sms, s);
+      launch_direction4(recur, (int)n, w.z, w.dring, w.xhi, w.xlo, w.st, h->cfg.n_ortho, h->num_sms, s);
     }
     {
       ProfScope ps(h, P_LAP, s);
