@@ -17,6 +17,8 @@ Also reported on the same line:
   roofline       the dominant kernel class of a profiled solve (CUDA events
                  around each launch on the solve's stream) against the
                  measured peaks in MEASURED_PEAKS.json
+  roofline_stencil_vector  the same for the Laplacian, update and direction
+                 kernels (algorithmic bytes per launch / launch time)
   served         p50 / p99 latency and solves per second of the serving
                  workload: 512 requests, Poisson arrivals at 200/s, sizes
                  64^3, 128^3, 192^3, 256^3, frames of evolving scenes, HBM
@@ -56,15 +58,15 @@ ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
 # CConv1 and CConv2 launches of one iteration, the summary kept in profiles/);
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_L1 = (197.6e6 + 337.8e6) / 2  # ncu: level-1 CConv1 and the fused level-1 CConv2 of one iteration
+TRAFFIC_L1 = (197.7e6 + 338.5e6) / 2  # ncu: level-1 CConv1 and the fused level-1 CConv2 of one iteration
 
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
 # (inputs read once, outputs written once).
 BYTES_PER_CELL = {
     "cconv_l1": 4 + 0.625 + 4,  # v, descriptors -> out (+ cached kernels, see below)
-    "lap_alpha": 4 + 1 + 4 + 4,  # d, labels, r -> q
-    "update": 8 + 8 + 4 + 4 + 4 + 4,  # x r/w (FP64), r r/w, d, q
-    "ortho_dir": 4 + 4 + 4 + 4,  # z, d1, d2 -> d
+    "lap_alpha": 4 + 2 + 4 + 4,  # d, stencil codes, r -> q
+    "update": 4 + 4 + 4,  # r r/w, q (the steps go into x in the direction kernel)
+    "ortho_dir": 4 + 4 + 4 + 4 + (4 + 16) / 3,  # z, d1, d2 -> d; every third: d_{k-3}, x (hi, lo) r/w
     "combine": 4 + 4 + 4 + 1 + 8,  # x1, x2 -> z, labels, q1, q2 (level 1, unfused)
     "interp": 4 + 0.5,           # fine out, coarse in (level 1 dominates)
     "pool": 4 + 0.5,
@@ -343,6 +345,15 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "kernel": dom, "algorithmic": f"{bpc} B/cell x {n} cells",
                 "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"]}
+    # the stencil and vector kernels against the same HBM peak (algorithmic bytes
+    # per launch / average launch time of the profiled solve)
+    vec_roof = {}
+    for cls in ("lap_alpha", "update", "ortho_dir"):
+        if cls in prof and prof[cls][1]:
+            t = prof[cls][0] / prof[cls][1] / 1e3
+            ach = BYTES_PER_CELL[cls] * n / t / 1e9
+            vec_roof[cls] = {"achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                             "bytes_per_cell": BYTES_PER_CELL[cls], "avg_launch_us": t * 1e6}
     total_prof = sum(v[0] for v in prof.values())
     breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total_prof, 4)}
                  for k, v in prof.items() if v[1]}
@@ -391,6 +402,7 @@ def main():
         "served": served,
         "accuracy": accuracy,
         "roofline": roof,
+        "roofline_stencil_vector": vec_roof,
         "kernel_breakdown": breakdown,
         "gpu_launches": int(launches_timed),
         "cpu_baseline": cpu,
