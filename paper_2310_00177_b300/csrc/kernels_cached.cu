@@ -213,7 +213,14 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t class_bit(const uint8_t *lab, const ushort2 *counts, const Dims &d, int x, int y,
                                               int z, uint32_t kF, uint32_t kA) {
-  const uint32_t k = image_key(lab, counts, d, x, y, z);
+  if ((unsigned)x >= (unsigned)d.nx || (unsigned)y >= (unsigned)d.ny || (unsigned)z >= (unsigned)d.nz) return 1u;
+  const uint32_t p = ((uint32_t)z * (uint32_t)d.ny + (uint32_t)y) * (uint32_t)d.nx + (uint32_t)x;  // n < 2^31
+  if (lab) {
+    const uint8_t l = __ldg(lab + p);
+    return l == kFluid ? 2u : (l == kAir ? 4u : 1u);  // level 1: every cell is pure
+  }
+  const ushort2 c = counts[p];
+  const uint32_t k = (uint32_t)c.x | ((uint32_t)c.y << 16);
   return k == 0u ? 1u : (k == kF ? 2u : (k == kA ? 4u : 8u));
 }
 
@@ -234,9 +241,11 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
     const int x = x0 + lane, y = y0 + warp;
     const int zs = c * zcc, nzu = min(zcc, d.nz - zs);
     const bool inside = x < d.nx && y < d.ny;
+    uint32_t own = 0u;  // this thread's class bit in the plane of the last row_or(y, .)
     // the OR of row yy's class bits over x-1 .. x+1 (plane z)
     auto row_or = [&](int yy, int z) -> uint32_t {
       const uint32_t b = class_bit(lab, counts, d, x, yy, z, kF, kA);
+      if (yy == y) own = b;
       uint32_t left = __shfl_up_sync(0xffffffffu, b, 1), right = __shfl_down_sync(0xffffffffu, b, 1);
       if (lane == 0) left = class_bit(lab, counts, d, x - 1, yy, z, kF, kA);
       if (lane == 31) right = class_bit(lab, counts, d, x + 1, yy, z, kF, kA);
@@ -253,12 +262,12 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
     };
     uint32_t pm = plane(zs - 1, 0), p0 = plane(zs, 1);
     for (int j = 0; j < nzu; ++j) {
-      const int z = zs + j;
-      const uint32_t pp = plane(z + 1, j & 1);
+      const uint32_t o0 = own;  // class bit of this thread's cell in plane z
+      const uint32_t pp = plane(zs + j + 1, j & 1);
       const uint32_t wor = pm | p0 | pp;
       const bool pure = wor == 1u || wor == 2u || wor == 4u;
       const bool mixed = inside && !pure, fl = inside && wor == 2u, ai = inside && wor == 4u;
-      const bool self = inside && lab != nullptr && image_key(lab, counts, d, x, y, z) == 1u;
+      const bool self = inside && lab != nullptr && o0 == 2u;
       const uint32_t bm = __ballot_sync(0xffffffffu, mixed), bf = __ballot_sync(0xffffffffu, fl);
       const uint32_t ba = __ballot_sync(0xffffffffu, ai), bs = __ballot_sync(0xffffffffu, self);
       if (lane == 0) {
@@ -1256,7 +1265,7 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
   if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3); units within the classification's
     const int zc = setup_chunk(d, num_sms);
     const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
-    const int g = grid_for_units(units, num_sms * 4);
+    const int g = grid_for_units(units, num_sms * 7);  // 7 CTAs per SM: 448 of the 512 TMEM columns
     if (nsplit == 1)
       k_generate_tc<1, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
                                               (uint32_t *)cache1, zc, err);
