@@ -58,7 +58,7 @@ ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
 # CConv1 and CConv2 launches of one iteration, the summary kept in profiles/);
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_L1 = (197.7e6 + 338.5e6) / 2  # ncu: level-1 CConv1 and the fused level-1 CConv2 of one iteration
+TRAFFIC_L1 = None
 
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
 # (inputs read once, outputs written once).
@@ -324,17 +324,18 @@ def main():
         # the level-1 CConv launches (TMA-streamed z-march) per cell: the input
         # (4 B), the plane descriptors (160 B per 256 cells), the cached kernels
         # of the mixed-window cells (56 B BF16 each), the output (4 B); CConv1
-        # adds the pooled output (0.5 B); the CConv2 fused with the level-1
+        # adds the pooled output (0.5 B) and the residual step it forms first
+        # (q read 4 B, r_{k+1} written 4 B); the CConv2 fused with the level-1
         # combination adds x1 (4 B) and the two previous q (8 B).  Averaged over
         # the two launches of an iteration.
         mixed = sol.mixed_cells(1)
         frac = mixed / n if mixed >= 0 else 0.0
         common = 4 + 160 / 256 + 56.0 * frac + 4
-        bpc = ((common + 0.5) + (common + 4 + 8)) / 2
+        bpc = ((common + 0.5 + 8) + (common + 4 + 8)) / 2
         achieved = bpc * n / avg_s / 1e9
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1; CConv2 fused with the "
+                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1 with the residual step; CConv2 fused with the "
                 "combination and orthogonalisation dots)",
                 "algorithmic": f"{bpc:.2f} B/cell x {n} cells (mixed-window fraction {frac:.4f})",
                 "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"] + " (hbm_gbs)"}

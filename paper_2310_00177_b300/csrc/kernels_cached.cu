@@ -107,20 +107,26 @@ constexpr int DBUF = ZCG * (int)sizeof(PlaneDesc);  // one unit's descriptors
 
 // Slots of the fused level-1 CConv2 (+ combination and orthogonalisation dots):
 // the vector box, x1 and up to two q boxes of the previous directions.
+// Slots of the level-1 CConv1 that also forms r_{k+1} = r_k - alpha q_k: the
+// residual box and the q box of the same geometry.
+constexpr int QUOFF = 3584;                   // q box (44 x 10 x 2) after the residual box
+constexpr int SLOT_U = 7168;                  // 3584 + 3520 bytes rounded up to 56 x 128
+static_assert(QUOFF >= 2 * VPLANE && QUOFF + 2 * VPLANE <= SLOT_U && SLOT_U % 128 == 0, "update slot layout");
 constexpr int QOFF = SLOT;                    // q box j (36 x 8 x 2) at QOFF + XBOX j
 constexpr int SLOT_F = SLOT + 2 * XBOX;       // 10496 bytes, 82 x 128
 constexpr int kMaxFusedOrtho = 2;
 
-template <bool BF16C, bool FUSE = false>
+template <bool BF16C, bool FUSE = false, bool UPD = false>
 struct KCfg {
   static constexpr int EB = BF16C ? 56 : 108;        // bytes per cached kernel
   static constexpr int CB = BF16C ? 28672 : 55296;   // circular kernel-block buffer (>= two full planes)
   static constexpr int NRV = FUSE ? 3 : RV;          // step slots
-  static constexpr int SL = FUSE ? SLOT_F : SLOT;    // bytes per slot
+  static constexpr int SL = FUSE ? SLOT_F : (UPD ? SLOT_U : SLOT);  // bytes per slot
   static constexpr int SMEM = NRV * SL + ND * DBUF + CB + kMetaBytes;
 };
 // three CTAs per SM (1 KB of shared memory reserved per CTA, 228 KB per SM) for the BF16 form
 static_assert(3 * (KCfg<true, true>::SMEM + 1024) <= 228 * 1024, "three fused BF16 CTAs per SM");
+static_assert(3 * (KCfg<true, false, true>::SMEM + 1024) <= 228 * 1024, "three update-fused BF16 CTAs per SM");
 
 // Image key of a cell: fluid count | air count << 16 (0/1 at level 1); zero
 // outside the grid (solid padding).
@@ -619,6 +625,14 @@ struct StreamParams {
   double *part;         // partial dots, one row per CTA
   unsigned *ticket;     // last-CTA-done counter
   SolveState *stw;      // the solve state (orthogonalisation coefficients are written)
+  // level-1 CConv1 that first forms r_{k+1} = r_k - alpha q_{k+1} (Alg. 1's
+  // recurrence) while a step is pending: r_k in buffer k mod 2
+  CUtensorMap tv2;      // the second residual buffer, as tv
+  CUtensorMap tqu;      // q ring: dims (nx, ny, nz, ring), box 44 x 10 x 2 x 1
+  float *rb[2];         // the residual buffers (r_{k+1} is written to rb[(k + 1) & 1])
+  double *upart;        // ||r_{k+1}||^2 partials, one per CTA
+  unsigned *uticket;
+  double *hist;
   PairKernel kp[3];              // kernels of the pure-solid, pure-fluid, pure-air windows, paired
   uint32_t ktab[3][27];          // the same as stored in the class tables (BF16 pairs or FP32 words)
 };
@@ -827,15 +841,58 @@ __device__ __noinline__ void fused_finish(const StreamParams &P, StreamMeta &M, 
   }
 }
 
+// End of the residual update fused into the level-1 CConv1: the CTA's
+// ||r_{k+1}||^2 partial (consumer warps in a fixed order) goes to its slot;
+// the last CTA sums the slots in a fixed order and, as k_update4's last
+// block does, advances the iteration, records ||r_{k+1}||, applies the stop
+// test ||r_{k+1}|| < tol ||b|| and the next input normalisation, then
+// re-arms the counter.
+__device__ __noinline__ void update_finish(const StreamParams &P, StreamMeta &M, DF unorm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double v = (double)unorm.hi + (double)unorm.lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) M.fsum[warp][0] = v;
+  consumers_sync();
+  if (tid == 0) {
+    P.upart[blockIdx.x] = ((M.fsum[0][0] + M.fsum[1][0]) + M.fsum[2][0]) + M.fsum[3][0];
+    __threadfence();
+    const unsigned t = atomicAdd(P.uticket, 1u);
+    M.last_ = t == gridDim.x - 1 ? 1 : 0;
+  }
+  consumers_sync();
+  if (!M.last_) return;
+  __threadfence();
+  double a = 0.0;
+  for (int i = tid; i < (int)gridDim.x; i += 128) a += __ldcg(P.upart + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if (lane == 0) M.fsum[warp][0] = a;
+  consumers_sync();
+  if (tid == 0) {
+    SolveState *st = P.stw;
+    const double rr = ((M.fsum[0][0] + M.fsum[1][0]) + M.fsum[2][0]) + M.fsum[3][0];
+    st->k += 1;
+    st->upd_pending = 0;
+    st->rnorm2 = rr;
+    P.hist[st->k] = sqrt(rr);
+    if (!isfinite(rr)) st->done = kDoneBreakdown;
+    else if (rr < st->eps2 || rr == 0.0) st->done = kDoneConverged;
+    else st->rscale = (float)(1.0 / sqrt(rr));
+    *P.uticket = 0u;
+  }
+}
+
 }  // namespace
 
 constexpr int NCW = 4;                    // consumer warps: two tile rows each
 constexpr int NTHREADS = NCW * 32 + 32;   // and one producer warp
 
-template <bool BF16C, bool FUSE, int MODE>
+template <bool BF16C, bool FUSE, int MODE, bool UPD = false>
 __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_constant__ StreamParams P) {
   static_assert(!FUSE || MODE == STREAM_MODE_FLUID_ONLY, "the fused CConv2 computes fluid outputs only");
-  using C = KCfg<BF16C, FUSE>;
+  static_assert(!UPD || (!FUSE && MODE == STREAM_MODE_ZERO_PURE), "the residual update goes with the level-1 CConv1");
+  using C = KCfg<BF16C, FUSE, UPD>;
   constexpr int NRV = C::NRV;
   if (P.st && P.st->done) return;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -882,6 +939,10 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       qcnt = min(min(no, k1 - 1), kMaxFusedOrtho);
       for (int j = 0; j < kMaxFusedOrtho; ++j) qslot[j] = ring_slot(max(k1 - 1 - j, 1), no);
     }
+    // the residual update: r_k from buffer k mod 2 and q of the pending step
+    const bool upd = UPD && P.st->upd_pending;
+    const CUtensorMap *tvm = (UPD && (P.st->k & 1)) ? &P.tv2 : &P.tv;
+    const int uslot = UPD ? ring_slot(P.st->k + 1, P.st->n_ortho) : 0;
     auto release_next = [&]() {
       const int sl = (int)(vrel % NRV);
       if (!mbar_sleep_wait(&M.empty[sl], (vrel / NRV) & 1u, kWaitNs)) {
@@ -959,8 +1020,10 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         const int zv = t < 0 ? U.zs - 1 : U.zs + 2 * t + 1;
         const bool x1 = has_x1 && t >= 0;
         const int nq = (FUSE && t >= 0) ? qcnt : 0;
-        mbar_expect_tx(bar, 2u * VPLANE + (x1 ? (uint32_t)XBOX : 0u) + (uint32_t)nq * (uint32_t)XBOX + kbytes);
-        tma_load_3d(dst, &P.tv, U.x0 - 4, U.y0 - 1, zv, bar);
+        mbar_expect_tx(bar, 2u * VPLANE + (upd ? 2u * VPLANE : 0u) + (x1 ? (uint32_t)XBOX : 0u) +
+                                (uint32_t)nq * (uint32_t)XBOX + kbytes);
+        tma_load_3d(dst, tvm, U.x0 - 4, U.y0 - 1, zv, bar);
+        if (upd) tma_load_4d(dst + QUOFF, &P.tqu, U.x0 - 4, U.y0 - 1, zv, uslot, bar);
         if (x1) tma_load_3d(dst + X1OFF, &P.tx1, U.x0, U.y0, U.zs + 2 * t, bar);
         if (FUSE)
           for (int j = 0; j < nq; ++j) tma_load_4d(dst + QOFF + XBOX * j, &P.tq, U.x0, U.y0, U.zs + 2 * t, qslot[j], bar);
@@ -1008,6 +1071,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   DF fdot[kMaxFusedOrtho];   // fused: per-thread double-float dots z . q_i
   int fqcnt = 0;
   if (FUSE) fqcnt = min(min(P.st->n_ortho, P.st->k), kMaxFusedOrtho);
+  // residual update: every window value is r_k - alpha q (the same FP32 FMA as
+  // k_update4), the thread's own cells are written to the other buffer and
+  // summed into ||r_{k+1}||^2
+  const bool upd = UPD && P.st->upd_pending;
+  const float uaf = upd ? (float)P.st->alpha : 0.f;
+  float *const rnext = upd ? P.rb[(P.st->k + 1) & 1] : nullptr;
+  DF unorm;
+  auto load_col = [&](const float *pl, int e) -> float {
+    return upd ? fmaf(-uaf, pl[(QUOFF / 4) + e], pl[e]) : pl[e];
+  };
 
   for (int m = 0; ok; ++m) {
     if (!wait(&M.dfull[m % ND], (m / ND) & 1)) break;
@@ -1025,8 +1098,8 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         const int e = vbase + (q / 3) * BXW + q % 3;
-        pA.set(q, pl[e]);
-        pB.set(q, pl[BXW * BYH + e]);
+        pA.set(q, load_col(pl, e));
+        pB.set(q, load_col(pl, BXW * BYH + e));
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&M.empty[sl]);
@@ -1036,6 +1109,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
       }
     }
     float *op = P.out + (long long)U.zs * nxy + (long long)gy * P.dm.nx + gx;
+    float *rp = upd ? rnext + (long long)U.zs * nxy + (long long)gy * P.dm.nx + gx : nullptr;
     float *pp = P.pooled ? P.pooled + ((long long)(U.zs >> 1) * cyn + (gy >> 1)) * cxn + (gx >> 1) : nullptr;
     const long long pstep = (long long)cxn * cyn;
     const bool pown = in_a && !(xi & 1);  // even column writes the 2x2x2 block's mean
@@ -1050,8 +1124,20 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         const int e = vbase + (q / 3) * BXW + q % 3;
-        pC.set(q, pl[e]);
-        pD.set(q, pl[BXW * BYH + e]);
+        pC.set(q, load_col(pl, e));
+        pD.set(q, load_col(pl, BXW * BYH + e));
+      }
+      if (UPD && upd) {  // r_{k+1} of the thread's cells: the window centres of planes z0 (pB) and z0+1 (pC)
+        const float ra0 = in_a ? pB.at(4) : 0.f, rb0 = in_b ? pB.at(7) : 0.f;
+        const float ra1 = in_a && two ? pC.at(4) : 0.f, rb1 = in_b && two ? pC.at(7) : 0.f;
+        if (in_a) rp[0] = ra0;
+        if (in_b) rp[P.dm.nx] = rb0;
+        if (two) {
+          if (in_a) rp[nxy] = ra1;
+          if (in_b) rp[nxy + P.dm.nx] = rb1;
+        }
+        rp += 2 * nxy;
+        df_add(unorm, (ra0 * ra0 + rb0 * rb0) + (ra1 * ra1 + rb1 * rb1));
       }
       float x1v[4] = {0.f, 0.f, 0.f, 0.f};  // (row a, z0), (row b, z0), (row a, z1), (row b, z1)
       if (has_x1) {
@@ -1131,6 +1217,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
     if (lane == 0) mbar_arrive(&M.dempty[m % ND]);
   }
   if (FUSE) fused_finish(P, M, fdot, fqcnt);
+  if (UPD && upd) update_finish(P, M, unorm);
 }
 
 // ---------------------------------------------------------------------------
@@ -1143,7 +1230,7 @@ int grid_for_units(long long units, int cap) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <bool BF16C, bool FUSE, int MODE>
+template <bool BF16C, bool FUSE, int MODE, bool UPD = false>
 int stream_occupancy() {
   // per device: the dynamic shared-memory opt-in is a per-device function attribute
   static int occ[64] = {};
@@ -1152,9 +1239,9 @@ int stream_occupancy() {
   if (dev < 0 || dev >= 64) dev = 0;
   if (!occ[dev]) {
     int o = 0;
-    using C = KCfg<BF16C, FUSE>;
-    cudaFuncSetAttribute(k_cconv_stream<BF16C, FUSE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C, FUSE, MODE>, NTHREADS, C::SMEM);
+    using C = KCfg<BF16C, FUSE, UPD>;
+    cudaFuncSetAttribute(k_cconv_stream<BF16C, FUSE, MODE, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_cconv_stream<BF16C, FUSE, MODE, UPD>, NTHREADS, C::SMEM);
     occ[dev] = o < 1 ? 1 : o;
   }
   return occ[dev];
@@ -1163,17 +1250,20 @@ int stream_occupancy() {
 // The instantiation for a (fused, mode) pair: the mode is a template argument
 // so that the level-1 launches carry only the fluid kernel's code.
 template <bool BF16C>
-int stream_occupancy_of(bool fused, int mode) {
+int stream_occupancy_of(bool fused, int mode, bool upd) {
   if (fused) return stream_occupancy<BF16C, true, STREAM_MODE_FLUID_ONLY>();
+  if (upd) return stream_occupancy<BF16C, false, STREAM_MODE_ZERO_PURE, true>();
   if (mode == STREAM_MODE_ZERO_PURE) return stream_occupancy<BF16C, false, STREAM_MODE_ZERO_PURE>();
   if (mode == STREAM_MODE_FLUID_ONLY) return stream_occupancy<BF16C, false, STREAM_MODE_FLUID_ONLY>();
   return stream_occupancy<BF16C, false, STREAM_MODE_ALL>();
 }
 
 template <bool BF16C>
-void launch_stream_of(bool fused, const StreamParams &P, int grid, cudaStream_t s) {
+void launch_stream_of(bool fused, bool upd, const StreamParams &P, int grid, cudaStream_t s) {
   if (fused)
     k_cconv_stream<BF16C, true, STREAM_MODE_FLUID_ONLY><<<grid, NTHREADS, KCfg<BF16C, true>::SMEM, s>>>(P);
+  else if (upd)
+    k_cconv_stream<BF16C, false, STREAM_MODE_ZERO_PURE, true><<<grid, NTHREADS, KCfg<BF16C, false, true>::SMEM, s>>>(P);
   else if (P.mode == STREAM_MODE_ZERO_PURE)
     k_cconv_stream<BF16C, false, STREAM_MODE_ZERO_PURE><<<grid, NTHREADS, KCfg<BF16C, false>::SMEM, s>>>(P);
   else if (P.mode == STREAM_MODE_FLUID_ONLY)
@@ -1214,13 +1304,13 @@ bool encode_map(CUtensorMap *m, const float *base, Dims d, int bw, int bh, int b
   return r == CUDA_SUCCESS;
 }
 
-CUresult encode_map_4d(CUtensorMap *m, const float *base, Dims d, int nring) {
+CUresult encode_map_4d(CUtensorMap *m, const float *base, Dims d, int nring, int bw = XBW, int bh = TY) {
   const EncodeTiledFn fn = encode_fn();
   if (!fn) return CUDA_ERROR_NOT_SUPPORTED;
   cuuint64_t dims[4] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz, (cuuint64_t)nring};
   const cuuint64_t rowb = (cuuint64_t)d.nx * 4u;
   cuuint64_t strides[3] = {rowb, rowb * (cuuint64_t)d.ny, rowb * (cuuint64_t)d.ny * (cuuint64_t)d.nz};
-  cuuint32_t box[4] = {(cuuint32_t)XBW, (cuuint32_t)TY, 2u, 1u};
+  cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)bh, 2u, 1u};
   cuuint32_t es[4] = {1u, 1u, 1u, 1u};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1287,10 +1377,22 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s,
-                        const StreamFusion *fuse) {
+                        const StreamFusion *fuse, const StreamUpdate *upd) {
   StreamParams P;
   memset(&P, 0, sizeof(P));
+  if (upd && (fuse || mode != STREAM_MODE_ZERO_PURE || c12)) return -1;
   P.mode = fuse ? STREAM_MODE_FLUID_ONLY : mode;
+  if (upd) {
+    // r_k is read from buffer k mod 2 (tv over rb[0], tv2 over rb[1]); q of the pending step from the ring
+    if (v != upd->rb[0] || !encode_map(&P.tv2, upd->rb[1], dm, BXW, BYH, 2)) return -1;
+    if (encode_map_4d(&P.tqu, upd->qring, dm, upd->nring, BXW, BYH) != CUDA_SUCCESS) return -1;
+    P.rb[0] = upd->rb[0];
+    P.rb[1] = upd->rb[1];
+    P.upart = upd->part;
+    P.uticket = upd->ticket;
+    P.hist = upd->hist;
+    P.stw = upd->st;
+  }
   if (fuse) {
     // the q ring as a 4-D tensor (nx, ny, nz, slot); slot stride = one grid
     const CUresult r = encode_map_4d(&P.tq, fuse->qring, dm, fuse->nring);
@@ -1341,10 +1443,10 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
       K.lo0[dz] = kz[0];
     }
   }
-  const int occ = bf16 ? stream_occupancy_of<true>(fuse != nullptr, P.mode)
-                       : stream_occupancy_of<false>(fuse != nullptr, P.mode);
+  const int occ = bf16 ? stream_occupancy_of<true>(fuse != nullptr, P.mode, upd != nullptr)
+                       : stream_occupancy_of<false>(fuse != nullptr, P.mode, upd != nullptr);
   int cap = num_sms * occ;
-  if (fuse && cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // one row of partials per CTA
+  if ((fuse || upd) && cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // one row of partials per CTA
   // the chunk of planes (even) that minimises the slots on the critical path:
   // units per CTA (rounded up) x (steps per unit + the prologue slot)
   int zc = 32;
@@ -1361,9 +1463,10 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
   P.zc = zc;
   P.units = P.ntiles * ((dm.nz + zc - 1) / zc);
   if (fuse && (size_t)cap * kMaxFusedOrtho > fuse->part_cap) return -1;  // partials do not fit
+  if (upd && (size_t)cap > upd->part_cap) return -1;
   const int grid = grid_for_units(P.units, cap);
-  if (bf16) launch_stream_of<true>(fuse != nullptr, P, grid, s);
-  else launch_stream_of<false>(fuse != nullptr, P, grid, s);
+  if (bf16) launch_stream_of<true>(fuse != nullptr, upd != nullptr, P, grid, s);
+  else launch_stream_of<false>(fuse != nullptr, upd != nullptr, P, grid, s);
   return 0;
 }
 

@@ -85,7 +85,7 @@ __global__ void k_init_final(const double *part, int nblocks, double tol, int ma
   s.k = 0;
   s.max_iter = max_iter;
   s.n_ortho = n_ortho;
-  s.pad_ = 0;
+  s.upd_pending = 0;
   s.x_upto = 0;
   for (int i = 0; i < kRing; ++i) s.alpha_slot[i] = 0.0;
   s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;

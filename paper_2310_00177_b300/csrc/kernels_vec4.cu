@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
     s.k = 0;
     s.max_iter = max_iter;
     s.n_ortho = n_ortho;
-    s.pad_ = 0;
+    s.upd_pending = 0;
     s.x_upto = 0;
     for (int i = 0; i < kRing; ++i) s.alpha_slot[i] = 0.0;
     s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
@@ -353,9 +353,10 @@ __global__ void __launch_bounds__(kThreads) k_lap_codes(const uint8_t *__restric
 // alpha = r^T d / d^T A d and flags breakdown (d^T A d <= 0 or non-finite).
 __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ code, Dims dm,
                                                    const float *__restrict__ dring, float *__restrict__ qring,
-                                                   const float *__restrict__ r, double *__restrict__ part,
-                                                   unsigned *ticket, SolveState *st) {
+                                                   const float *__restrict__ r0, const float *__restrict__ r1,
+                                                   double *__restrict__ part, unsigned *ticket, SolveState *st) {
   if (st->done) return;
+  const float *__restrict__ r = (r1 && (st->k & 1)) ? r1 : r0;  // r_k (two buffers: r_k in buffer k mod 2)
   const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
   const int n = nx * ny * nz, nxy = nx * ny;
   const int slot = ring_slot(st->k + 1, st->n_ortho);
@@ -418,6 +419,7 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
     st->alpha = rd / dq;
     st->alpha_slot[slot] = st->alpha;
     st->dAd[slot] = dq;
+    st->upd_pending = 1;
   });
 }
 
@@ -425,12 +427,19 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
 // iteration and applies the stop test ||r_k|| < tol ||b|| (the step's
 // alpha d goes into x later, in k_direction4 or k_flush_x).  Explicit mode:
 // x += alpha d in FP64 (the residual is then recomputed from x).
+// With two residual buffers (r_alt non-null) it forms r_{k+1} = r_k - alpha q
+// from buffer k mod 2 into the other one, and only while the step is
+// pending (the level-1 CConv1 usually forms it, see k_cconv_stream).
 template <bool RECUR>
-__global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict__ x, float *__restrict__ r,
-                                                      const float *__restrict__ dring, const float *__restrict__ qring,
-                                                      double *__restrict__ part, unsigned *ticket, SolveState *st,
-                                                      double *hist) {
+__global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict__ x, float *__restrict__ r_buf,
+                                                      float *__restrict__ r_alt, const float *__restrict__ dring,
+                                                      const float *__restrict__ qring, double *__restrict__ part,
+                                                      unsigned *ticket, SolveState *st, double *hist) {
   if (st->done) return;
+  if (RECUR && r_alt && !st->upd_pending) return;
+  const bool odd = r_alt && (st->k & 1);
+  const float *__restrict__ r_in = odd ? r_alt : r_buf;
+  float *__restrict__ r_out = r_alt ? (odd ? r_buf : r_alt) : r_buf;
   const int slot = ring_slot(st->k + 1, st->n_ortho);
   const double a = st->alpha;
   const int n4 = n >> 2;
@@ -457,12 +466,12 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
   auto group = [&](int g) {
     const int p = g << 2;
     const float4 qv = ld4(q + p);
-    float4 rv = ld4(r + p);
+    float4 rv = ld4(r_in + p);
     rv.x = fmaf(-af, qv.x, rv.x);
     rv.y = fmaf(-af, qv.y, rv.y);
     rv.z = fmaf(-af, qv.z, rv.z);
     rv.w = fmaf(-af, qv.w, rv.w);
-    st4(r + p, rv);
+    st4(r_out + p, rv);
     df_add(acc, rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
   };
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -475,6 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
   reduce_and_finish<1>(v, part, ticket, [&](const double *t) {
     const double rr = t[0];
     st->k += 1;
+    st->upd_pending = 0;
     st->rnorm2 = rr;
     hist[st->k] = sqrt(rr);
     if (!isfinite(rr)) st->done = kDoneBreakdown;
@@ -553,21 +563,21 @@ void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t 
   if (b > 148LL * 16) b = 148LL * 16;
   k_lap_codes<<<(int)(b < 1 ? 1 : b), kThreads, 0, s>>>(lab, dm, code);
 }
-void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
-                 unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
-  k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(code, dm, dring, qring, r, part, ticket, st);
+void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, const float *r_alt,
+                 double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
+  k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(code, dm, dring, qring, r, r_alt, part, ticket, st);
 }
 void launch_flush_x(int n, float *xhi, float *xlo, double *x, const float *dring, SolveState *st, int num_sms,
                     cudaStream_t s) {
   k_flush_x<<<grid4(n / 4, num_sms, resident_blocks<k_flush_x>()), kThreads, 0, s>>>(n, xhi, xlo, x, dring, st);
   k_clear_pend<<<1, 1, 0, s>>>(st);
 }
-void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
+void launch_update4(bool recurrence, int n, double *x, float *r, float *r_alt, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s) {
   if (recurrence)
-    k_update4<true><<<grid4(n / 4, num_sms, resident_blocks<k_update4<true>>()), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
+    k_update4<true><<<grid4(n / 4, num_sms, resident_blocks<k_update4<true>>()), kThreads, 0, s>>>(n, x, r, r_alt, dring, qring, part, ticket, st, hist);
   else
-    k_update4<false><<<grid4(n / 4, num_sms, resident_blocks<k_update4<false>>()), kThreads, 0, s>>>(n, x, r, dring, qring, part, ticket, st, hist);
+    k_update4<false><<<grid4(n / 4, num_sms, resident_blocks<k_update4<false>>()), kThreads, 0, s>>>(n, x, r, nullptr, dring, qring, part, ticket, st, hist);
 }
 
 }  // namespace nps

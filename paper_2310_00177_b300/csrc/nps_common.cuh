@@ -58,7 +58,7 @@ struct SolveState {
   int max_iter;
   int n_ortho;
   int x_upto;           // steps 1..x_upto are in x (the recurrence mode adds several steps to x at once)
-  int pad_;
+  int upd_pending;      // alpha of step k + 1 is known and r_{k+1} = r_k - alpha q not yet formed
   double alpha_slot[kRing];  // alpha of the step whose direction is in each ring slot
 };
 

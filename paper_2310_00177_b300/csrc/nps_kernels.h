@@ -65,12 +65,13 @@ void launch_direction4(bool defer_x, int n, const float *z, float *dring, float 
                        int n_ortho, int num_sms, cudaStream_t s);
 // per-cell stencil codes of the masked Laplacian (once per solve) and q = A d with them
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s);
-void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, double *part,
-                 unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
+void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, const float *r_alt,
+                 double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
 // Adds the pending steps to (xhi, xlo) and writes x = xhi + xlo in FP64.
 void launch_flush_x(int n, float *xhi, float *xlo, double *x, const float *dring, SolveState *st, int num_sms,
                     cudaStream_t s);
-void launch_update4(bool recurrence, int n, double *x, float *r, const float *dring, const float *qring,
+// r_alt non-null: two residual buffers (r_k in buffer k mod 2), applied only while a step is pending
+void launch_update4(bool recurrence, int n, double *x, float *r, float *r_alt, const float *dring, const float *qring,
                     double *part, unsigned *ticket, SolveState *st, double *hist, int num_sms, cudaStream_t s);
 
 // kernels_umma.cu
@@ -114,10 +115,24 @@ struct StreamFusion {
   SolveState *st;
 };
 bool stream_fusion_ok(int n_ortho);  // the fused kernel loads up to two previous directions
+// The level-1 CConv1 that first forms the pending residual step: r_{k+1} =
+// r_k - alpha q_{k+1} with r_k in rb[k mod 2] (the launch's v must be rb[0]),
+// written to rb[(k + 1) mod 2], with ||r_{k+1}||^2 and the end-of-step state
+// update of the recurrence (k_update4's), when SolveState.upd_pending is set.
+struct StreamUpdate {
+  float *rb[2];
+  const float *qring;
+  int nring;
+  double *part;     // one partial per CTA
+  size_t part_cap;  // doubles part can hold
+  unsigned *ticket;
+  double *hist;
+  SolveState *st;
+};
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s,
-                        const StreamFusion *fuse = nullptr);
+                        const StreamFusion *fuse = nullptr, const StreamUpdate *upd = nullptr);
 void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
 
 // kernels_train.cu

@@ -51,6 +51,7 @@ struct Workspace {
   size_t bytes = 0;   // device bytes held by this workspace
   float *r = nullptr, *z = nullptr, *dring = nullptr, *qring = nullptr;
   float *xhi = nullptr, *xlo = nullptr;  // x as a double-float pair during recurrence-mode iterations
+  float *r_alt = nullptr;  // second residual buffer when the update is fused into the level-1 CConv1
   uint16_t *lapcode = nullptr;  // per-cell stencil codes of the masked Laplacian (vec4 path)
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
@@ -222,6 +223,7 @@ void free_ws(Workspace &w) {
   cudaFree(w.z);
   cudaFree(w.xhi);
   cudaFree(w.xlo);
+  cudaFree(w.r_alt);
   cudaFree(w.lapcode);
   cudaFree(w.dring);
   cudaFree(w.qring);
@@ -281,6 +283,7 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     CK(h, dalloc(&w.bytes, &w.z, cap));
     CK(h, dalloc(&w.bytes, &w.xhi, cap));
     CK(h, dalloc(&w.bytes, &w.xlo, cap));
+    CK(h, dalloc(&w.bytes, &w.r_alt, cap));
     CK(h, dalloc(&w.bytes, &w.lapcode, cap));
     CK(h, dalloc(&w.bytes, &w.dring, cap * R));
     CK(h, dalloc(&w.bytes, &w.qring, cap * R));
@@ -463,6 +466,14 @@ bool cached_path(const npsolve *h, Dims d1) {
   return true;
 }
 
+// The recurrence step r_{k+1} = r_k - alpha q of an iteration is formed by the
+// next iteration's level-1 CConv1 (two residual buffers, r_k in buffer k mod
+// 2) on the multilevel, 16-byte-vector, cached path.
+bool fused_update(const npsolve *h, Dims d1) {
+  return h->cfg.levels > 1 && d1.nx % 4 == 0 && d1.n() <= (long long)INT32_MAX &&
+         h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE && cached_path(h, d1);
+}
+
 // One CConv block of level lvl (type 1 or 2), CUDA-core kernel.
 void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const float *in, const float *vscale,
            int mask_input, float *out, const SolveState *st, cudaStream_t s) {
@@ -495,14 +506,14 @@ void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const 
 // combination out = c1 x1 + c2 CConv(...).
 void cconv_cached(npsolve *h, Dims d1, int lvl, int type, const float *in, const float *vscale, float *out,
                   float *pooled, const float *x1, const double *c12, const SolveState *st, cudaStream_t s,
-                  int mode = STREAM_MODE_ALL, const StreamFusion *fuse = nullptr) {
+                  int mode = STREAM_MODE_ALL, const StreamFusion *fuse = nullptr, const StreamUpdate *upd = nullptr) {
   Workspace &w = h->ws;
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   if (launch_cconv_stream(h->cfg.precision == NPSOLVE_BF16, level_dims(d1, lvl), h->kfix_host.data() + (size_t)idx * 81,
                           w.kdesc[lvl], w.kcache[idx], in, vscale, out, pooled, x1, c12, mode, st, h->umma_err,
-                          h->num_sms, s, fuse))
+                          h->num_sms, s, fuse, upd))
     h->stream_err = true;
 }
 
@@ -532,7 +543,12 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   for (int l = 1; l < L; ++l) {
     const float *in = l == 1 ? r : w.r1[l];
     const float *vs = l == 1 ? vscale : nullptr;
-    if (cached) {
+    if (cached && l == 1 && st && fused_update(h, d1)) {
+      // the pending residual step first (r_k from buffer k mod 2, in = w.r is buffer 0)
+      const StreamUpdate up{{w.r, w.r_alt}, w.qring, kRing, w.part, w.part_cap, w.tickets + kTicketUpdate, w.hist, st};
+      cconv_cached(h, d1, l, 1, w.r, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s, STREAM_MODE_ZERO_PURE,
+                   nullptr, &up);
+    } else if (cached) {
       cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s,
                    l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL);
     } else if (tensor_level(h, l)) {
@@ -878,7 +894,8 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   const bool fast = vec4_path(d1) && h->cfg.levels > 1;
   run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s);
   const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
-  h->launches += fast ? (recur ? 3 : 5) : (recur ? 6 : 7);
+  const bool fused = fused_update(h, d1);  // the step's r update happens in the next level-1 CConv1
+  h->launches += fast ? (recur ? (fused ? 2 : 3) : 5) : (recur ? 6 : 7);
   if (fast) {
     {
       ProfScope ps(h, P_ORTHO_DIR, s);
@@ -886,10 +903,12 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
     }
     {
       ProfScope ps(h, P_LAP, s);
-      launch_lap4(w.lapcode, d1, w.dring, w.qring, w.r, w.part, w.tickets + kTicketLap, w.st, h->num_sms, s);
+      launch_lap4(w.lapcode, d1, w.dring, w.qring, w.r, fused ? w.r_alt : nullptr, w.part, w.tickets + kTicketLap,
+                  w.st, h->num_sms, s);
     }
+    if (fused) return;
     ProfScope ps(h, P_UPDATE, s);
-    launch_update4(recur, (int)n, x, w.r, w.dring, w.qring, w.part, w.tickets + kTicketUpdate, w.st, w.hist,
+    launch_update4(recur, (int)n, x, w.r, nullptr, w.dring, w.qring, w.part, w.tickets + kTicketUpdate, w.st, w.hist,
                    h->num_sms, s);
     if (!recur) launch_explicit_residual(lab, d1, b, x, w.r, w.part, w.st, w.hist, s);
     return;
@@ -1024,6 +1043,17 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     }
     CK(h, cudaStreamSynchronize(s));
     if (nb) hs = w.h_st[(nb - 1) & 1];
+    const bool fused = fused_update(h, d1);
+    if (fused) {
+      // the last iteration's r step (no next level-1 CConv1 formed it); a no-op when none is pending
+      ProfScope ps(h, P_UPDATE, s);
+      launch_update4(true, (int)d1.n(), x, w.r, w.r_alt, w.dring, w.qring, w.part, w.tickets + kTicketUpdate, w.st,
+                     w.hist, h->num_sms, s);
+      h->launches += 1;
+      CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+      CK(h, cudaStreamSynchronize(s));
+      hs = w.h_st[0];
+    }
     if (vec4_path(d1) && h->cfg.levels > 1 &&
         h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE) {  // the last steps may still be pending
       launch_flush_x((int)d1.n(), w.xhi, w.xlo, x, w.dring, w.st, h->num_sms, s);
@@ -1032,7 +1062,9 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&
         restarts < kMaxRestarts) {
       ProfScope ps(h, P_FINAL, s);
-      launch_replace_residual(lab, d1, b, x, w.r, w.part, w.st, w.reopened, w.relres, s);
+      // r_k lives in buffer k mod 2 when the update is fused into the level-1 CConv1
+      float *r_cur = (fused && (hs.k & 1)) ? w.r_alt : w.r;
+      launch_replace_residual(lab, d1, b, x, r_cur, w.part, w.st, w.reopened, w.relres, s);
       h->launches += 2;
       CK(h, cudaMemcpyAsync(w.h_flag, w.reopened, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
