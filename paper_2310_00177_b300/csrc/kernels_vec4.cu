@@ -493,6 +493,20 @@ __global__ void __launch_bounds__(kThreads) k_update4(int n, double *__restrict_
   });
 }
 
+// Exact FP32 -> FP64 widening by re-biasing the exponent field (binary32:
+// 8-bit exponent, bias 127, 23-bit fraction; binary64: 11-bit exponent, bias
+// 1023, 52-bit fraction) on the integer units; zeros keep their sign,
+// subnormal, infinite and NaN inputs take the conversion instruction.  B300's
+// FP64 pipe is 1/64 of its FP32 rate, so x = hi + lo then costs one FP64 add.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u || e == 0xFFu) return (u & 0x7FFFFFFFu) == 0u ? __longlong_as_double((long long)sign) : (double)f;
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 // Adds the steps not yet in x (x_upto < i <= k, at most n_ortho + 1 of them,
 // their directions still in the ring) to the double-float pair, oldest
 // first, and writes x = xhi + xlo in FP64; k_clear_pend then marks them
@@ -516,8 +530,8 @@ __global__ void __launch_bounds__(kThreads) k_flush_x(int n, float *__restrict__
       st4(xlo + p, l);
     }
     double2 *xp = reinterpret_cast<double2 *>(x + p);
-    xp[0] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-    xp[1] = make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w);
+    xp[0] = make_double2(widen(h.x) + widen(l.x), widen(h.y) + widen(l.y));
+    xp[1] = make_double2(widen(h.z) + widen(l.z), widen(h.w) + widen(l.w));
   }
 }
 __global__ void k_clear_pend(SolveState *st) { st->x_upto = st->k; }
