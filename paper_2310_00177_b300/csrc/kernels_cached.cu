@@ -1447,11 +1447,12 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
                        : stream_occupancy_of<false>(fuse != nullptr, P.mode, upd != nullptr);
   int cap = num_sms * occ;
   if ((fuse || upd) && cap > kRedMaxBlocks) cap = kRedMaxBlocks;  // one row of partials per CTA
-  // the chunk of planes (even) that minimises the slots on the critical path:
+  // the chunk of planes (even, so that a step's two planes never straddle a
+  // classification unit) that minimises the slots on the critical path:
   // units per CTA (rounded up) x (steps per unit + the prologue slot)
   int zc = 32;
   long long best = -1;
-  for (int c = 32; c >= 2; c >>= 1) {
+  for (int c = 32; c >= 2; c -= 2) {
     const long long units = (long long)P.ntiles * ((dm.nz + c - 1) / c);
     const long long per_cta = (units + cap - 1) / cap;
     const long long cost = per_cta * ((c + 1) / 2 + 1);
