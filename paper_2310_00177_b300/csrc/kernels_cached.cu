@@ -55,6 +55,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "nps_common.cuh"
@@ -232,7 +233,7 @@ __device__ __forceinline__ uint32_t class_bit(const uint8_t *lab, const ushort2 
 
 __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
                                                  Dims d, uint32_t full, int zcc, PlaneDesc *__restrict__ desc,
-                                                 unsigned *__restrict__ totals) {
+                                                 unsigned *__restrict__ totals, uint8_t *__restrict__ skip) {
   __shared__ uint32_t sd[ZCG][DWORDS];
   __shared__ uint8_t rows[2][TY + 2][TX];  // x-ORed class bits of rows y0-1 .. y0+8 of one plane, two buffers
   __shared__ uint32_t sbase;
@@ -308,6 +309,11 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
       sd[j][4 * TY + 1] = m;
       sd[j][4 * TY + 2] = (m + 3u) & ~3u;
       sd[j][4 * TY + 3] = pc;
+      if (skip) {  // bit 0: every window pure solid or pure air (a zero CConv1 output); bit 1: no fluid cell
+        uint32_t anyf = 0u;
+        for (int w = 0; w < TY; ++w) anyf |= sd[j][4 * w + 3];
+        skip[(size_t)t * d.nz + zs + j] = (uint8_t)(((pc & 0x55u) == 0u ? 1u : 0u) | (anyf == 0u ? 2u : 0u));
+      }
       sd[j][4 * TY + 4] = rb[0];
       sd[j][4 * TY + 5] = rb[1];
       sd[j][4 * TY + 6] = 0u;
@@ -611,6 +617,7 @@ struct StreamParams {
   CUtensorMap tx1;  // x1 of the level (combination only): box 36 x 8 x 2
   Dims dm;
   int ntx, ntiles, zc, units;
+  const int *ulist;     // optional: the units to process (indices c * ntiles + t), `units` of them
   const PlaneDesc *desc;
   const uint8_t *cache;
   const float *vscale;  // optional scale of the output (the input normalisation)
@@ -641,7 +648,8 @@ struct Unit {
   int t, x0, y0, zs, nzu;
 };
 
-__device__ __forceinline__ Unit unit_at(const StreamParams &P, int u) {
+__device__ __forceinline__ Unit unit_at(const StreamParams &P, int i) {
+  const int u = P.ulist ? __ldg(P.ulist + i) : i;
   Unit U;
   U.t = u % P.ntiles;
   const int c = u / P.ntiles;
@@ -1331,6 +1339,54 @@ int cached_entry_bytes(bool bf16) { return bf16 ? KCfg<true>::EB : KCfg<false>::
 
 bool stream_fusion_ok(int n_ortho) { return n_ortho <= kMaxFusedOrtho; }
 
+int stream_cap(bool bf16, bool fused, int mode, bool upd, int num_sms) {
+  const int occ = bf16 ? stream_occupancy_of<true>(fused, mode, upd) : stream_occupancy_of<false>(fused, mode, upd);
+  int cap = num_sms * occ;
+  if ((fused || upd) && cap > kRedMaxBlocks) cap = kRedMaxBlocks;
+  return cap;
+}
+
+int choose_stream_units(Dims d, const uint8_t *skip, int bit, int cap, int *list, int *n) {
+  // the even chunk with the fewest slots per CTA over the units that have a
+  // plane without the skip bit, and those units in ascending order
+  const int ntiles = ((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+  int zc = 32;
+  long long best = -1;
+  for (int c = 32; c >= 2; c -= 2) {
+    const int nch = (d.nz + c - 1) / c;
+    long long act = 0;
+    for (int ch = 0; ch < nch; ++ch)
+      for (int t = 0; t < ntiles; ++t) {
+        const uint8_t *f = skip + (size_t)t * d.nz;
+        const int z1 = std::min(d.nz, (ch + 1) * c);
+        for (int z = ch * c; z < z1; ++z)
+          if (!(f[z] & bit)) {
+            ++act;
+            break;
+          }
+      }
+    const long long cost = ((act + cap - 1) / cap) * ((c + 1) / 2 + 1);
+    if (best < 0 || cost < best) {
+      best = cost;
+      zc = c;
+    }
+  }
+  const int nch = (d.nz + zc - 1) / zc;
+  int m = 0;
+  for (int ch = 0; ch < nch; ++ch)
+    for (int t = 0; t < ntiles; ++t) {
+      const uint8_t *f = skip + (size_t)t * d.nz;
+      const int z1 = std::min(d.nz, (ch + 1) * zc);
+      for (int z = ch * zc; z < z1; ++z)
+        if (!(f[z] & bit)) {
+          list[m++] = ch * ntiles + t;
+          break;
+        }
+    }
+  *n = m;
+  return zc;
+}
+
 // Planes per unit of the setup kernels at a level: up to 32 (a unit's kernel
 // blocks are contiguous in the cache, so the chunks must be even), fewer when
 // the level is too small to give every SM a few units.
@@ -1342,10 +1398,11 @@ static int setup_chunk(Dims d, int num_sms) {
 }
 
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
-                     int num_sms, cudaStream_t s) {
+                     uint8_t *skip, int num_sms, cudaStream_t s) {
   const int zc = setup_chunk(d, num_sms);
   const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
-  k_classify<<<grid_for_units(units, num_sms * 8), NT, 0, s>>>(lab, counts, d, full, zc, (PlaneDesc *)desc, totals);
+  k_classify<<<grid_for_units(units, num_sms * 8), NT, 0, s>>>(lab, counts, d, full, zc, (PlaneDesc *)desc, totals,
+                                                                 skip);
 }
 
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
@@ -1377,7 +1434,7 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s,
-                        const StreamFusion *fuse, const StreamUpdate *upd) {
+                        const StreamFusion *fuse, const StreamUpdate *upd, const StreamUnits *units) {
   StreamParams P;
   memset(&P, 0, sizeof(P));
   if (upd && (fuse || mode != STREAM_MODE_ZERO_PURE || c12)) return -1;
@@ -1450,19 +1507,25 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
   // the chunk of planes (even, so that a step's two planes never straddle a
   // classification unit) that minimises the slots on the critical path:
   // units per CTA (rounded up) x (steps per unit + the prologue slot)
-  int zc = 32;
-  long long best = -1;
-  for (int c = 32; c >= 2; c -= 2) {
-    const long long units = (long long)P.ntiles * ((dm.nz + c - 1) / c);
-    const long long per_cta = (units + cap - 1) / cap;
-    const long long cost = per_cta * ((c + 1) / 2 + 1);
-    if (best < 0 || cost < best) {
-      best = cost;
-      zc = c;
+  if (units) {  // a list of the units that have work, with its chunk
+    P.zc = units->zc;
+    P.units = units->n;
+    P.ulist = units->list;
+  } else {
+    int zc = 32;
+    long long best = -1;
+    for (int c = 32; c >= 2; c -= 2) {
+      const long long nu = (long long)P.ntiles * ((dm.nz + c - 1) / c);
+      const long long per_cta = (nu + cap - 1) / cap;
+      const long long cost = per_cta * ((c + 1) / 2 + 1);
+      if (best < 0 || cost < best) {
+        best = cost;
+        zc = c;
+      }
     }
+    P.zc = zc;
+    P.units = P.ntiles * ((dm.nz + zc - 1) / zc);
   }
-  P.zc = zc;
-  P.units = P.ntiles * ((dm.nz + zc - 1) / zc);
   if (fuse && (size_t)cap * kMaxFusedOrtho > fuse->part_cap) return -1;  // partials do not fit
   if (upd && (size_t)cap > upd->part_cap) return -1;
   const int grid = grid_for_units(P.units, cap);

@@ -88,8 +88,10 @@ long long stream_desc_count(Dims d);   // plane descriptors of a level (tiles x 
 size_t stream_desc_bytes();            // bytes of one plane descriptor
 int cached_entry_bytes(bool bf16);     // bytes of one cached kernel
 // totals[0] += cache entries (blocks padded to 4), totals[1] += mixed cells
+// skip (optional, ntiles x nz bytes, tile-major): bit 0 = every window of the
+// tile's plane is pure solid or pure air, bit 1 = the plane has no fluid cell.
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
-                     int num_sms, cudaStream_t s);
+                     uint8_t *skip, int num_sms, cudaStream_t s);
 // wsplit0/1: the tensor-core weight splits of the two blocks (nsplit BF16
 // terms each) to generate on the tensor cores, or null for CUDA cores
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
@@ -115,6 +117,19 @@ struct StreamFusion {
   SolveState *st;
 };
 bool stream_fusion_ok(int n_ortho);  // the fused kernel loads up to two previous directions
+// The units (tile x chunk of zc planes, index chunk * ntiles + tile) a launch
+// processes when the others have nothing to compute (occupancy-aware
+// sparsity: a level-1 CConv1 over windows that are all pure solid or air
+// outputs zeros, a level-1 CConv2 is needed on fluid cells only).
+struct StreamUnits {
+  const int *list;  // device
+  int n;
+  int zc;
+};
+int stream_cap(bool bf16, bool fused, int mode, bool upd, int num_sms);  // CTAs of one wave
+// Picks the chunk for the units with a plane whose skip byte lacks `bit`,
+// writes their indices to list (ntiles x nz / 2 entries at most), returns the chunk.
+int choose_stream_units(Dims d, const uint8_t *skip, int bit, int cap, int *list, int *n);
 // The level-1 CConv1 that first forms the pending residual step: r_{k+1} =
 // r_k - alpha q_{k+1} with r_k in rb[k mod 2] (the launch's v must be rb[0]),
 // written to rb[(k + 1) mod 2], with ||r_{k+1}||^2 and the end-of-step state
@@ -132,7 +147,8 @@ struct StreamUpdate {
 int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc, const void *cache, const float *v,
                         const float *vscale, float *out, float *pooled, const float *x1, const double *c12, int mode,
                         const SolveState *st, int *err, int num_sms, cudaStream_t s,
-                        const StreamFusion *fuse = nullptr, const StreamUpdate *upd = nullptr);
+                        const StreamFusion *fuse = nullptr, const StreamUpdate *upd = nullptr,
+                        const StreamUnits *units = nullptr);
 void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *out, cudaStream_t s);
 
 // kernels_train.cu

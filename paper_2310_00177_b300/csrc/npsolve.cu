@@ -63,6 +63,13 @@ struct Workspace {
   size_t kcap[(kMaxLevels + 1) * 2] = {};    // cache entries kcache can hold
   // per level: [2 l] cache entries (blocks padded to 4), [2 l + 1] mixed cells
   unsigned *ktotal = nullptr, *h_ktotal = nullptr;
+  // level-1 occupancy-aware sparsity: per (tile, plane) skip bytes and the
+  // units of the level-1 CConv1 ([0, kskip_cap)) and CConv2 ([kskip_cap, 2 kskip_cap)) that have work
+  uint8_t *kskip = nullptr, *h_kskip = nullptr;
+  int *ulist = nullptr, *h_ulist = nullptr;
+  long long kskip_cap = 0;
+  int un[2] = {0, 0}, uzc[2] = {0, 0};
+  bool ulist_ok = false;
   size_t part_cap = 0;        // doubles of part
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
   int hist_cap = 0;
@@ -86,6 +93,7 @@ struct Workspace {
   const float *graph_b = nullptr;
   double *graph_x = nullptr;
   int graph_pcg = 0;
+  int graph_units[4] = {0, 0, 0, 0};  // the unit counts and chunks baked into the captured launches
   long long graph_kernels = 0;  // kernels per replay of the graph
 };
 
@@ -239,6 +247,10 @@ void free_ws(Workspace &w) {
   for (int i = 0; i < (kMaxLevels + 1) * 2; ++i) cudaFree(w.kcache[i]);
   cudaFree(w.ktotal);
   cudaFreeHost(w.h_ktotal);
+  cudaFree(w.kskip);
+  cudaFreeHost(w.h_kskip);
+  cudaFree(w.ulist);
+  cudaFreeHost(w.h_ulist);
   cudaFree(w.part);
   cudaFree(w.affc);
   cudaFree(w.relres);
@@ -506,14 +518,15 @@ void cconv_tc(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const 
 // combination out = c1 x1 + c2 CConv(...).
 void cconv_cached(npsolve *h, Dims d1, int lvl, int type, const float *in, const float *vscale, float *out,
                   float *pooled, const float *x1, const double *c12, const SolveState *st, cudaStream_t s,
-                  int mode = STREAM_MODE_ALL, const StreamFusion *fuse = nullptr, const StreamUpdate *upd = nullptr) {
+                  int mode = STREAM_MODE_ALL, const StreamFusion *fuse = nullptr, const StreamUpdate *upd = nullptr,
+                  const StreamUnits *units = nullptr) {
   Workspace &w = h->ws;
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   if (launch_cconv_stream(h->cfg.precision == NPSOLVE_BF16, level_dims(d1, lvl), h->kfix_host.data() + (size_t)idx * 81,
                           w.kdesc[lvl], w.kcache[idx], in, vscale, out, pooled, x1, c12, mode, st, h->umma_err,
-                          h->num_sms, s, fuse, upd))
+                          h->num_sms, s, fuse, upd, units))
     h->stream_err = true;
 }
 
@@ -539,6 +552,12 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     launch_mask_copy(lab, d1.n(), r, w.r, s);
     r = w.r;
   }
+  // inside a solve the level-1 CConvs process only the units with work (the
+  // rest of z, the pooled input of level 2 and the second residual buffer
+  // were zeroed once for the solve)
+  const bool lists = st && cached && w.ulist_ok;
+  const StreamUnits u1{w.ulist, w.un[0], w.uzc[0]}, u2{w.ulist + w.kskip_cap, w.un[1], w.uzc[1]};
+  const StreamUnits *pu1 = lists ? &u1 : nullptr, *pu2 = lists ? &u2 : nullptr;
   // down pass: x1^l = CConv1^l(r1^l), r1^{l+1} = Pool(x1^l)
   for (int l = 1; l < L; ++l) {
     const float *in = l == 1 ? r : w.r1[l];
@@ -547,10 +566,10 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       // the pending residual step first (r_k from buffer k mod 2, in = w.r is buffer 0)
       const StreamUpdate up{{w.r, w.r_alt}, w.qring, kRing, w.part, w.part_cap, w.tickets + kTicketUpdate, w.hist, st};
       cconv_cached(h, d1, l, 1, w.r, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s, STREAM_MODE_ZERO_PURE,
-                   nullptr, &up);
+                   nullptr, &up, pu1);
     } else if (cached) {
       cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s,
-                   l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL);
+                   l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL, nullptr, nullptr, l == 1 ? pu1 : nullptr);
     } else if (tensor_level(h, l)) {
       cconv_tc(h, lab, d1, l, 1, in, nullptr, vs, l == 1, w.x1[l], w.r1[l + 1], st, s);
     } else {
@@ -593,12 +612,13 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       if (st && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
         // level-1 CConv2, z = mask_fluid(c1 x1 + c2 x2) and the orthogonalisation dots in one pass
         const StreamFusion fu{w.qring, kRing, w.part, w.part_cap, w.tickets + kTicketCombine, st};
-        cconv_cached(h, d1, 1, 2, w.r2[1], nullptr, z, nullptr, w.x1[1], c12, st, s, STREAM_MODE_FLUID_ONLY, &fu);
+        cconv_cached(h, d1, 1, 2, w.r2[1], nullptr, z, nullptr, w.x1[1], c12, st, s, STREAM_MODE_FLUID_ONLY, &fu,
+                     nullptr, pu2);
         continue;
       }
       // level 1: only the fluid cells of x2 enter z (the output restriction)
       cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s,
-                   STREAM_MODE_FLUID_ONLY);
+                   STREAM_MODE_FLUID_ONLY, nullptr, nullptr, pu2);
     } else if (tensor_level(h, l) && !unfused) {
       cconv_tc(h, lab, d1, l, 2, nullptr, coarse, nullptr, 0, w.x2[l], nullptr, st, s);
     } else {
@@ -656,13 +676,50 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
         w.kdesc_cap[l] = nd;
       }
     }
+    const long long nsk = stream_desc_count(d1);  // level-1 (tile, plane) pairs
+    if (nsk > w.kskip_cap) {
+      if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old lists
+      w.graph = nullptr;
+      CK(h, cudaStreamSynchronize(s));
+      cudaFree(w.kskip);
+      cudaFreeHost(w.h_kskip);
+      cudaFree(w.ulist);
+      cudaFreeHost(w.h_ulist);
+      w.kskip = nullptr;
+      w.h_kskip = nullptr;
+      w.ulist = nullptr;
+      w.h_ulist = nullptr;
+      w.kskip_cap = 0;
+      CK(h, cudaMalloc(&w.kskip, (size_t)nsk));
+      CK(h, cudaHostAlloc((void **)&w.h_kskip, (size_t)nsk, cudaHostAllocDefault));
+      CK(h, cudaMalloc(&w.ulist, sizeof(int) * 2 * (size_t)nsk));
+      CK(h, cudaHostAlloc((void **)&w.h_ulist, sizeof(int) * 2 * (size_t)nsk, cudaHostAllocDefault));
+      w.kskip_cap = nsk;
+    }
     CK(h, cudaMemsetAsync(w.ktotal, 0, sizeof(unsigned) * 2 * (kMaxLevels + 1), s));
     for (int l = 1; l <= L; ++l)
       launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
-                      1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l, h->num_sms, s);
+                      1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l, l == 1 ? w.kskip : nullptr, h->num_sms, s);
     h->launches += L;
     CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(w.h_kskip, w.kskip, (size_t)nsk, cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
+    {
+      // the level-1 units with work: CConv1 (a window that is not pure solid or
+      // air) and CConv2 (a fluid cell), each with its plane chunk
+      const bool fusedc2 = vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho);
+      const int cap1 = stream_cap(bf16, false, STREAM_MODE_ZERO_PURE, fused_update(h, d1), h->num_sms);
+      const int cap2 = stream_cap(bf16, fusedc2, STREAM_MODE_FLUID_ONLY, false, h->num_sms);
+      const long long off2 = w.kskip_cap;  // the second list's place (run_network reads it there)
+      w.uzc[0] = choose_stream_units(d1, w.h_kskip, 1, cap1, w.h_ulist, &w.un[0]);
+      w.uzc[1] = choose_stream_units(d1, w.h_kskip, 2, cap2, w.h_ulist + off2, &w.un[1]);
+      if (w.un[0])
+        CK(h, cudaMemcpyAsync(w.ulist, w.h_ulist, sizeof(int) * (size_t)w.un[0], cudaMemcpyHostToDevice, s));
+      if (w.un[1])
+        CK(h, cudaMemcpyAsync(w.ulist + off2, w.h_ulist + off2, sizeof(int) * (size_t)w.un[1], cudaMemcpyHostToDevice,
+                              s));
+      w.ulist_ok = true;
+    }
     for (int l = 1; l <= L; ++l) {
       const int nblk = l < L ? 2 : 1;
       for (int t = 0; t < nblk; ++t) {
@@ -946,7 +1003,8 @@ int check_umma_err(npsolve *h) {
 int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x) {
   Workspace &w = h->ws;
   if (w.graph && w.graph_dims.nx == d1.nx && w.graph_dims.ny == d1.ny && w.graph_dims.nz == d1.nz &&
-      w.graph_lab == lab && w.graph_b == b && w.graph_x == x && !w.graph_pcg)
+      w.graph_lab == lab && w.graph_b == b && w.graph_x == x && !w.graph_pcg && w.graph_units[0] == w.un[0] &&
+      w.graph_units[1] == w.uzc[0] && w.graph_units[2] == w.un[1] && w.graph_units[3] == w.uzc[1])
     return NPSOLVE_OK;
   if (w.graph) cudaGraphExecDestroy(w.graph);
   w.graph = nullptr;
@@ -965,6 +1023,10 @@ int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x
   w.graph_b = b;
   w.graph_x = x;
   w.graph_pcg = 0;
+  w.graph_units[0] = w.un[0];
+  w.graph_units[1] = w.uzc[0];
+  w.graph_units[2] = w.un[1];
+  w.graph_units[3] = w.uzc[1];
   return NPSOLVE_OK;
 }
 
@@ -985,6 +1047,12 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     ProfScope ps(h, P_SETUP, s);
     st = setup_image(h, lab, d1, s, true);
     if (st) return st;
+    if (cached_path(h, d1) && w.ulist_ok) {
+      // the level-1 CConvs skip the units without work: what they would write there is zero
+      CK(h, cudaMemsetAsync(w.z, 0, sizeof(float) * (size_t)d1.n(), s));
+      if (h->cfg.levels > 1) CK(h, cudaMemsetAsync(w.r1[2], 0, sizeof(float) * (size_t)level_dims(d1, 2).n(), s));
+      if (fused_update(h, d1)) CK(h, cudaMemsetAsync(w.r_alt, 0, sizeof(float) * (size_t)d1.n(), s));
+    }
     if (vec4_path(d1)) {
       // the recurrence mode of the multilevel path keeps x as a double-float pair until the end
       const bool xdf = h->cfg.levels > 1 && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
