@@ -251,7 +251,7 @@ __device__ __forceinline__ void split_alpha(double a, float &ah, float &al) {
 template <bool DEFER, int NO>
 __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__restrict__ zv, float *__restrict__ dring,
                                                          float *__restrict__ xhi, float *__restrict__ xlo,
-                                                         const SolveState *st) {
+                                                         const uint32_t *__restrict__ gmask, const SolveState *st) {
   if (st->done) return;
   constexpr int NA = NO > 0 ? NO : 1;  // array extents (n_ortho is a template argument)
   const int k1 = st->k + 1, no = NO;
@@ -290,6 +290,10 @@ __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__r
     split_alpha(st->alpha_slot[ring_slot(k1, no)], oh, ol);
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += stride) {
       const int p = g << 2;
+      if (!((__ldg(gmask + (g >> 5)) >> (g & 31)) & 1u)) {  // no fluid: z, d and x are zero there
+        st4(dst + p, make_float4(0.f, 0.f, 0.f, 0.f));
+        continue;
+      }
       float4 sv[NA];
       const float4 v = ortho(p, sv);
       const float4 dold = ld4(dst + p);
@@ -306,6 +310,10 @@ __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__r
   }
   auto group = [&](int g) {
     const int p = g << 2;
+    if (!((__ldg(gmask + (g >> 5)) >> (g & 31)) & 1u)) {  // no fluid: z and the d_i are zero there
+      st4(dst + p, make_float4(0.f, 0.f, 0.f, 0.f));
+      return;
+    }
     float4 sv[NA];
     st4(dst + p, ortho(p, sv));
   };
@@ -536,6 +544,23 @@ __global__ void __launch_bounds__(kThreads) k_flush_x(int n, float *__restrict__
 }
 __global__ void k_clear_pend(SolveState *st) { st->x_upto = st->k; }
 
+// One bit per 4-cell group (bit g & 31 of word g >> 5): the group holds a
+// fluid cell.  Vectors are zero on the other groups, so the direction kernel
+// skips their loads (occupancy-aware sparsity).
+__global__ void __launch_bounds__(kThreads) k_group_mask(const uint16_t *__restrict__ code, int n4,
+                                                         uint32_t *__restrict__ gmask) {
+  const int words = (n4 + 31) >> 5;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < words * 32; g += gridDim.x * blockDim.x) {
+    bool f = false;
+    if (g < n4) {
+      const ushort4 c = *reinterpret_cast<const ushort4 *>(code + 4 * (size_t)g);
+      f = ((c.x | c.y | c.z | c.w) & 0x8000u) != 0u;
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0) gmask[g >> 5] = b;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers.
 // ---------------------------------------------------------------------------
@@ -549,13 +574,13 @@ void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *
                        cudaStream_t s) {
   k_combine1_4<<<grid4(n / 4, num_sms, resident_blocks<k_combine1_4>()), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
 }
-void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const SolveState *st,
-                       int n_ortho, int num_sms, cudaStream_t s) {
+void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const uint32_t *gmask,
+                       const SolveState *st, int n_ortho, int num_sms, cudaStream_t s) {
   switch ((defer_x ? 8 : 0) + n_ortho) {
 #define NPS_DIR_CASE(D, NO)                                                                                        \
   case (D ? 8 : 0) + NO:                                                                                           \
     k_direction4<D, NO><<<grid4(n / 4, num_sms, resident_blocks<k_direction4<D, NO>>()), kThreads, 0, s>>>(       \
-        n, z, dring, xhi, xlo, st);                                                                                \
+        n, z, dring, xhi, xlo, gmask, st);                                                                         \
     break;
     NPS_DIR_CASE(false, 0)
     NPS_DIR_CASE(false, 1)
@@ -572,10 +597,14 @@ void launch_direction4(bool defer_x, int n, const float *z, float *dring, float 
       break;
   }
 }
-void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s) {
+void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, uint32_t *gmask, cudaStream_t s) {
   long long b = (dm.n() + kThreads - 1) / kThreads;
   if (b > 148LL * 16) b = 148LL * 16;
   k_lap_codes<<<(int)(b < 1 ? 1 : b), kThreads, 0, s>>>(lab, dm, code);
+  const int n4 = (int)(dm.n() / 4);
+  long long g = ((long long)((n4 + 31) / 32) * 32 + kThreads - 1) / kThreads;
+  if (g > 148LL * 16) g = 148LL * 16;
+  k_group_mask<<<(int)(g < 1 ? 1 : g), kThreads, 0, s>>>(code, n4, gmask);
 }
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, const float *r_alt,
                  double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {

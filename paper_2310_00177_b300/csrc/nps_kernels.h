@@ -61,10 +61,11 @@ void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x
 void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
                        const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
                        cudaStream_t s);
-void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const SolveState *st,
-                       int n_ortho, int num_sms, cudaStream_t s);
+void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const uint32_t *gmask,
+                       const SolveState *st, int n_ortho, int num_sms, cudaStream_t s);
 // per-cell stencil codes of the masked Laplacian (once per solve) and q = A d with them
-void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, cudaStream_t s);
+// per-cell stencil codes and the 1-bit-per-4-cell-group fluid mask ((n / 4 + 31) / 32 words)
+void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, uint32_t *gmask, cudaStream_t s);
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, const float *r_alt,
                  double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s);
 // Adds the pending steps to (xhi, xlo) and writes x = xhi + xlo in FP64.

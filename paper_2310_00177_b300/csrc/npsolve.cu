@@ -53,6 +53,7 @@ struct Workspace {
   float *xhi = nullptr, *xlo = nullptr;  // x as a double-float pair during recurrence-mode iterations
   float *r_alt = nullptr;  // second residual buffer when the update is fused into the level-1 CConv1
   uint16_t *lapcode = nullptr;  // per-cell stencil codes of the masked Laplacian (vec4 path)
+  uint32_t *gmask = nullptr;    // one bit per 4-cell group: the group holds a fluid cell (vec4 path)
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
   ushort2 *counts[kMaxLevels + 1] = {};
@@ -233,6 +234,7 @@ void free_ws(Workspace &w) {
   cudaFree(w.xlo);
   cudaFree(w.r_alt);
   cudaFree(w.lapcode);
+  cudaFree(w.gmask);
   cudaFree(w.dring);
   cudaFree(w.qring);
   for (int l = 0; l <= kMaxLevels; ++l) {
@@ -297,6 +299,7 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     CK(h, dalloc(&w.bytes, &w.xlo, cap));
     CK(h, dalloc(&w.bytes, &w.r_alt, cap));
     CK(h, dalloc(&w.bytes, &w.lapcode, cap));
+    CK(h, dalloc(&w.bytes, &w.gmask, cap / 128 + 64));
     CK(h, dalloc(&w.bytes, &w.dring, cap * R));
     CK(h, dalloc(&w.bytes, &w.qring, cap * R));
     long long cl = cap;
@@ -654,8 +657,8 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
   }
   launch_pyramid(lab, d1, w.counts, L, s);
   if (vec4_path(d1)) {
-    launch_lap_codes(lab, d1, w.lapcode, s);
-    h->launches += 1;
+    launch_lap_codes(lab, d1, w.lapcode, w.gmask, s);
+    h->launches += 2;
   }
   for (int l = 1; l < L; ++l)
     launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
@@ -956,7 +959,7 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   if (fast) {
     {
       ProfScope ps(h, P_ORTHO_DIR, s);
-      launch_direction4(recur, (int)n, w.z, w.dring, w.xhi, w.xlo, w.st, h->cfg.n_ortho, h->num_sms, s);
+      launch_direction4(recur, (int)n, w.z, w.dring, w.xhi, w.xlo, w.gmask, w.st, h->cfg.n_ortho, h->num_sms, s);
     }
     {
       ProfScope ps(h, P_LAP, s);
