@@ -57,6 +57,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "nps_common.cuh"
 #include "nps_kernels.h"
@@ -274,7 +275,10 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
       const uint32_t wor = pm | p0 | pp;
       const bool pure = wor == 1u || wor == 2u || wor == 4u;
       const bool mixed = inside && !pure, fl = inside && wor == 2u, ai = inside && wor == 4u;
-      const bool self = inside && lab != nullptr && o0 == 2u;
+      // the cell holds fluid: level 1 its label, coarser levels a non-zero fluid count
+      const bool self = inside && (lab != nullptr ? o0 == 2u
+                                                  : (o0 == 2u || (o0 == 8u && counts[((size_t)(zs + j) * d.ny + y) *
+                                                                                       d.nx + x].x > 0)));
       const uint32_t bm = __ballot_sync(0xffffffffu, mixed), bf = __ballot_sync(0xffffffffu, fl);
       const uint32_t ba = __ballot_sync(0xffffffffu, ai), bs = __ballot_sync(0xffffffffu, self);
       if (lane == 0) {
@@ -309,7 +313,7 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
       sd[j][4 * TY + 1] = m;
       sd[j][4 * TY + 2] = (m + 3u) & ~3u;
       sd[j][4 * TY + 3] = pc;
-      if (skip) {  // bit 0: every window pure solid or pure air (a zero CConv1 output); bit 1: no fluid cell
+      if (skip) {  // bit 0: every window pure solid or pure air (a zero level-1 CConv1 output); bit 1: no fluid cell
         uint32_t anyf = 0u;
         for (int w = 0; w < TY; ++w) anyf |= sd[j][4 * w + 3];
         skip[(size_t)t * d.nz + zs + j] = (uint8_t)(((pc & 0x55u) == 0u ? 1u : 0u) | (anyf == 0u ? 2u : 0u));
@@ -1348,23 +1352,27 @@ int stream_cap(bool bf16, bool fused, int mode, bool upd, int num_sms) {
 
 int choose_stream_units(Dims d, const uint8_t *skip, int bit, int cap, int *list, int *n) {
   // the even chunk with the fewest slots per CTA over the units that have a
-  // plane without the skip bit, and those units in ascending order
+  // plane without the skip bit (per-tile prefix counts of those planes), and
+  // those units in ascending order
   const int ntiles = ((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+  std::vector<int> pre((size_t)ntiles * (d.nz + 1));
+  for (int t = 0; t < ntiles; ++t) {
+    const uint8_t *f = skip + (size_t)t * d.nz;
+    int *pt = pre.data() + (size_t)t * (d.nz + 1);
+    pt[0] = 0;
+    for (int z = 0; z < d.nz; ++z) pt[z + 1] = pt[z] + ((f[z] & bit) ? 0 : 1);
+  }
+  auto active = [&](int t, int z0, int z1) {
+    const int *pt = pre.data() + (size_t)t * (d.nz + 1);
+    return pt[std::min(z1, d.nz)] > pt[z0];
+  };
   int zc = 32;
   long long best = -1;
   for (int c = 32; c >= 2; c -= 2) {
     const int nch = (d.nz + c - 1) / c;
     long long act = 0;
     for (int ch = 0; ch < nch; ++ch)
-      for (int t = 0; t < ntiles; ++t) {
-        const uint8_t *f = skip + (size_t)t * d.nz;
-        const int z1 = std::min(d.nz, (ch + 1) * c);
-        for (int z = ch * c; z < z1; ++z)
-          if (!(f[z] & bit)) {
-            ++act;
-            break;
-          }
-      }
+      for (int t = 0; t < ntiles; ++t) act += active(t, ch * c, (ch + 1) * c) ? 1 : 0;
     const long long cost = ((act + cap - 1) / cap) * ((c + 1) / 2 + 1);
     if (best < 0 || cost < best) {
       best = cost;
@@ -1374,17 +1382,45 @@ int choose_stream_units(Dims d, const uint8_t *skip, int bit, int cap, int *list
   const int nch = (d.nz + zc - 1) / zc;
   int m = 0;
   for (int ch = 0; ch < nch; ++ch)
-    for (int t = 0; t < ntiles; ++t) {
-      const uint8_t *f = skip + (size_t)t * d.nz;
-      const int z1 = std::min(d.nz, (ch + 1) * zc);
-      for (int z = ch * zc; z < z1; ++z)
-        if (!(f[z] & bit)) {
-          list[m++] = ch * ntiles + t;
-          break;
-        }
-    }
+    for (int t = 0; t < ntiles; ++t)
+      if (active(t, ch * zc, (ch + 1) * zc)) list[m++] = ch * ntiles + t;
   *n = m;
   return zc;
+}
+
+namespace {
+// out[t][z] = any (tile, plane) within (+-rx, +-ry, +-rz) tiles and planes of
+// (t, z) lacks `bit` in skip; stored inverted (1 = none does) when `invert`.
+__global__ void k_dilate_flags(const uint8_t *__restrict__ skip, int ntx, int nty, int nz, int bit, int rx, int ry,
+                               int rz, int invert, uint8_t *__restrict__ out) {
+  const int total = ntx * nty * nz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int z = i % nz, t = i / nz, tx = t % ntx, ty = t / ntx;
+    bool any = false;
+    for (int dy = -ry; dy <= ry && !any; ++dy)
+      for (int dx = -rx; dx <= rx && !any; ++dx) {
+        const int ux = tx + dx, uy = ty + dy;
+        if (ux < 0 || uy < 0 || ux >= ntx || uy >= nty) continue;
+        const uint8_t *f = skip + (size_t)(uy * ntx + ux) * nz;
+        for (int dz = -rz; dz <= rz; ++dz) {
+          const int uz = z + dz;
+          if (uz >= 0 && uz < nz && !(f[uz] & bit)) {
+            any = true;
+            break;
+          }
+        }
+      }
+    out[i] = (uint8_t)(invert ? !any : any);
+  }
+}
+}  // namespace
+
+void launch_dilate_flags(const uint8_t *skip, Dims d, int bit, int rx, int ry, int rz, bool invert, uint8_t *out,
+                         cudaStream_t s) {
+  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY;
+  const long long total = (long long)ntx * nty * d.nz;
+  const int g = (int)std::min<long long>((total + 255) / 256, 148LL * 8);
+  k_dilate_flags<<<g < 1 ? 1 : g, 256, 0, s>>>(skip, ntx, nty, d.nz, bit, rx, ry, rz, invert ? 1 : 0, out);
 }
 
 // Planes per unit of the setup kernels at a level: up to 32 (a unit's kernel

@@ -46,7 +46,10 @@ void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const 
                       const float *vscale, int mask_input, int round_k, float *out, const SolveState *st,
                       cudaStream_t s);
 void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, cudaStream_t s);
-void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s);
+// need (optional, even coarse nx only): per (32 x 8 fine tile, fine plane) byte, tile-major;
+// the fine cells of planes marked 0 are left unwritten
+void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s,
+                   const uint8_t *need = nullptr);
 void launch_combine(long long n, const float *x1, const float *x2, const double *c12, float *out,
                     const SolveState *st, cudaStream_t s);
 void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
@@ -131,6 +134,10 @@ int stream_cap(bool bf16, bool fused, int mode, bool upd, int num_sms);  // CTAs
 // Picks the chunk for the units with a plane whose skip byte lacks `bit`,
 // writes their indices to list (ntiles x nz / 2 entries at most), returns the chunk.
 int choose_stream_units(Dims d, const uint8_t *skip, int bit, int cap, int *list, int *n);
+// out[t][z] (ntiles x nz, tile-major) = some (tile, plane) within +-rx, +-ry tiles and +-rz
+// planes of (t, z) lacks `bit` in skip; inverted (1 = none) when `invert`.
+void launch_dilate_flags(const uint8_t *skip, Dims d, int bit, int rx, int ry, int rz, bool invert, uint8_t *out,
+                         cudaStream_t s);
 // The level-1 CConv1 that first forms the pending residual step: r_{k+1} =
 // r_k - alpha q_{k+1} with r_k in rb[k mod 2] (the launch's v must be rb[0]),
 // written to rb[(k + 1) mod 2], with ||r_{k+1}||^2 and the end-of-step state

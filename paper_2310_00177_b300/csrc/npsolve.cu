@@ -71,6 +71,15 @@ struct Workspace {
   long long kskip_cap = 0;
   int un[2] = {0, 0}, uzc[2] = {0, 0};
   bool ulist_ok = false;
+  // level 1: per (tile, plane) whether the level-2 -> 1 interpolation output is read
+  uint8_t *ineed = nullptr;
+  // level 2 (not the coarsest): per (tile, plane) skip bytes, the units within
+  // two coarse cells of fluid (both level-2 CConvs), and their count and chunk
+  uint8_t *kskip2 = nullptr, *h_kskip2 = nullptr;
+  int *ulist2 = nullptr, *h_ulist2 = nullptr;
+  long long kskip2_cap = 0;
+  int un2 = 0, uzc2 = 0;
+  bool ulist2_ok = false;
   size_t part_cap = 0;        // doubles of part
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
   int hist_cap = 0;
@@ -94,7 +103,7 @@ struct Workspace {
   const float *graph_b = nullptr;
   double *graph_x = nullptr;
   int graph_pcg = 0;
-  int graph_units[4] = {0, 0, 0, 0};  // the unit counts and chunks baked into the captured launches
+  int graph_units[6] = {0, 0, 0, 0, 0, 0};  // the unit counts and chunks baked into the captured launches
   long long graph_kernels = 0;  // kernels per replay of the graph
 };
 
@@ -253,6 +262,11 @@ void free_ws(Workspace &w) {
   cudaFreeHost(w.h_kskip);
   cudaFree(w.ulist);
   cudaFreeHost(w.h_ulist);
+  cudaFree(w.ineed);
+  cudaFree(w.kskip2);
+  cudaFreeHost(w.h_kskip2);
+  cudaFree(w.ulist2);
+  cudaFreeHost(w.h_ulist2);
   cudaFree(w.part);
   cudaFree(w.affc);
   cudaFree(w.relres);
@@ -561,6 +575,9 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   const bool lists = st && cached && w.ulist_ok;
   const StreamUnits u1{w.ulist, w.un[0], w.uzc[0]}, u2{w.ulist + w.kskip_cap, w.un[1], w.uzc[1]};
   const StreamUnits *pu1 = lists ? &u1 : nullptr, *pu2 = lists ? &u2 : nullptr;
+  const StreamUnits ul2{w.ulist2, w.un2, w.uzc2};
+  const StreamUnits *pl2 = lists && w.ulist2_ok ? &ul2 : nullptr;  // level 2 (L >= 3)
+  const uint8_t *need1 = lists ? w.ineed : nullptr;                // what the level-1 CConv2 reads of r2
   // down pass: x1^l = CConv1^l(r1^l), r1^{l+1} = Pool(x1^l)
   for (int l = 1; l < L; ++l) {
     const float *in = l == 1 ? r : w.r1[l];
@@ -572,7 +589,8 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
                    nullptr, &up, pu1);
     } else if (cached) {
       cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s,
-                   l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL, nullptr, nullptr, l == 1 ? pu1 : nullptr);
+                   l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL, nullptr, nullptr,
+                   l == 1 ? pu1 : (l == 2 ? pl2 : nullptr));
     } else if (tensor_level(h, l)) {
       cconv_tc(h, lab, d1, l, 1, in, nullptr, vs, l == 1, w.x1[l], w.r1[l + 1], st, s);
     } else {
@@ -606,10 +624,11 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       {
         ProfScope ps(h, P_INTERP, s);
         h->launches += 1;
-        launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
+        launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s, l == 1 ? need1 : nullptr);
       }
       if (l > 1) {  // CConv2 and the combination in one pass
-        cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s);
+        cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s, STREAM_MODE_ALL, nullptr,
+                     nullptr, l == 2 ? pl2 : nullptr);
         continue;
       }
       if (st && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
@@ -693,19 +712,55 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       w.ulist = nullptr;
       w.h_ulist = nullptr;
       w.kskip_cap = 0;
+      cudaFree(w.ineed);
+      w.ineed = nullptr;
       CK(h, cudaMalloc(&w.kskip, (size_t)nsk));
       CK(h, cudaHostAlloc((void **)&w.h_kskip, (size_t)nsk, cudaHostAllocDefault));
       CK(h, cudaMalloc(&w.ulist, sizeof(int) * 2 * (size_t)nsk));
       CK(h, cudaHostAlloc((void **)&w.h_ulist, sizeof(int) * 2 * (size_t)nsk, cudaHostAllocDefault));
+      CK(h, cudaMalloc(&w.ineed, (size_t)nsk));
       w.kskip_cap = nsk;
+    }
+    const bool lv2 = L >= 3;  // level 2 has a CConv1 and a CConv2
+    const long long nsk2 = lv2 ? stream_desc_count(level_dims(d1, 2)) : 0;
+    if (nsk2 > w.kskip2_cap) {
+      if (w.graph) cudaGraphExecDestroy(w.graph);
+      w.graph = nullptr;
+      CK(h, cudaStreamSynchronize(s));
+      cudaFree(w.kskip2);
+      cudaFreeHost(w.h_kskip2);
+      cudaFree(w.ulist2);
+      cudaFreeHost(w.h_ulist2);
+      w.kskip2 = nullptr;
+      w.h_kskip2 = nullptr;
+      w.ulist2 = nullptr;
+      w.h_ulist2 = nullptr;
+      w.kskip2_cap = 0;
+      CK(h, cudaMalloc(&w.kskip2, 2 * (size_t)nsk2));
+      CK(h, cudaHostAlloc((void **)&w.h_kskip2, (size_t)nsk2, cudaHostAllocDefault));
+      CK(h, cudaMalloc(&w.ulist2, sizeof(int) * (size_t)nsk2));
+      CK(h, cudaHostAlloc((void **)&w.h_ulist2, sizeof(int) * (size_t)nsk2, cudaHostAllocDefault));
+      w.kskip2_cap = nsk2;
     }
     CK(h, cudaMemsetAsync(w.ktotal, 0, sizeof(unsigned) * 2 * (kMaxLevels + 1), s));
     for (int l = 1; l <= L; ++l)
       launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
-                      1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l, l == 1 ? w.kskip : nullptr, h->num_sms, s);
+                      1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l,
+                      l == 1 ? w.kskip : (l == 2 && lv2 ? w.kskip2 : nullptr), h->num_sms, s);
     h->launches += L;
     CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
     CK(h, cudaMemcpyAsync(w.h_kskip, w.kskip, (size_t)nsk, cudaMemcpyDeviceToHost, s));
+    // what the level-1 CConv2 reads of the level-2 -> 1 interpolation: its units' (tile, plane) pairs (with
+    // fluid) and their one-cell halo, taken as the neighbouring tiles and planes
+    launch_dilate_flags(w.kskip, d1, 2, 1, 1, 1, false, w.ineed, s);
+    h->launches += 1;
+    if (lv2) {
+      // level 2: the units within two coarse cells (one tile across, two planes along z) of a cell with
+      // fluid; elsewhere both level-2 CConv outputs are zero or never read (1 = may be skipped)
+      launch_dilate_flags(w.kskip2, level_dims(d1, 2), 2, 1, 1, 2, true, w.kskip2 + nsk2, s);
+      h->launches += 1;
+      CK(h, cudaMemcpyAsync(w.h_kskip2, w.kskip2 + nsk2, (size_t)nsk2, cudaMemcpyDeviceToHost, s));
+    }
     CK(h, cudaStreamSynchronize(s));
     {
       // the level-1 units with work: CConv1 (a window that is not pure solid or
@@ -722,6 +777,14 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
         CK(h, cudaMemcpyAsync(w.ulist + off2, w.h_ulist + off2, sizeof(int) * (size_t)w.un[1], cudaMemcpyHostToDevice,
                               s));
       w.ulist_ok = true;
+      w.ulist2_ok = false;
+      if (lv2) {
+        const Dims d2 = level_dims(d1, 2);
+        const int cap2l = stream_cap(bf16, false, STREAM_MODE_ALL, false, h->num_sms);
+        w.uzc2 = choose_stream_units(d2, w.h_kskip2, 1, cap2l, w.h_ulist2, &w.un2);
+        if (w.un2) CK(h, cudaMemcpyAsync(w.ulist2, w.h_ulist2, sizeof(int) * (size_t)w.un2, cudaMemcpyHostToDevice, s));
+        w.ulist2_ok = true;
+      }
     }
     for (int l = 1; l <= L; ++l) {
       const int nblk = l < L ? 2 : 1;
@@ -1007,7 +1070,8 @@ int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x
   Workspace &w = h->ws;
   if (w.graph && w.graph_dims.nx == d1.nx && w.graph_dims.ny == d1.ny && w.graph_dims.nz == d1.nz &&
       w.graph_lab == lab && w.graph_b == b && w.graph_x == x && !w.graph_pcg && w.graph_units[0] == w.un[0] &&
-      w.graph_units[1] == w.uzc[0] && w.graph_units[2] == w.un[1] && w.graph_units[3] == w.uzc[1])
+      w.graph_units[1] == w.uzc[0] && w.graph_units[2] == w.un[1] && w.graph_units[3] == w.uzc[1] &&
+      w.graph_units[4] == w.un2 && w.graph_units[5] == w.uzc2)
     return NPSOLVE_OK;
   if (w.graph) cudaGraphExecDestroy(w.graph);
   w.graph = nullptr;
@@ -1030,6 +1094,8 @@ int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x
   w.graph_units[1] = w.uzc[0];
   w.graph_units[2] = w.un[1];
   w.graph_units[3] = w.uzc[1];
+  w.graph_units[4] = w.un2;
+  w.graph_units[5] = w.uzc2;
   return NPSOLVE_OK;
 }
 
@@ -1055,6 +1121,12 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       CK(h, cudaMemsetAsync(w.z, 0, sizeof(float) * (size_t)d1.n(), s));
       if (h->cfg.levels > 1) CK(h, cudaMemsetAsync(w.r1[2], 0, sizeof(float) * (size_t)level_dims(d1, 2).n(), s));
       if (fused_update(h, d1)) CK(h, cudaMemsetAsync(w.r_alt, 0, sizeof(float) * (size_t)d1.n(), s));
+      if (w.ulist2_ok) {  // the level-2 units without work: their outputs and pooled inputs of level 3 are zero
+        const size_t n2 = (size_t)level_dims(d1, 2).n();
+        CK(h, cudaMemsetAsync(w.x1[2], 0, sizeof(float) * n2, s));
+        CK(h, cudaMemsetAsync(w.xc[2], 0, sizeof(float) * n2, s));
+        CK(h, cudaMemsetAsync(w.r1[3], 0, sizeof(float) * (size_t)level_dims(d1, 3).n(), s));
+      }
     }
     if (vec4_path(d1)) {
       // the recurrence mode of the multilevel path keeps x as a double-float pair until the end
