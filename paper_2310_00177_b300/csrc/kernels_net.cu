@@ -290,10 +290,10 @@ __global__ void k_interp(const float *__restrict__ in, Dims coarse, float *__res
 __device__ __forceinline__ float lerp_lo(float a, float b) { return 0.25f * a + 0.75f * b; }  // fine 2j from c[j-1], c[j]
 __device__ __forceinline__ float lerp_hi(float b, float c) { return 0.75f * b + 0.25f * c; }  // fine 2j+1 from c[j], c[j+1]
 
-// need (optional): one byte per (32 x 8 fine tile, fine plane), tile-major;
-// blocks whose two planes are both marked 0 are not written (no later read).
+// skip (optional): one byte per (32 x 8 fine tile, fine plane), tile-major;
+// blocks whose two planes are both marked non-zero are not written (no later read).
 __global__ void __launch_bounds__(256) k_interp_blk(const float *__restrict__ in, Dims coarse, float *__restrict__ out,
-                                                    const uint8_t *__restrict__ need, const SolveState *st) {
+                                                    const uint8_t *__restrict__ skip, const SolveState *st) {
   if (st && st->done) return;
   const int cx = coarse.nx, cy = coarse.ny, cz = coarse.nz;
   const int fx = 2 * cx, fy = 2 * cy;
@@ -305,10 +305,10 @@ __global__ void __launch_bounds__(256) k_interp_blk(const float *__restrict__ in
     const int q = (int)(t % (unsigned)nq);
     const unsigned r = t / (unsigned)nq;
     const int jy = (int)(r % (unsigned)cy), kz = (int)(r / (unsigned)cy);  // fine rows 2jy, 2jy+1; planes 2kz, 2kz+1
-    if (need) {
+    if (skip) {
       const int fz = 2 * cz;
       const size_t nt = (size_t)((4 * q) / 32) + (size_t)((2 * jy) / 8) * (size_t)((fx + 31) / 32);
-      if (!need[nt * fz + 2 * kz] && !need[nt * fz + 2 * kz + 1]) continue;
+      if (skip[nt * fz + 2 * kz] && skip[nt * fz + 2 * kz + 1]) continue;
     }
     const int xm = max(2 * q - 1, 0), x0 = 2 * q, x1 = 2 * q + 1, xp = min(2 * q + 2, cx - 1);
     const int ym = max(jy - 1, 0), yp = min(jy + 1, cy - 1);
@@ -436,10 +436,10 @@ void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, c
 }
 
 void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s,
-                   const uint8_t *need) {
+                   const uint8_t *skip) {
   if (coarse.nx % 2 == 0) {  // fine rows of a multiple of 4 cells: 16-byte stores
     k_interp_blk<<<grid_for((long long)(coarse.nx / 2) * coarse.ny * coarse.nz, 256), 256, 0, s>>>(in, coarse, out,
-                                                                                                    need, st);
+                                                                                                    skip, st);
     return;
   }
   k_interp<<<grid_for(coarse.n() * 8, 256), 256, 0, s>>>(in, coarse, out, st);

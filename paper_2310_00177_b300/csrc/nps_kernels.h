@@ -46,10 +46,10 @@ void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const 
                       const float *vscale, int mask_input, int round_k, float *out, const SolveState *st,
                       cudaStream_t s);
 void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, cudaStream_t s);
-// need (optional, even coarse nx only): per (32 x 8 fine tile, fine plane) byte, tile-major;
-// the fine cells of planes marked 0 are left unwritten
+// skip (optional, even coarse nx only): per (32 x 8 fine tile, fine plane) byte, tile-major;
+// the fine cells of planes marked non-zero are left unwritten
 void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s,
-                   const uint8_t *need = nullptr);
+                   const uint8_t *skip = nullptr);
 void launch_combine(long long n, const float *x1, const float *x2, const double *c12, float *out,
                     const SolveState *st, cudaStream_t s);
 void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,

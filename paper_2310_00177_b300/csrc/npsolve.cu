@@ -64,14 +64,15 @@ struct Workspace {
   size_t kcap[(kMaxLevels + 1) * 2] = {};    // cache entries kcache can hold
   // per level: [2 l] cache entries (blocks padded to 4), [2 l + 1] mixed cells
   unsigned *ktotal = nullptr, *h_ktotal = nullptr;
-  // level-1 occupancy-aware sparsity: per (tile, plane) skip bytes and the
-  // units of the level-1 CConv1 ([0, kskip_cap)) and CConv2 ([kskip_cap, 2 kskip_cap)) that have work
+  // level-1 occupancy-aware sparsity: per (tile, plane) skip bytes (host copy: the dilated flags, then the
+  // classification's) and the units of the level-1 CConv1 ([0, kskip_cap)) and CConv2 ([kskip_cap, 2 kskip_cap))
   uint8_t *kskip = nullptr, *h_kskip = nullptr;
   int *ulist = nullptr, *h_ulist = nullptr;
   long long kskip_cap = 0;
   int un[2] = {0, 0}, uzc[2] = {0, 0};
   bool ulist_ok = false;
-  // level 1: per (tile, plane) whether the level-2 -> 1 interpolation output is read
+  // level 1: per (tile, plane) 1 = no fluid within one tile or plane (the CConv1 output is zero and the
+  // level-2 -> 1 interpolation output is not read there)
   uint8_t *ineed = nullptr;
   // level 2 (not the coarsest): per (tile, plane) skip bytes, the units within
   // two coarse cells of fluid (both level-2 CConvs), and their count and chunk
@@ -577,7 +578,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   const StreamUnits *pu1 = lists ? &u1 : nullptr, *pu2 = lists ? &u2 : nullptr;
   const StreamUnits ul2{w.ulist2, w.un2, w.uzc2};
   const StreamUnits *pl2 = lists && w.ulist2_ok ? &ul2 : nullptr;  // level 2 (L >= 3)
-  const uint8_t *need1 = lists ? w.ineed : nullptr;                // what the level-1 CConv2 reads of r2
+  const uint8_t *skip1 = lists ? w.ineed : nullptr;                // what the level-1 CConv2 does not read of r2
   // down pass: x1^l = CConv1^l(r1^l), r1^{l+1} = Pool(x1^l)
   for (int l = 1; l < L; ++l) {
     const float *in = l == 1 ? r : w.r1[l];
@@ -624,7 +625,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       {
         ProfScope ps(h, P_INTERP, s);
         h->launches += 1;
-        launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s, l == 1 ? need1 : nullptr);
+        launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s, l == 1 ? skip1 : nullptr);
       }
       if (l > 1) {  // CConv2 and the combination in one pass
         cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.xc[l], nullptr, w.x1[l], c12, st, s, STREAM_MODE_ALL, nullptr,
@@ -715,7 +716,7 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       cudaFree(w.ineed);
       w.ineed = nullptr;
       CK(h, cudaMalloc(&w.kskip, (size_t)nsk));
-      CK(h, cudaHostAlloc((void **)&w.h_kskip, (size_t)nsk, cudaHostAllocDefault));
+      CK(h, cudaHostAlloc((void **)&w.h_kskip, 2 * (size_t)nsk, cudaHostAllocDefault));
       CK(h, cudaMalloc(&w.ulist, sizeof(int) * 2 * (size_t)nsk));
       CK(h, cudaHostAlloc((void **)&w.h_ulist, sizeof(int) * 2 * (size_t)nsk, cudaHostAllocDefault));
       CK(h, cudaMalloc(&w.ineed, (size_t)nsk));
@@ -749,11 +750,13 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
                       l == 1 ? w.kskip : (l == 2 && lv2 ? w.kskip2 : nullptr), h->num_sms, s);
     h->launches += L;
     CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
-    CK(h, cudaMemcpyAsync(w.h_kskip, w.kskip, (size_t)nsk, cudaMemcpyDeviceToHost, s));
-    // what the level-1 CConv2 reads of the level-2 -> 1 interpolation: its units' (tile, plane) pairs (with
-    // fluid) and their one-cell halo, taken as the neighbouring tiles and planes
-    launch_dilate_flags(w.kskip, d1, 2, 1, 1, 1, false, w.ineed, s);
+    CK(h, cudaMemcpyAsync(w.h_kskip + nsk, w.kskip, (size_t)nsk, cudaMemcpyDeviceToHost, s));
+    // level-1 (tile, plane) pairs with no fluid within one tile or plane (1 = skip): the level-1 CConv1
+    // output is exactly zero there (a window without fluid sees a zero input), and the level-1 CConv2 reads
+    // nothing of the level-2 -> 1 interpolation there (its units hold fluid; their halo is one cell)
+    launch_dilate_flags(w.kskip, d1, 2, 1, 1, 1, true, w.ineed, s);
     h->launches += 1;
+    CK(h, cudaMemcpyAsync(w.h_kskip, w.ineed, (size_t)nsk, cudaMemcpyDeviceToHost, s));
     if (lv2) {
       // level 2: the units within two coarse cells (one tile across, two planes along z) of a cell with
       // fluid; elsewhere both level-2 CConv outputs are zero or never read (1 = may be skipped)
@@ -770,7 +773,7 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       const int cap2 = stream_cap(bf16, fusedc2, STREAM_MODE_FLUID_ONLY, false, h->num_sms);
       const long long off2 = w.kskip_cap;  // the second list's place (run_network reads it there)
       w.uzc[0] = choose_stream_units(d1, w.h_kskip, 1, cap1, w.h_ulist, &w.un[0]);
-      w.uzc[1] = choose_stream_units(d1, w.h_kskip, 2, cap2, w.h_ulist + off2, &w.un[1]);
+      w.uzc[1] = choose_stream_units(d1, w.h_kskip + nsk, 2, cap2, w.h_ulist + off2, &w.un[1]);
       if (w.un[0])
         CK(h, cudaMemcpyAsync(w.ulist, w.h_ulist, sizeof(int) * (size_t)w.un[0], cudaMemcpyHostToDevice, s));
       if (w.un[1])
