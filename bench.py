@@ -17,8 +17,9 @@ Also reported on the same line:
   roofline       the dominant kernel class of a profiled solve (CUDA events
                  around each launch on the solve's stream) against the
                  measured peaks in MEASURED_PEAKS.json
-  roofline_stencil_vector  the same for the Laplacian, update and direction
-                 kernels (algorithmic bytes per launch / launch time)
+  roofline_stencil_vector  the same for the Laplacian and direction kernels
+                 (algorithmic bytes per launch / launch time; the residual
+                 update is formed inside the level-1 CConv1)
   served         p50 / p99 latency and solves per second of the serving
                  workload: 512 requests, Poisson arrivals at 200/s, sizes
                  64^3, 128^3, 192^3, 256^3, frames of evolving scenes, HBM
@@ -58,7 +59,7 @@ ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
 # CConv1 and CConv2 launches of one iteration, the summary kept in profiles/);
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_L1 = None
+TRAFFIC_L1 = (209.8e6 + 214.2e6) / 2  # ncu: level-1 CConv1 (with the residual step) and the fused CConv2
 
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
 # (inputs read once, outputs written once).
@@ -320,24 +321,28 @@ def main():
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms / max(dom_launches, 1) / 1e3
+    # 4-cell x-groups with a fluid cell: the vector kernels skip the loads of the others
+    fg = float((lab.reshape(lab.shape[0], lab.shape[1], -1, 4) == 1).any(-1).mean())
     if dom == "cconv_l1":
-        # the level-1 CConv launches (TMA-streamed z-march) per cell: the input
-        # (4 B), the plane descriptors (160 B per 256 cells), the cached kernels
-        # of the mixed-window cells (56 B BF16 each), the output (4 B); CConv1
-        # adds the pooled output (0.5 B) and the residual step it forms first
-        # (q read 4 B, r_{k+1} written 4 B); the CConv2 fused with the level-1
-        # combination adds x1 (4 B) and the two previous q (8 B).  Averaged over
-        # the two launches of an iteration.
-        mixed = sol.mixed_cells(1)
-        frac = mixed / n if mixed >= 0 else 0.0
-        common = 4 + 160 / 256 + 56.0 * frac + 4
-        bpc = ((common + 0.5 + 8) + (common + 4 + 8)) / 2
-        achieved = bpc * n / avg_s / 1e9
+        # the level-1 CConv launches (TMA-streamed z-march) over the units they
+        # process (occupancy-aware sparsity), per processed cell: the input
+        # (4 B), the plane descriptors (160 B per 256 cells), the output (4 B);
+        # CConv1 adds the pooled output (0.5 B) and the residual step it forms
+        # first (q read 4 B, r_{k+1} written 4 B); the CConv2 fused with the
+        # level-1 combination adds x1 (4 B) and the two previous q (8 B); plus
+        # 56 B (BF16) per mixed-window cell of the processed units.  Both
+        # launches of an iteration over their average time.
+        c1, m1 = sol.level1_work(0)
+        c2, m2 = sol.level1_work(1)
+        b1 = c1 * (4 + 160 / 256 + 4 + 0.5 + 8) + 56.0 * m1
+        b2 = c2 * (4 + 160 / 256 + 4 + 4 + 8) + 56.0 * m2
+        achieved = (b1 + b2) / 2 / avg_s / 1e9
         peak = pk["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1 with the residual step; CConv2 fused with the "
-                "combination and orthogonalisation dots)",
-                "algorithmic": f"{bpc:.2f} B/cell x {n} cells (mixed-window fraction {frac:.4f})",
+                "traffic": TRAFFIC_L1, "kernel": "k_cconv_stream<bf16> (level-1 CConv1 with the residual step; CConv2 "
+                "fused with the combination and orthogonalisation dots)",
+                "algorithmic": f"CConv1 {b1 / 1e6:.1f} MB ({c1} cells processed, {m1} mixed), CConv2 {b2 / 1e6:.1f} MB "
+                               f"({c2} cells, {m2} mixed) of the {n}-cell grid",
                 "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"] + " (hbm_gbs)"}
     else:
         bpc = BYTES_PER_CELL.get(dom, 0.0)
@@ -347,14 +352,19 @@ def main():
                 "traffic": None, "kernel": dom, "algorithmic": f"{bpc} B/cell x {n} cells",
                 "avg_launch_us": avg_s * 1e6, "peak_src": pk["src"]}
     # the stencil and vector kernels against the same HBM peak (algorithmic bytes
-    # per launch / average launch time of the profiled solve)
+    # per launch / average launch time of the profiled solve); groups without
+    # fluid: the Laplacian reads the codes and writes q = 0 (6 B per cell), the
+    # direction writes d = 0 (4 B per cell)
+    vec_bytes = {"lap_alpha": fg * BYTES_PER_CELL["lap_alpha"] + (1 - fg) * 6,
+                 "ortho_dir": fg * BYTES_PER_CELL["ortho_dir"] + (1 - fg) * 4}
     vec_roof = {}
-    for cls in ("lap_alpha", "update", "ortho_dir"):
+    for cls, bpc_v in vec_bytes.items():
         if cls in prof and prof[cls][1]:
             t = prof[cls][0] / prof[cls][1] / 1e3
-            ach = BYTES_PER_CELL[cls] * n / t / 1e9
+            ach = bpc_v * n / t / 1e9
             vec_roof[cls] = {"achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                             "bytes_per_cell": BYTES_PER_CELL[cls], "avg_launch_us": t * 1e6}
+                             "bytes_per_cell": round(bpc_v, 3), "fluid_group_fraction": round(fg, 4),
+                             "avg_launch_us": t * 1e6}
     total_prof = sum(v[0] for v in prof.values())
     breakdown = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total_prof, 4)}
                  for k, v in prof.items() if v[1]}

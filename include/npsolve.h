@@ -283,6 +283,13 @@ size_t npsolve_workspace_bytes(npsolve_t h);
  * setup of the cached path (their kernels are generated and cached; all other
  * cells use the closed form of a uniform window); -1 when not available. */
 long long npsolve_mixed_cells(npsolve_t h, int level);
+/* Work of the level-1 CConvs in the last solve setup (occupancy-aware
+ * sparsity: only the units of 32 x 8 cells x a chunk of planes that have work
+ * are processed): which = 0 the CConv1 (cells with fluid within one tile or
+ * plane), 1 the CConv2 (units holding fluid).  *cells = level-1 cells of the
+ * processed units, *mixed = their mixed-window cells (whose cached kernels are
+ * read).  Returns NPSOLVE_BAD_ARG before the first solve on the cached path. */
+int npsolve_level1_work(npsolve_t h, int which, long long *cells, long long *mixed);
 const char *npsolve_profile_name(int cls);
 int npsolve_set_profiling(npsolve_t h, int on);
 int npsolve_get_profile(npsolve_t h, double *ms_host, long long *launches_host);

@@ -75,6 +75,7 @@ SIGNATURES = {
     "npsolve_profile_count": ([], _i),
     "npsolve_launch_count": ([_vp], ctypes.c_longlong),
     "npsolve_mixed_cells": ([_vp, _i], ctypes.c_longlong),
+    "npsolve_level1_work": ([_vp, _i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], _i),
     "npsolve_profile_name": ([_i], ctypes.c_char_p),
     "npsolve_set_profiling": ([_vp, _i], _i),
     "npsolve_get_profile": ([_vp, _vp, _vp], _i),
@@ -208,6 +209,13 @@ class Solver:
     def mixed_cells(self, level):
         """Cells of `level` with a non-uniform image window in the last setup (-1 if unknown)."""
         return int(load_library().npsolve_mixed_cells(self._h, level))
+
+    def level1_work(self, which):
+        """(cells, mixed cells) of the units the level-1 CConv1 (which=0) or
+        CConv2 (which=1) processed in the last solve (occupancy-aware sparsity)."""
+        c, m = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        _check(load_library().npsolve_level1_work(self._h, int(which), ctypes.byref(c), ctypes.byref(m)), self._h)
+        return c.value, m.value
 
     def launch_count(self):
         """Kernels enqueued by this handle since creation."""

@@ -234,7 +234,8 @@ __device__ __forceinline__ uint32_t class_bit(const uint8_t *lab, const ushort2 
 
 __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
                                                  Dims d, uint32_t full, int zcc, PlaneDesc *__restrict__ desc,
-                                                 unsigned *__restrict__ totals, uint8_t *__restrict__ skip) {
+                                                 unsigned *__restrict__ totals, uint8_t *__restrict__ skip,
+                                                 uint16_t *__restrict__ mcount) {
   __shared__ uint32_t sd[ZCG][DWORDS];
   __shared__ uint8_t rows[2][TY + 2][TX];  // x-ORed class bits of rows y0-1 .. y0+8 of one plane, two buffers
   __shared__ uint32_t sbase;
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
         for (int w = 0; w < TY; ++w) anyf |= sd[j][4 * w + 3];
         skip[(size_t)t * d.nz + zs + j] = (uint8_t)(((pc & 0x55u) == 0u ? 1u : 0u) | (anyf == 0u ? 2u : 0u));
       }
+      if (mcount) mcount[(size_t)t * d.nz + zs + j] = (uint16_t)m;  // mixed cells of the (tile, plane)
       sd[j][4 * TY + 4] = rb[0];
       sd[j][4 * TY + 5] = rb[1];
       sd[j][4 * TY + 6] = 0u;
@@ -438,8 +440,8 @@ __global__ void __launch_bounds__(NT) k_generate(const uint8_t *__restrict__ lab
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t image_code_bf16(const uint8_t *lab, const ushort2 *counts, const Dims &d, int x,
                                                     int y, int z) {
-  if (x < 0 || y < 0 || z < 0 || x >= d.nx || y >= d.ny || z >= d.nz) return 0u;
-  const long long p = ((long long)z * d.ny + y) * d.nx + x;
+  if ((unsigned)x >= (unsigned)d.nx || (unsigned)y >= (unsigned)d.ny || (unsigned)z >= (unsigned)d.nz) return 0u;
+  const uint32_t p = ((uint32_t)z * (uint32_t)d.ny + (uint32_t)y) * (uint32_t)d.nx + (uint32_t)x;  // n < 2^31
   if (lab) {
     const uint8_t l = __ldg(lab + p);
     return l == kFluid ? 0x00003F80u : (l == kAir ? 0x3F800000u : 0u);
@@ -1388,6 +1390,22 @@ int choose_stream_units(Dims d, const uint8_t *skip, int bit, int cap, int *list
   return zc;
 }
 
+void stream_units_work(Dims d, const int *list, int n, int zc, const uint16_t *mcount, long long *cells,
+                       long long *mixed) {
+  const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, ntiles = ntx * nty;
+  long long c = 0, m = 0;
+  for (int i = 0; i < n; ++i) {
+    const int t = list[i] % ntiles, ch = list[i] / ntiles;
+    const int w = std::min(TX, d.nx - (t % ntx) * TX), hgt = std::min(TY, d.ny - (t / ntx) * TY);
+    const int z0 = ch * zc, z1 = std::min(d.nz, z0 + zc);
+    c += (long long)w * hgt * (z1 - z0);
+    if (mcount)
+      for (int z = z0; z < z1; ++z) m += mcount[(size_t)t * d.nz + z];
+  }
+  *cells = c;
+  *mixed = m;
+}
+
 namespace {
 // out[t][z] = any (tile, plane) within (+-rx, +-ry, +-rz) tiles and planes of
 // (t, z) lacks `bit` in skip; stored inverted (1 = none does) when `invert`.
@@ -1434,11 +1452,11 @@ static int setup_chunk(Dims d, int num_sms) {
 }
 
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
-                     uint8_t *skip, int num_sms, cudaStream_t s) {
+                     uint8_t *skip, uint16_t *mcount, int num_sms, cudaStream_t s) {
   const int zc = setup_chunk(d, num_sms);
   const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
   k_classify<<<grid_for_units(units, num_sms * 8), NT, 0, s>>>(lab, counts, d, full, zc, (PlaneDesc *)desc, totals,
-                                                                 skip);
+                                                                 skip, mcount);
 }
 
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,

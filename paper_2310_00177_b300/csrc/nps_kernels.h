@@ -94,8 +94,12 @@ int cached_entry_bytes(bool bf16);     // bytes of one cached kernel
 // totals[0] += cache entries (blocks padded to 4), totals[1] += mixed cells
 // skip (optional, ntiles x nz bytes, tile-major): bit 0 = every window of the
 // tile's plane is pure solid or pure air, bit 1 = the plane has no fluid cell.
+// mcount (optional, same layout): the mixed-window cells of each (tile, plane).
 void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t full, void *desc, unsigned *totals,
-                     uint8_t *skip, int num_sms, cudaStream_t s);
+                     uint8_t *skip, uint16_t *mcount, int num_sms, cudaStream_t s);
+// Cells and mixed-window cells (from mcount, host) of the units of a list (host).
+void stream_units_work(Dims d, const int *list, int n, int zc, const uint16_t *mcount, long long *cells,
+                       long long *mixed);
 // wsplit0/1: the tensor-core weight splits of the two blocks (nsplit BF16
 // terms each) to generate on the tensor cores, or null for CUDA cores
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,

@@ -67,6 +67,8 @@ struct Workspace {
   // level-1 occupancy-aware sparsity: per (tile, plane) skip bytes (host copy: the dilated flags, then the
   // classification's) and the units of the level-1 CConv1 ([0, kskip_cap)) and CConv2 ([kskip_cap, 2 kskip_cap))
   uint8_t *kskip = nullptr, *h_kskip = nullptr;
+  uint16_t *kmcount = nullptr, *h_kmcount = nullptr;  // mixed cells per level-1 (tile, plane)
+  long long uwork[2][2] = {{0, 0}, {0, 0}};           // cells and mixed cells of the two level-1 lists
   int *ulist = nullptr, *h_ulist = nullptr;
   long long kskip_cap = 0;
   int un[2] = {0, 0}, uzc[2] = {0, 0};
@@ -261,6 +263,8 @@ void free_ws(Workspace &w) {
   cudaFreeHost(w.h_ktotal);
   cudaFree(w.kskip);
   cudaFreeHost(w.h_kskip);
+  cudaFree(w.kmcount);
+  cudaFreeHost(w.h_kmcount);
   cudaFree(w.ulist);
   cudaFreeHost(w.h_ulist);
   cudaFree(w.ineed);
@@ -715,6 +719,12 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       w.kskip_cap = 0;
       cudaFree(w.ineed);
       w.ineed = nullptr;
+      cudaFree(w.kmcount);
+      cudaFreeHost(w.h_kmcount);
+      w.kmcount = nullptr;
+      w.h_kmcount = nullptr;
+      CK(h, cudaMalloc(&w.kmcount, sizeof(uint16_t) * (size_t)nsk));
+      CK(h, cudaHostAlloc((void **)&w.h_kmcount, sizeof(uint16_t) * (size_t)nsk, cudaHostAllocDefault));
       CK(h, cudaMalloc(&w.kskip, (size_t)nsk));
       CK(h, cudaHostAlloc((void **)&w.h_kskip, 2 * (size_t)nsk, cudaHostAllocDefault));
       CK(h, cudaMalloc(&w.ulist, sizeof(int) * 2 * (size_t)nsk));
@@ -747,10 +757,12 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
     for (int l = 1; l <= L; ++l)
       launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
                       1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l,
-                      l == 1 ? w.kskip : (l == 2 && lv2 ? w.kskip2 : nullptr), h->num_sms, s);
+                      l == 1 ? w.kskip : (l == 2 && lv2 ? w.kskip2 : nullptr), l == 1 ? w.kmcount : nullptr,
+                      h->num_sms, s);
     h->launches += L;
     CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
     CK(h, cudaMemcpyAsync(w.h_kskip + nsk, w.kskip, (size_t)nsk, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(w.h_kmcount, w.kmcount, sizeof(uint16_t) * (size_t)nsk, cudaMemcpyDeviceToHost, s));
     // level-1 (tile, plane) pairs with no fluid within one tile or plane (1 = skip): the level-1 CConv1
     // output is exactly zero there (a window without fluid sees a zero input), and the level-1 CConv2 reads
     // nothing of the level-2 -> 1 interpolation there (its units hold fluid; their halo is one cell)
@@ -780,6 +792,9 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
         CK(h, cudaMemcpyAsync(w.ulist + off2, w.h_ulist + off2, sizeof(int) * (size_t)w.un[1], cudaMemcpyHostToDevice,
                               s));
       w.ulist_ok = true;
+      for (int i = 0; i < 2; ++i)
+        stream_units_work(d1, w.h_ulist + (i ? off2 : 0), w.un[i], w.uzc[i], w.h_kmcount, &w.uwork[i][0],
+                          &w.uwork[i][1]);
       w.ulist2_ok = false;
       if (lv2) {
         const Dims d2 = level_dims(d1, 2);
@@ -1525,6 +1540,14 @@ size_t npsolve_workspace_bytes(npsolve_t h) { return h ? h->ws.bytes : 0; }
 long long npsolve_mixed_cells(npsolve_t h, int level) {
   if (!h || level < 1 || level > h->cfg.levels || !h->ws.h_ktotal || !cached_path(h, h->ws.dims)) return -1;
   return (long long)h->ws.h_ktotal[2 * level + 1];
+}
+
+int npsolve_level1_work(npsolve_t h, int which, long long *cells, long long *mixed) {
+  if (!h || !cells || !mixed || which < 0 || which > 1) return fail(h, NPSOLVE_BAD_ARG, "bad argument");
+  if (!h->ws.ulist_ok) return fail(h, NPSOLVE_BAD_ARG, "no level-1 unit lists (no cached-path solve yet)");
+  *cells = h->ws.uwork[which][0];
+  *mixed = h->ws.uwork[which][1];
+  return NPSOLVE_OK;
 }
 
 int npsolve_profile_count(void) { return P_COUNT; }
