@@ -359,10 +359,11 @@ __global__ void __launch_bounds__(kThreads) k_lap_codes(const uint8_t *__restric
 // neighbours n of (d_p - d_n), plus d_p per air neighbour, 0 off fluid) with
 // the dot products d.q and r.d; the last block computes the line search
 // alpha = r^T d / d^T A d and flags breakdown (d^T A d <= 0 or non-finite).
-__global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ code, Dims dm,
-                                                   const float *__restrict__ dring, float *__restrict__ qring,
-                                                   const float *__restrict__ r0, const float *__restrict__ r1,
-                                                   double *__restrict__ part, unsigned *ticket, SolveState *st) {
+__global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ code, Dims dm, FastDiv dnx,
+                                                   FastDiv dny, const float *__restrict__ dring,
+                                                   float *__restrict__ qring, const float *__restrict__ r0,
+                                                   const float *__restrict__ r1, double *__restrict__ part,
+                                                   unsigned *ticket, SolveState *st) {
   if (st->done) return;
   const float *__restrict__ r = (r1 && (st->k & 1)) ? r1 : r0;  // r_k (two buffers: r_k in buffer k mod 2)
   const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
@@ -380,9 +381,10 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
       st4(q + p, zero4);
       return;
     }
-    const int x0 = p % nx;
-    const int yz = p / nx;
-    const int y = yz % ny, z = yz / ny;
+    const int yz = (int)fdiv(dnx, (uint32_t)p);  // p / nx, (p / nx) / ny without the divide sequence
+    const int x0 = p - yz * nx;
+    const int z = (int)fdiv(dny, (uint32_t)yz);
+    const int y = yz - z * ny;
     const float4 dc = ld4(d + p);
     const float dxl = x0 > 0 ? d[p - 1] : 0.f;
     const float dxr = x0 + 4 < nx ? d[p + 4] : 0.f;
@@ -608,7 +610,8 @@ void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, uint32_t *gma
 }
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, const float *r_alt,
                  double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
-  k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(code, dm, dring, qring, r, r_alt, part, ticket, st);
+  k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(
+      code, dm, make_fastdiv((uint32_t)dm.nx), make_fastdiv((uint32_t)dm.ny), dring, qring, r, r_alt, part, ticket, st);
 }
 void launch_flush_x(int n, float *xhi, float *xlo, double *x, const float *dring, SolveState *st, int num_sms,
                     cudaStream_t s) {

@@ -14,6 +14,29 @@
 
 namespace nps {
 
+// Division of 32-bit unsigned integers by a divisor fixed for a launch, by a
+// multiply-high and shifts (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994, Fig. 4.1): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (t + ((n - t) >> 1)) >> (l - 1)
+// with t = mulhi(m, n); d = 1 returns n.  Exact for every 32-bit n.
+struct FastDiv {
+  uint32_t d, m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.s = l;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t n) {
+  if (f.d == 1) return n;
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> 1)) >> (f.s - 1);
+}
+
 constexpr int kSolid = 0, kFluid = 1, kAir = 2;
 constexpr int kMaxLevels = 7;
 constexpr int kMaxOrtho = 4;

@@ -133,3 +133,27 @@ def test_cached_path_matches_cuda_core_path(shape, L, precision, tol):
         assert _rel(z0, zo) <= 1e-5
     s0.close()
     s1.close()
+
+
+def test_sparse_level1_work_matches_dense_solve():
+    # occupancy-aware sparsity: the cached path runs the level-1 and level-2
+    # CConvs over the units with work only (zero or unread outputs elsewhere);
+    # the CUDA-core path computes every cell.  A scene with a large air region
+    # (the top third of the grid) must give the same iterations and x.
+    b = _b()
+    lab = synth.slosh_scene(64, 4242)
+    rhs = synth.rhs_normal(lab, 4243).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    lab_d, rhs_d = _dev(lab, torch.uint8), _dev(rhs, torch.float32)
+    s0 = b.Solver(w, levels=4, precision=b.FP32, kernel_path=b.PATH_CACHED)
+    s1 = b.Solver(w, levels=4, precision=b.FP32, kernel_path=b.PATH_CUDA_CORE)
+    x0, it0, rr0, st0 = s0.solve(lab_d, rhs_d, 1e-6, 3000)
+    x1, it1, rr1, st1 = s1.solve(lab_d, rhs_d, 1e-6, 3000)
+    assert st0 == st1 == b.OK and it0 == it1
+    assert _rel(x0.cpu().numpy(), x1.cpu().numpy()) <= 1e-5
+    c1, m1 = s0.level1_work(0)
+    c2, m2 = s0.level1_work(1)
+    n = lab.size
+    assert 0 < c2 <= c1 < n and 0 <= m1 and 0 <= m2 <= m1  # some units were skipped
+    s0.close()
+    s1.close()
