@@ -17,6 +17,8 @@ Contents (each wraps a C function of ``npsdo_oracle.c``):
 * ``network``, ``network_level``, ``network_backward`` Alg. 2 and its reverse
 * ``loss``               training loss of Sec. 4.2.3 and its weight gradient
 * ``npsdo``              Alg. 1
+* ``npcg``               PCG / flexible PCG with the network as preconditioner
+                         (Sec. 4.1, the appendix's solver variants)
 * ``jacobi_pcg``         textbook Jacobi-preconditioned CG
 """
 from __future__ import annotations
@@ -89,6 +91,8 @@ def _declare(L):
                            _dp, ctypes.POINTER(_i), _dp, _dp]
     L.or_jacobi_pcg.argtypes = [_u8p, _i, _i, _i, _dp, ctypes.c_double, _i, _dp,
                                 ctypes.POINTER(_i), _dp]
+    L.or_npcg.argtypes = [_u8p, _i, _i, _i, _i, _dp, _i, _dp, _dp, ctypes.c_double, _i, _i, _i,
+                          _dp, ctypes.POINTER(_i), _dp, _dp]
     L.or_check_labels.argtypes = [_u8p, _i, _i, _i]
 
 
@@ -310,6 +314,37 @@ def npsdo(labels, b, *, L=4, w=None, tol=1e-6, max_iter=1000, n_ortho=2, residua
     st = lib().or_npsdo(lp, nx, ny, nz, L, wp, prec, pdp, bp, float(tol), int(max_iter), int(n_ortho),
                         int(residual_mode), x.ctypes.data_as(_dp), ctypes.byref(it),
                         hist.ctypes.data_as(_dp), ctypes.byref(relres))
+    if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
+        raise ValueError(f"oracle status {st}")
+    return {"x": x, "iters": it.value, "status": st, "res_hist": hist[: it.value + 1].copy(),
+            "relres": relres.value}
+
+
+def npcg(labels, b, *, L=4, w=None, tol=1e-6, max_iter=1000, flexible=False, residual_mode=0,
+         prec=PREC_NETWORK, pdense=None):
+    """PCG (flexible=False) or flexible PCG (flexible=True) with the network
+    as preconditioner (Sec. 4.1; the appendix's solver-variant comparison).
+    Returns dict(x, iters, status, res_hist, relres) as npsdo does."""
+    labels, lp, nx, ny, nz = _lab(labels)
+    n = labels.size
+    if prec == PREC_NETWORK:
+        w, wp = _f64(w)
+        assert w.size == weight_count(L)
+    else:
+        wp = _null()
+    if prec == PREC_DENSE:
+        pdense, pdp = _f64(pdense)
+        assert pdense.shape == (n, n)
+    else:
+        pdp = _null()
+    b, bp = _f64(b)
+    x = np.zeros(labels.shape)
+    it = ctypes.c_int(0)
+    hist = np.zeros(max_iter + 1)
+    relres = ctypes.c_double(0.0)
+    st = lib().or_npcg(lp, nx, ny, nz, L, wp, prec, pdp, bp, float(tol), int(max_iter), int(bool(flexible)),
+                       int(residual_mode), x.ctypes.data_as(_dp), ctypes.byref(it),
+                       hist.ctypes.data_as(_dp), ctypes.byref(relres))
     if st not in (OK, NO_CONVERGENCE, BREAKDOWN):
         raise ValueError(f"oracle status {st}")
     return {"x": x, "iters": it.value, "status": st, "res_hist": hist[: it.value + 1].copy(),

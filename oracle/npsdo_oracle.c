@@ -15,6 +15,8 @@
  *     interpolation, network forward        (Sec. 4.2, Algorithm 2)
  *   - network backward (reverse of Alg. 2)  (Sec. 4.2.3, training loss)
  *   - NPSDO solver                          (Sec. 4.1, Algorithm 1)
+ *   - PCG / flexible PCG with the network   (Sec. 4.1, appendix: solver
+ *     as preconditioner                      variant comparison)
  *   - Jacobi-preconditioned CG              (textbook PCG, Sec. 4.1)
  *
  * Conventions (the readings where the paper is silent):
@@ -804,5 +806,137 @@ int or_jacobi_pcg(const uint8_t *lab, int nx, int ny, int nz, const double *b, d
   free(pp);
   free(q);
   free(dg);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1 and the solver-variant comparison of the appendix: PCG and      */
+/* flexible PCG with the network (or another preconditioner of or_npsdo) as */
+/* the preconditioner.                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* out = P(v) for the preconditioner choices of or_npsdo, restricted to fluid
+ * cells (the network's output restriction, Sec. 4.2). */
+static void apply_prec(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, int prec,
+                       const double *pdense, const double *v, double *out) {
+  size_t n = cells(nx, ny, nz);
+  if (prec == PREC_NETWORK) {
+    or_network(lab, nx, ny, nz, L, w, v, out);
+  } else if (prec == PREC_IDENTITY) {
+    for (size_t p = 0; p < n; ++p) out[p] = lab[p] == LAB_FLUID ? v[p] : 0.0;
+  } else {
+    for (size_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (size_t j = 0; j < n; ++j) s += pdense[i * n + j] * v[j];
+      out[i] = lab[i] == LAB_FLUID ? s : 0.0;
+    }
+  }
+}
+
+/* PCG in the textbook arrangement (Shewchuk 1994, the preconditioned CG
+ * algorithm): z_k = P(r_k), rho_k = r_k^T z_k, d_1 = z_0, later
+ * d = z_k + beta_k d, alpha = rho_k / d^T A d, x += alpha d, r -= alpha A d.
+ *   flexible = 0: beta_k = rho_k / rho_{k-1} (Fletcher-Reeves form);
+ *   flexible = 1: beta_k = z_k^T (r_k - r_{k-1}) / rho_{k-1} (the Polak-Ribiere
+ *                 form of flexible PCG for non-symmetric preconditioners).
+ * The network is linear in r (Sec. 4.2), and it is given the unit residual as
+ * in Alg. 1: z_k = ||r_k|| P(r_k / ||r_k||).  Stop test, residual modes and
+ * the replacement of the recurrence residual on exit are those of or_npsdo;
+ * after a replacement the conjugate sequence restarts (beta = 0).  rho_k = 0
+ * or non-finite (beta would divide by it) and d^T A d <= 0 are breakdowns. */
+int or_npcg(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, int prec, const double *pdense,
+            const double *b, double tol, int max_iter, int flexible, int residual_mode, double *x, int *iters,
+            double *res_hist, double *final_relres) {
+  size_t n = cells(nx, ny, nz);
+  if (prec == PREC_NETWORK) {
+    int st = check_dims(nx, ny, nz, L);
+    if (st) return st;
+  }
+  if (or_check_labels(lab, nx, ny, nz)) return OR_BAD_LABELS;
+  if (max_iter < 0 || !(tol >= 0.0)) return OR_BAD_ARG;
+  double *bm = malloc(sizeof(double) * n), *r = malloc(sizeof(double) * n), *rprev = malloc(sizeof(double) * n);
+  double *rn = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n), *d = malloc(sizeof(double) * n);
+  double *ad = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
+  for (size_t p = 0; p < n; ++p) {
+    bm[p] = lab[p] == LAB_FLUID ? b[p] : 0.0;
+    x[p] = 0.0;
+    r[p] = bm[p];
+    d[p] = 0.0;
+  }
+  double nb = sqrt(dot(bm, bm, n));
+  int status = OR_OK;
+  if (!isfinite(nb)) status = OR_BAD_ARG;
+  double eps = tol * nb, nr = nb, rho_prev = 0.0;
+  int k = 0, restarts = 0, fresh = 1;
+  if (res_hist) res_hist[0] = nb;
+  while (status == OR_OK) {
+    while (nr >= eps && nr > 0.0) {
+      if (k >= max_iter) {
+        status = OR_NO_CONVERGENCE;
+        break;
+      }
+      k += 1;
+      for (size_t p = 0; p < n; ++p) rn[p] = r[p] / nr;
+      apply_prec(lab, nx, ny, nz, L, w, prec, pdense, rn, z);
+      for (size_t p = 0; p < n; ++p) z[p] *= nr;
+      double rho = dot(r, z, n);
+      if (!(rho != 0.0) || !isfinite(rho)) {
+        status = OR_BREAKDOWN;
+        break;
+      }
+      if (fresh) {
+        memcpy(d, z, sizeof(double) * n);
+      } else {
+        double beta;
+        if (flexible) {
+          for (size_t p = 0; p < n; ++p) tmp[p] = r[p] - rprev[p];
+          beta = dot(z, tmp, n) / rho_prev;
+        } else {
+          beta = rho / rho_prev;
+        }
+        for (size_t p = 0; p < n; ++p) d[p] = z[p] + beta * d[p];
+      }
+      fresh = 0;
+      or_lap_apply(lab, nx, ny, nz, d, ad);
+      double dAd = dot(d, ad, n);
+      if (!(dAd > 0.0) || !isfinite(dAd)) {
+        status = OR_BREAKDOWN;
+        break;
+      }
+      double alpha = rho / dAd;
+      for (size_t p = 0; p < n; ++p) x[p] += alpha * d[p];
+      memcpy(rprev, r, sizeof(double) * n);
+      if (residual_mode == 1) {
+        or_lap_apply(lab, nx, ny, nz, x, tmp);
+        for (size_t p = 0; p < n; ++p) r[p] = bm[p] - tmp[p];
+      } else {
+        for (size_t p = 0; p < n; ++p) r[p] -= alpha * ad[p];
+      }
+      rho_prev = rho;
+      nr = sqrt(dot(r, r, n));
+      if (res_hist) res_hist[k] = nr;
+    }
+    if (status != OR_OK || residual_mode == 1 || restarts >= 4) break;
+    or_lap_apply(lab, nx, ny, nz, x, tmp);
+    for (size_t p = 0; p < n; ++p) tmp[p] = bm[p] - tmp[p];
+    double ntrue = sqrt(dot(tmp, tmp, n));
+    if (ntrue < eps || ntrue == 0.0) break;
+    memcpy(r, tmp, sizeof(double) * n);
+    nr = ntrue;
+    fresh = 1;
+    restarts += 1;
+  }
+  or_lap_apply(lab, nx, ny, nz, x, tmp);
+  for (size_t p = 0; p < n; ++p) tmp[p] = bm[p] - tmp[p];
+  *final_relres = nb > 0.0 ? sqrt(dot(tmp, tmp, n)) / nb : 0.0;
+  *iters = k;
+  free(bm);
+  free(r);
+  free(rprev);
+  free(rn);
+  free(z);
+  free(d);
+  free(ad);
+  free(tmp);
   return status;
 }
