@@ -12,6 +12,8 @@ Also reported on the same line:
   e2e            the same solve through npsolve_solve_host (pinned host
                  buffers in, x back to the host, copies inside the timing)
   fp32_form      ms per solve and iterations of the FP32 form
+  solver_variants  PCG and flexible PCG with the same network (BF16 form):
+                 ms per solve, iterations, true relative residual
   accuracy       true relative residuals (FP64 oracle Laplacian), iterations
                  of both forms, ||x_bf16 - x_fp32|| / ||x_fp32||
   roofline       the dominant kernel class of a profiled solve (CUDA events
@@ -306,6 +308,25 @@ def main():
     torch.cuda.synchronize()
     fp32_ms = e0.elapsed_time(e1) / n32
     x_fp32 = x32.cpu().numpy()
+    sol32.close()
+
+    # ---- solver variants with the same network (Sec. 4.1; the appendix's
+    # comparison): PCG and flexible PCG, BF16 form, the same problem
+    # (capped at 500 iterations: PCG's Fletcher-Reeves beta with the non-symmetric
+    # network can stall on this problem)
+    variants = {}
+    for name, method in (("pcg", binding.PCG), ("fpcg", binding.FPCG)):
+        sv = binding.Solver(w, levels=4, precision=binding.BF16, method=method)
+        xv = torch.empty_like(x_d)
+        sv.solve(lab_d, rhs_d, 1e-6, 500, x=xv)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, it_v, rr_v, st_v = sv.solve(lab_d, rhs_d, 1e-6, 500, x=xv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        variants[name] = {"ms_per_solve": e0.elapsed_time(e1), "iters": it_v, "relres": rr_v,
+                          "status": binding.STATUS_NAMES[st_v]}
+        sv.close()
 
     # ---- profiled solve: per-kernel-class device time (roofline) -------------
     sol.set_profiling(True)
@@ -410,6 +431,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": int(lab.nbytes + rhs.nbytes),
                 "d2h_bytes_per_step": int(n * 8)},
         "fp32_form": {"ms_per_solve": fp32_ms, "iters": it_fp32},
+        "solver_variants": variants,
         "served": served,
         "accuracy": accuracy,
         "roofline": roof,

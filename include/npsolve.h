@@ -85,12 +85,23 @@ enum {
                                  (levels 1-3, BF16 operands, FP32 accumulation), CUDA cores beyond */
 };
 
+/* The Krylov method that npsolve_solve runs with the network as preconditioner
+ * (Sec. 4.1 and the solver-variant comparison of the appendix). */
+enum {
+  NPSOLVE_METHOD_NPSDO = 0, /* Alg. 1: steepest descent with A-orthogonalisation against n_ortho directions */
+  NPSOLVE_METHOD_PCG = 1,   /* preconditioned CG (Shewchuk's form): z_k = P(r_k), rho_k = r_k^T z_k,
+                               d_k = z_k + (rho_k / rho_{k-1}) d_{k-1}, alpha_k = rho_k / d_k^T A d_k */
+  NPSOLVE_METHOD_FPCG = 2   /* flexible PCG (Polak-Ribiere form for a non-symmetric preconditioner):
+                               beta_k = z_k^T (r_k - r_{k-1}) / rho_{k-1}, otherwise as PCG */
+};
+
 typedef struct {
   int levels;        /* L, number of network levels, 1..7 (paper: 6; L = 4 ~ 16k parameters) */
-  int n_ortho;       /* directions to A-orthogonalise against, 0..4 (paper: 2, Sec. 4.1) */
+  int n_ortho;       /* directions to A-orthogonalise against, 0..4 (paper: 2, Sec. 4.1); NPSDO only */
   int precision;     /* NPSOLVE_FP32 or NPSOLVE_BF16 */
   int residual_mode; /* NPSOLVE_RESIDUAL_RECURRENCE or NPSOLVE_RESIDUAL_EXPLICIT */
   int kernel_path;   /* NPSOLVE_PATH_CACHED, NPSOLVE_PATH_CUDA_CORE or NPSOLVE_PATH_TENSOR */
+  int method;        /* NPSOLVE_METHOD_NPSDO (0, the paper's solver), _PCG or _FPCG */
 } npsolve_config;
 
 /* Number of FP32 network parameters for L levels (Alg. 2): for each level
@@ -130,7 +141,13 @@ const char *npsolve_last_error(npsolve_t h);
  *   rel_residual (host, written) FP64 ||b - A x|| / ||b|| of the returned x.
  * Each dimension must be divisible by 2^(L-1).  Returns NPSOLVE_OK,
  * NPSOLVE_NO_CONVERGENCE or NPSOLVE_BREAKDOWN with all outputs written, or an
- * argument/CUDA error with outputs unspecified. */
+ * argument/CUDA error with outputs unspecified.
+ * With cfg.method = NPSOLVE_METHOD_PCG or _FPCG the same call runs PCG or
+ * flexible PCG with the network as preconditioner, z_k = ||r_k|| P_net(I,
+ * r_k/||r_k||) (the network is linear in r); n_ortho is then not used.  Their
+ * BREAKDOWN also covers rho_k = r_k^T z_k = 0 or non-finite (the network is
+ * not symmetric positive definite, so rho_k can vanish).  After a residual
+ * replacement both restart with beta = 0. */
 int npsolve_solve(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol,
                   int max_iter, void *stream, double *x, int *iters, double *rel_residual);
 

@@ -19,6 +19,7 @@ OK, BAD_ARG, BAD_DIMS, BAD_LABELS, NO_CONVERGENCE, BREAKDOWN, OOM, CUDA_ERROR = 
 FP32, BF16 = 0, 1
 PATH_CACHED, PATH_CUDA_CORE, PATH_TENSOR = 0, 1, 2
 RECURRENCE, EXPLICIT = 0, 1
+NPSDO, PCG, FPCG = 0, 1, 2  # npsolve_config.method: Alg. 1, or (flexible) PCG with the network as preconditioner
 STATUS_NAMES = ["OK", "BAD_ARG", "BAD_DIMS", "BAD_LABELS", "NO_CONVERGENCE", "BREAKDOWN", "OOM", "CUDA_ERROR"]
 
 
@@ -30,7 +31,7 @@ class NpsolveError(RuntimeError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("n_ortho", ctypes.c_int), ("precision", ctypes.c_int),
-                ("residual_mode", ctypes.c_int), ("kernel_path", ctypes.c_int)]
+                ("residual_mode", ctypes.c_int), ("kernel_path", ctypes.c_int), ("method", ctypes.c_int)]
 
 
 _lib = None
@@ -140,17 +141,17 @@ class Solver:
     """A solver handle: network weights + device workspace (npsolve_t)."""
 
     def __init__(self, weights, levels=4, n_ortho=2, precision=FP32, residual_mode=RECURRENCE,
-                 kernel_path=PATH_CACHED):
+                 kernel_path=PATH_CACHED, method=NPSDO):
         lib = load_library()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
-        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path)
+        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path, method)
         h = ctypes.c_void_p()
         st = lib.npsolve_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, ctypes.byref(h))
         if st != OK:
             raise NpsolveError(st, lib.npsolve_last_error(None).decode())
         self._h = h
         self.levels, self.n_ortho, self.precision, self.residual_mode = levels, n_ortho, precision, residual_mode
-        self.kernel_path = kernel_path
+        self.kernel_path, self.method = kernel_path, method
 
     def close(self):
         if getattr(self, "_h", None):
@@ -405,10 +406,10 @@ class Server:
     poll for finished ids, fetch results."""
 
     def __init__(self, weights, levels=4, n_ortho=2, precision=BF16, residual_mode=RECURRENCE,
-                 kernel_path=PATH_CACHED, hbm_budget_bytes=150 << 30, max_active=16):
+                 kernel_path=PATH_CACHED, hbm_budget_bytes=150 << 30, max_active=16, method=NPSDO):
         lib = load_library()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
-        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path)
+        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path, method)
         h = ctypes.c_void_p()
         st = lib.npsolve_server_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, int(hbm_budget_bytes),
                                        int(max_active), ctypes.byref(h))

@@ -633,6 +633,7 @@ struct StreamParams {
   const SolveState *st;
   int *err;
   int mode;             // which outputs are computed (STREAM_MODE_*)
+  int method;           // fused CConv2: the solver's method (kMethod*), fixed for a solve
   // fused level-1 combination: z = mask_fluid(c1 x1 + c2 CConv2) and the dots z . q_i
   CUtensorMap tq;       // q ring: dims (nx, ny, nz, ring), box 36 x 8 x 2 x 1
   double *part;         // partial dots, one row per CTA
@@ -640,8 +641,12 @@ struct StreamParams {
   SolveState *stw;      // the solve state (orthogonalisation coefficients are written)
   // level-1 CConv1 that first forms r_{k+1} = r_k - alpha q_{k+1} (Alg. 1's
   // recurrence) while a step is pending: r_k in buffer k mod 2
-  CUtensorMap tv2;      // the second residual buffer, as tv
-  CUtensorMap tqu;      // q ring: dims (nx, ny, nz, ring), box 44 x 10 x 2 x 1
+  // (one pair of maps serves both fusions, which never share a launch:)
+  //   residual update: aux[0] the second residual buffer, as tv; aux[1] the q
+  //                    ring, dims (nx, ny, nz, ring), box 44 x 10 x 2 x 1;
+  //   fused CConv2 of PCG / FPCG: the residual buffers (r_k in aux[k & 1]),
+  //                    one-slot 4-D maps with tq's 36 x 8 x 2 x 1 box.
+  CUtensorMap aux[2];
   float *rb[2];         // the residual buffers (r_{k+1} is written to rb[(k + 1) & 1])
   double *upart;        // ||r_{k+1}||^2 partials, one per CTA
   unsigned *uticket;
@@ -812,7 +817,8 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, 128
 // patch in all of the CTA's units; the units of a CTA are fixed by the grid,
 // blockIdx.x + m gridDim.x) go to the CTA's row of partials in a fixed order;
 // the last CTA to arrive reduces the rows in a fixed order and sets the
-// orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i (Alg. 1), then
+// orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i (Alg. 1; for
+// PCG / FPCG the conjugation coefficient from r_k . z and q_k . z), then
 // re-arms the counter.  Deterministic for a given grid.
 __device__ __noinline__ void fused_finish(const StreamParams &P, StreamMeta &M, DF (&fdot)[kMaxFusedOrtho], int cnt) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -844,13 +850,9 @@ __device__ __noinline__ void fused_finish(const StreamParams &P, StreamMeta &M, 
   }
   consumers_sync();
   if (tid == 0) {
-    SolveState *st = P.stw;
-    const int k1 = st->k + 1, no = st->n_ortho;
-    for (int j = 0; j < kMaxOrtho; ++j) st->coef[j] = 0.0;
-    for (int j = 0; j < cnt; ++j) {
-      const double t = ((M.fsum[0][j] + M.fsum[1][j]) + M.fsum[2][j]) + M.fsum[3][j];
-      st->coef[j] = t / st->dAd[ring_slot(k1 - 1 - j, no)];
-    }
+    double t[kMaxFusedOrtho];
+    for (int j = 0; j < kMaxFusedOrtho; ++j) t[j] = ((M.fsum[0][j] + M.fsum[1][j]) + M.fsum[2][j]) + M.fsum[3][j];
+    set_direction_coefs(P.stw, t, cnt);
     *P.ticket = 0u;
   }
 }
@@ -946,16 +948,23 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
     uint32_t vi = 0, vrel = 0;  // loads issued / slots known released
     uint32_t khead = 0, ktail = 0, kpos = 0;
     uint32_t di = 0;            // descriptor loads issued (= units)
-    // fused: q of the previous directions i = k1-1-j (j < qcnt, i >= 1) of Alg. 1
+    // fused: q of the previous directions i = k1-1-j (j < qcnt, i >= 1) of Alg. 1; for PCG / FPCG the
+    // current residual r_k and (FPCG) q_k
     int qcnt = 0, qslot[kMaxFusedOrtho] = {0, 0};
+    const CUtensorMap *qmap0 = &P.tq;  // the map of box 0 (box 1 is always from the q ring)
     if (FUSE) {
       const int k1 = P.st->k + 1, no = P.st->n_ortho;
-      qcnt = min(min(no, k1 - 1), kMaxFusedOrtho);
-      for (int j = 0; j < kMaxFusedOrtho; ++j) qslot[j] = ring_slot(max(k1 - 1 - j, 1), no);
+      qcnt = direction_dot_count(P.method, k1, no, kMaxFusedOrtho);
+      if (P.method == kMethodNpsdo) {
+        for (int j = 0; j < kMaxFusedOrtho; ++j) qslot[j] = ring_slot(max(k1 - 1 - j, 1), no);
+      } else {
+        qmap0 = &P.aux[P.st->k & 1];
+        qslot[1] = ring_slot(max(k1 - 1, 1), no);
+      }
     }
     // the residual update: r_k from buffer k mod 2 and q of the pending step
     const bool upd = UPD && P.st->upd_pending;
-    const CUtensorMap *tvm = (UPD && (P.st->k & 1)) ? &P.tv2 : &P.tv;
+    const CUtensorMap *tvm = (UPD && (P.st->k & 1)) ? &P.aux[0] : &P.tv;
     const int uslot = UPD ? ring_slot(P.st->k + 1, P.st->n_ortho) : 0;
     auto release_next = [&]() {
       const int sl = (int)(vrel % NRV);
@@ -1037,10 +1046,11 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
         mbar_expect_tx(bar, 2u * VPLANE + (upd ? 2u * VPLANE : 0u) + (x1 ? (uint32_t)XBOX : 0u) +
                                 (uint32_t)nq * (uint32_t)XBOX + kbytes);
         tma_load_3d(dst, tvm, U.x0 - 4, U.y0 - 1, zv, bar);
-        if (upd) tma_load_4d(dst + QUOFF, &P.tqu, U.x0 - 4, U.y0 - 1, zv, uslot, bar);
+        if (upd) tma_load_4d(dst + QUOFF, &P.aux[1], U.x0 - 4, U.y0 - 1, zv, uslot, bar);
         if (x1) tma_load_3d(dst + X1OFF, &P.tx1, U.x0, U.y0, U.zs + 2 * t, bar);
         if (FUSE)
-          for (int j = 0; j < nq; ++j) tma_load_4d(dst + QOFF + XBOX * j, &P.tq, U.x0, U.y0, U.zs + 2 * t, qslot[j], bar);
+          for (int j = 0; j < nq; ++j)
+            tma_load_4d(dst + QOFF + XBOX * j, j ? &P.tq : qmap0, U.x0, U.y0, U.zs + 2 * t, qslot[j], bar);
         if (kbytes) bulk_load(kb + kpos, P.cache + (size_t)koff * C::EB, kbytes, bar);
         kpos += kbytes;
         ++vi;
@@ -1084,7 +1094,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_cconv_stream(const __grid_const
   uint32_t sl = 0, sph = 0;  // next slot and the parity of its phase
   DF fdot[kMaxFusedOrtho];   // fused: per-thread double-float dots z . q_i
   int fqcnt = 0;
-  if (FUSE) fqcnt = min(min(P.st->n_ortho, P.st->k), kMaxFusedOrtho);
+  if (FUSE) fqcnt = direction_dot_count(P.method, P.st->k + 1, P.st->n_ortho, kMaxFusedOrtho);
   // residual update: every window value is r_k - alpha q (the same FP32 FMA as
   // k_update4), the thread's own cells are written to the other buffer and
   // summed into ||r_{k+1}||^2
@@ -1494,9 +1504,9 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
   if (upd && (fuse || mode != STREAM_MODE_ZERO_PURE || c12)) return -1;
   P.mode = fuse ? STREAM_MODE_FLUID_ONLY : mode;
   if (upd) {
-    // r_k is read from buffer k mod 2 (tv over rb[0], tv2 over rb[1]); q of the pending step from the ring
-    if (v != upd->rb[0] || !encode_map(&P.tv2, upd->rb[1], dm, BXW, BYH, 2)) return -1;
-    if (encode_map_4d(&P.tqu, upd->qring, dm, upd->nring, BXW, BYH) != CUDA_SUCCESS) return -1;
+    // r_k is read from buffer k mod 2 (tv over rb[0], aux[0] over rb[1]); q of the pending step from the ring
+    if (v != upd->rb[0] || !encode_map(&P.aux[0], upd->rb[1], dm, BXW, BYH, 2)) return -1;
+    if (encode_map_4d(&P.aux[1], upd->qring, dm, upd->nring, BXW, BYH) != CUDA_SUCCESS) return -1;
     P.rb[0] = upd->rb[0];
     P.rb[1] = upd->rb[1];
     P.upart = upd->part;
@@ -1508,8 +1518,12 @@ int launch_cconv_stream(bool bf16, Dims dm, const float *kfix, const void *desc,
     // the q ring as a 4-D tensor (nx, ny, nz, slot); slot stride = one grid
     const CUresult r = encode_map_4d(&P.tq, fuse->qring, dm, fuse->nring);
     if (r != CUDA_SUCCESS) return -1;
+    // the residual buffers as one-slot tensors of the same shape (read by PCG / FPCG)
+    for (int i = 0; i < 2; ++i)
+      if (encode_map_4d(&P.aux[i], fuse->rb[i] ? fuse->rb[i] : fuse->rb[0], dm, 1) != CUDA_SUCCESS) return -1;
     P.part = fuse->part;
     P.ticket = fuse->ticket;
+    P.method = fuse->method;
     P.stw = fuse->st;
   }
   if (!encode_map(&P.tv, v, dm, BXW, BYH, 2)) return -1;

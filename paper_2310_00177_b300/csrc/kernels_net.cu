@@ -363,19 +363,26 @@ __global__ void k_combine(long long n, const float *__restrict__ x1, const float
 
 // Level 1: z = mask_fluid(c1 x1 + c2 x2) (the output restriction of Sec.
 // 4.2) and, inside a solve, the partial dot products z.(A d_i) for the
-// previous directions i = k-1, k-2, ... (Alg. 1 orthogonalisation).
+// previous directions i = k-1, k-2, ... (Alg. 1 orthogonalisation), or for
+// PCG / FPCG z.r_k and z.(A d_k).
 __global__ void __launch_bounds__(kRedThreads) k_combine1(const uint8_t *__restrict__ lab, long long n,
                                                             const float *__restrict__ x1, const float *__restrict__ x2,
                                                             const double *__restrict__ c12, float *__restrict__ z,
-                                                            const float *__restrict__ qring, double *__restrict__ part,
-                                                            const SolveState *st) {
+                                                            const float *__restrict__ qring, const float *rk,
+                                                            double *__restrict__ part, const SolveState *st) {
   if (st && st->done) return;
   const float c1 = (float)c12[0], c2 = (float)c12[1];
   const float *qs[kMaxOrtho];
   int cnt = 0;
   if (st) {
     const int k1 = st->k + 1, no = st->n_ortho;
-    for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) qs[cnt++] = qring + (size_t)ring_slot(i, no) * n;
+    if (st->method == kMethodNpsdo) {
+      for (int i = k1 - 1; i >= k1 - no && i >= 1; --i) qs[cnt++] = qring + (size_t)ring_slot(i, no) * n;
+    } else {
+      cnt = direction_dot_count(st->method, k1, no, kMaxOrtho);
+      qs[0] = rk;
+      qs[1] = qring + (size_t)ring_slot(k1 > 1 ? k1 - 1 : 1, no) * n;
+    }
   }
   double v[kMaxOrtho] = {0.0, 0.0, 0.0, 0.0};
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
@@ -451,8 +458,8 @@ void launch_combine(long long n, const float *x1, const float *x2, const double 
 }
 
 void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
-                     const float *qring, double *part, const SolveState *st, cudaStream_t s) {
-  k_combine1<<<red_blocks(n), kRedThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, st);
+                     const float *qring, const float *rk, double *part, const SolveState *st, cudaStream_t s) {
+  k_combine1<<<red_blocks(n), kRedThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, rk, part, st);
 }
 
 }  // namespace nps

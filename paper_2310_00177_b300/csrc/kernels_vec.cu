@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kRedThreads) k_init(const uint8_t *__restrict_
 }
 
 // Initial scalars: ||b||, the stopping threshold, the first input scale.
-__global__ void k_init_final(const double *part, int nblocks, double tol, int max_iter, int n_ortho, SolveState *st,
-                             double *hist) {
+__global__ void k_init_final(const double *part, int nblocks, double tol, int max_iter, int n_ortho, int method,
+                             SolveState *st, double *hist) {
   double t[1];
   reduce_partials<1>(part, nblocks, t);
   if (threadIdx.x != 0) return;
@@ -88,6 +88,9 @@ __global__ void k_init_final(const double *part, int nblocks, double tol, int ma
   s.upd_pending = 0;
   s.x_upto = 0;
   for (int i = 0; i < kRing; ++i) s.alpha_slot[i] = 0.0;
+  s.method = method;
+  s.fresh = 1;
+  s.sigma = 0.0;
   s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
   if (!isfinite(t[0])) s.done = kDoneBadInput;
   else if (!(t[0] >= s.eps2) || t[0] == 0.0) s.done = kDoneConverged;  // ||r_0|| < tol ||b|| or b = 0
@@ -97,21 +100,15 @@ __global__ void k_init_final(const double *part, int nblocks, double tol, int ma
 }
 
 // Alg. 1 inner loop, classical Gram-Schmidt form: c_i = z^T (A d_i) / d_i^T A d_i
-// for the previous directions i = max(1, k - n_ortho) .. k-1.  The partials
-// hold z.q_i per ring slot (written by the level-1 combine kernel).
+// for the previous directions i = max(1, k - n_ortho) .. k-1 (or the PCG /
+// FPCG conjugation coefficient).  The partials hold the dots of z with the
+// vectors of direction_dot_count (written by the level-1 combine kernel).
 __global__ void k_ortho_final(const double *part, int nblocks, SolveState *st) {
   if (st->done) return;
   double t[kMaxOrtho];
   reduce_partials<kMaxOrtho>(part, nblocks, t);
   if (threadIdx.x != 0) return;
-  const int k1 = st->k + 1;  // the iteration being formed (1-based)
-  const int no = st->n_ortho;
-  for (int j = 0; j < kMaxOrtho; ++j) st->coef[j] = 0.0;
-  for (int i = k1 - no; i < k1; ++i) {
-    if (i < 1) continue;
-    const int j = k1 - 1 - i;  // 0 = previous direction, 1 = the one before ...
-    st->coef[j] = t[j] / st->dAd[ring_slot(i, no)];
-  }
+  set_direction_coefs(st, t, direction_dot_count(st->method, st->k + 1, st->n_ortho, kMaxOrtho));
 }
 
 // d_k = z - sum_j c_j d_{k-1-j}  (into ring slot of iteration k).
@@ -141,7 +138,8 @@ __global__ void __launch_bounds__(kRedThreads) k_lap_ring(const uint8_t *__restr
                                                             const float *__restrict__ r, double *__restrict__ part,
                                                             const SolveState *st);
 
-// alpha_k = r^T d_k / d_k^T A d_k; breakdown when d^T A d <= 0 or non-finite.
+// alpha_k = r^T d_k / d_k^T A d_k (PCG / FPCG: sigma_k / d_k^T A d_k); breakdown
+// when d^T A d <= 0 or non-finite.
 __global__ void k_alpha_final(const double *part, int nblocks, SolveState *st) {
   if (st->done) return;
   double t[2];
@@ -153,7 +151,7 @@ __global__ void k_alpha_final(const double *part, int nblocks, SolveState *st) {
     st->done = kDoneBreakdown;
     return;
   }
-  st->alpha = rd / dq;
+  st->alpha = (st->method == kMethodNpsdo ? rd : st->sigma) / dq;
   st->dAd[ring_slot(k1, st->n_ortho)] = dq;
 }
 
@@ -266,6 +264,7 @@ __global__ void k_restart_final(const double *part, int nblocks, SolveState *st,
     st->rnorm2 = rr;
     st->rscale = (float)(1.0 / sqrt(rr));
     st->done = kDoneRunning;
+    st->fresh = 1;  // PCG / FPCG restart their conjugate sequence from the replaced residual
     *reopened = 1;
   }
 }
@@ -488,10 +487,10 @@ void launch_check_labels(const uint8_t *lab, long long n, unsigned int *bad, cud
   k_check_labels<<<red_blocks(n), kRedThreads, 0, s>>>(lab, n, bad);
 }
 void launch_init(const uint8_t *lab, long long n, const float *b, float *r, double *x, double *part, double tol,
-                 int max_iter, int n_ortho, SolveState *st, double *hist, cudaStream_t s) {
+                 int max_iter, int n_ortho, int method, SolveState *st, double *hist, cudaStream_t s) {
   const int nb = red_blocks(n);
   k_init<<<nb, kRedThreads, 0, s>>>(lab, n, b, r, x, part);
-  k_init_final<<<1, kRedThreads, 0, s>>>(part, nb, tol, max_iter, n_ortho, st, hist);
+  k_init_final<<<1, kRedThreads, 0, s>>>(part, nb, tol, max_iter, n_ortho, method, st, hist);
 }
 void launch_ortho_final(const double *part, long long n, SolveState *st, cudaStream_t s) {
   k_ortho_final<<<1, kRedThreads, 0, s>>>(part, red_blocks(n), st);

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
                                                     float *__restrict__ r, double *__restrict__ x,
                                                     float *__restrict__ xhi, float *__restrict__ xlo,
                                                     double *__restrict__ part, unsigned *ticket, double tol,
-                                                    int max_iter, int n_ortho, SolveState *st, double *hist) {
+                                                    int max_iter, int n_ortho, int method, SolveState *st,
+                                                    double *hist) {
   DF acc;
   const int n4 = n >> 2;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
@@ -140,6 +141,9 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
     s.upd_pending = 0;
     s.x_upto = 0;
     for (int i = 0; i < kRing; ++i) s.alpha_slot[i] = 0.0;
+    s.method = method;
+    s.fresh = 1;
+    s.sigma = 0.0;
     s.rscale = t[0] > 0.0 ? (float)(1.0 / sqrt(t[0])) : 0.f;
     if (!isfinite(t[0])) s.done = kDoneBadInput;
     else if (!(t[0] >= s.eps2) || t[0] == 0.0) s.done = kDoneConverged;
@@ -152,20 +156,24 @@ __global__ void __launch_bounds__(kThreads) k_init4(const uint8_t *__restrict__ 
 // ---------------------------------------------------------------------------
 // Level-1 combination z = mask_fluid(c1 x1 + c2 x2) with the dot products
 // z . (A d_i) of the previous directions; the last block turns them into the
-// orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i (Alg. 1).
+// orthogonalisation coefficients c_i = z^T A d_i / d_i^T A d_i (Alg. 1).  For
+// PCG / FPCG the dots are r_k . z and q_k . z (r_k in r0, or in r0 / r1 by
+// the parity of k when the residual alternates between two buffers).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_combine1_4(const uint8_t *__restrict__ lab, int n,
                                                          const float *__restrict__ x1, const float *__restrict__ x2,
                                                          const double *__restrict__ c12, float *__restrict__ z,
-                                                         const float *__restrict__ qring, double *__restrict__ part,
+                                                         const float *__restrict__ qring, const float *r0,
+                                                         const float *r1, double *__restrict__ part,
                                                          unsigned *ticket, SolveState *st) {
   if (st->done) return;
   const float c1 = (float)c12[0], c2 = (float)c12[1];
   const int k1 = st->k + 1, no = st->n_ortho;
   // q of the previous directions i = k1-1-j (j < no, i >= 1), each without dynamic indexing
-  const int cnt = min(no, k1 - 1);
-  const float *q0 = qring + (size_t)ring_slot(max(k1 - 1, 1), no) * n;
-  const float *q1 = qring + (size_t)ring_slot(max(k1 - 2, 1), no) * n;
+  const int cnt = direction_dot_count(st->method, k1, no, kMaxOrtho);
+  const bool pcg = st->method != kMethodNpsdo;
+  const float *q0 = pcg ? ((r1 && (st->k & 1)) ? r1 : r0) : qring + (size_t)ring_slot(max(k1 - 1, 1), no) * n;
+  const float *q1 = qring + (size_t)ring_slot(max(k1 - (pcg ? 1 : 2), 1), no) * n;
   const float *q2 = qring + (size_t)ring_slot(max(k1 - 3, 1), no) * n;
   const float *q3 = qring + (size_t)ring_slot(max(k1 - 4, 1), no) * n;
   DF acc[kMaxOrtho];
@@ -199,14 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_combine1_4(const uint8_t *__restri
   double v[kMaxOrtho];
 #pragma unroll
   for (int j = 0; j < kMaxOrtho; ++j) v[j] = df_val(acc[j]);
-  reduce_and_finish<kMaxOrtho>(v, part, ticket, [&](const double *t) {
-    for (int j = 0; j < kMaxOrtho; ++j) st->coef[j] = 0.0;
-    for (int i = k1 - no; i < k1; ++i) {
-      if (i < 1) continue;
-      const int j = k1 - 1 - i;
-      st->coef[j] = t[j] / st->dAd[ring_slot(i, no)];
-    }
-  });
+  reduce_and_finish<kMaxOrtho>(v, part, ticket, [&](const double *t) { set_direction_coefs(st, t, cnt); });
 }
 
 // x += a d for x held as a double-float pair (hi, lo) (|lo| <= ulp(hi) / 2,
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_lap4(const uint16_t *__restrict__ 
       st->done = kDoneBreakdown;
       return;
     }
-    st->alpha = rd / dq;
+    st->alpha = (st->method == kMethodNpsdo ? rd : st->sigma) / dq;  // PCG / FPCG: sigma_k / d^T A d
     st->alpha_slot[slot] = st->alpha;
     st->dAd[slot] = dq;
     st->upd_pending = 1;
@@ -567,14 +568,17 @@ __global__ void __launch_bounds__(kThreads) k_group_mask(const uint16_t *__restr
 // Host-side launchers.
 // ---------------------------------------------------------------------------
 void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, float *xhi, float *xlo, double *part,
-                  unsigned *ticket, double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms,
-                  cudaStream_t s) {
-  k_init4<<<grid4(n / 4, num_sms, resident_blocks<k_init4>()), kThreads, 0, s>>>(lab, n, b, r, x, xhi, xlo, part, ticket, tol, max_iter, n_ortho, st, hist);
+                  unsigned *ticket, double tol, int max_iter, int n_ortho, int method, SolveState *st, double *hist,
+                  int num_sms, cudaStream_t s) {
+  k_init4<<<grid4(n / 4, num_sms, resident_blocks<k_init4>()), kThreads, 0, s>>>(
+      lab, n, b, r, x, xhi, xlo, part, ticket, tol, max_iter, n_ortho, method, st, hist);
 }
 void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
-                       const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
-                       cudaStream_t s) {
-  k_combine1_4<<<grid4(n / 4, num_sms, resident_blocks<k_combine1_4>()), kThreads, 0, s>>>(lab, n, x1, x2, c12, z, qring, part, ticket, st);
+                       const float *qring, const float *r0, const float *r1, double *part, unsigned *ticket,
+                       SolveState *st, int num_sms, cudaStream_t s) {
+  k_combine1_4<<<grid4(n / 4, num_sms, resident_blocks<k_combine1_4>()), kThreads, 0, s>>>(lab, n, x1, x2, c12, z,
+                                                                                          qring, r0, r1, part, ticket,
+                                                                                          st);
 }
 void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const uint32_t *gmask,
                        const SolveState *st, int n_ortho, int num_sms, cudaStream_t s) {

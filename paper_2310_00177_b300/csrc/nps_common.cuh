@@ -83,11 +83,62 @@ struct SolveState {
   int x_upto;           // steps 1..x_upto are in x (the recurrence mode adds several steps to x at once)
   int upd_pending;      // alpha of step k + 1 is known and r_{k+1} = r_k - alpha q not yet formed
   double alpha_slot[kRing];  // alpha of the step whose direction is in each ring slot
+  // PCG / flexible PCG with the network as preconditioner (method != 0): the
+  // ring holds two directions (n_ortho = 1) and the step uses sigma
+  int method;           // kMethodNpsdo, kMethodPcg or kMethodFpcg
+  int fresh;            // the next direction starts a new conjugate sequence (beta = 0)
+  double sigma;         // r_k^T zhat_k of the current direction (zhat = P_net(r_k / ||r_k||))
 };
 
 enum { kDoneRunning = 0, kDoneConverged = 1, kDoneBreakdown = 2, kDoneBadInput = 3 };
+enum { kMethodNpsdo = 0, kMethodPcg = 1, kMethodFpcg = 2 };
 
 __host__ __device__ inline int ring_slot(int iter1, int n_ortho) { return (iter1 - 1) % (n_ortho + 1); }
+
+// Vectors whose dot products with the network output z are taken before the
+// direction is formed, for the iteration k1 = k + 1 being formed:
+//   NPSDO: q_i = A d_i, i = k1-1, k1-2, ... (at most n_ortho, i >= 1) (Alg. 1);
+//   PCG:   the current residual r_k (sigma = r_k^T z);
+//   FPCG:  r_k and, from the second direction on, q_k = A d_k.
+// Returns the count; entry j is the residual when dot_is_residual(st, j).
+__host__ __device__ inline int direction_dot_count(int method, int k1, int n_ortho, int cap) {
+  int c;
+  if (method == kMethodNpsdo) c = n_ortho < k1 - 1 ? n_ortho : k1 - 1;
+  else c = (method == kMethodFpcg && k1 > 1) ? 2 : 1;
+  return c < cap ? c : cap;
+}
+
+// The coefficients of d_{k1} = z - sum_j coef[j] d_{k1-1-j} from the reduced
+// dots t[] (the vectors above), on the single thread of a finishing block.
+//   NPSDO (Alg. 1, classical Gram-Schmidt form): coef[j] = z^T A d_i / d_i^T A d_i.
+//   PCG (preconditioned CG with z = ||r|| P_net(r / ||r||), the network being
+//   linear in r, Sec. 4.2): beta = rho_k / rho_{k-1} with rho = r^T z.  With
+//   zhat = P_net(r / ||r||) and the directions kept scaled by 1 / ||r_k||,
+//   beta becomes sigma_k / sigma_{k-1} (sigma = r^T zhat), the step
+//   alpha = sigma_k / dhat^T A dhat and x, r are unchanged.
+//   FPCG (flexible PCG): beta = z_k^T (r_k - r_{k-1}) / rho_{k-1}; with
+//   r_k - r_{k-1} = -alpha_k A d_k it is -alpha_k zhat^T q_k / sigma_{k-1}
+//   in the scaled form.
+// sigma = 0 or non-finite ends the solve as a breakdown (beta divides by it).
+__device__ __forceinline__ void set_direction_coefs(SolveState *st, const double *t, int cnt) {
+  const int k1 = st->k + 1, no = st->n_ortho;
+  for (int j = 0; j < kMaxOrtho; ++j) st->coef[j] = 0.0;
+  if (st->method == kMethodNpsdo) {
+    for (int j = 0; j < cnt; ++j) st->coef[j] = t[j] / st->dAd[ring_slot(k1 - 1 - j, no)];
+    return;
+  }
+  const double sig = t[0];
+  if (!(sig != 0.0) || !isfinite(sig)) {
+    st->done = kDoneBreakdown;
+    return;
+  }
+  if (!st->fresh && k1 > 1) {
+    const double beta = st->method == kMethodPcg ? sig / st->sigma : -st->alpha * t[1] / st->sigma;
+    st->coef[0] = -beta;
+  }
+  st->fresh = 0;
+  st->sigma = sig;
+}
 
 // ---------------------------------------------------------------------------
 // Deterministic reductions: fixed grid, fixed tree, FP64 above the thread.

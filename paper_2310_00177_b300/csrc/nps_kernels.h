@@ -15,7 +15,7 @@ void set_thread_error(const char *msg);
 void launch_lap(const uint8_t *lab, Dims dm, const float *d, float *q, cudaStream_t s);
 void launch_check_labels(const uint8_t *lab, long long n, unsigned int *bad, cudaStream_t s);
 void launch_init(const uint8_t *lab, long long n, const float *b, float *r, double *x, double *part, double tol,
-                 int max_iter, int n_ortho, SolveState *st, double *hist, cudaStream_t s);
+                 int max_iter, int n_ortho, int method, SolveState *st, double *hist, cudaStream_t s);
 void launch_ortho_final(const double *part, long long n, SolveState *st, cudaStream_t s);
 void launch_direction(long long n, const float *z, float *dring, const SolveState *st, cudaStream_t s);
 void launch_lap_ring(const uint8_t *lab, Dims dm, const float *dring, float *qring, const float *r, double *part,
@@ -53,17 +53,17 @@ void launch_interp(const float *in, Dims coarse, float *out, const SolveState *s
 void launch_combine(long long n, const float *x1, const float *x2, const double *c12, float *out,
                     const SolveState *st, cudaStream_t s);
 void launch_combine1(const uint8_t *lab, long long n, const float *x1, const float *x2, const double *c12, float *z,
-                     const float *qring, double *part, const SolveState *st, cudaStream_t s);
+                     const float *qring, const float *rk, double *part, const SolveState *st, cudaStream_t s);
 
 // kernels_vec4.cu (nx % 4 == 0, n < 2^31)
 // r = mask(b), ||b||^2 -> the solver state; x = 0, or (xhi, xlo) = 0 when
 // xhi is non-null (x is then written by launch_flush_x at the end).
 void launch_init4(const uint8_t *lab, int n, const float *b, float *r, double *x, float *xhi, float *xlo, double *part,
-                  unsigned *ticket, double tol, int max_iter, int n_ortho, SolveState *st, double *hist, int num_sms,
-                  cudaStream_t s);
+                  unsigned *ticket, double tol, int max_iter, int n_ortho, int method, SolveState *st, double *hist,
+                  int num_sms, cudaStream_t s);
 void launch_combine1_4(const uint8_t *lab, int n, const float *x1, const float *x2, const double *c12, float *z,
-                       const float *qring, double *part, unsigned *ticket, SolveState *st, int num_sms,
-                       cudaStream_t s);
+                       const float *qring, const float *r0, const float *r1, double *part, unsigned *ticket,
+                       SolveState *st, int num_sms, cudaStream_t s);
 void launch_direction4(bool defer_x, int n, const float *z, float *dring, float *xhi, float *xlo, const uint32_t *gmask,
                        const SolveState *st, int n_ortho, int num_sms, cudaStream_t s);
 // per-cell stencil codes of the masked Laplacian (once per solve) and q = A d with them
@@ -119,6 +119,8 @@ enum { STREAM_MODE_ALL = 0, STREAM_MODE_ZERO_PURE = 1, STREAM_MODE_FLUID_ONLY = 
 struct StreamFusion {
   const float *qring;
   int nring;
+  const float *rb[2];  // the residual buffers: r_k in rb[k & 1] (rb[1] null: one buffer)
+  int method;          // the solver's method (kMethod*; the state holds the same)
   double *part;     // partial dots: one row of 2 per (unit, consumer warp)
   size_t part_cap;  // doubles part can hold
   unsigned *ticket;

@@ -618,7 +618,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   if (L == 1) {
     ProfScope ps(h, P_COMBINE, s);
     h->launches += 1;
-    launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.part, st, s);
+    launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.r, w.part, st, s);
     return;
   }
   // up pass: r2^l = Interp(x^{l+1}); x2^l = CConv2^l(r2^l); x^l = c1 x1^l + c2 x2^l
@@ -638,7 +638,9 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       }
       if (st && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
         // level-1 CConv2, z = mask_fluid(c1 x1 + c2 x2) and the orthogonalisation dots in one pass
-        const StreamFusion fu{w.qring, kRing, w.part, w.part_cap, w.tickets + kTicketCombine, st};
+        const StreamFusion fu{w.qring,   kRing,     {w.r, fused_update(h, d1) ? w.r_alt : nullptr},
+                              h->cfg.method, w.part,  w.part_cap, w.tickets + kTicketCombine,
+                              st};
         cconv_cached(h, d1, 1, 2, w.r2[1], nullptr, z, nullptr, w.x1[1], c12, st, s, STREAM_MODE_FLUID_ONLY, &fu,
                      nullptr, pu2);
         continue;
@@ -663,9 +665,10 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     h->launches += 1;
     if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], c12, w.xc[l], st, s);
     else if (st && vec4_path(d1))  // fused: dots and orthogonalisation coefficients in one launch
-      launch_combine1_4(lab, (int)d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.part, w.tickets + kTicketCombine, st,
-                        h->num_sms, s);
-    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.part, st, s);
+      launch_combine1_4(lab, (int)d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.r,
+                        fused_update(h, d1) ? w.r_alt : nullptr, w.part, w.tickets + kTicketCombine, st, h->num_sms,
+                        s);
+    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.r, w.part, st, s);
   }
 }
 
@@ -1150,10 +1153,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       // the recurrence mode of the multilevel path keeps x as a double-float pair until the end
       const bool xdf = h->cfg.levels > 1 && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
       launch_init4(lab, (int)d1.n(), b, w.r, x, xdf ? w.xhi : nullptr, xdf ? w.xlo : nullptr, w.part,
-                   w.tickets + kTicketInit, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, h->num_sms, s);
+                   w.tickets + kTicketInit, tol, max_iter, h->cfg.n_ortho, h->cfg.method, w.st, w.hist, h->num_sms, s);
       h->launches += 1;
     } else {
-      launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, w.st, w.hist, s);
+      launch_init(lab, d1.n(), b, w.r, x, w.part, tol, max_iter, h->cfg.n_ortho, h->cfg.method, w.st, w.hist, s);
       h->launches += 2;
     }
   }
@@ -1296,8 +1299,12 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
   if (cfg->kernel_path != NPSOLVE_PATH_CACHED && cfg->kernel_path != NPSOLVE_PATH_CUDA_CORE &&
       cfg->kernel_path != NPSOLVE_PATH_TENSOR)
     return fail(nullptr, NPSOLVE_BAD_ARG, "bad kernel_path");
+  if (cfg->method != NPSOLVE_METHOD_NPSDO && cfg->method != NPSOLVE_METHOD_PCG && cfg->method != NPSOLVE_METHOD_FPCG)
+    return fail(nullptr, NPSOLVE_BAD_ARG, "bad method");
   npsolve *h = new npsolve();
   h->cfg = *cfg;
+  // PCG and FPCG keep one previous direction: the ring of two slots of n_ortho = 1
+  if (cfg->method != NPSOLVE_METHOD_NPSDO) h->cfg.n_ortho = 1;
   h->device = dev;
   h->nsplit = cfg->precision == NPSOLVE_BF16 ? 1 : 3;
   h->num_sms = prop.multiProcessorCount;
