@@ -39,7 +39,7 @@ AFF_PARAMS = 3 * 27 + 1
 
 OK, BAD_ARG, BAD_DIMS, BAD_LABELS, NO_CONVERGENCE, BREAKDOWN = 0, 1, 2, 3, 4, 5
 
-PREC_NETWORK, PREC_IDENTITY, PREC_DENSE = 0, 1, 2
+PREC_NETWORK, PREC_IDENTITY, PREC_DENSE, PREC_NETWORK_SYM = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -296,7 +296,7 @@ def npsdo(labels, b, *, L=4, w=None, tol=1e-6, max_iter=1000, n_ortho=2, residua
     """Alg. 1.  Returns dict(x, iters, status, res_hist, relres)."""
     labels, lp, nx, ny, nz = _lab(labels)
     n = labels.size
-    if prec == PREC_NETWORK:
+    if prec in (PREC_NETWORK, PREC_NETWORK_SYM):
         w, wp = _f64(w)
         assert w.size == weight_count(L)
     else:
@@ -327,7 +327,7 @@ def npcg(labels, b, *, L=4, w=None, tol=1e-6, max_iter=1000, flexible=False, res
     Returns dict(x, iters, status, res_hist, relres) as npsdo does."""
     labels, lp, nx, ny, nz = _lab(labels)
     n = labels.size
-    if prec == PREC_NETWORK:
+    if prec in (PREC_NETWORK, PREC_NETWORK_SYM):
         w, wp = _f64(w)
         assert w.size == weight_count(L)
     else:
@@ -360,6 +360,21 @@ def jacobi_pcg(labels, b, *, tol=1e-6, max_iter=10000):
     st = lib().or_jacobi_pcg(lp, nx, ny, nz, bp, float(tol), int(max_iter), x.ctypes.data_as(_dp),
                              ctypes.byref(it), ctypes.byref(relres))
     return {"x": x, "iters": it.value, "status": st, "relres": relres.value}
+
+
+def network_transpose(labels, L, w, g):
+    """P_net^T g: the input gradient of <g, P_net(I, r)> (the network is linear in r)."""
+    _, gr = network_backward(labels, L, w, np.zeros(np.shape(labels)), g)
+    return gr
+
+
+def asymmetry(labels, L, w, x, y):
+    """The relative asymmetry measure of the appendix's symmetry analysis:
+    S(x, y; I) = |x . P(y) - y . P(x)| / sqrt(|x . P(x)| |y . P(y)|)."""
+    px, py = network(labels, L, w, x), network(labels, L, w, y)
+    xpy, ypx = float(np.sum(x * py)), float(np.sum(y * px))
+    xpx, ypy = float(np.sum(x * px)), float(np.sum(y * py))
+    return abs(xpy - ypx) / np.sqrt(abs(xpx) * abs(ypy))
 
 
 def split_weights(w, L):

@@ -626,10 +626,38 @@ static double dot(const double *a, const double *b, size_t n) {
 
 /* Preconditioner choices for the solver, so that the reductions stated in
  * Sec. 4.1 can be checked: 0 = the network of Alg. 2, 1 = identity (masked),
- * 2 = a dense n x n matrix applied to the masked vector. */
+ * 2 = a dense n x n matrix applied to the masked vector, 3 = the symmetric
+ * variant P_sym,1 = P_net^T P_net of the appendix's symmetry analysis. */
 #define PREC_NETWORK 0
 #define PREC_IDENTITY 1
 #define PREC_DENSE 2
+#define PREC_NETWORK_SYM 3
+
+/* out = P(v) for the preconditioner choices above, restricted to fluid cells
+ * (the network's output restriction, Sec. 4.2).  P_net^T is the input
+ * gradient of <g, P_net(v)> (the network is linear in v), taken from the
+ * reverse of Alg. 2; its weight gradient is discarded. */
+static void apply_prec(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, int prec,
+                       const double *pdense, const double *v, double *out) {
+  size_t n = cells(nx, ny, nz);
+  if (prec == PREC_NETWORK) {
+    or_network(lab, nx, ny, nz, L, w, v, out);
+  } else if (prec == PREC_NETWORK_SYM) {
+    double *t = malloc(sizeof(double) * n), *gw = malloc(sizeof(double) * or_weight_count(L));
+    or_network(lab, nx, ny, nz, L, w, v, t);
+    or_network_backward(lab, nx, ny, nz, L, w, v, t, gw, out);
+    free(t);
+    free(gw);
+  } else if (prec == PREC_IDENTITY) {
+    for (size_t p = 0; p < n; ++p) out[p] = lab[p] == LAB_FLUID ? v[p] : 0.0;
+  } else {
+    for (size_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (size_t j = 0; j < n; ++j) s += pdense[i * n + j] * v[j];
+      out[i] = lab[i] == LAB_FLUID ? s : 0.0;
+    }
+  }
+}
 
 /* Residual modes: 0 = recurrence r_k = r_{k-1} - alpha A d_k, with a true-
  * residual check on exit that restarts from r = b - A x if it fails (at most
@@ -638,7 +666,7 @@ int or_npsdo(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w,
              const double *b, double tol, int max_iter, int n_ortho, int residual_mode, double *x, int *iters,
              double *res_hist, double *final_relres) {
   size_t n = cells(nx, ny, nz);
-  if (prec == PREC_NETWORK) {
+  if (prec == PREC_NETWORK || prec == PREC_NETWORK_SYM) {
     int st = check_dims(nx, ny, nz, L);
     if (st) return st;
   }
@@ -680,17 +708,7 @@ int or_npsdo(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w,
       k += 1;
       /* d_k = P_net(I, r_{k-1} / ||r_{k-1}||) */
       for (size_t p = 0; p < n; ++p) rn[p] = r[p] / nr;
-      if (prec == PREC_NETWORK) {
-        or_network(lab, nx, ny, nz, L, w, rn, d);
-      } else if (prec == PREC_IDENTITY) {
-        for (size_t p = 0; p < n; ++p) d[p] = lab[p] == LAB_FLUID ? rn[p] : 0.0;
-      } else {
-        for (size_t i = 0; i < n; ++i) {
-          double s = 0.0;
-          for (size_t j = 0; j < n; ++j) s += pdense[i * n + j] * rn[j];
-          d[i] = lab[i] == LAB_FLUID ? s : 0.0;
-        }
-      }
+      apply_prec(lab, nx, ny, nz, L, w, prec, pdense, rn, d);
       /* for k - n_ortho <= i < k (and i >= 1): d_k -= (d_k^T A d_i)/(d_i^T A d_i) d_i,
        * in ascending i, each coefficient using the already-updated d_k. */
       int i0 = k - n_ortho;
@@ -815,24 +833,6 @@ int or_jacobi_pcg(const uint8_t *lab, int nx, int ny, int nz, const double *b, d
 /* the preconditioner.                                                      */
 /* ------------------------------------------------------------------------ */
 
-/* out = P(v) for the preconditioner choices of or_npsdo, restricted to fluid
- * cells (the network's output restriction, Sec. 4.2). */
-static void apply_prec(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, int prec,
-                       const double *pdense, const double *v, double *out) {
-  size_t n = cells(nx, ny, nz);
-  if (prec == PREC_NETWORK) {
-    or_network(lab, nx, ny, nz, L, w, v, out);
-  } else if (prec == PREC_IDENTITY) {
-    for (size_t p = 0; p < n; ++p) out[p] = lab[p] == LAB_FLUID ? v[p] : 0.0;
-  } else {
-    for (size_t i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (size_t j = 0; j < n; ++j) s += pdense[i * n + j] * v[j];
-      out[i] = lab[i] == LAB_FLUID ? s : 0.0;
-    }
-  }
-}
-
 /* PCG in the textbook arrangement (Shewchuk 1994, the preconditioned CG
  * algorithm): z_k = P(r_k), rho_k = r_k^T z_k, d_1 = z_0, later
  * d = z_k + beta_k d, alpha = rho_k / d^T A d, x += alpha d, r -= alpha A d.
@@ -848,7 +848,7 @@ int or_npcg(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, 
             const double *b, double tol, int max_iter, int flexible, int residual_mode, double *x, int *iters,
             double *res_hist, double *final_relres) {
   size_t n = cells(nx, ny, nz);
-  if (prec == PREC_NETWORK) {
+  if (prec == PREC_NETWORK || prec == PREC_NETWORK_SYM) {
     int st = check_dims(nx, ny, nz, L);
     if (st) return st;
   }
