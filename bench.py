@@ -13,7 +13,9 @@ Also reported on the same line:
                  buffers in, x back to the host, copies inside the timing)
   fp32_form      ms per solve and iterations of the FP32 form
   solver_variants  PCG and flexible PCG with the same network (BF16 form):
-                 ms per solve, iterations, true relative residual
+                 ms per solve, iterations, true relative residual; PCG with
+                 the symmetric variant P_net^T P_net; the network's relative
+                 asymmetry measure S on random vector pairs
   accuracy       true relative residuals (FP64 oracle Laplacian), iterations
                  of both forms, ||x_bf16 - x_fp32|| / ||x_fp32||
   roofline       the dominant kernel class of a profiled solve (CUDA events
@@ -327,6 +329,29 @@ def main():
         variants[name] = {"ms_per_solve": e0.elapsed_time(e1), "iters": it_v, "relres": rr_v,
                           "status": binding.STATUS_NAMES[st_v]}
         sv.close()
+    # the symmetric variant P_sym,1 = P_net^T P_net with PCG (the appendix's
+    # symmetry analysis; built from the same weights, not retrained), and the
+    # relative asymmetry measure S of the network on three pairs of random
+    # vectors on the fluid cells of this problem
+    sv = binding.Solver(w, levels=4, method=binding.PCG, symmetric=True)
+    xv = torch.empty_like(x_d)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, it_v, rr_v, st_v = sv.solve(lab_d, rhs_d, 1e-6, 500, x=xv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    variants["pcg_symmetric"] = {"ms_per_solve": e0.elapsed_time(e1), "iters": it_v, "relres": rr_v,
+                                 "status": binding.STATUS_NAMES[st_v], "includes_setup_and_graph_capture": True}
+    sv.close()
+    gen = torch.Generator(device=dev).manual_seed(7)
+    fl_d = (lab_d == 1).float()
+    svals = []
+    for _ in range(3):
+        xa = torch.randn(lab.shape, device=dev, generator=gen) * fl_d
+        ya = torch.randn(lab.shape, device=dev, generator=gen) * fl_d
+        svals.append(sol.asymmetry(lab_d, xa, ya)[0])
+    variants["asymmetry_S"] = {"values": svals, "median": float(np.median(svals)),
+                               "vectors": "N(0,1) on fluid cells, 3 pairs"}
 
     # ---- profiled solve: per-kernel-class device time (roofline) -------------
     sol.set_profiling(True)

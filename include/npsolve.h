@@ -102,6 +102,8 @@ typedef struct {
   int residual_mode; /* NPSOLVE_RESIDUAL_RECURRENCE or NPSOLVE_RESIDUAL_EXPLICIT */
   int kernel_path;   /* NPSOLVE_PATH_CACHED, NPSOLVE_PATH_CUDA_CORE or NPSOLVE_PATH_TENSOR */
   int method;        /* NPSOLVE_METHOD_NPSDO (0, the paper's solver), _PCG or _FPCG */
+  int symmetric;     /* 0: the preconditioner is P_net; 1: the symmetric variant P_sym,1 = P_net^T P_net
+                        of the paper's symmetry analysis (appendix), with any method */
 } npsolve_config;
 
 /* Number of FP32 network parameters for L levels (Alg. 2): for each level
@@ -176,6 +178,27 @@ int npsolve_apply_network(npsolve_t h, const uint8_t *labels, int nx, int ny, in
  * c12_host (2 doubles, may be NULL) receives Aff1^l, Aff2^l. */
 int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r,
                                  int level, int which, float *out, double *c12_host, void *stream);
+
+/* The adjoint of npsolve_apply_network: out = P_net^T g = mask_fluid(N^T(mask_fluid(g)))
+ * for the network z = mask_fluid(N(mask_fluid(r))) of Alg. 2, which is
+ * linear in r (Sec. 4.2): the reverse of Alg. 2 without weight gradients
+ * (combinations, CConv^T, trilinear interpolation^T, pooling^T), FP32 on
+ * CUDA cores with the per-cell kernels materialised (27 FP32 per cell of
+ * each level).  g, out: [nz][ny][nx] FP32 device buffers (out written,
+ * 0 off fluid); synchronous on `stream`.  The symmetric variant
+ * P_sym,1 = P_net^T P_net of the paper's symmetry analysis (appendix) is
+ * npsolve_network_transpose(npsolve_apply_network(r)). */
+int npsolve_network_transpose(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *g, float *out,
+                              void *stream);
+
+/* The relative asymmetry measure of the paper's symmetry analysis
+ * (appendix): S(x, y; I) = |x.P(y) - y.P(x)| / sqrt(|x.P(x)| |y.P(y)|)
+ * with P = P_net of this handle (two network applications; FP64 dots of
+ * the FP32 vectors).  x, y: [nz][ny][nx] FP32 device buffers; *S (host)
+ * written; dots_host (optional, host, 4 doubles) receives x.P(y), x.P(x),
+ * y.P(x), y.P(y).  S = 0 when the denominator is 0. */
+int npsolve_asymmetry(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *x, const float *y,
+                      void *stream, double *S, double *dots_host);
 
 /* q = A d, the masked 7-point Laplacian of Sec. 3.2, FP32 (device arrays). */
 int npsolve_apply_laplacian(const uint8_t *labels, int nx, int ny, int nz, const float *d, float *q, void *stream);

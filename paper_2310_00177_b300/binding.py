@@ -31,7 +31,8 @@ class NpsolveError(RuntimeError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("n_ortho", ctypes.c_int), ("precision", ctypes.c_int),
-                ("residual_mode", ctypes.c_int), ("kernel_path", ctypes.c_int), ("method", ctypes.c_int)]
+                ("residual_mode", ctypes.c_int), ("kernel_path", ctypes.c_int), ("method", ctypes.c_int),
+                ("symmetric", ctypes.c_int)]
 
 
 _lib = None
@@ -52,6 +53,8 @@ SIGNATURES = {
                            _i),
     "npsolve_residual_history": ([_vp, _vp, _i, ctypes.POINTER(_i)], _i),
     "npsolve_apply_network": ([_vp, _vp, _i, _i, _i, _vp, _vp, _vp], _i),
+    "npsolve_network_transpose": ([_vp, _vp, _i, _i, _i, _vp, _vp, _vp], _i),
+    "npsolve_asymmetry": ([_vp, _vp, _i, _i, _i, _vp, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
     "npsolve_network_intermediate": ([_vp, _vp, _i, _i, _i, _vp, _i, _i, _vp, _vp, _vp], _i),
     "npsolve_apply_laplacian": ([_vp, _i, _i, _i, _vp, _vp, _vp], _i),
     "npsolve_true_residual": ([_vp, _i, _i, _i, _vp, _vp, ctypes.POINTER(_d), _vp], _i),
@@ -141,17 +144,17 @@ class Solver:
     """A solver handle: network weights + device workspace (npsolve_t)."""
 
     def __init__(self, weights, levels=4, n_ortho=2, precision=FP32, residual_mode=RECURRENCE,
-                 kernel_path=PATH_CACHED, method=NPSDO):
+                 kernel_path=PATH_CACHED, method=NPSDO, symmetric=False):
         lib = load_library()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
-        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path, method)
+        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path, method, int(bool(symmetric)))
         h = ctypes.c_void_p()
         st = lib.npsolve_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, ctypes.byref(h))
         if st != OK:
             raise NpsolveError(st, lib.npsolve_last_error(None).decode())
         self._h = h
         self.levels, self.n_ortho, self.precision, self.residual_mode = levels, n_ortho, precision, residual_mode
-        self.kernel_path, self.method = kernel_path, method
+        self.kernel_path, self.method, self.symmetric = kernel_path, method, bool(symmetric)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -290,6 +293,31 @@ class Solver:
                                                     _stream()), self._h)
         return z
 
+    def network_transpose(self, labels, g, out=None):
+        """P_net^T g (the adjoint of apply_network)."""
+        import torch
+
+        nx, ny, nz = _dims(labels)
+        if out is None:
+            out = torch.empty(labels.shape, dtype=torch.float32, device=labels.device)
+        _check(load_library().npsolve_network_transpose(self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                                        _ptr(g, torch.float32, "g"), _ptr(out, torch.float32, "out"),
+                                                        _stream()), self._h)
+        return out
+
+    def asymmetry(self, labels, x, y):
+        """The relative asymmetry measure S(x, y; I) of the network and its four
+        dots (x.P(y), x.P(x), y.P(x), y.P(y))."""
+        import torch
+
+        nx, ny, nz = _dims(labels)
+        S = ctypes.c_double(0.0)
+        dots = np.zeros(4, np.float64)
+        _check(load_library().npsolve_asymmetry(self._h, _ptr(labels, torch.uint8, "labels"), nx, ny, nz,
+                                                _ptr(x, torch.float32, "x"), _ptr(y, torch.float32, "y"), _stream(),
+                                                ctypes.byref(S), dots.ctypes.data_as(_vp)), self._h)
+        return S.value, dots
+
     def network_intermediate(self, labels, r, level, which):
         """which: 'x1', 'r2', 'x2', 'x', 'r1'.  Returns (field, (c1, c2))."""
         import torch
@@ -406,10 +434,11 @@ class Server:
     poll for finished ids, fetch results."""
 
     def __init__(self, weights, levels=4, n_ortho=2, precision=BF16, residual_mode=RECURRENCE,
-                 kernel_path=PATH_CACHED, hbm_budget_bytes=150 << 30, max_active=16, method=NPSDO):
+                 kernel_path=PATH_CACHED, hbm_budget_bytes=150 << 30, max_active=16, method=NPSDO,
+                 symmetric=False):
         lib = load_library()
         w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).ravel())
-        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path, method)
+        cfg = _Config(levels, n_ortho, precision, residual_mode, kernel_path, method, int(bool(symmetric)))
         h = ctypes.c_void_p()
         st = lib.npsolve_server_create(ctypes.byref(cfg), w.ctypes.data_as(_vp), w.size, int(hbm_budget_bytes),
                                        int(max_active), ctypes.byref(h))

@@ -306,6 +306,19 @@ __global__ void k_axpby(const uint8_t *__restrict__ lab, long long n, float alph
   }
 }
 
+// out = alpha[0] * a + beta * b (b optional; zero off fluid when lab is given)
+// with alpha a device scalar (an Aff coefficient of the current image).
+__global__ void k_axpby_dev(const uint8_t *__restrict__ lab, long long n, const double *__restrict__ alpha,
+                            const float *__restrict__ a, float beta, const float *__restrict__ b,
+                            float *__restrict__ out) {
+  const float al = (float)alpha[0];
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    float v = al * a[p] + (b ? beta * b[p] : 0.f);
+    if (lab && lab[p] != kFluid) v = 0.f;
+    out[p] = v;
+  }
+}
+
 // out = alpha * a (masked) with a device scalar alpha = scale / sqrt(*norm2) (loss gradient).
 __global__ void k_scale_by_inv_norm(const uint8_t *__restrict__ lab, long long n, float scale,
                                     const double *__restrict__ norm2, const float *__restrict__ a,
@@ -358,6 +371,10 @@ void launch_dot2(const float *a, const float *b, const float *c, long long n, do
 void launch_axpby(const uint8_t *lab, long long n, float alpha, const float *a, float beta, const float *b, float *out,
                   cudaStream_t s) {
   k_axpby<<<gridn(n, 256), 256, 0, s>>>(lab, n, alpha, a, beta, b, out);
+}
+void launch_axpby_dev(const uint8_t *lab, long long n, const double *alpha, const float *a, float beta,
+                      const float *b, float *out, cudaStream_t s) {
+  k_axpby_dev<<<gridn(n, 256), 256, 0, s>>>(lab, n, alpha, a, beta, b, out);
 }
 void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, const double *norm2, const float *a,
                               float *out, cudaStream_t s) {

@@ -179,6 +179,8 @@ void launch_aff_stats(const uint8_t *lab, const ushort2 *counts, Dims d, double 
                       double *out, cudaStream_t s);
 void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
                  cudaStream_t s);
+void launch_axpby_dev(const uint8_t *lab, long long n, const double *alpha, const float *a, float beta,
+                      const float *b, float *out, cudaStream_t s);
 void launch_axpby(const uint8_t *lab, long long n, float alpha, const float *a, float beta, const float *b, float *out,
                   cudaStream_t s);
 void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, const double *norm2, const float *a,

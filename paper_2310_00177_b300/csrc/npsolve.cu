@@ -504,7 +504,7 @@ bool cached_path(const npsolve *h, Dims d1) {
 // next iteration's level-1 CConv1 (two residual buffers, r_k in buffer k mod
 // 2) on the multilevel, 16-byte-vector, cached path.
 bool fused_update(const npsolve *h, Dims d1) {
-  return h->cfg.levels > 1 && d1.nx % 4 == 0 && d1.n() <= (long long)INT32_MAX &&
+  return h->cfg.levels > 1 && !h->cfg.symmetric && d1.nx % 4 == 0 && d1.n() <= (long long)INT32_MAX &&
          h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE && cached_path(h, d1);
 }
 
@@ -563,7 +563,9 @@ enum { kTicketInit = 0, kTicketCombine = 1, kTicketLap = 2, kTicketUpdate = 3 };
 // last combination.  `unfused` materialises every intermediate (r2, x2) for
 // the per-level inspection entry point.
 void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const float *vscale, float *z,
-                 SolveState *st, cudaStream_t s, bool unfused = false) {
+                 SolveState *st, cudaStream_t s, bool unfused = false, bool dots = true) {
+  // dots = false inside a solve: z is not the preconditioned vector itself (the
+  // symmetric variant applies the transpose to it), so no dots are taken here
   Workspace &w = h->ws;
   const int L = h->cfg.levels;
   const bool cached = cached_path(h, d1);
@@ -618,7 +620,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   if (L == 1) {
     ProfScope ps(h, P_COMBINE, s);
     h->launches += 1;
-    launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.r, w.part, st, s);
+    launch_combine1(lab, d1.n(), w.x1[1], w.x1[1], h->unit_c12, z, w.qring, w.r, w.part, dots ? st : nullptr, s);
     return;
   }
   // up pass: r2^l = Interp(x^{l+1}); x2^l = CConv2^l(r2^l); x^l = c1 x1^l + c2 x2^l
@@ -636,7 +638,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
                      nullptr, l == 2 ? pl2 : nullptr);
         continue;
       }
-      if (st && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
+      if (st && dots && vec4_path(d1) && stream_fusion_ok(h->cfg.n_ortho)) {
         // level-1 CConv2, z = mask_fluid(c1 x1 + c2 x2) and the orthogonalisation dots in one pass
         const StreamFusion fu{w.qring,   kRing,     {w.r, fused_update(h, d1) ? w.r_alt : nullptr},
                               h->cfg.method, w.part,  w.part_cap, w.tickets + kTicketCombine,
@@ -664,11 +666,11 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     ProfScope ps(h, P_COMBINE, s);
     h->launches += 1;
     if (l > 1) launch_combine(level_dims(d1, l).n(), w.x1[l], w.x2[l], c12, w.xc[l], st, s);
-    else if (st && vec4_path(d1))  // fused: dots and orthogonalisation coefficients in one launch
+    else if (st && dots && vec4_path(d1))  // fused: dots and orthogonalisation coefficients in one launch
       launch_combine1_4(lab, (int)d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.r,
                         fused_update(h, d1) ? w.r_alt : nullptr, w.part, w.tickets + kTicketCombine, st, h->num_sms,
                         s);
-    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.r, w.part, st, s);
+    else launch_combine1(lab, d1.n(), w.x1[1], w.x2[1], c12, z, w.qring, w.r, w.part, dots ? st : nullptr, s);
   }
 }
 
@@ -872,6 +874,10 @@ int ensure_train(npsolve *h, Dims d1) {
   auto &t = h->tr;
   const long long n = d1.n();
   if (t.cap >= n) return NPSOLVE_OK;
+  if (h->ws.graph) {  // a symmetric-variant iteration graph refers to these buffers
+    cudaGraphExecDestroy(h->ws.graph);
+    h->ws.graph = nullptr;
+  }
   free_train(h);
   const int L = h->cfg.levels;
   long long cl = n;
@@ -1009,6 +1015,52 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std
   return NPSOLVE_OK;
 }
 
+// out = P_net^T g: the adjoint of the network z = mask_fluid(N(mask_fluid(r)))
+// (Alg. 2 is linear in r, Sec. 4.2), needed for the symmetric variant
+// P_sym,1 = P_net^T P_net of the paper's symmetry analysis (appendix).  The
+// reverse of Alg. 2 without the weight gradients: combinations (c1, c2 read
+// on the device), CConv^T by gathering K_a(q - a) g(q - a) from the
+// materialised kernels, trilinear interpolation^T and pooling^T.  No host
+// synchronisation, so it can be captured in the iteration graph; the train
+// workspace must be sized for d1 (ensure_train).
+void run_network_transpose(npsolve *h, const uint8_t *lab, Dims d1, const float *g, float *out, cudaStream_t s) {
+  Workspace &w = h->ws;
+  auto &t = h->tr;
+  const int L = h->cfg.levels;
+  const long long n1 = d1.n();
+  auto lc = [&](int l) { return l == 1 ? nullptr : w.counts[l]; };
+  auto ll = [&](int l) { return l == 1 ? lab : nullptr; };
+  for (int l = 1; l <= L; ++l) {
+    const size_t nl = (size_t)level_dims(d1, l).n();
+    cudaMemsetAsync(t.gx[l], 0, sizeof(float) * nl, s);  // errors surface at the caller's launch check
+    cudaMemsetAsync(t.gx1[l], 0, sizeof(float) * nl, s);
+  }
+  launch_axpby(lab, n1, 1.f, g, 0.f, nullptr, t.gx[1], s);  // output restriction
+  h->launches += 1;
+  if (L == 1) {
+    launch_axpby(nullptr, n1, 1.f, t.gx[1], 0.f, nullptr, t.gx1[1], s);
+    h->launches += 1;
+  }
+  for (int l = 1; l < L; ++l) {  // up pass in reverse: combination, CConv2, interpolation
+    const Dims dl = level_dims(d1, l);
+    const long long nl = dl.n();
+    launch_axpby_dev(nullptr, nl, w.affc + 2 * l, t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);       // gx1 += c1 gx
+    launch_axpby_dev(nullptr, nl, w.affc + 2 * l + 1, t.gx[l], 0.f, nullptr, t.tmp, s);         // g x2 = c2 gx
+    launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2 + 1, t.K, s);
+    launch_cconv_transpose(t.K, t.tmp, dl, t.tmp2, s);                                          // g r2
+    launch_interp_adjoint_add(t.tmp2, level_dims(d1, l + 1), (l + 1 == L) ? t.gx1[L] : t.gx[l + 1], s);
+    h->launches += 5;
+  }
+  for (int l = L; l >= 1; --l) {  // down pass in reverse: CConv1 and pooling
+    const Dims dl = level_dims(d1, l);
+    launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2, t.K, s);
+    launch_cconv_transpose(t.K, t.gx1[l], dl, t.tmp, s);  // g r1^l
+    if (l > 1) launch_pool_adjoint_add(t.tmp, level_dims(d1, l - 1), t.gx1[l - 1], s);
+    else launch_axpby(lab, n1, 1.f, t.tmp, 0.f, nullptr, out, s);  // input restriction
+    h->launches += 3;
+  }
+}
+
 // Loss = || b - A P_net(I, b) || (Sec. 4.2.3) and its weight gradient
 // accumulated into gw (scaled by `weight`).
 int loss_grad_impl(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *loss, std::vector<double> &gw,
@@ -1036,7 +1088,20 @@ void enqueue_iteration(npsolve *h, const uint8_t *lab, Dims d1, const float *b, 
   Workspace &w = h->ws;
   const long long n = d1.n();
   const bool fast = vec4_path(d1) && h->cfg.levels > 1;
-  run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s);
+  const bool sym = h->cfg.symmetric != 0;
+  run_network(h, lab, d1, w.r, &w.st->rscale, w.z, w.st, s, false, !sym);
+  if (sym) {
+    // P_sym,1 = P_net^T P_net (appendix, symmetry analysis): the transpose of the
+    // network applied to its output, then the dots of the combination kernel
+    // (unit coefficients) on the symmetric preconditioned vector
+    ProfScope ps(h, P_COMBINE, s);
+    run_network_transpose(h, lab, d1, w.z, h->tr.res, s);
+    h->launches += 1;
+    if (vec4_path(d1) && h->cfg.levels > 1)
+      launch_combine1_4(lab, (int)n, h->tr.res, h->tr.res, h->unit_c12, w.z, w.qring, w.r, nullptr, w.part,
+                        w.tickets + kTicketCombine, w.st, h->num_sms, s);
+    else launch_combine1(lab, n, h->tr.res, h->tr.res, h->unit_c12, w.z, w.qring, w.r, w.part, w.st, s);
+  }
   const bool recur = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
   const bool fused = fused_update(h, d1);  // the step's r update happens in the next level-1 CConv1
   h->launches += fast ? (recur ? (fused ? 2 : 3) : 5) : (recur ? 6 : 7);
@@ -1132,6 +1197,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
   const Dims d1{nx, ny, nz};
   st = ensure_ws(h, d1, max_iter + 1);
   if (st) return st;
+  if (h->cfg.symmetric) {  // the transpose pass of P_sym uses the train workspace
+    st = ensure_train(h, d1);
+    if (st) return st;
+  }
   Workspace &w = h->ws;
   {
     ProfScope ps(h, P_SETUP, s);
@@ -1301,6 +1370,7 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
     return fail(nullptr, NPSOLVE_BAD_ARG, "bad kernel_path");
   if (cfg->method != NPSOLVE_METHOD_NPSDO && cfg->method != NPSOLVE_METHOD_PCG && cfg->method != NPSOLVE_METHOD_FPCG)
     return fail(nullptr, NPSOLVE_BAD_ARG, "bad method");
+  if (cfg->symmetric != 0 && cfg->symmetric != 1) return fail(nullptr, NPSOLVE_BAD_ARG, "symmetric must be 0 or 1");
   npsolve *h = new npsolve();
   h->cfg = *cfg;
   // PCG and FPCG keep one previous direction: the ring of two slots of n_ortho = 1
@@ -1455,6 +1525,66 @@ int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int
 int npsolve_apply_network(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *r, float *z,
                           void *stream) {
   return npsolve_network_intermediate(h, labels, nx, ny, nz, r, 0, 0, z, nullptr, stream);
+}
+
+// Shared prologue of the symmetry entry points: dims, workspaces (the train
+// workspace holds the transpose's buffers), image setup and the label check.
+static int symmetry_setup(npsolve *h, const uint8_t *labels, Dims d1, cudaStream_t s) {
+  int st = check_dims(h, d1.nx, d1.ny, d1.nz);
+  if (st) return st;
+  CK(h, cudaSetDevice(h->device));
+  st = ensure_ws(h, d1, 1);
+  if (st) return st;
+  st = ensure_train(h, d1);
+  if (st) return st;
+  st = setup_image(h, labels, d1, s, true);
+  if (st) return st;
+  CK(h, cudaMemcpyAsync(h->ws.h_flag, h->ws.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  if (h->ws.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
+  return NPSOLVE_OK;
+}
+
+int npsolve_network_transpose(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *g, float *out,
+                              void *stream) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!labels || !g || !out) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d1{nx, ny, nz};
+  int st = symmetry_setup(h, labels, d1, s);
+  if (st) return st;
+  run_network_transpose(h, labels, d1, g, out, s);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(s));
+  return NPSOLVE_OK;
+}
+
+int npsolve_asymmetry(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz, const float *x, const float *y,
+                      void *stream, double *S, double *dots_host) {
+  if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
+  if (!labels || !x || !y || !S) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Dims d1{nx, ny, nz};
+  int st = symmetry_setup(h, labels, d1, s);
+  if (st) return st;
+  Workspace &w = h->ws;
+  auto &t = h->tr;
+  const long long n = d1.n();
+  run_network(h, labels, d1, x, nullptr, w.z, nullptr, s);  // P(x)
+  CK(h, cudaMemcpyAsync(t.res, w.z, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  run_network(h, labels, d1, y, nullptr, w.z, nullptr, s);  // P(y)
+  launch_dot2(x, w.z, t.res, n, t.part, t.out, s);          // x.P(y), x.P(x)
+  launch_dot2(y, t.res, w.z, n, t.part, t.out + 2, s);      // y.P(x), y.P(y)
+  h->launches += 4;
+  double d[4] = {0, 0, 0, 0};
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(d, t.out, sizeof(d), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaStreamSynchronize(s));
+  const double den = sqrt(fabs(d[1]) * fabs(d[3]));
+  *S = den > 0.0 ? fabs(d[0] - d[2]) / den : 0.0;
+  if (dots_host)
+    for (int i = 0; i < 4; ++i) dots_host[i] = d[i];
+  return check_umma_err(h);
 }
 
 int npsolve_apply_laplacian(const uint8_t *labels, int nx, int ny, int nz, const float *d, float *q, void *stream) {
