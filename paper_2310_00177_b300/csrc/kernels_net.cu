@@ -292,63 +292,86 @@ __device__ __forceinline__ float lerp_hi(float b, float c) { return 0.75f * b + 
 
 // skip (optional): one byte per (32 x 8 fine tile, fine plane), tile-major;
 // blocks whose two planes are both marked non-zero are not written (no later read).
+//
+// Each thread marches along z over zc coarse planes: it keeps the x- and
+// y-interpolated values of the coarse planes kz-1, kz, kz+1 (4 fine columns x
+// 2 fine rows each) and loads one new plane's three coarse rows per step, so
+// the loads and the x/y interpolation are shared by the two fine planes of a
+// coarse plane and by the neighbouring coarse planes.  The arithmetic per
+// output does not depend on zc (same operands, same order).  zc = 4 on grids
+// with threads to spare (at least 2^19 of one block each), else 1.
+constexpr int kInterpZC = 4;
+
+__device__ __forceinline__ void interp_xy(const float *__restrict__ in, int cx, int cy, int q, int jy, int zc,
+                                          float (&yl)[2][4]) {
+  const int xm = max(2 * q - 1, 0), x0 = 2 * q, xp = min(2 * q + 2, cx - 1);  // x0, x0 + 1 by one 8-byte load
+  const int ys[3] = {max(jy - 1, 0), jy, min(jy + 1, cy - 1)};
+  float xl[3][4];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float *row = in + ((long long)zc * cy + ys[b]) * cx;
+    const float2 v01 = __ldg(reinterpret_cast<const float2 *>(row + x0));
+    const float vm = __ldg(row + xm), vp = __ldg(row + xp);
+    xl[b][0] = q > 0 ? lerp_lo(vm, v01.x) : v01.x;
+    xl[b][1] = lerp_hi(v01.x, v01.y);
+    xl[b][2] = lerp_lo(v01.x, v01.y);
+    xl[b][3] = lerp_hi(v01.y, vp);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    yl[0][i] = jy > 0 ? lerp_lo(xl[0][i], xl[1][i]) : xl[1][i];
+    yl[1][i] = lerp_hi(xl[1][i], xl[2][i]);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_interp_blk(const float *__restrict__ in, Dims coarse, float *__restrict__ out,
-                                                    const uint8_t *__restrict__ skip, const SolveState *st) {
+                                                    const uint8_t *__restrict__ skip, int zc, const SolveState *st) {
   if (st && st->done) return;
   const int cx = coarse.nx, cy = coarse.ny, cz = coarse.nz;
-  const int fx = 2 * cx, fy = 2 * cy;
+  const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
   const int nq = fx >> 2;  // x groups of 4 fine cells (cx / 2)
-  const long long nthr = (long long)nq * cy * cz;
+  const int nzc = (cz + zc - 1) / zc;
+  const long long nthr = (long long)nq * cy * nzc;
   const long long fxy = (long long)fx * fy;
   // 32-bit index arithmetic (a fine grid below 2^31 cells has nthr < 2^27)
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < (unsigned)nthr; t += gridDim.x * blockDim.x) {
     const int q = (int)(t % (unsigned)nq);
     const unsigned r = t / (unsigned)nq;
-    const int jy = (int)(r % (unsigned)cy), kz = (int)(r / (unsigned)cy);  // fine rows 2jy, 2jy+1; planes 2kz, 2kz+1
+    const int jy = (int)(r % (unsigned)cy), kc = (int)(r / (unsigned)cy);  // fine rows 2jy, 2jy+1
+    const int k0 = kc * zc, k1 = min(k0 + zc, cz);
+    const uint8_t *sk = nullptr;
     if (skip) {
-      const int fz = 2 * cz;
-      const size_t nt = (size_t)((4 * q) / 32) + (size_t)((2 * jy) / 8) * (size_t)((fx + 31) / 32);
-      if (skip[nt * fz + 2 * kz] && skip[nt * fz + 2 * kz + 1]) continue;
+      sk = skip + ((size_t)((4 * q) / 32) + (size_t)((2 * jy) / 8) * (size_t)((fx + 31) / 32)) * fz;
+      bool all = true;
+      for (int kz = k0; kz < k1; ++kz) all = all && sk[2 * kz] && sk[2 * kz + 1];
+      if (all) continue;
     }
-    const int xm = max(2 * q - 1, 0), x0 = 2 * q, x1 = 2 * q + 1, xp = min(2 * q + 2, cx - 1);
-    const int ym = max(jy - 1, 0), yp = min(jy + 1, cy - 1);
-    const int zm = max(kz - 1, 0), zp = min(kz + 1, cz - 1);
-    const int ys[3] = {ym, jy, yp}, zs[3] = {zm, kz, zp};
-    // x-interpolated values of the 3 x 3 coarse rows at the 4 fine columns
-    float xl[3][3][4];
+    float ym[2][4], yc[2][4], yp[2][4];  // coarse planes kz-1, kz, kz+1 (clamped)
+    interp_xy(in, cx, cy, q, jy, max(k0 - 1, 0), ym);
+    interp_xy(in, cx, cy, q, jy, k0, yc);
+    for (int kz = k0; kz < k1; ++kz) {
+      interp_xy(in, cx, cy, q, jy, min(kz + 1, cz - 1), yp);
+      if (!sk || !(sk[2 * kz] && sk[2 * kz + 1])) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+        for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float *row = in + ((long long)zs[a] * cy + ys[b]) * cx;
-        const float vm = __ldg(row + xm), v0 = __ldg(row + x0), v1 = __ldg(row + x1), vp = __ldg(row + xp);
-        xl[a][b][0] = q > 0 ? lerp_lo(vm, v0) : v0;
-        xl[a][b][1] = lerp_hi(v0, v1);
-        xl[a][b][2] = lerp_lo(v0, v1);
-        xl[a][b][3] = lerp_hi(v1, vp);
+          for (int dy = 0; dy < 2; ++dy) {
+            float o[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              o[i] = dz == 0 ? (kz > 0 ? lerp_lo(ym[dy][i], yc[dy][i]) : yc[dy][i]) : lerp_hi(yc[dy][i], yp[dy][i]);
+            const long long p = (long long)(2 * kz + dz) * fxy + (long long)(2 * jy + dy) * fx + 4 * q;
+            *reinterpret_cast<float4 *>(out + p) = make_float4(o[0], o[1], o[2], o[3]);
+          }
       }
-    // then y: fine rows 2jy (from coarse rows jy-1, jy) and 2jy+1 (jy, jy+1)
-    float yl[3][2][4];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+      for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        yl[a][0][i] = jy > 0 ? lerp_lo(xl[a][0][i], xl[a][1][i]) : xl[a][1][i];
-        yl[a][1][i] = lerp_hi(xl[a][1][i], xl[a][2][i]);
-      }
-    // then z, and the four 16-byte rows of the block
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy) {
-        float o[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          o[i] = dz == 0 ? (kz > 0 ? lerp_lo(yl[0][dy][i], yl[1][dy][i]) : yl[1][dy][i])
-                         : lerp_hi(yl[1][dy][i], yl[2][dy][i]);
-        const long long p = (long long)(2 * kz + dz) * fxy + (long long)(2 * jy + dy) * fx + 4 * q;
-        *reinterpret_cast<float4 *>(out + p) = make_float4(o[0], o[1], o[2], o[3]);
-      }
+        for (int i = 0; i < 4; ++i) {
+          ym[dy][i] = yc[dy][i];
+          yc[dy][i] = yp[dy][i];
+        }
+    }
   }
 }
 
@@ -445,8 +468,10 @@ void launch_pool(const float *in, Dims fine, float *out, const SolveState *st, c
 void launch_interp(const float *in, Dims coarse, float *out, const SolveState *st, cudaStream_t s,
                    const uint8_t *skip) {
   if (coarse.nx % 2 == 0) {  // fine rows of a multiple of 4 cells: 16-byte stores
-    k_interp_blk<<<grid_for((long long)(coarse.nx / 2) * coarse.ny * coarse.nz, 256), 256, 0, s>>>(in, coarse, out,
-                                                                                                    skip, st);
+    const long long blocks = (long long)(coarse.nx / 2) * coarse.ny * coarse.nz;
+    const int zc = blocks >= (1LL << 19) ? kInterpZC : 1;
+    const long long nthr = (long long)(coarse.nx / 2) * coarse.ny * ((coarse.nz + zc - 1) / zc);
+    k_interp_blk<<<grid_for(nthr, 256), 256, 0, s>>>(in, coarse, out, skip, zc, st);
     return;
   }
   k_interp<<<grid_for(coarse.n() * 8, 256), 256, 0, s>>>(in, coarse, out, st);
