@@ -782,6 +782,33 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       CK(h, cudaMemcpyAsync(w.h_kskip2, w.kskip2 + nsk2, (size_t)nsk2, cudaMemcpyDeviceToHost, s));
     }
     CK(h, cudaStreamSynchronize(s));
+    for (int l = 1; l <= L; ++l) {
+      const int nblk = l < L ? 2 : 1;
+      for (int t = 0; t < nblk; ++t) {
+        const int idx = l * 2 + t;
+        const size_t need = (size_t)w.h_ktotal[2 * l] + 4;
+        if (need > w.kcap[idx]) {
+          if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old cache buffer
+          w.graph = nullptr;
+          CK(h, cudaStreamSynchronize(s));
+          if (w.kcache[idx]) w.bytes -= w.kcap[idx] * (size_t)cached_entry_bytes(bf16) + 256;
+          cudaFree(w.kcache[idx]);
+          w.kcache[idx] = nullptr;
+          const size_t cap = (need + need / 4 + 3) & ~(size_t)3;
+          CK(h, dalloc(&w.bytes, (uint8_t **)&w.kcache[idx], cap * cached_entry_bytes(bf16)));
+          w.kcap[idx] = cap;
+        }
+      }
+      // kernel generation on the tensor cores where the image counts are exact in BF16 (<= 64 fine cells)
+      const bool tc = l <= 3;
+      const size_t wb = (size_t)umma_weight_bytes(3);
+      launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->cw + l * 2,
+                      nblk, w.kdesc[l], w.kcache[l * 2], nblk > 1 ? w.kcache[l * 2 + 1] : nullptr,
+                      tc ? h->uw + (size_t)(l * 2) * wb : nullptr, tc ? h->uw + (size_t)(l * 2 + 1) * wb : nullptr,
+                      h->nsplit, h->umma_err, h->num_sms, s);
+      h->launches += 1;
+    }
+    // the unit lists are built on the host while the GPU generates the kernels
     {
       // the level-1 units with work: CConv1 (a window that is not pure solid or
       // air) and CConv2 (a fluid cell), each with its plane chunk
@@ -808,32 +835,6 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
         if (w.un2) CK(h, cudaMemcpyAsync(w.ulist2, w.h_ulist2, sizeof(int) * (size_t)w.un2, cudaMemcpyHostToDevice, s));
         w.ulist2_ok = true;
       }
-    }
-    for (int l = 1; l <= L; ++l) {
-      const int nblk = l < L ? 2 : 1;
-      for (int t = 0; t < nblk; ++t) {
-        const int idx = l * 2 + t;
-        const size_t need = (size_t)w.h_ktotal[2 * l] + 4;
-        if (need > w.kcap[idx]) {
-          if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old cache buffer
-          w.graph = nullptr;
-          CK(h, cudaStreamSynchronize(s));
-          if (w.kcache[idx]) w.bytes -= w.kcap[idx] * (size_t)cached_entry_bytes(bf16) + 256;
-          cudaFree(w.kcache[idx]);
-          w.kcache[idx] = nullptr;
-          const size_t cap = (need + need / 4 + 3) & ~(size_t)3;
-          CK(h, dalloc(&w.bytes, (uint8_t **)&w.kcache[idx], cap * cached_entry_bytes(bf16)));
-          w.kcap[idx] = cap;
-        }
-      }
-      // kernel generation on the tensor cores where the image counts are exact in BF16 (<= 64 fine cells)
-      const bool tc = l <= 3;
-      const size_t wb = (size_t)umma_weight_bytes(3);
-      launch_generate(bf16, l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->cw + l * 2,
-                      nblk, w.kdesc[l], w.kcache[l * 2], nblk > 1 ? w.kcache[l * 2 + 1] : nullptr,
-                      tc ? h->uw + (size_t)(l * 2) * wb : nullptr, tc ? h->uw + (size_t)(l * 2 + 1) * wb : nullptr,
-                      h->nsplit, h->umma_err, h->num_sms, s);
-      h->launches += 1;
     }
   }
   CK(h, cudaGetLastError());
