@@ -28,6 +28,9 @@ Also reported on the same line:
                  workload: 512 requests, Poisson arrivals at 200/s, sizes
                  64^3, 128^3, 192^3, 256^3, frames of evolving scenes, HBM
                  budget 150 GB (rank 0 only; --no-serve skips it)
+  slosh128_vs_jacobi_pcg  a 128^3 problem, FP32 form, against Jacobi-PCG on the
+                 same GPU (ms per solve and iterations, both to 1e-6)
+  train_step     ms per training step on a batch of 8 x 64^3 + 8 x 128^3
   cpu_baseline   the FP64 CPU oracle on a bounded sample of the same solve
   clocks         nvidia-smi samples taken during the timed region
 
@@ -240,7 +243,7 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    from paper_2310_00177_b300 import binding
+    from paper_2310_00177_b300 import binding, synth
 
     lab, rhs = workload(args.n)
     w, wdesc = load_weights()
@@ -353,6 +356,48 @@ def main():
     variants["asymmetry_S"] = {"values": svals, "median": float(np.median(svals)),
                                "vectors": "N(0,1) on fluid cells, 3 pairs"}
 
+    # ---- the 128^3 problem (FP32 form, trained network) against Jacobi-PCG on
+    # the same GPU, both to 1e-6 (device-resident inputs, one warm-up solve each)
+    lab128 = synth.slosh_scene(128, 2000)
+    rhs128 = synth.rhs_normal(lab128, 2001).astype(np.float32)
+    l128, b128 = torch.from_numpy(lab128).to(dev), torch.from_numpy(rhs128).to(dev)
+    x128 = torch.empty(lab128.shape, dtype=torch.float64, device=dev)
+    s128 = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
+    cmp128 = {}
+    for name, run in (("npsdo_fp32", lambda: s128.solve(l128, b128, 1e-6, args.max_iter, x=x128)),
+                      ("jacobi_pcg", lambda: binding.jacobi_pcg(l128, b128, 1e-6, 100000, x=x128))):
+        run()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, it_c, rr_c, st_c = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cmp128[name] = {"ms_per_solve": e0.elapsed_time(e1), "iters": it_c, "relres": rr_c,
+                        "status": binding.STATUS_NAMES[st_c]}
+    s128.close()
+
+    # ---- one training step (Sec. 4.2.3): a batch of 8 systems at 64^3 and 8 at
+    # 128^3, loss, hand-written backward and the Adam update (N(0,1) right-hand
+    # sides here: the step's cost does not depend on them)
+    st_sol = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
+    tl, tb = [], []
+    for i, nn in enumerate([64] * 8 + [128] * 8):
+        lt = synth.slosh_scene(nn, 5000 + i)
+        bt = synth.rhs_normal(lt, 6000 + i).astype(np.float32)
+        bt /= max(float(np.linalg.norm(bt)), 1e-30)
+        tl.append(torch.from_numpy(lt).to(dev))
+        tb.append(torch.from_numpy(bt).to(dev))
+    st_sol.train_step(tl, tb, lr=1e-30)
+    torch.cuda.synchronize()
+    t_tr = time.perf_counter()
+    n_tr = 3
+    for _ in range(n_tr):
+        loss_tr = st_sol.train_step(tl, tb, lr=1e-30)
+    torch.cuda.synchronize()
+    train = {"ms_per_step": (time.perf_counter() - t_tr) * 1e3 / n_tr, "batch": "8 x 64^3 + 8 x 128^3",
+             "loss": loss_tr, "note": "lr 1e-30: the timed Adam steps leave the FP32 weights unchanged"}
+    st_sol.close()
+
     # ---- profiled solve: per-kernel-class device time (roofline) -------------
     sol.set_profiling(True)
     sol.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x_d)
@@ -457,6 +502,8 @@ def main():
                 "d2h_bytes_per_step": int(n * 8)},
         "fp32_form": {"ms_per_solve": fp32_ms, "iters": it_fp32},
         "solver_variants": variants,
+        "slosh128_vs_jacobi_pcg": cmp128,
+        "train_step": train,
         "served": served,
         "accuracy": accuracy,
         "roofline": roof,
