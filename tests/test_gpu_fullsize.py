@@ -1,0 +1,124 @@
+"""Parity at the benchmark's full size: the 256^3 sloshing problem (scene
+seed 3000, right-hand side seed 3001, the trained L = 4 network), in the
+configuration bench.py times.
+
+* The FP32-form solve against the FP64 oracle's own solve of the same
+  problem: the iteration count and the residual history stored by
+  oracle/count_iterations.py (a committed script that calls only the oracle;
+  it takes about 25 minutes on the host cores, so its result is stored).  The
+  oracle's last two residuals are 8% below and 9% above tol ||b||, outside the
+  band where FP32 rounding could move the stop, so the count must match.
+* The returned x of both forms through the property that holds at any size:
+  its FP64 true residual ||b - A x|| / ||b||, with the oracle's Laplacian,
+  below the tolerance.
+* The Laplacian on the whole grid, element by element.
+* The level-1 CConv1 output on sampled cells, each against the oracle's
+  CConv on the 3 x 3 x 3 crop around it (the output of a cell depends only on
+  the image and the input in its window; cells outside the grid are solid
+  with a zero input).  Tolerance: 1e-5 of the field's largest magnitude.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_00177_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+WEIGHTS = os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32")
+
+
+def _b():
+    from paper_2310_00177_b300 import binding
+
+    return binding
+
+
+@pytest.fixture(scope="module")
+def problem():
+    lab = synth.slosh_scene(256, 3000)
+    rhs = synth.rhs_normal(lab, 3001).astype(np.float32)
+    w = np.fromfile(WEIGHTS, np.float32)
+    stored = json.load(open(os.path.join(ROOT, "oracle", "iterations_slosh256.json")))
+    assert stored["weights_sha256_16"] == hashlib.sha256(open(WEIGHTS, "rb").read()).hexdigest()[:16]
+    return lab, rhs, w, stored
+
+
+def _true_rel(lab, rhs, x):
+    bm = np.where(lab == 1, rhs.astype(np.float64), 0.0)
+    return float(np.linalg.norm(bm - oracle.lap_apply(lab, x)) / np.linalg.norm(bm))
+
+
+def test_fp32_solve_matches_oracle_count_and_history(problem):
+    b = _b()
+    lab, rhs, w, stored = problem
+    h = np.array(stored["res_hist"])
+    assert h[-1] < 0.95e-6 and h[-2] > 1.05e-6  # the oracle's stop is clear of the threshold
+    s = b.Solver(w, levels=4, n_ortho=2, precision=b.FP32)
+    x, iters, relres, st = s.solve(torch.from_numpy(lab).cuda(), torch.from_numpy(rhs).cuda(), 1e-6, 1000)
+    assert st == b.OK and iters == stored["iters"]
+    hist = s.residual_history()
+    np.testing.assert_allclose(hist / hist[0], h, rtol=1e-3, atol=1e-9)
+    xg = x.cpu().numpy()
+    tr = _true_rel(lab, rhs, xg)
+    assert tr < 1e-6 and abs(tr - relres) <= 1e-3 * tr
+    s.close()
+
+
+def test_bf16_solve_converges_with_oracle_true_residual(problem):
+    b = _b()
+    lab, rhs, w, stored = problem
+    s = b.Solver(w, levels=4, n_ortho=2, precision=b.BF16)
+    x, iters, relres, st = s.solve(torch.from_numpy(lab).cuda(), torch.from_numpy(rhs).cuda(), 1e-6, 1000)
+    assert st == b.OK and abs(iters - stored["iters"]) <= 3
+    assert _true_rel(lab, rhs, x.cpu().numpy()) < 1e-6
+    s.close()
+
+
+def test_laplacian_full_grid(problem):
+    b = _b()
+    lab = problem[0]
+    d = np.random.default_rng(5).standard_normal(lab.shape).astype(np.float32)
+    q = b.apply_laplacian(torch.from_numpy(lab).cuda(), torch.from_numpy(d).cuda()).cpu().numpy()
+    qo = oracle.lap_apply(lab, d.astype(np.float64))
+    assert np.abs(q - qo).max() <= 4 * np.finfo(np.float32).eps * 7 * np.abs(d).max()
+    assert not q[lab != 1].any()
+
+
+def test_level1_cconv_sampled_cells(problem):
+    b = _b()
+    lab, rhs, w, _ = problem
+    r = np.random.default_rng(6).standard_normal(lab.shape).astype(np.float32)
+    s = b.Solver(w, levels=4, precision=b.FP32)
+    x1, _ = s.network_intermediate(torch.from_numpy(lab).cuda(), torch.from_numpy(r).cuda(), 1, "x1")
+    x1 = x1.cpu().numpy()
+    s.close()
+    blk = oracle.split_weights(w.astype(np.float64), 4)[1]["cconv1"]
+    W, B = blk[: 27 * 3 * 27].reshape(27, 3, 27), blk[27 * 3 * 27:]
+    v = np.where(lab == 1, r.astype(np.float64), 0.0)  # the network's input restriction
+    n = lab.shape[0]
+    rng = np.random.default_rng(7)
+    fluid = np.argwhere(lab == 1)
+    cells = [tuple(c) for c in fluid[rng.choice(len(fluid), 150, replace=False)]]
+    cells += [tuple(c) for c in rng.integers(0, n, size=(100, 3))]
+    cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n // 2, n - 1), (n - 1, 0, n // 2), (n // 2, n - 1, 0)]
+    scale = np.abs(x1).max()
+    for (z, y, x) in cells:
+        cl = np.zeros((3, 3, 3), np.uint8)  # solid outside the grid
+        cv = np.zeros((3, 3, 3))
+        for dz in range(3):
+            for dy in range(3):
+                for dx in range(3):
+                    zz, yy, xx = z + dz - 1, y + dy - 1, x + dx - 1
+                    if 0 <= zz < n and 0 <= yy < n and 0 <= xx < n:
+                        cl[dz, dy, dx] = lab[zz, yy, xx]
+                        cv[dz, dy, dx] = v[zz, yy, xx]
+        want = oracle.cconv(oracle.image(cl), W, B, cv)[1, 1, 1]
+        assert abs(x1[z, y, x] - want) <= 1e-5 * scale, ((z, y, x), x1[z, y, x], want)
