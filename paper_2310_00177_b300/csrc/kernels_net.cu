@@ -134,10 +134,15 @@ __global__ void __launch_bounds__(256) k_aff_counts(ImgSrc im, Dims dm, unsigned
 // axis stays inside the window sum of offset o unless o pushes it out.
 __device__ __forceinline__ bool keeps(int c, int o) { return !((o == 1 && (c & 1)) || (o == -1 && (c & 2))); }
 
-__global__ void k_aff_from_counts(const unsigned long long *__restrict__ cnt, const AffW *a1, const AffW *a2,
+// 128 threads: the 128 counters are loaded into shared memory at once (one
+// load each), then 27 threads form the window sums.
+__global__ void k_aff_from_counts(const unsigned long long *__restrict__ gcnt, const AffW *a1, const AffW *a2,
                                   long long n, double *out) {
+  __shared__ unsigned long long cnt[128];
   __shared__ double t1[27], t2[27];
   const int l = threadIdx.x;
+  cnt[l] = gcnt[l];
+  __syncthreads();
   if (l < 27) {
     const int ox = l % 3 - 1, oy = (l / 3) % 3 - 1, oz = l / 9 - 1;
     double sf = 0.0, sa = 0.0;  // exact: integer counts below 2^53
@@ -445,7 +450,7 @@ void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *
   long long g = (rows + 7) / 8;
   if (g > 148LL * 8) g = 148LL * 8;
   k_aff_counts<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(im, dm, cnt);
-  k_aff_from_counts<<<1, 32, 0, s>>>(cnt, a1, a2, dm.n(), out);
+  k_aff_from_counts<<<1, 128, 0, s>>>(cnt, a1, a2, dm.n(), out);
 }
 
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,
