@@ -66,7 +66,7 @@ ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
 # CConv1 and CConv2 launches of one iteration, the summary kept in profiles/);
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_L1 = (210.4e6 + 214.1e6) / 2  # ncu DRAM bytes per launch: CConv1, fused CConv2 (iteration_kernels_slosh256_bf16.md)
+TRAFFIC_L1 = (210.8e6 + 214.1e6) / 2  # ncu DRAM bytes per launch: CConv1, fused CConv2 (iteration_kernels_slosh256_bf16.md)
 
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
 # (inputs read once, outputs written once).
