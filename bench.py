@@ -184,6 +184,24 @@ def oracle_iterations(n):
     return None, None
 
 
+def max_over_ranks(v, dist, device):
+    """The maximum of a per-rank float over all ranks (the slowest replica's
+    time); v itself without a process group."""
+    if dist is None:
+        return float(v)
+    import torch
+
+    t = torch.tensor([float(v)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(max_total_ms, steps, world):
+    """ms per solve of the whole job: every rank solves `steps` independent
+    problems in the timed region, and the job takes the slowest rank's time."""
+    return max_total_ms / (steps * world)
+
+
 def run_reference(args, rank, world):
     """--impl reference: the FP64 CPU oracle (rank 0 only)."""
     if rank != 0:
@@ -273,13 +291,9 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches_timed = sol.launch_count() - launches0
-    total_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = total_ms / (args.steps * world)
+    value = replica_value(total_ms, args.steps, world)
     x_bf16 = x_d.cpu().numpy()
 
     # ---- end to end through the host-buffer C-ABI call -------------------
@@ -292,12 +306,8 @@ def main():
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(e2e_steps):
         sol.solve_host(lab_h.numpy(), rhs_h.numpy(), 1e-6, args.max_iter, x=x_h.numpy())
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = e2e_ms / world
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, dist, dev)
+    e2e_value = replica_value(e2e_ms, 1, world)
 
     # ---- FP32 form -----------------------------------------------------
     sol32 = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
