@@ -155,6 +155,10 @@ struct npsolve {
   double *unit_c12 = nullptr;      // {1, 0} for L = 1
   Workspace ws;
   cudaStream_t cap_stream = nullptr;
+  // npsolve_solve_host: the right-hand side is uploaded on copy_stream while the
+  // solve's stream runs the setup from the labels; b_ready orders init after it
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t b_ready = nullptr;
   std::string err;
   std::vector<double> last_hist;
   Profiler prof;
@@ -1187,7 +1191,7 @@ int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x
 }
 
 int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const float *b, double tol, int max_iter,
-               cudaStream_t s, double *x, int *iters, double *rel_residual) {
+               cudaStream_t s, double *x, int *iters, double *rel_residual, cudaEvent_t b_ready = nullptr) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!lab || !b || !x || !iters || !rel_residual) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
   if (!(tol > 0.0) || !isfinite(tol)) return fail(h, NPSOLVE_BAD_ARG, "tolerance must be finite and > 0");
@@ -1219,6 +1223,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
         CK(h, cudaMemsetAsync(w.r1[3], 0, sizeof(float) * (size_t)level_dims(d1, 3).n(), s));
       }
     }
+    if (b_ready) CK(h, cudaStreamWaitEvent(s, b_ready, 0));  // b arrives on another stream during the setup
     if (vec4_path(d1)) {
       // the recurrence mode of the multilevel path keeps x as a double-float pair until the end
       const bool xdf = h->cfg.levels > 1 && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
@@ -1386,6 +1391,8 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
     cudaError_t e2 = cudaMalloc(&h->aw, sizeof(AffW) * (kMaxLevels + 1) * 2);
     cudaError_t e3 = cudaMalloc(&h->unit_c12, 2 * sizeof(double));
     cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e4 == cudaSuccess) e4 = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    if (e4 == cudaSuccess) e4 = cudaEventCreateWithFlags(&h->b_ready, cudaEventDisableTiming);
     cudaError_t e5 = cudaMalloc(&h->uw, (size_t)(kMaxLevels + 1) * 2 * umma_weight_bytes(3));
     cudaError_t e6 = cudaMalloc(&h->umma_err, sizeof(int));
     cudaError_t e7 = cudaMalloc(&h->uni, sizeof(float) * (kMaxLevels + 1) * 2 * 81);
@@ -1436,6 +1443,8 @@ void npsolve_destroy(npsolve_t h) {
   cudaFree(h->uni);
   cudaFree(h->umma_err);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->b_ready) cudaEventDestroy(h->b_ready);
   delete h;
 }
 
@@ -1463,9 +1472,14 @@ int npsolve_solve_host(npsolve_t h, const uint8_t *labels_host, int nx, int ny, 
     CK(h, dalloc(&w.bytes, &w.stage_b, (size_t)w.cap));
     CK(h, dalloc(&w.bytes, &w.stage_x, (size_t)w.cap));
   }
+  // the labels first on the solve's stream (the setup needs them), b beside the setup on the copy stream
   CK(h, cudaMemcpyAsync(w.stage_lab, labels_host, n, cudaMemcpyHostToDevice, s));
-  CK(h, cudaMemcpyAsync(w.stage_b, b_host, n * sizeof(float), cudaMemcpyHostToDevice, s));
-  int ret = solve_impl(h, w.stage_lab, nx, ny, nz, w.stage_b, tol, max_iter, s, w.stage_x, iters, rel_residual);
+  CK(h, cudaEventRecord(h->b_ready, s));  // after the previous user of the staging buffers on s
+  CK(h, cudaStreamWaitEvent(h->copy_stream, h->b_ready, 0));
+  CK(h, cudaMemcpyAsync(w.stage_b, b_host, n * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream));
+  CK(h, cudaEventRecord(h->b_ready, h->copy_stream));
+  int ret = solve_impl(h, w.stage_lab, nx, ny, nz, w.stage_b, tol, max_iter, s, w.stage_x, iters, rel_residual,
+                       h->b_ready);
   if (ret == NPSOLVE_OK || ret == NPSOLVE_NO_CONVERGENCE || ret == NPSOLVE_BREAKDOWN) {
     CK(h, cudaMemcpyAsync(x_host, w.stage_x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
