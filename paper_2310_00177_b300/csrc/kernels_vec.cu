@@ -184,11 +184,15 @@ __global__ void __launch_bounds__(kRedThreads) k_update(long long n, double *__r
 // r = b - A x evaluated in FP64 (x FP64, b FP32), stored as FP32; partials of
 // ||b - A x||^2 (FP64 values) and ||mask(b)||^2.  Used by the explicit
 // residual mode, residual replacement and the final true-residual check.
+// r (optional) receives b - A x; with r_alt, r_k's buffer by the parity of
+// sel->k (the residual alternates between two buffers on the fused path).
 __global__ void __launch_bounds__(kRedThreads) k_true_residual(const uint8_t *__restrict__ lab, Dims dm,
                                                                  const float *__restrict__ b,
-                                                                 const double *__restrict__ x, float *__restrict__ r,
+                                                                 const double *__restrict__ x, float *r,
+                                                                 float *r_alt, const SolveState *sel,
                                                                  double *__restrict__ part, const SolveState *st) {
   if (st && st->done) return;
+  if (r_alt && sel && (sel->k & 1)) r = r_alt;
   const long long n = dm.n();
   const long long sxy = (long long)dm.nx * dm.ny;
   double v[2] = {0.0, 0.0};
@@ -517,19 +521,19 @@ void launch_update(bool recurrence, long long n, double *x, float *r, const floa
 void launch_explicit_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, double *part,
                               SolveState *st, double *hist, cudaStream_t s) {
   const int nb = red_blocks(dm.n());
-  k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, r, part, st);
+  k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, r, nullptr, nullptr, part, st);
   k_converge_final<<<1, kRedThreads, 0, s>>>(part, nb, 2, st, hist);
 }
-void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, double *part,
-                             SolveState *st, int *reopened, double *relres, cudaStream_t s) {
+void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, float *r_alt,
+                             double *part, SolveState *st, int *reopened, double *relres, cudaStream_t s) {
   const int nb = red_blocks(dm.n());
-  k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, r, part, nullptr);
+  k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, r, r_alt, st, part, nullptr);
   k_restart_final<<<1, kRedThreads, 0, s>>>(part, nb, st, reopened, relres);
 }
 void launch_relres(const uint8_t *lab, Dims dm, const float *b, const double *x, double *part, double *out,
                    cudaStream_t s) {
   const int nb = red_blocks(dm.n());
-  k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, nullptr, part, nullptr);
+  k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, nullptr, nullptr, nullptr, part, nullptr);
   k_relres_final<<<1, kRedThreads, 0, s>>>(part, nb, out);
 }
 

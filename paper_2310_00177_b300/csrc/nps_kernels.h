@@ -26,8 +26,8 @@ void launch_explicit_residual(const uint8_t *lab, Dims dm, const float *b, const
                               SolveState *st, double *hist, cudaStream_t s);
 // r = b - A x (FP64 arithmetic); re-opens a converged solve whose true
 // residual is above tolerance; relres[0..1] = ||b - A x|| / ||b||, ||b||.
-void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, double *part,
-                             SolveState *st, int *reopened, double *relres, cudaStream_t s);
+void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, float *r_alt,
+                             double *part, SolveState *st, int *reopened, double *relres, cudaStream_t s);
 void launch_relres(const uint8_t *lab, Dims dm, const float *b, const double *x, double *part, double *out,
                    cudaStream_t s);
 size_t pcg_state_bytes();

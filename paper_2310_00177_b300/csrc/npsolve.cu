@@ -1246,7 +1246,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     if (st) return st;
   }
   int launched = 0, restarts = 0;
-  bool have_relres = false;  // the last residual replacement check left the final figures
+  double rr[2] = {0.0, 0.0};  // final relative true residual, ||b||
   SolveState hs = w.h_st[0];
   for (;;) {
     // Replay the captured iterations until the device flags completion or the
@@ -1280,61 +1280,55 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       }
       nb += 1;
     }
-    CK(h, cudaStreamSynchronize(s));
-    if (nb) hs = w.h_st[(nb - 1) & 1];
+    // The end of a pass, decided on the device and read back with one host
+    // synchronisation: the last pending residual step (a no-op when none is
+    // pending), the pending steps of x, and in the recurrence mode the FP64
+    // true residual that replaces r and re-opens the iteration when a converged
+    // solve's true residual is still above tolerance (k_restart_final);
+    // otherwise the final figures only.
     const bool fused = fused_update(h, d1);
     if (fused) {
-      // the last iteration's r step (no next level-1 CConv1 formed it); a no-op when none is pending
       ProfScope ps(h, P_UPDATE, s);
       launch_update4(true, (int)d1.n(), x, w.r, w.r_alt, w.dring, w.qring, w.part, w.tickets + kTicketUpdate, w.st,
                      w.hist, h->num_sms, s);
       h->launches += 1;
-      CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-      CK(h, cudaStreamSynchronize(s));
-      hs = w.h_st[0];
     }
     if (vec4_path(d1) && h->cfg.levels > 1 &&
         h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE) {  // the last steps may still be pending
       launch_flush_x((int)d1.n(), w.xhi, w.xlo, x, w.dring, w.st, h->num_sms, s);
       h->launches += 2;
     }
-    if (hs.done == kDoneConverged && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE &&
-        restarts < kMaxRestarts) {
+    const bool check = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE && restarts < kMaxRestarts;
+    {
       ProfScope ps(h, P_FINAL, s);
       // r_k lives in buffer k mod 2 when the update is fused into the level-1 CConv1
-      float *r_cur = (fused && (hs.k & 1)) ? w.r_alt : w.r;
-      launch_replace_residual(lab, d1, b, x, r_cur, w.part, w.st, w.reopened, w.relres, s);
+      if (check) launch_replace_residual(lab, d1, b, x, w.r, fused ? w.r_alt : nullptr, w.part, w.st, w.reopened,
+                                         w.relres, s);
+      else launch_relres(lab, d1, b, x, w.part, w.relres, s);
       h->launches += 2;
-      CK(h, cudaMemcpyAsync(w.h_flag, w.reopened, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-      CK(h, cudaStreamSynchronize(s));
-      hs = w.h_st[0];
-      if (w.h_flag[0]) {
-        restarts += 1;
-        launched = hs.k;
-        continue;
-      }
-      have_relres = true;
+    }
+    if (check) CK(h, cudaMemcpyAsync(w.h_flag, w.reopened, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(rr, w.relres, sizeof(rr), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    // the residual history up to the iterations launched so far (an upper bound of k + 1 entries)
+    h->last_hist.resize((size_t)std::min(launched, max_iter) + 1);
+    CK(h, cudaMemcpyAsync(h->last_hist.data(), w.hist, sizeof(double) * h->last_hist.size(), cudaMemcpyDeviceToHost,
+                          s));
+    CK(h, cudaStreamSynchronize(s));
+    hs = w.h_st[0];
+    if (check && w.h_flag[0]) {
+      restarts += 1;
+      launched = hs.k;
+      continue;
     }
     break;
   }
-  if (!have_relres) {
-    ProfScope ps(h, P_FINAL, s);
-    launch_relres(lab, d1, b, x, w.part, w.relres, s);
-    h->launches += 2;
-  }
-  double rr[2];
-  CK(h, cudaMemcpyAsync(rr, w.relres, sizeof(rr), cudaMemcpyDeviceToHost, s));
-  CK(h, cudaMemcpyAsync(&w.h_st[0], w.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-  CK(h, cudaStreamSynchronize(s));
-  hs = w.h_st[0];
   *iters = hs.k;
   *rel_residual = rr[0];
   prof_collect(h);
   st = check_umma_err(h);
   if (st) return st;
   h->last_hist.resize(hs.k + 1);
-  CK(h, cudaMemcpy(h->last_hist.data(), w.hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost));
   if (hs.done == kDoneBreakdown) return fail(h, NPSOLVE_BREAKDOWN, "breakdown: d^T A d <= 0 or non-finite at iteration %d", hs.k + 1);
   if (hs.done != kDoneConverged) return fail(h, NPSOLVE_NO_CONVERGENCE, "no convergence in %d iterations", hs.k);
   h->err.clear();
