@@ -150,7 +150,11 @@ void worker(npsolve_server *s, int idx) {
     r->t_start = Clock::now();
     const long long n = r->cells();
     int st = NPSOLVE_OK;
-    if (n > sl.cap_cells) {  // grow this slot's request buffers
+    if (r->x) {
+      // through the host-buffer call: the handle's staging buffers, b uploaded beside the setup
+      st = npsolve_solve_host(sl.h, r->lab, r->nx, r->ny, r->nz, r->b, r->tol, r->max_iter, sl.stream, r->x,
+                              &r->iters, &r->relres);
+    } else if (n > sl.cap_cells) {  // grow this slot's request buffers
       cudaFree(sl.d_lab);
       cudaFree(sl.d_b);
       cudaFree(sl.d_x);
@@ -165,15 +169,11 @@ void worker(npsolve_server *s, int idx) {
         sl.cap_cells = n;
       }
     }
-    if (st == NPSOLVE_OK) {
+    if (st == NPSOLVE_OK && !r->x) {
       cudaMemcpyAsync(sl.d_lab, r->lab, n, cudaMemcpyHostToDevice, sl.stream);
       cudaMemcpyAsync(sl.d_b, r->b, n * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
       st = npsolve_solve(sl.h, sl.d_lab, r->nx, r->ny, r->nz, sl.d_b, r->tol, r->max_iter, sl.stream, sl.d_x,
                          &r->iters, &r->relres);
-      if ((st == NPSOLVE_OK || st == NPSOLVE_NO_CONVERGENCE || st == NPSOLVE_BREAKDOWN) && r->x) {
-        cudaMemcpyAsync(r->x, sl.d_x, n * sizeof(double), cudaMemcpyDeviceToHost, sl.stream);
-        if (cudaStreamSynchronize(sl.stream) != cudaSuccess) st = NPSOLVE_CUDA_ERROR;
-      }
     }
     r->status = st;
     r->t_end = Clock::now();
