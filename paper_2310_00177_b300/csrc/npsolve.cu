@@ -159,6 +159,7 @@ struct npsolve {
   // solve's stream runs the setup from the labels; b_ready orders init after it
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t b_ready = nullptr;
+  cudaEvent_t x_ready = nullptr;  // the final x is written: its download may start
   std::string err;
   std::vector<double> last_hist;
   Profiler prof;
@@ -1191,7 +1192,8 @@ int get_graph(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *x
 }
 
 int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const float *b, double tol, int max_iter,
-               cudaStream_t s, double *x, int *iters, double *rel_residual, cudaEvent_t b_ready = nullptr) {
+               cudaStream_t s, double *x, int *iters, double *rel_residual, cudaEvent_t b_ready = nullptr,
+               double *x_host = nullptr) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!lab || !b || !x || !iters || !rel_residual) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
   if (!(tol > 0.0) || !isfinite(tol)) return fail(h, NPSOLVE_BAD_ARG, "tolerance must be finite and > 0");
@@ -1298,6 +1300,13 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       launch_flush_x((int)d1.n(), w.xhi, w.xlo, x, w.dring, w.st, h->num_sms, s);
       h->launches += 2;
     }
+    if (x_host) {
+      // x is final unless the check below re-opens the iteration: its download runs beside
+      // the check on the copy stream (a re-opened pass copies it again, in order on that stream)
+      CK(h, cudaEventRecord(h->x_ready, s));
+      CK(h, cudaStreamWaitEvent(h->copy_stream, h->x_ready, 0));
+      CK(h, cudaMemcpyAsync(x_host, x, sizeof(double) * (size_t)d1.n(), cudaMemcpyDeviceToHost, h->copy_stream));
+    }
     const bool check = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE && restarts < kMaxRestarts;
     {
       ProfScope ps(h, P_FINAL, s);
@@ -1315,6 +1324,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     CK(h, cudaMemcpyAsync(h->last_hist.data(), w.hist, sizeof(double) * h->last_hist.size(), cudaMemcpyDeviceToHost,
                           s));
     CK(h, cudaStreamSynchronize(s));
+    if (x_host) CK(h, cudaStreamSynchronize(h->copy_stream));
     hs = w.h_st[0];
     if (check && w.h_flag[0]) {
       restarts += 1;
@@ -1387,6 +1397,7 @@ int npsolve_create(const npsolve_config *cfg, const float *weights_host, size_t 
     cudaError_t e4 = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e4 == cudaSuccess) e4 = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
     if (e4 == cudaSuccess) e4 = cudaEventCreateWithFlags(&h->b_ready, cudaEventDisableTiming);
+    if (e4 == cudaSuccess) e4 = cudaEventCreateWithFlags(&h->x_ready, cudaEventDisableTiming);
     cudaError_t e5 = cudaMalloc(&h->uw, (size_t)(kMaxLevels + 1) * 2 * umma_weight_bytes(3));
     cudaError_t e6 = cudaMalloc(&h->umma_err, sizeof(int));
     cudaError_t e7 = cudaMalloc(&h->uni, sizeof(float) * (kMaxLevels + 1) * 2 * 81);
@@ -1439,6 +1450,7 @@ void npsolve_destroy(npsolve_t h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->b_ready) cudaEventDestroy(h->b_ready);
+  if (h->x_ready) cudaEventDestroy(h->x_ready);
   delete h;
 }
 
@@ -1472,13 +1484,9 @@ int npsolve_solve_host(npsolve_t h, const uint8_t *labels_host, int nx, int ny, 
   CK(h, cudaStreamWaitEvent(h->copy_stream, h->b_ready, 0));
   CK(h, cudaMemcpyAsync(w.stage_b, b_host, n * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream));
   CK(h, cudaEventRecord(h->b_ready, h->copy_stream));
-  int ret = solve_impl(h, w.stage_lab, nx, ny, nz, w.stage_b, tol, max_iter, s, w.stage_x, iters, rel_residual,
-                       h->b_ready);
-  if (ret == NPSOLVE_OK || ret == NPSOLVE_NO_CONVERGENCE || ret == NPSOLVE_BREAKDOWN) {
-    CK(h, cudaMemcpyAsync(x_host, w.stage_x, n * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(h, cudaStreamSynchronize(s));
-  }
-  return ret;
+  // x comes back inside solve_impl, beside the final residual check
+  return solve_impl(h, w.stage_lab, nx, ny, nz, w.stage_b, tol, max_iter, s, w.stage_x, iters, rel_residual,
+                    h->b_ready, x_host);
 }
 
 int npsolve_residual_history(npsolve_t h, double *hist_host, int cap, int *count) {
