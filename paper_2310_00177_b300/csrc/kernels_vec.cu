@@ -530,6 +530,13 @@ void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const 
   k_true_residual<<<nb, kRedThreads, 0, s>>>(lab, dm, b, x, r, r_alt, st, part, nullptr);
   k_restart_final<<<1, kRedThreads, 0, s>>>(part, nb, st, reopened, relres);
 }
+void launch_restart_final(const double *part, int nblocks, SolveState *st, int *reopened, double *relres,
+                          cudaStream_t s) {
+  k_restart_final<<<1, kRedThreads, 0, s>>>(part, nblocks, st, reopened, relres);
+}
+void launch_relres_final(const double *part, int nblocks, double *relres, cudaStream_t s) {
+  k_relres_final<<<1, kRedThreads, 0, s>>>(part, nblocks, relres);
+}
 void launch_relres(const uint8_t *lab, Dims dm, const float *b, const double *x, double *part, double *out,
                    cudaStream_t s) {
   const int nb = red_blocks(dm.n());

@@ -547,6 +547,103 @@ __global__ void __launch_bounds__(kThreads) k_flush_x(int n, float *__restrict__
 }
 __global__ void k_clear_pend(SolveState *st) { st->x_upto = st->k; }
 
+// ---------------------------------------------------------------------------
+// The true residual b - A x of the recurrence mode's x, held as a double-float
+// pair (xhi, xlo) after the last flush (the returned FP64 x is the same value,
+// widened).  Double-float arithmetic on FP32 (Knuth's TwoSum, the FMA exact
+// product, Dekker's renormalisation; about 48 significant bits) instead of
+// FP64, which B300 runs at 1/64 of its FP32 rate:
+//   (A x)_p = sum over fluid neighbours (x_p - x_n) + (air neighbours) x_p
+// (Sec. 3.2, from the stencil codes of k_lap4), r_p = b_p - (A x)_p, and the
+// per-thread sums of r^2 and b^2 in double-float, FP64 only above the thread.
+// Writes r (FP32, 0 off fluid) into r_k's buffer when r is given; the partials
+// are those of k_true_residual (two per block of kRedThreads).
+// ---------------------------------------------------------------------------
+struct DD {
+  float h, l;
+};
+__device__ __forceinline__ DD dd_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DD dd_norm(float s, float e) {  // |e| small against s
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  const DD s = dd_two_sum(a.h, b.h);
+  return dd_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ DD dd_sub(DD a, DD b) { return dd_add(a, DD{-b.h, -b.l}); }
+__device__ __forceinline__ DD dd_mul(DD a, float m) {
+  const float p = __fmul_rn(a.h, m);
+  return dd_norm(p, fmaf(a.l, m, fmaf(a.h, m, -p)));
+}
+__device__ __forceinline__ DD dd_sqr(DD a) {
+  const float p = __fmul_rn(a.h, a.h);
+  return dd_norm(p, fmaf(__fmul_rn(2.f, a.h), a.l, fmaf(a.h, a.h, -p)));
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_true_residual4(const uint16_t *__restrict__ code, Dims dm,
+                                                                  const float *__restrict__ b,
+                                                                  const float *__restrict__ xhi,
+                                                                  const float *__restrict__ xlo, float *r,
+                                                                  float *r_alt, const SolveState *sel,
+                                                                  double *__restrict__ part) {
+  if (r_alt && sel && (sel->k & 1)) r = r_alt;
+  const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
+  const int n = nx * ny * nz, nxy = nx * ny, n4 = n >> 2;
+  DD sr{0.f, 0.f}, sb{0.f, 0.f};
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+    const int p = g << 2;
+    const ushort4 cc = *reinterpret_cast<const ushort4 *>(code + p);
+    if (((cc.x | cc.y | cc.z | cc.w) & 0x8000u) == 0u) {
+      if (r) st4(r + p, make_float4(0.f, 0.f, 0.f, 0.f));
+      continue;
+    }
+    const int yz = p / nx, x0 = p - yz * nx, z = yz / ny, y = yz - z * ny;
+    const float4 bv = ld4(b + p);
+    const float4 hc = ld4(xhi + p), lc = ld4(xlo + p);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float hxl = x0 > 0 ? xhi[p - 1] : 0.f, lxl = x0 > 0 ? xlo[p - 1] : 0.f;
+    const float hxr = x0 + 4 < nx ? xhi[p + 4] : 0.f, lxr = x0 + 4 < nx ? xlo[p + 4] : 0.f;
+    const float4 hym = y > 0 ? ld4(xhi + p - nx) : zero4, lym = y > 0 ? ld4(xlo + p - nx) : zero4;
+    const float4 hyp = y < ny - 1 ? ld4(xhi + p + nx) : zero4, lyp = y < ny - 1 ? ld4(xlo + p + nx) : zero4;
+    const float4 hzm = z > 0 ? ld4(xhi + p - nxy) : zero4, lzm = z > 0 ? ld4(xlo + p - nxy) : zero4;
+    const float4 hzp = z < nz - 1 ? ld4(xhi + p + nxy) : zero4, lzp = z < nz - 1 ? ld4(xlo + p + nxy) : zero4;
+    const uint16_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
+    float ro[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t c = cs[e];
+      if (!(c & 0x8000u)) {
+        ro[e] = 0.f;
+        continue;
+      }
+      const DD xp{f4(hc, e), f4(lc, e)};
+      const DD nb[6] = {DD{e == 0 ? hxl : f4(hc, e - 1), e == 0 ? lxl : f4(lc, e - 1)},
+                        DD{e == 3 ? hxr : f4(hc, e + 1), e == 3 ? lxr : f4(lc, e + 1)},
+                        DD{f4(hym, e), f4(lym, e)}, DD{f4(hyp, e), f4(lyp, e)},
+                        DD{f4(hzm, e), f4(lzm, e)}, DD{f4(hzp, e), f4(lzp, e)}};
+      DD ax{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (c & (1u << k)) ax = dd_add(ax, dd_sub(xp, nb[k]));
+      ax = dd_add(ax, dd_mul(xp, (float)((c >> 8) & 7u)));
+      const float bp = f4(bv, e);
+      const DD res = dd_sub(DD{bp, 0.f}, ax);
+      ro[e] = res.h;
+      sr = dd_add(sr, dd_sqr(res));
+      sb = dd_add(sb, dd_sqr(DD{bp, 0.f}));
+    }
+    if (r) st4(r + p, make_float4(ro[0], ro[1], ro[2], ro[3]));
+  }
+  double v[2] = {(double)sr.h + (double)sr.l, (double)sb.h + (double)sb.l};
+  block_sum_store<2>(v, part + (size_t)blockIdx.x * 2);
+}
+
+
 // One bit per 4-cell group (bit g & 31 of word g >> 5): the group holds a
 // fluid cell.  Vectors are zero on the other groups, so the direction kernel
 // skips their loads (occupancy-aware sparsity).
@@ -616,6 +713,17 @@ void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring
                  double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
   k_lap4<<<grid4(dm.n() / 4, num_sms, resident_blocks<k_lap4>()), kThreads, 0, s>>>(
       code, dm, make_fastdiv((uint32_t)dm.nx), make_fastdiv((uint32_t)dm.ny), dring, qring, r, r_alt, part, ticket, st);
+}
+// The true residual from the double-float x: the figures only (r null), or
+// the residual replacement of the recurrence (r_k's buffer by parity) with the
+// re-opening decision; the final kernels are those of the FP64 form.
+void launch_true_residual4(const uint16_t *code, Dims dm, const float *b, const float *xhi, const float *xlo, float *r,
+                           float *r_alt, double *part, SolveState *st, int *reopened, double *relres,
+                           cudaStream_t s) {
+  const int nb = red_blocks(dm.n());
+  k_true_residual4<<<nb, kRedThreads, 0, s>>>(code, dm, b, xhi, xlo, r, r_alt, st, part);
+  if (reopened) launch_restart_final(part, nb, st, reopened, relres, s);
+  else launch_relres_final(part, nb, relres, s);
 }
 void launch_flush_x(int n, float *xhi, float *xlo, double *x, const float *dring, SolveState *st, int num_sms,
                     cudaStream_t s) {

@@ -26,6 +26,15 @@ void launch_explicit_residual(const uint8_t *lab, Dims dm, const float *b, const
                               SolveState *st, double *hist, cudaStream_t s);
 // r = b - A x (FP64 arithmetic); re-opens a converged solve whose true
 // residual is above tolerance; relres[0..1] = ||b - A x|| / ||b||, ||b||.
+// The final kernels of the true residual (partials of two per block).
+void launch_restart_final(const double *part, int nblocks, SolveState *st, int *reopened, double *relres,
+                          cudaStream_t s);
+void launch_relres_final(const double *part, int nblocks, double *relres, cudaStream_t s);
+// The true residual of the double-float x (xhi, xlo) in double-float FP32 arithmetic, with the stencil codes;
+// reopened null: the figures only; else the residual replacement (r_k's buffer by parity) and re-opening.
+void launch_true_residual4(const uint16_t *code, Dims dm, const float *b, const float *xhi, const float *xlo, float *r,
+                           float *r_alt, double *part, SolveState *st, int *reopened, double *relres,
+                           cudaStream_t s);
 void launch_replace_residual(const uint8_t *lab, Dims dm, const float *b, const double *x, float *r, float *r_alt,
                              double *part, SolveState *st, int *reopened, double *relres, cudaStream_t s);
 void launch_relres(const uint8_t *lab, Dims dm, const float *b, const double *x, double *part, double *out,

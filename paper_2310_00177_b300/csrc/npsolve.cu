@@ -1308,11 +1308,18 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
       CK(h, cudaMemcpyAsync(x_host, x, sizeof(double) * (size_t)d1.n(), cudaMemcpyDeviceToHost, h->copy_stream));
     }
     const bool check = h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE && restarts < kMaxRestarts;
+    // x as the double-float pair (the recurrence mode of the multilevel vector path): the
+    // check in double-float FP32 arithmetic; otherwise in FP64 from x
+    const bool xdf = vec4_path(d1) && h->cfg.levels > 1 && h->cfg.residual_mode == NPSOLVE_RESIDUAL_RECURRENCE;
     {
       ProfScope ps(h, P_FINAL, s);
       // r_k lives in buffer k mod 2 when the update is fused into the level-1 CConv1
-      if (check) launch_replace_residual(lab, d1, b, x, w.r, fused ? w.r_alt : nullptr, w.part, w.st, w.reopened,
-                                         w.relres, s);
+      float *r_alt = fused ? w.r_alt : nullptr;
+      if (xdf)
+        launch_true_residual4(w.lapcode, d1, b, w.xhi, w.xlo, check ? w.r : nullptr, check ? r_alt : nullptr, w.part,
+                              w.st, check ? w.reopened : nullptr, w.relres, s);
+      else if (check)
+        launch_replace_residual(lab, d1, b, x, w.r, r_alt, w.part, w.st, w.reopened, w.relres, s);
       else launch_relres(lab, d1, b, x, w.part, w.relres, s);
       h->launches += 2;
     }
