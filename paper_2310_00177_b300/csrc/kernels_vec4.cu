@@ -326,33 +326,55 @@ __global__ void __launch_bounds__(kThreads) k_direction4(int n, const float *__r
   if (g < n4) group(g);
 }
 
+
 // Per-cell stencil code of the masked 7-point Laplacian (Sec. 3.2), built once
 // per solve from the labels: bits 0-5 = the neighbour -x, +x, -y, +y, -z, +z
 // is fluid (inside the grid), bits 8-10 = number of air neighbours, bit 15 =
-// the cell itself is fluid.
-__global__ void __launch_bounds__(kThreads) k_lap_codes(const uint8_t *__restrict__ lab, Dims dm,
-                                                        uint16_t *__restrict__ code) {
+// the cell itself is fluid.  With it, one bit per 4-cell group (bit g & 31 of
+// word g >> 5 of gmask): the group holds a fluid cell; vectors are zero on
+// the other groups, so the direction kernel skips their loads (occupancy-aware
+// sparsity).  A thread codes a 4-cell group (nx % 4 == 0) from one 4-byte
+// label load per row (the group, y +- 1, z +- 1) and the two x-neighbours; the
+// mask word comes from a warp ballot.  Outside the grid is solid.
+__global__ void __launch_bounds__(kThreads) k_lap_codes4(const uint8_t *__restrict__ lab, Dims dm,
+                                                         uint16_t *__restrict__ code, uint32_t *__restrict__ gmask) {
   const int nx = dm.nx, ny = dm.ny, nz = dm.nz;
-  const long long n = dm.n();
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(p, dm, x, y, z);
-    uint32_t c = 0;
-    if (lab[p] == kFluid) {
-      c = 0x8000u;
-      const long long nb[6] = {p - 1, p + 1, p - nx, p + nx, p - (long long)nx * ny, p + (long long)nx * ny};
-      const bool in[6] = {x > 0, x < nx - 1, y > 0, y < ny - 1, z > 0, z < nz - 1};
-      uint32_t nair = 0;
+  const int nxy = nx * ny, n4 = (nx * ny * nz) >> 2, words = (n4 + 31) >> 5;
+  const uchar4 solid4 = make_uchar4(0, 0, 0, 0);
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < words * 32; g += gridDim.x * blockDim.x) {
+    bool f = false;
+    if (g < n4) {
+      const int p = g << 2;
+      const int yz = p / nx, x0 = p - yz * nx, z = yz / ny, y = yz - z * ny;
+      const uchar4 lc = ldl4(lab + p);
+      const uchar4 ym = y > 0 ? ldl4(lab + p - nx) : solid4, yp = y < ny - 1 ? ldl4(lab + p + nx) : solid4;
+      const uchar4 zm = z > 0 ? ldl4(lab + p - nxy) : solid4, zp = z < nz - 1 ? ldl4(lab + p + nxy) : solid4;
+      const uint8_t xl = x0 > 0 ? lab[p - 1] : (uint8_t)0, xr = x0 + 4 < nx ? lab[p + 4] : (uint8_t)0;
+      const uint8_t c4[4] = {lc.x, lc.y, lc.z, lc.w};
+      const uint8_t m4[4] = {ym.x, ym.y, ym.z, ym.w}, p4[4] = {yp.x, yp.y, yp.z, yp.w};
+      const uint8_t zm4[4] = {zm.x, zm.y, zm.z, zm.w}, zp4[4] = {zp.x, zp.y, zp.z, zp.w};
+      uint16_t out[4];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        if (!in[k]) continue;
-        const uint8_t l = lab[nb[k]];
-        if (l == kFluid) c |= 1u << k;
-        else if (l == kAir) nair += 1;
+      for (int e = 0; e < 4; ++e) {
+        uint32_t c = 0;
+        if (c4[e] == kFluid) {
+          const uint8_t nb[6] = {e == 0 ? xl : c4[e - 1], e == 3 ? xr : c4[e + 1], m4[e], p4[e], zm4[e], zp4[e]};
+          uint32_t nair = 0;
+          c = 0x8000u;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            if (nb[k] == kFluid) c |= 1u << k;
+            else if (nb[k] == kAir) nair += 1;
+          }
+          c |= nair << 8;
+          f = true;
+        }
+        out[e] = (uint16_t)c;
       }
-      c |= nair << 8;
+      *reinterpret_cast<ushort4 *>(code + p) = make_ushort4(out[0], out[1], out[2], out[3]);
     }
-    code[p] = (uint16_t)c;
+    const uint32_t bm = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0) gmask[g >> 5] = bm;
   }
 }
 
@@ -644,22 +666,6 @@ __global__ void __launch_bounds__(kRedThreads) k_true_residual4(const uint16_t *
 }
 
 
-// One bit per 4-cell group (bit g & 31 of word g >> 5): the group holds a
-// fluid cell.  Vectors are zero on the other groups, so the direction kernel
-// skips their loads (occupancy-aware sparsity).
-__global__ void __launch_bounds__(kThreads) k_group_mask(const uint16_t *__restrict__ code, int n4,
-                                                         uint32_t *__restrict__ gmask) {
-  const int words = (n4 + 31) >> 5;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < words * 32; g += gridDim.x * blockDim.x) {
-    bool f = false;
-    if (g < n4) {
-      const ushort4 c = *reinterpret_cast<const ushort4 *>(code + 4 * (size_t)g);
-      f = ((c.x | c.y | c.z | c.w) & 0x8000u) != 0u;
-    }
-    const uint32_t b = __ballot_sync(0xffffffffu, f);
-    if ((threadIdx.x & 31) == 0) gmask[g >> 5] = b;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Host-side launchers.
@@ -701,13 +707,10 @@ void launch_direction4(bool defer_x, int n, const float *z, float *dring, float 
   }
 }
 void launch_lap_codes(const uint8_t *lab, Dims dm, uint16_t *code, uint32_t *gmask, cudaStream_t s) {
-  long long b = (dm.n() + kThreads - 1) / kThreads;
-  if (b > 148LL * 16) b = 148LL * 16;
-  k_lap_codes<<<(int)(b < 1 ? 1 : b), kThreads, 0, s>>>(lab, dm, code);
   const int n4 = (int)(dm.n() / 4);
   long long g = ((long long)((n4 + 31) / 32) * 32 + kThreads - 1) / kThreads;
   if (g > 148LL * 16) g = 148LL * 16;
-  k_group_mask<<<(int)(g < 1 ? 1 : g), kThreads, 0, s>>>(code, n4, gmask);
+  k_lap_codes4<<<(int)(g < 1 ? 1 : g), kThreads, 0, s>>>(lab, dm, code, gmask);
 }
 void launch_lap4(const uint16_t *code, Dims dm, const float *dring, float *qring, const float *r, const float *r_alt,
                  double *part, unsigned *ticket, SolveState *st, int num_sms, cudaStream_t s) {
