@@ -276,3 +276,27 @@ def test_solve_generic_path_matches_oracle(shape, L):
         assert abs(iters - ores["iters"]) <= 1
     assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-5
     s.close()
+
+
+def test_residual_replacement_host_and_device_agree():
+    # a tolerance below what the FP32 recurrence can track: the recurrence
+    # residual passes tol * ||b|| while the true residual does not, so the
+    # check replaces r by b - A x and re-opens the iteration (R2).  The host-
+    # buffer call downloads x beside that check and again after a re-opened
+    # pass; both calls must return the same x, count and residual, and the
+    # residual must be the true one of the returned x.
+    b = _binding()
+    lab, rhs, w = _config1()
+    s = b.Solver(w, levels=4, n_ortho=2, precision=b.FP32)
+    x, it, rr, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-9, max_iter=400)
+    hist = s.residual_history()
+    jumps = np.flatnonzero(hist[1:] > 2.0 * hist[:-1])
+    assert len(jumps) >= 1  # a replacement raised ||r|| back to the true residual
+    xh = np.empty(lab.shape, np.float64)
+    x2, it2, rr2, st2 = s.solve_host(lab, rhs, 1e-9, 400, x=xh)
+    assert (st2, it2) == (st, it) and rr2 == rr
+    assert np.array_equal(xh, x.cpu().numpy())
+    bm = np.where(lab == 1, rhs.astype(np.float64), 0.0)
+    true = np.linalg.norm(bm - oracle.lap_apply(lab, xh)) / np.linalg.norm(bm)
+    assert abs(true - rr) <= 1e-6 * true
+    s.close()
