@@ -122,3 +122,28 @@ def test_level1_cconv_sampled_cells(problem):
                         cv[dz, dy, dx] = v[zz, yy, xx]
         want = oracle.cconv(oracle.image(cl), W, B, cv)[1, 1, 1]
         assert abs(x1[z, y, x] - want) <= 1e-5 * scale, ((z, y, x), x1[z, y, x], want)
+
+
+def test_non_cubic_dambreak_shape_truncated():
+    # the shape of the paper's dambreak scenes, (x, y, z) = (256, 128, 128): a
+    # z-crop of the 256^3 sloshing scene holding the free surface.  x after
+    # one and two iterations against the oracle (whole oracle solves at this
+    # size take minutes).
+    b = _b()
+    lab = np.ascontiguousarray(synth.slosh_scene(256, 31)[96:224, 64:192, :])
+    assert lab.shape == (128, 128, 256) and (lab == 1).any() and (lab == 2).any()
+    rhs = synth.rhs_normal(lab, 32).astype(np.float32)
+    w = np.fromfile(WEIGHTS, np.float32)
+    s = b.Solver(w, levels=4, n_ortho=2, precision=b.FP32)
+    for m in (1, 2):
+        ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-12, max_iter=m)
+        x, iters, relres, st = s.solve(torch.from_numpy(lab).cuda(), torch.from_numpy(rhs).cuda(), 1e-12, m)
+        assert st == b.NO_CONVERGENCE and iters == ores["iters"] == m
+        xg, xo = x.cpu().numpy(), ores["x"]
+        comp, pure = synth.neumann_components(lab)
+        for c in pure:
+            msk = comp == c
+            xg[msk] -= xg[msk].mean()
+            xo[msk] -= xo[msk].mean()
+        assert np.linalg.norm(xg - xo) <= 2e-5 * np.linalg.norm(xo)
+    s.close()
