@@ -161,3 +161,19 @@ def test_zero_network_breaks_down():
     for flexible in (False, True):
         res = oracle.npcg(lab, b, L=2, w=np.zeros(oracle.weight_count(2)), max_iter=5, flexible=flexible)
         assert res["status"] == oracle.BREAKDOWN and res["iters"] == 1
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+def test_explicit_and_recurrence_residual_modes_agree(flexible):
+    # R2 for the PCG variants: r_k = b - A x_k or the recurrence give the same
+    # iterates up to rounding; both converge and their counts differ by at most one
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    w = np.fromfile(os.path.join(here, "..", "paper_2310_00177_b300", "weights", "npsdo_L4.f32"), np.float32)
+    lab, b = _scene(16, 26)
+    r0 = oracle.npcg(lab, b, L=4, w=w, tol=1e-6, max_iter=300, flexible=flexible, residual_mode=0)
+    r1 = oracle.npcg(lab, b, L=4, w=w, tol=1e-6, max_iter=300, flexible=flexible, residual_mode=1)
+    assert r0["status"] == r1["status"] == oracle.OK and abs(r0["iters"] - r1["iters"]) <= 1
+    assert r0["relres"] < 1e-6 and r1["relres"] < 1e-6
+    m = min(r0["iters"], r1["iters"])
+    np.testing.assert_allclose(r0["res_hist"][:m], r1["res_hist"][:m], rtol=1e-6)
