@@ -124,7 +124,7 @@ def summarize(recs):
 
 
 def serve_workload(w, requests=512, rate=200.0, sizes=(64, 128, 192, 256), frames=6, budget_gb=150.0,
-                   max_active=16):
+                   max_active=8):
     """Run the serving workload (seeded Poisson arrivals, mixed sizes, evolving
     frames, BF16 network, tol 1e-6, HBM-budget admission) on a fresh server
     and return the summary: p50 / p99 latency, solves per second, convergence
@@ -161,7 +161,7 @@ def main():
     ap.add_argument("--sizes", default="64,128,192,256")
     ap.add_argument("--frames", type=int, default=6)
     ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--max-active", type=int, default=16)
+    ap.add_argument("--max-active", type=int, default=8)
     args = ap.parse_args()
     from paper_2310_00177_b300 import synth
 
