@@ -549,11 +549,24 @@ __global__ void __launch_bounds__(kThreads) k_flush_x(int n, float *__restrict__
                                                       const SolveState *st) {
   const int k = st->k, from = st->x_upto + 1, no = st->n_ortho;
   const int n4 = n >> 2;
+  // the pending steps' alphas split once per thread (FP64, off the per-cell path)
+  const int npend = k - from + 1;
+  float pah[kRing], pal[kRing];
+  int psl[kRing];
+#pragma unroll
+  for (int i = 0; i < kRing; ++i) {
+    psl[i] = ring_slot(from + i, no);
+    pah[i] = pal[i] = 0.f;
+    if (i < npend) split_alpha(st->alpha_slot[psl[i]], pah[i], pal[i]);
+  }
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
     const int p = g << 2;
     float4 h = ld4(xhi + p), l = ld4(xlo + p);
-    if (from <= k) {
-      for (int it = from; it <= k; ++it) {
+    if (npend > 0) {
+#pragma unroll
+      for (int i = 0; i < kRing; ++i)
+        if (i < npend) df_axpy4(h, l, pah[i], pal[i], ld4(dring + (size_t)psl[i] * n + p));
+      for (int it = from + kRing; it <= k; ++it) {  // more pending steps than ring slots: never on this path
         const int sl = ring_slot(it, no);
         float ah, al;
         split_alpha(st->alpha_slot[sl], ah, al);
