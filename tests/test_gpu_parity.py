@@ -300,3 +300,46 @@ def test_residual_replacement_host_and_device_agree():
     true = np.linalg.norm(bm - oracle.lap_apply(lab, xh)) / np.linalg.norm(bm)
     assert abs(true - rr) <= 1e-6 * true
     s.close()
+
+
+@pytest.mark.parametrize("fill", [synth.SOLID, synth.AIR])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grid_without_fluid_is_solved_at_zero_iterations(fill, precision):
+    # degenerate scene: no fluid cell, so b restricted to the fluid is zero;
+    # the occupancy-aware unit lists are empty (one CTA that finds no unit)
+    b = _binding()
+    lab = np.full((32, 32, 32), fill, np.uint8)
+    rhs = np.random.default_rng(77).standard_normal(lab.shape).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64))
+    assert ores["iters"] == 0 and not ores["x"].any()
+    s = b.Solver(w, levels=4, precision=precision)
+    x, it, rr, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32))
+    assert st == b.OK and it == 0 and not x.cpu().numpy().any()
+    s.close()
+
+
+@pytest.mark.parametrize("cell", [(0, 0, 0), (31, 31, 63), (9, 17, 40)])
+def test_single_fluid_cell_matches_oracle(cell):
+    # degenerate scene: one fluid cell with one air neighbour, all else solid:
+    # A is the 1 x 1 matrix [1], so x = b at that cell; single-unit lists at
+    # every level, the cell at a grid corner or inside
+    b = _binding()
+    shape = (32, 32, 64)
+    lab = np.full(shape, synth.SOLID, np.uint8)
+    lab[cell] = synth.FLUID
+    nb = list(cell)
+    nb[0] = cell[0] + 1 if cell[0] + 1 < shape[0] else cell[0] - 1
+    lab[tuple(nb)] = synth.AIR
+    rhs = np.random.default_rng(78).standard_normal(shape).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    ores = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), max_iter=20)
+    assert abs(ores["x"][cell] - rhs[cell]) <= 1e-12 * abs(rhs[cell])
+    s = b.Solver(w, levels=4, precision=b.FP32)
+    x, it, rr, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), max_iter=20)
+    xg = x.cpu().numpy()
+    assert st == ores["status"] == b.OK and it == ores["iters"]
+    assert abs(xg[cell] - rhs[cell]) <= 1e-6 * abs(rhs[cell])
+    xg[cell] = 0.0
+    assert not xg.any()
+    s.close()
