@@ -343,3 +343,50 @@ def test_single_fluid_cell_matches_oracle(cell):
     xg[cell] = 0.0
     assert not xg.any()
     s.close()
+
+
+def _single_cell_scene(cell, shape=(32, 32, 64)):
+    lab = np.full(shape, synth.SOLID, np.uint8)
+    lab[cell] = synth.FLUID
+    nb = list(cell)
+    nb[0] = cell[0] + 1 if cell[0] + 1 < shape[0] else cell[0] - 1
+    lab[tuple(nb)] = synth.AIR
+    return lab
+
+
+@pytest.mark.parametrize("method", ["pcg", "fpcg"])
+def test_single_fluid_cell_pcg_variants_match_oracle(method):
+    b = _binding()
+    cell = (31, 31, 63)
+    lab = _single_cell_scene(cell)
+    rhs = np.random.default_rng(79).standard_normal(lab.shape).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    ores = oracle.npcg(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), max_iter=20,
+                       flexible=(method == "fpcg"))
+    s = b.Solver(w, levels=4, precision=b.FP32, method=b.PCG if method == "pcg" else b.FPCG)
+    x, it, rr, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), max_iter=20)
+    xg = x.cpu().numpy()
+    assert st == ores["status"] == b.OK and it == ores["iters"] == 1
+    assert abs(xg[cell] - rhs[cell]) <= 1e-6 * abs(rhs[cell])
+    xg[cell] = 0.0
+    assert not xg.any()
+    s.close()
+
+
+@pytest.mark.parametrize("scene", ["no_fluid", "single_cell"])
+def test_degenerate_scenes_through_host_buffers(scene):
+    # the host-buffer entry point (copies inside the call, the end phase with
+    # the residual check decided on the device) on the same degenerate scenes
+    b = _binding()
+    cell = (9, 17, 40)
+    lab = np.full((32, 32, 64), synth.AIR, np.uint8) if scene == "no_fluid" else _single_cell_scene(cell)
+    rhs = np.random.default_rng(80).standard_normal(lab.shape).astype(np.float32)
+    w = synth.init_weights(4, 7).astype(np.float32)
+    s = b.Solver(w, levels=4, precision=b.BF16)
+    xh, ith, rrh, sth = s.solve_host(lab, rhs, max_iter=20)
+    xd, itd, rrd, std = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), max_iter=20)
+    assert sth == std == b.OK and ith == itd == (0 if scene == "no_fluid" else 1)
+    assert np.array_equal(np.asarray(xh), xd.cpu().numpy())
+    if scene == "single_cell":
+        assert abs(xh[cell] - rhs[cell]) <= 1e-6 * abs(rhs[cell])
+    s.close()
