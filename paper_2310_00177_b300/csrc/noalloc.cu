@@ -80,8 +80,15 @@ int scratch_for_current_device(double **out) {
 
 }  // namespace
 
-// The same arithmetic as the library's true-residual kernel: for a fluid
-// cell, res = b - (sum_{fluid n} (x_p - x_n) + n_air x_p) in FP64.
+// block_sum_store sizes its shared array for nps::kRedThreads threads.
+static_assert(kNAThreads == nps::kRedThreads, "the partial-sum kernel runs kRedThreads threads per block");
+
+// Per fluid cell the same FP64 operations, in the same order, as the
+// library's true-residual kernel: (A x)_p = diag_p x_p - sum of the fluid
+// neighbours' x (Sec. 3.2), res = b_p - fma(diag_p, x_p, -sum), and the
+// squares accumulated with FMAs.  Only the order of the cross-thread
+// reduction differs (this grid has its own block count), so the two results
+// agree to FP64 rounding of the final sums.
 __global__ void __launch_bounds__(kNAThreads) k_relres_partials_na(const uint8_t *__restrict__ lab, nps::Dims dm,
                                                                    const float *__restrict__ b,
                                                                    const double *__restrict__ x,
@@ -93,22 +100,25 @@ __global__ void __launch_bounds__(kNAThreads) k_relres_partials_na(const uint8_t
     int xx, yy, zz;
     nps::cell_xyz(p, dm, xx, yy, zz);
     if (lab[p] != nps::kFluid) continue;
-    const double xp = x[p];
-    double acc = 0.0;
-    int nair = 0;
     const long long nb[6] = {p - 1, p + 1, p - dm.nx, p + dm.nx, p - sxy, p + sxy};
     const bool ok[6] = {xx > 0, xx < dm.nx - 1, yy > 0, yy < dm.ny - 1, zz > 0, zz < dm.nz - 1};
+    double sum = 0.0;
+    int diag = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       if (!ok[k]) continue;
       const uint8_t ln = lab[nb[k]];
-      if (ln == nps::kFluid) acc += xp - x[nb[k]];
-      else if (ln == nps::kAir) nair += 1;
+      if (ln == nps::kFluid) {
+        sum += x[nb[k]];
+        diag += 1;
+      } else if (ln == nps::kAir) {
+        diag += 1;
+      }
     }
     const double bp = (double)b[p];
-    const double res = bp - (acc + (double)nair * xp);
-    v[0] += res * res;
-    v[1] += bp * bp;
+    const double res = bp - fma((double)diag, x[p], -sum);
+    v[0] = fma(res, res, v[0]);
+    v[1] = fma(bp, bp, v[1]);
   }
   nps::block_sum_store<2>(v, part + (size_t)blockIdx.x * 2);
 }
@@ -137,10 +147,18 @@ extern "C" int npsolve_true_residual_noalloc(const uint8_t *labels, int nx, int 
   cudaStream_t s = (cudaStream_t)stream;
   const long long per_block = (long long)kNAThreads * kNACellsPerThread;
   const int nblocks = (int)((n + per_block - 1) / per_block);  // <= kNoAllocMaxBlocks by the check above
+  // An error already pending on this thread belongs to earlier work: peek
+  // (never clear) so that it stays with its owner, and take a launch error
+  // as this call's only when nothing was pending before.
+  const cudaError_t prior = cudaPeekAtLastError();
   k_relres_partials_na<<<nblocks, kNAThreads, 0, s>>>(labels, nps::Dims{nx, ny, nz}, b, x, scratch);
   k_relres_final_na<<<1, nps::kRedThreads, 0, s>>>(scratch, nblocks, scratch + 2 * kNoAllocMaxBlocks);
   double res[2] = {0.0, 0.0};
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (prior == cudaSuccess) {
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) (void)cudaGetLastError();  // this call's launch error: report it here
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(res, scratch + 2 * kNoAllocMaxBlocks, sizeof(res), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -147,13 +147,17 @@ void worker(npsolve_server *s, int idx) {
       if (s->stop && !sl.job) return;
       r = sl.job;
     }
-    r->t_start = Clock::now();
+    // The outputs go to locals first: a caller may call npsolve_server_result
+    // as soon as r->status is non-negative, so r's fields are published (and
+    // the status last) only under s->mu, below.
+    const Clock::time_point t_start = Clock::now();
     const long long n = r->cells();
-    int st = NPSOLVE_OK;
+    int st = NPSOLVE_OK, iters = 0;
+    double relres = 0.0;
     if (r->x) {
       // through the host-buffer call: the handle's staging buffers, b uploaded beside the setup
       st = npsolve_solve_host(sl.h, r->lab, r->nx, r->ny, r->nz, r->b, r->tol, r->max_iter, sl.stream, r->x,
-                              &r->iters, &r->relres);
+                              &iters, &relres);
     } else if (n > sl.cap_cells) {  // grow this slot's request buffers
       cudaFree(sl.d_lab);
       cudaFree(sl.d_b);
@@ -173,12 +177,16 @@ void worker(npsolve_server *s, int idx) {
       cudaMemcpyAsync(sl.d_lab, r->lab, n, cudaMemcpyHostToDevice, sl.stream);
       cudaMemcpyAsync(sl.d_b, r->b, n * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
       st = npsolve_solve(sl.h, sl.d_lab, r->nx, r->ny, r->nz, sl.d_b, r->tol, r->max_iter, sl.stream, sl.d_x,
-                         &r->iters, &r->relres);
+                         &iters, &relres);
     }
-    r->status = st;
-    r->t_end = Clock::now();
+    const Clock::time_point t_end = Clock::now();
     {
       std::lock_guard<std::mutex> lk(s->mu);
+      r->iters = iters;
+      r->relres = relres;
+      r->t_start = t_start;
+      r->t_end = t_end;
+      r->status = st;
       if (n > sl.ws_cells) sl.ws_cells = n;
       // the measured footprint replaces the estimate
       const size_t actual = npsolve_workspace_bytes(sl.h) + (size_t)sl.cap_cells * (1 + sizeof(float) + sizeof(double));
@@ -278,6 +286,13 @@ int npsolve_server_result(npsolve_server_t s, long long id, int *iters, double *
     r = it->second;
     if (r->status < 0) return sfail(s, NPSOLVE_BAD_ARG, "request %lld not finished", id);
     s->reqs.erase(it);
+    // a result read before the poll that would have reported it: drop the id
+    // from the finished list so that no later poll returns a released request
+    for (auto f = s->finished.begin(); f != s->finished.end(); ++f)
+      if (*f == id) {
+        s->finished.erase(f);
+        break;
+      }
   }
   if (iters) *iters = r->iters;
   if (rel_residual) *rel_residual = r->relres;
