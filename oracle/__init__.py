@@ -13,6 +13,10 @@ Contents (each wraps a C function of ``npsdo_oracle.c``):
 * ``image``, ``avgpool2``, ``interp_up2`` image pyramid / pooling /
   interpolation of Alg. 2
 * ``cconv``, ``cconv_kernels``, ``cconv_backward``  CConv block (Sec. 4.2.1)
+* ``round_bf16``, ``cconv_bf16``, ``cconv_kernels_bf16``  the CUDA library's
+  BF16 form of CConv (kernel values rounded to BF16; a numerical form of the
+  library, not of the paper), used by ``network(form="bf16")`` and by the
+  solvers with ``prec=PREC_NETWORK_BF16``
 * ``aff``, ``aff_grad``  Aff block (Sec. 4.2.1)
 * ``network``, ``network_level``, ``network_backward`` Alg. 2 and its reverse
 * ``loss``               training loss of Sec. 4.2.3 and its weight gradient
@@ -39,7 +43,8 @@ AFF_PARAMS = 3 * 27 + 1
 
 OK, BAD_ARG, BAD_DIMS, BAD_LABELS, NO_CONVERGENCE, BREAKDOWN = 0, 1, 2, 3, 4, 5
 
-PREC_NETWORK, PREC_IDENTITY, PREC_DENSE, PREC_NETWORK_SYM = 0, 1, 2, 3
+PREC_NETWORK, PREC_IDENTITY, PREC_DENSE, PREC_NETWORK_SYM, PREC_NETWORK_BF16 = 0, 1, 2, 3, 4
+_NET_PRECS = (PREC_NETWORK, PREC_NETWORK_SYM, PREC_NETWORK_BF16)
 
 
 def build(force: bool = False) -> str:
@@ -90,10 +95,15 @@ def _declare(L):
     L.or_npsdo.argtypes = [_u8p, _i, _i, _i, _i, _dp, _i, _dp, _dp, ctypes.c_double, _i, _i, _i,
                            _dp, ctypes.POINTER(_i), _dp, _dp]
     L.or_jacobi_pcg.argtypes = [_u8p, _i, _i, _i, _dp, ctypes.c_double, _i, _dp,
-                                ctypes.POINTER(_i), _dp]
+                                ctypes.POINTER(_i), _dp, _dp]
     L.or_npcg.argtypes = [_u8p, _i, _i, _i, _i, _dp, _i, _dp, _dp, ctypes.c_double, _i, _i, _i,
                           _dp, ctypes.POINTER(_i), _dp, _dp]
     L.or_check_labels.argtypes = [_u8p, _i, _i, _i]
+    L.or_round_bf16.argtypes = [ctypes.c_double]
+    L.or_round_bf16.restype = ctypes.c_double
+    L.or_cconv_bf16.argtypes = [_dp, _i, _i, _i, _dp, _dp, _i, _dp, _dp]
+    L.or_cconv_kernels_bf16.argtypes = [_dp, _i, _i, _i, _dp, _dp, _i, _dp]
+    L.or_network_form.argtypes = [_u8p, _i, _i, _i, _i, _dp, _i, _dp, _dp]
 
 
 def _f64(a):
@@ -240,15 +250,50 @@ def _check(st):
     return st
 
 
-def network(labels, L, w, r):
-    """z = P_net(I, r) (Alg. 2), output restricted to fluid."""
+def network(labels, L, w, r, form="fp64"):
+    """z = P_net(I, r) (Alg. 2), output restricted to fluid; form="bf16" gives
+    the library's BF16 form (every CConv kernel value rounded to BF16)."""
     labels, lp, nx, ny, nz = _lab(labels)
     w, wp = _f64(w)
     assert w.size == weight_count(L)
     r, rp = _f64(r)
     z = np.empty(labels.shape, np.float64)
-    _check(lib().or_network(lp, nx, ny, nz, L, wp, rp, z.ctypes.data_as(_dp)))
+    if form == "fp64":
+        _check(lib().or_network(lp, nx, ny, nz, L, wp, rp, z.ctypes.data_as(_dp)))
+    else:
+        assert form == "bf16"
+        _check(lib().or_network_form(lp, nx, ny, nz, L, wp, 1, rp, z.ctypes.data_as(_dp)))
     return z
+
+
+def round_bf16(v):
+    """Nearest BF16 value (ties to even) of the FP32 rounding of each entry."""
+    f = lib().or_round_bf16
+    return np.vectorize(lambda t: f(float(t)), otypes=[np.float64])(np.asarray(v, np.float64))
+
+
+def cconv_bf16(img, W, B, v, lvl):
+    """The BF16-form CConv of a level-``lvl`` field (fold by the channel-sum
+    identity, round the folded weights and every kernel value to BF16)."""
+    img, ip = _f64(img)
+    _, nz, ny, nx = img.shape
+    W, wp = _f64(np.reshape(W, (27, 3, 27)))
+    B, bp = _f64(np.reshape(B, (27,)))
+    v, vp = _f64(v)
+    out = np.empty((nz, ny, nx))
+    lib().or_cconv_bf16(ip, nx, ny, nz, wp, bp, int(lvl), vp, out.ctypes.data_as(_dp))
+    return out
+
+
+def cconv_kernels_bf16(img, W, B, lvl):
+    """BF16-form per-cell kernels K[z, y, x, a] of a level-``lvl`` image."""
+    img, ip = _f64(img)
+    _, nz, ny, nx = img.shape
+    W, wp = _f64(np.reshape(W, (27, 3, 27)))
+    B, bp = _f64(np.reshape(B, (27,)))
+    K = np.empty((nz, ny, nx, 27))
+    lib().or_cconv_kernels_bf16(ip, nx, ny, nz, wp, bp, int(lvl), K.ctypes.data_as(_dp))
+    return K
 
 
 WHICH = {"x1": 0, "r2": 1, "x2": 2, "x": 3, "r1": 4}
@@ -296,7 +341,7 @@ def npsdo(labels, b, *, L=4, w=None, tol=1e-6, max_iter=1000, n_ortho=2, residua
     """Alg. 1.  Returns dict(x, iters, status, res_hist, relres)."""
     labels, lp, nx, ny, nz = _lab(labels)
     n = labels.size
-    if prec in (PREC_NETWORK, PREC_NETWORK_SYM):
+    if prec in _NET_PRECS:
         w, wp = _f64(w)
         assert w.size == weight_count(L)
     else:
@@ -327,7 +372,7 @@ def npcg(labels, b, *, L=4, w=None, tol=1e-6, max_iter=1000, flexible=False, res
     Returns dict(x, iters, status, res_hist, relres) as npsdo does."""
     labels, lp, nx, ny, nz = _lab(labels)
     n = labels.size
-    if prec in (PREC_NETWORK, PREC_NETWORK_SYM):
+    if prec in _NET_PRECS:
         w, wp = _f64(w)
         assert w.size == weight_count(L)
     else:
@@ -356,10 +401,12 @@ def jacobi_pcg(labels, b, *, tol=1e-6, max_iter=10000):
     b, bp = _f64(b)
     x = np.zeros(labels.shape)
     it = ctypes.c_int(0)
+    hist = np.zeros(max_iter + 1)
     relres = ctypes.c_double(0.0)
     st = lib().or_jacobi_pcg(lp, nx, ny, nz, bp, float(tol), int(max_iter), x.ctypes.data_as(_dp),
-                             ctypes.byref(it), ctypes.byref(relres))
-    return {"x": x, "iters": it.value, "status": st, "relres": relres.value}
+                             ctypes.byref(it), hist.ctypes.data_as(_dp), ctypes.byref(relres))
+    return {"x": x, "iters": it.value, "status": st, "relres": relres.value,
+            "res_hist": hist[: it.value + 1].copy()}
 
 
 def network_transpose(labels, L, w, g):

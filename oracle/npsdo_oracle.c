@@ -324,6 +324,113 @@ void or_cconv_backward(const double *img, int nx, int ny, int nz, const double *
 }
 
 /* ------------------------------------------------------------------------ */
+/* The BF16 precision form.  This is a numerical form of the CUDA library    */
+/* (its NPSOLVE_BF16 setting), not something the paper defines; it is        */
+/* modelled here so that the library's BF16 solves can be compared with a    */
+/* definition of what they compute.  The form is the network of Alg. 2 with */
+/* every CConv kernel value rounded to BF16:                                  */
+/*  1. The three image channels sum to one (Sec. 3.2), also at the solid     */
+/*     padding, so I_solid = 1 - I_fluid - I_air and the kernel of Sec. 4.2.1 */
+/*     K_a(p) = B_a + sum_c sum_l W[a][c][l] I_c(p+l) equals                 */
+/*       B'_a + sum_l ( Wf'[a][l] nF(p+l) + Wa'[a][l] nA(p+l) )              */
+/*     with B'_a = B_a + sum_l W[a][solid][l],                               */
+/*          Wf'[a][l] = (W[a][fluid][l] - W[a][solid][l]) / F,               */
+/*          Wa'[a][l] = (W[a][air][l] - W[a][solid][l]) / F,                 */
+/*     F = 8^(lvl-1) fine cells per cell of level lvl, and the integer       */
+/*     counts nF = F I_fluid, nA = F I_air (0 at the padding).               */
+/*  2. B', Wf', Wa' are rounded to FP32 and then to BF16.                    */
+/*  3. Each K_a(p), summed exactly from the rounded terms, is rounded to     */
+/*     FP32 and then to BF16.                                                */
+/*  4. Everything else (applying the kernels, pooling, interpolation, Aff,   */
+/*     the solver) is unchanged, in FP64.                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Round to BF16 (8 significant bits, FP32's exponent range), ties to even,
+ * after rounding to FP32.  Written from the definition of the format: a
+ * normal value m 2^e (0.5 <= |m| < 1) keeps round(m 2^8) 2^(e-8); below the
+ * smallest normal 2^-126 the spacing is fixed at 2^-133. */
+double or_round_bf16(double v) {
+  float f = (float)v;
+  if (f == 0.0f || isnan(f) || isinf(f)) return f;
+  double a = (double)f, r;
+  if (fabs(a) < ldexp(1.0, -126)) {
+    r = ldexp(nearbyint(ldexp(a, 133)), -133);
+  } else {
+    int e;
+    double m = frexp(a, &e);
+    r = ldexp(nearbyint(ldexp(m, 8)), e - 8);
+  }
+  if (fabs(r) > 3.4028234663852886e38) r = r > 0 ? INFINITY : -INFINITY;
+  return r;
+}
+
+/* Step 1-2: the rounded folded parameters of one CConv block at level lvl. */
+static void bf16_fold(const double *W, const double *B, int lvl, double Wf[27][27], double Wa[27][27], double Bp[27]) {
+  double F = pow(8.0, lvl - 1);
+  for (int a = 0; a < 27; ++a) {
+    double bsum = B[a];
+    for (int l = 0; l < 27; ++l) bsum += W[(a * 3 + 2) * 27 + l];
+    Bp[a] = or_round_bf16(bsum);
+    for (int l = 0; l < 27; ++l) {
+      Wf[a][l] = or_round_bf16((W[(a * 3 + 0) * 27 + l] - W[(a * 3 + 2) * 27 + l]) / F);
+      Wa[a][l] = or_round_bf16((W[(a * 3 + 1) * 27 + l] - W[(a * 3 + 2) * 27 + l]) / F);
+    }
+  }
+}
+
+/* Step 3: the BF16-form kernel of the cell (x,y,z) of level lvl. */
+static void bf16_kernel_at(const double *img, int nx, int ny, int nz, double Wf[27][27], double Wa[27][27],
+                           const double Bp[27], int lvl, int x, int y, int z, double K[27]) {
+  double F = pow(8.0, lvl - 1), nF[27], nA[27];
+  for (int l = 0; l < 27; ++l) {
+    int xx = x + (l % 3) - 1, yy = y + (l / 3) % 3 - 1, zz = z + l / 9 - 1;
+    nF[l] = F * image_at(img, 0, nx, ny, nz, xx, yy, zz);
+    nA[l] = F * image_at(img, 1, nx, ny, nz, xx, yy, zz);
+  }
+  for (int a = 0; a < 27; ++a) {
+    double k = Bp[a];
+    for (int l = 0; l < 27; ++l) k += Wf[a][l] * nF[l] + Wa[a][l] * nA[l];
+    K[a] = or_round_bf16(k);
+  }
+}
+
+/* CConv of level lvl in the BF16 form (step 4: the kernels applied in FP64). */
+void or_cconv_bf16(const double *img, int nx, int ny, int nz, const double *W, const double *B, int lvl,
+                   const double *v, double *out) {
+  double Wf[27][27], Wa[27][27], Bp[27];
+  bf16_fold(W, B, lvl, Wf, Wa, Bp);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        double K[27];
+        bf16_kernel_at(img, nx, ny, nz, Wf, Wa, Bp, lvl, x, y, z, K);
+        double acc = 0.0;
+        for (int a = 0; a < 27; ++a)
+          acc += K[a] * vec_at(v, nx, ny, nz, x + (a % 3) - 1, y + (a / 3) % 3 - 1, z + a / 9 - 1);
+        out[((size_t)z * ny + y) * nx + x] = acc;
+      }
+}
+
+/* BF16-form kernels of every cell of level lvl, K[p*27 + a] (for the tests). */
+void or_cconv_kernels_bf16(const double *img, int nx, int ny, int nz, const double *W, const double *B, int lvl,
+                           double *K) {
+  double Wf[27][27], Wa[27][27], Bp[27];
+  bf16_fold(W, B, lvl, Wf, Wa, Bp);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x)
+        bf16_kernel_at(img, nx, ny, nz, Wf, Wa, Bp, lvl, x, y, z, K + 27 * (((size_t)z * ny + y) * nx + x));
+}
+
+/* A CConv of level lvl in the exact form (form 0) or the BF16 form (form 1). */
+static void cconv_form(const double *img, int nx, int ny, int nz, const double *W, int lvl, int form, const double *v,
+                       double *out) {
+  if (form == 1) or_cconv_bf16(img, nx, ny, nz, W, W + 27 * 3 * 27, lvl, v, out);
+  else or_cconv(img, nx, ny, nz, W, W + 27 * 3 * 27, v, out);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 4.2.1: the affine block Aff, read in 3D with normaliser 1/(27 n_l):    */
 /*   Aff(I) = Bbar + 1/(27 n) sum_p sum_c sum_l Wbar[c][l] I_c(p + l).        */
 /* ------------------------------------------------------------------------ */
@@ -405,8 +512,8 @@ static int check_dims(int nx, int ny, int nz, int L) {
 
 /* Forward pass of Alg. 2, keeping all intermediates.  The input r is first
  * zeroed outside the fluid (the reduced vector padded with zeros, Sec. 4.2). */
-static int network_forward(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, const double *r,
-                           or_fwd *f) {
+static int network_forward(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, int form,
+                           const double *r, or_fwd *f) {
   int st = check_dims(nx, ny, nz, L);
   if (st) return st;
   memset(f, 0, sizeof(*f));
@@ -431,14 +538,14 @@ static int network_forward(const uint8_t *lab, int nx, int ny, int nz, int L, co
     int *d = f->dims[l];
     or_avgpool2(f->img[l], 3, d[0], d[1], d[2], f->img[l + 1]);
     const double *W = w_cconv1(w, L, l);
-    or_cconv(f->img[l], d[0], d[1], d[2], W, W + 27 * 3 * 27, f->r1[l], f->x1[l]);
+    cconv_form(f->img[l], d[0], d[1], d[2], W, l, form, f->r1[l], f->x1[l]);
     or_avgpool2(f->x1[l], 1, d[0], d[1], d[2], f->r1[l + 1]);
   }
   /* Coarsest level: a single convolution. */
   {
     int *d = f->dims[L];
     const double *W = w_cconv1(w, L, L);
-    or_cconv(f->img[L], d[0], d[1], d[2], W, W + 27 * 3 * 27, f->r1[L], f->x1[L]);
+    cconv_form(f->img[L], d[0], d[1], d[2], W, L, form, f->r1[L], f->x1[L]);
     f->x[L] = f->x1[L];
   }
   /* Up pass: r2^l = Interp(x^{l+1}); x2^l = CConv2^l(r2^l, I^l);
@@ -448,7 +555,7 @@ static int network_forward(const uint8_t *lab, int nx, int ny, int nz, int L, co
     int *dc = f->dims[l + 1];
     or_interp_up2(f->x[l + 1], dc[0], dc[1], dc[2], f->r2[l]);
     const double *W = w_cconv2(w, l);
-    or_cconv(f->img[l], d[0], d[1], d[2], W, W + 27 * 3 * 27, f->r2[l], f->x2[l]);
+    cconv_form(f->img[l], d[0], d[1], d[2], W, l, form, f->r2[l], f->x2[l]);
     const double *A1 = w_aff(w, l, 0), *A2 = w_aff(w, l, 1);
     f->c1[l] = or_aff(f->img[l], d[0], d[1], d[2], A1, A1[81]);
     f->c2[l] = or_aff(f->img[l], d[0], d[1], d[2], A2, A2[81]);
@@ -462,7 +569,20 @@ static int network_forward(const uint8_t *lab, int nx, int ny, int nz, int L, co
  * (Sec. 4.2: the non-fluid entries of the output are removed). */
 int or_network(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, const double *r, double *z) {
   or_fwd f;
-  int st = network_forward(lab, nx, ny, nz, L, w, r, &f);
+  int st = network_forward(lab, nx, ny, nz, L, w, 0, r, &f);
+  if (st) return st;
+  size_t n = cells(nx, ny, nz);
+  for (size_t p = 0; p < n; ++p) z[p] = lab[p] == LAB_FLUID ? f.x[1][p] : 0.0;
+  fwd_free(&f);
+  return OR_OK;
+}
+
+/* z = P_net(I, r) in the exact form (form 0, as or_network) or the BF16
+ * form (form 1). */
+int or_network_form(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, int form, const double *r,
+                    double *z) {
+  or_fwd f;
+  int st = network_forward(lab, nx, ny, nz, L, w, form, r, &f);
   if (st) return st;
   size_t n = cells(nx, ny, nz);
   for (size_t p = 0; p < n; ++p) z[p] = lab[p] == LAB_FLUID ? f.x[1][p] : 0.0;
@@ -475,7 +595,7 @@ int or_network(const uint8_t *lab, int nx, int ny, int nz, int L, const double *
 int or_network_level(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, const double *r, int lvl,
                      int which, double *out, double *c12) {
   or_fwd f;
-  int st = network_forward(lab, nx, ny, nz, L, w, r, &f);
+  int st = network_forward(lab, nx, ny, nz, L, w, 0, r, &f);
   if (st) return st;
   if (lvl < 1 || lvl > L) {
     fwd_free(&f);
@@ -499,7 +619,7 @@ int or_network_level(const uint8_t *lab, int nx, int ny, int nz, int L, const do
 int or_network_backward(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, const double *r,
                         const double *gz, double *gw, double *gr) {
   or_fwd f;
-  int st = network_forward(lab, nx, ny, nz, L, w, r, &f);
+  int st = network_forward(lab, nx, ny, nz, L, w, 0, r, &f);
   if (st) return st;
   size_t nw = or_weight_count(L);
   memset(gw, 0, sizeof(double) * nw);
@@ -627,11 +747,13 @@ static double dot(const double *a, const double *b, size_t n) {
 /* Preconditioner choices for the solver, so that the reductions stated in
  * Sec. 4.1 can be checked: 0 = the network of Alg. 2, 1 = identity (masked),
  * 2 = a dense n x n matrix applied to the masked vector, 3 = the symmetric
- * variant P_sym,1 = P_net^T P_net of the appendix's symmetry analysis. */
+ * variant P_sym,1 = P_net^T P_net of the appendix's symmetry analysis, 4 =
+ * the network in the BF16 form (or_cconv_bf16). */
 #define PREC_NETWORK 0
 #define PREC_IDENTITY 1
 #define PREC_DENSE 2
 #define PREC_NETWORK_SYM 3
+#define PREC_NETWORK_BF16 4
 
 /* out = P(v) for the preconditioner choices above, restricted to fluid cells
  * (the network's output restriction, Sec. 4.2).  P_net^T is the input
@@ -642,6 +764,8 @@ static void apply_prec(const uint8_t *lab, int nx, int ny, int nz, int L, const 
   size_t n = cells(nx, ny, nz);
   if (prec == PREC_NETWORK) {
     or_network(lab, nx, ny, nz, L, w, v, out);
+  } else if (prec == PREC_NETWORK_BF16) {
+    or_network_form(lab, nx, ny, nz, L, w, 1, v, out);
   } else if (prec == PREC_NETWORK_SYM) {
     double *t = malloc(sizeof(double) * n), *gw = malloc(sizeof(double) * or_weight_count(L));
     or_network(lab, nx, ny, nz, L, w, v, t);
@@ -666,7 +790,7 @@ int or_npsdo(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w,
              const double *b, double tol, int max_iter, int n_ortho, int residual_mode, double *x, int *iters,
              double *res_hist, double *final_relres) {
   size_t n = cells(nx, ny, nz);
-  if (prec == PREC_NETWORK || prec == PREC_NETWORK_SYM) {
+  if (prec == PREC_NETWORK || prec == PREC_NETWORK_SYM || prec == PREC_NETWORK_BF16) {
     int st = check_dims(nx, ny, nz, L);
     if (st) return st;
   }
@@ -772,7 +896,7 @@ int or_npsdo(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w,
 /* Textbook PCG with the Jacobi preconditioner M = diag(A) on fluid cells.   */
 /* ------------------------------------------------------------------------ */
 int or_jacobi_pcg(const uint8_t *lab, int nx, int ny, int nz, const double *b, double tol, int max_iter, double *x,
-                  int *iters, double *final_relres) {
+                  int *iters, double *res_hist, double *final_relres) {
   size_t n = cells(nx, ny, nz);
   if (or_check_labels(lab, nx, ny, nz)) return OR_BAD_LABELS;
   double *r = malloc(sizeof(double) * n), *zz = malloc(sizeof(double) * n), *pp = malloc(sizeof(double) * n);
@@ -786,6 +910,7 @@ int or_jacobi_pcg(const uint8_t *lab, int nx, int ny, int nz, const double *b, d
   }
   double nb = sqrt(dot(r, r, n)), nr = nb, rz = dot(r, zz, n);
   int k = 0, status = OR_OK;
+  if (res_hist) res_hist[0] = nb; /* ||r_k|| for k = 0 .. iters (res_hist may be NULL) */
   while (nr >= tol * nb && nr > 0.0) {
     if (k >= max_iter) {
       status = OR_NO_CONVERGENCE;
@@ -809,6 +934,7 @@ int or_jacobi_pcg(const uint8_t *lab, int nx, int ny, int nz, const double *b, d
     rz = rz_new;
     for (size_t p = 0; p < n; ++p) pp[p] = zz[p] + beta * pp[p];
     nr = sqrt(dot(r, r, n));
+    if (res_hist) res_hist[k] = nr;
   }
   double *ax = q;
   or_lap_apply(lab, nx, ny, nz, x, ax);
@@ -848,7 +974,7 @@ int or_npcg(const uint8_t *lab, int nx, int ny, int nz, int L, const double *w, 
             const double *b, double tol, int max_iter, int flexible, int residual_mode, double *x, int *iters,
             double *res_hist, double *final_relres) {
   size_t n = cells(nx, ny, nz);
-  if (prec == PREC_NETWORK || prec == PREC_NETWORK_SYM) {
+  if (prec == PREC_NETWORK || prec == PREC_NETWORK_SYM || prec == PREC_NETWORK_BF16) {
     int st = check_dims(nx, ny, nz, L);
     if (st) return st;
   }
