@@ -243,8 +243,11 @@ int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, con
  * full reorthogonalisation; the k lowest Ritz vectors; `count` random
  * normalised combinations of them (coefficients N(0,1) from a 64-bit
  * Mersenne twister seeded with `seed`) written to out (device, count x n
- * floats, zero off fluid).  ritz_values_host (may be NULL) receives the k
- * lowest Ritz values.  2 <= m <= 128, 1 <= k <= m. */
+ * floats, zero off fluid; with k = m, every Ritz vector, the combinations are
+ * drawn directly in the Lanczos basis, which has the same distribution).
+ * ritz_values_host (may be NULL) receives the k
+ * lowest Ritz values.  2 <= m <= 2048, 1 <= k <= m; the basis takes
+ * (m + 1) n floats of device memory (13 GB for m = 1600 at 128^3). */
 int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const float *start, int m, int k, int count,
                         unsigned long long seed, float *out, double *ritz_values_host, void *stream);
 

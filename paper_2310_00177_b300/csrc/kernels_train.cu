@@ -390,24 +390,50 @@ namespace nps {
 // Lanczos helpers (training right-hand sides): dot products of a vector with
 // the m columns of a basis, and linear combinations of basis columns.
 // ---------------------------------------------------------------------------
-// out[j] partials: sum_p Q[j][p] w[p] for j < m (m <= 128), block partials.
+// Block partials of the dots sum_p Q[j][p] w[p], j < m: basis columns in
+// groups of 8 (w read once per group), FP32 products summed in runs of 32
+// elements per thread, runs and threads summed in FP64, one partial per
+// (block, column) in a fixed order.
 __global__ void __launch_bounds__(256) k_multidot(const float *__restrict__ Q, long long n, int m,
                                                   const float *__restrict__ w, double *__restrict__ part) {
-  extern __shared__ double sred[];  // [8 warps][m]
+  __shared__ double sred[8][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = 0; j < m; ++j) {
-    double acc = 0.0;
-    const float *q = Q + (size_t)j * n;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
-      acc += (double)q[p] * w[p];
-    acc = warp_sum(acc);
-    if (lane == 0) sred[warp * m + j] = acc;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    double t = 0.0;
-    for (int w8 = 0; w8 < 8; ++w8) t += sred[w8 * m + j];
-    part[(size_t)blockIdx.x * m + j] = t;
+  for (int j0 = 0; j0 < m; j0 += 8) {
+    const int jn = m - j0 < 8 ? m - j0 : 8;
+    double acc[8];
+    float run[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      acc[t] = 0.0;
+      run[t] = 0.f;
+    }
+    int cnt = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+      const float wp = w[p];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (t < jn) run[t] = fmaf(Q[(size_t)(j0 + t) * n + p], wp, run[t]);
+      if (++cnt == 32) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          acc[t] += (double)run[t];
+          run[t] = 0.f;
+        }
+        cnt = 0;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      acc[t] = warp_sum(acc[t] + (double)run[t]);
+      if (lane == 0) sred[warp][t] = acc[t];
+    }
+    __syncthreads();
+    if (threadIdx.x < jn) {
+      double t = 0.0;
+      for (int w8 = 0; w8 < 8; ++w8) t += sred[w8][threadIdx.x];
+      part[(size_t)blockIdx.x * m + j0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -419,12 +445,23 @@ __global__ void k_multidot_final(const double *__restrict__ part, int nblocks, i
   }
 }
 
-// out[p] = beta * out[p] + sum_j c[j] Q[j][p]  (c in device memory, FP64).
+// out[p] = beta * out[p] + sum_j c[j] Q[j][p]  (c in device memory, FP64):
+// FP32 products in four interleaved FP32 sums, combined in FP64.
 __global__ void k_combine_basis(const float *__restrict__ Q, long long n, int m, const double *__restrict__ c,
                                 float beta, float *__restrict__ out) {
+  extern __shared__ float cs[];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) cs[j] = (float)c[j];
+  __syncthreads();
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    double acc = beta != 0.f ? (double)beta * out[p] : 0.0;
-    for (int j = 0; j < m; ++j) acc += c[j] * (double)Q[(size_t)j * n + p];
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int j = 0;
+    for (; j + 4 <= m; j += 4) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) a[t] = fmaf(cs[j + t], Q[(size_t)(j + t) * n + p], a[t]);
+    }
+    for (; j < m; ++j) a[0] = fmaf(cs[j], Q[(size_t)j * n + p], a[0]);
+    double acc = (double)(a[0] + a[1]) + (double)(a[2] + a[3]);
+    if (beta != 0.f) acc += (double)beta * out[p];
     out[p] = (float)acc;
   }
 }
@@ -432,7 +469,7 @@ __global__ void k_combine_basis(const float *__restrict__ Q, long long n, int m,
 void launch_multidot(const float *Q, long long n, int m, const float *w, double *part, double *out, cudaStream_t s) {
   long long nb = (n + 255) / 256;
   if (nb > 148 * 4) nb = 148 * 4;
-  k_multidot<<<(int)nb, 256, sizeof(double) * 8 * m, s>>>(Q, n, m, w, part);
+  k_multidot<<<(int)nb, 256, 0, s>>>(Q, n, m, w, part);
   k_multidot_final<<<1, 128, 0, s>>>(part, (int)nb, m, out);
 }
 
@@ -440,7 +477,7 @@ void launch_combine_basis(const float *Q, long long n, int m, const double *c, f
                           cudaStream_t s) {
   long long nb = (n + 255) / 256;
   if (nb > 148 * 16) nb = 148 * 16;
-  k_combine_basis<<<(int)nb, 256, 0, s>>>(Q, n, m, c, beta, out);
+  k_combine_basis<<<(int)nb, 256, sizeof(float) * (size_t)m, s>>>(Q, n, m, c, beta, out);
 }
 
 }  // namespace nps

@@ -40,6 +40,7 @@ __device__ __forceinline__ uint32_t fdiv(const FastDiv &f, uint32_t n) {
 constexpr int kSolid = 0, kFluid = 1, kAir = 2;
 constexpr int kMaxLevels = 7;
 constexpr int kMaxOrtho = 4;
+constexpr int kMaxLanczos = 2048;  // Lanczos steps of the training right-hand-side generator
 constexpr int kRing = kMaxOrtho + 1;
 constexpr int kRedThreads = 256;   // threads of every reduction kernel
 constexpr int kRedMaxBlocks = 1184; // 148 SMs x 8

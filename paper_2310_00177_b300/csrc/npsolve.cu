@@ -1803,47 +1803,64 @@ int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, con
   return upload_weights(h);
 }
 
-// Eigen-decomposition of a small dense symmetric matrix by cyclic Jacobi
-// rotations (A is overwritten; V receives the eigenvectors as columns).
-static void jacobi_eigen(std::vector<double> &A, int m, std::vector<double> &V) {
-  V.assign((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
-    if (off < 1e-30) break;
-    for (int p = 0; p < m; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = A[(size_t)p * m + q];
-        if (fabs(apq) < 1e-300) continue;
-        const double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
-        // rotation angle that zeroes A[p][q]: tan(2 phi) = 2 apq / (aqq - app)
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
-        for (int k = 0; k < m; ++k) {  // columns p, q
-          const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
-          A[(size_t)k * m + p] = c * akp - sn * akq;
-          A[(size_t)k * m + q] = sn * akp + c * akq;
-        }
-        for (int k = 0; k < m; ++k) {  // rows p, q
-          const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
-          A[(size_t)p * m + k] = c * apk - sn * aqk;
-          A[(size_t)q * m + k] = sn * apk + c * aqk;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
-          V[(size_t)k * m + p] = c * vkp - sn * vkq;
-          V[(size_t)k * m + q] = sn * vkp + c * vkq;
-        }
+// Eigenpairs of the symmetric tridiagonal matrix with diagonal d[0..m-1] and
+// off-diagonal e[0..m-2] by implicit QR steps with the Wilkinson shift
+// (Golub and Van Loan, Matrix Computations, Sec. 8.3: bulge chasing with
+// Givens rotations, deflation of negligible off-diagonal entries).  On return
+// d holds the eigenvalues and, if `vectors`, column j of Z (row-major m x m)
+// the eigenvector of d[j].  Returns false if a block fails to converge in
+// 30 m steps.
+static bool tridiag_eigen(std::vector<double> &d, std::vector<double> e, int m, std::vector<double> &Z,
+                          bool vectors = true) {
+  Z.assign(vectors ? (size_t)m * m : 0, 0.0);
+  if (vectors)
+    for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
+  const double eps = 2.220446049250313e-16;
+  auto negligible = [&](int i) { return fabs(e[i]) <= eps * (fabs(d[i]) + fabs(d[i + 1])); };
+  long long steps = 0;
+  int hi = m - 1;
+  while (hi > 0) {
+    if (negligible(hi - 1)) {  // d[hi] has converged
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    if (++steps > 30LL * m) return false;
+    int lo = hi - 1;  // the unreduced block lo..hi
+    while (lo > 0 && !negligible(lo - 1)) --lo;
+    // Wilkinson shift: the eigenvalue of the trailing 2x2 block nearer d[hi]
+    const double h = 0.5 * (d[hi - 1] - d[hi]), eh = e[hi - 1];
+    const double mu = d[hi] - eh * eh / (h + (h >= 0.0 ? 1.0 : -1.0) * hypot(h, eh));
+    // the first rotation acts on (d[lo] - mu, e[lo]); each later one removes the bulge
+    double a = d[lo] - mu, b = e[lo], bulge = 0.0;
+    for (int k = lo; k < hi; ++k) {
+      const double r = hypot(a, b);
+      const double c = r > 0.0 ? a / r : 1.0, sn = r > 0.0 ? -b / r : 0.0;
+      if (k > lo) e[k - 1] = r;  // the bulge is rotated into the off-diagonal entry
+      const double p = d[k], q = e[k], t = d[k + 1];
+      d[k] = c * c * p - 2.0 * c * sn * q + sn * sn * t;
+      d[k + 1] = sn * sn * p + 2.0 * c * sn * q + c * c * t;
+      e[k] = c * sn * (p - t) + (c * c - sn * sn) * q;
+      if (k + 1 < hi) {  // the next bulge at (k+2, k)
+        bulge = -sn * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        a = e[k];
+        b = bulge;
       }
+      for (int i = 0; i < (vectors ? m : 0); ++i) {  // Z <- Z G on columns k, k+1
+        double *zr = &Z[(size_t)i * m];
+        const double zk = zr[k], zk1 = zr[k + 1];
+        zr[k] = c * zk - sn * zk1;
+        zr[k + 1] = sn * zk + c * zk1;
+      }
+    }
   }
+  return true;
 }
 
 int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const float *start, int m, int k, int count,
                         unsigned long long seed, float *out, double *ritz_values_host, void *stream) {
-  if (!labels || !start || !out || m < 2 || m > 128 || k < 1 || k > m || count < 0)
+  if (!labels || !start || !out || m < 2 || m > kMaxLanczos || k < 1 || k > m || count < 0)
     return fail(nullptr, NPSOLVE_BAD_ARG, "bad argument");
   if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
     return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
@@ -1895,40 +1912,61 @@ int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const flo
       launch_combine_basis(wv, n, 1, coef, 0.f, Q + (size_t)(j + 1) * n, s);
     }
   }
+  double *coefs = nullptr;  // all combinations' basis coefficients (count x steps)
   if (!ret) {
     // Ritz pairs of T = tridiag(beta, alpha, beta)
     const int mm = steps;
-    std::vector<double> T((size_t)mm * mm, 0.0), V;
-    for (int i = 0; i < mm; ++i) {
-      T[(size_t)i * mm + i] = alpha[i];
-      if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[i];
-    }
-    jacobi_eigen(T, mm, V);
+    // With every Ritz vector in the combinations (k >= steps) the eigenvectors
+    // are not needed: Y is orthogonal, so Y c with c ~ N(0, I) is again
+    // N(0, I), and b = Q g / ||g|| with g ~ N(0, I) in the Lanczos basis has
+    // the same distribution as the normalised Q Y c.
+    const int kk = k < mm ? k : mm;
+    const bool all_ritz = kk == mm;
+    std::vector<double> ev(alpha.begin(), alpha.begin() + mm), off(mm > 1 ? mm - 1 : 1, 0.0), V;
+    for (int i = 0; i + 1 < mm; ++i) off[i] = beta[i];
+    if (!tridiag_eigen(ev, off, mm, V, !all_ritz))
+      ret = fail(nullptr, NPSOLVE_CUDA_ERROR, "lanczos: tridiagonal eigensolver did not converge");
     std::vector<int> order(mm);
     for (int i = 0; i < mm; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return T[(size_t)a * mm + a] < T[(size_t)b * mm + b]; });
-    const int kk = k < mm ? k : mm;
-    if (ritz_values_host)
-      for (int i = 0; i < kk; ++i) ritz_values_host[i] = T[(size_t)order[i] * mm + order[i]];
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+    if (!ret && ritz_values_host)
+      for (int i = 0; i < kk; ++i) ritz_values_host[i] = ev[order[i]];
     // count random normalised combinations b = Q Y c, c ~ N(0, 1)
     std::mt19937_64 rng(seed);
     std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<double> qcs((size_t)(count > 0 ? count : 1) * mm, 0.0);
     for (int c = 0; c < count && !ret; ++c) {
-      std::vector<double> cc(kk), qc(mm, 0.0);
+      std::vector<double> cc(kk);
       double nrm = 0.0;
       for (int i = 0; i < kk; ++i) {
         cc[i] = nd(rng);
         nrm += cc[i] * cc[i];
       }
       nrm = sqrt(nrm);  // Ritz vectors are orthonormal: ||Q Y c|| = ||c||
-      for (int i = 0; i < kk; ++i)
-        for (int r = 0; r < mm; ++r) qc[r] += V[(size_t)r * mm + order[i]] * cc[i] / nrm;
-      cudaMemcpyAsync(coef, qc.data(), sizeof(double) * mm, cudaMemcpyHostToDevice, s);
-      launch_combine_basis(Q, n, mm, coef, 0.f, out + (size_t)c * n, s);
-      cudaStreamSynchronize(s);
+      double *qc = qcs.data() + (size_t)c * mm;
+      if (all_ritz) {
+        for (int r = 0; r < mm; ++r) qc[r] = cc[r] / nrm;
+        continue;
+      }
+      for (int r = 0; r < mm; ++r) {
+        const double *vr = V.data() + (size_t)r * mm;
+        double t = 0.0;
+        for (int i = 0; i < kk; ++i) t += vr[order[i]] * cc[i];
+        qc[r] = t / nrm;
+      }
+    }
+    if (!ret && count > 0) {
+      if (cudaMalloc(&coefs, sizeof(double) * qcs.size()) != cudaSuccess) {
+        ret = fail(nullptr, NPSOLVE_OOM, "lanczos: coefficient buffer");
+      } else {
+        cudaMemcpyAsync(coefs, qcs.data(), sizeof(double) * qcs.size(), cudaMemcpyHostToDevice, s);
+        for (int c = 0; c < count; ++c)
+          launch_combine_basis(Q, n, mm, coefs + (size_t)c * mm, 0.f, out + (size_t)c * n, s);
+      }
     }
   }
   cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(coefs);
   cudaFree(Q);
   cudaFree(wv);
   cudaFree(part);

@@ -194,14 +194,33 @@ def test_true_residual_matches_oracle():
     assert g == pytest.approx(ref, rel=1e-12)
 
 
-def test_jacobi_pcg_matches_oracle():
+@pytest.mark.parametrize("scene", ["pool32", "slosh64"])
+@pytest.mark.parametrize("tol", [1e-6, 1e-5])
+def test_jacobi_pcg_matches_oracle(scene, tol):
+    # The count exactly where the oracle's stop is clear of tol ||b|| by 1% or
+    # more on both sides, else within one; x to 1e-5.  CG's residual falls by
+    # only 3-5% per step here, so the 5% margin of the NPSDO tests is rarely
+    # met; the GPU iteration (FP32 vectors, FP64 dots) tracks the FP64 one to
+    # a few 1e-3 relative in the residual over these 150-400 steps (the true
+    # residuals at the stop agree to 3e-3), a third of the 1% margin.  Three
+    # of the four cases here are clear (slosh64 at 1e-5 stops 0.4% above).
+    # (1e-7 is at the FP32 vectors' floor: the true residual stalls near
+    # 1.2e-7 there, so it is not a parity case.)
     b = _binding()
-    lab, rhs, _ = _config1()
-    ores = oracle.jacobi_pcg(lab, rhs.astype(np.float64), tol=1e-6)
-    x, iters, relres, st = b.jacobi_pcg(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=1e-6)
-    assert st == b.OK and relres < 1.2e-6
-    assert abs(iters - ores["iters"]) <= max(2, ores["iters"] // 50)
-    assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-4
+    if scene == "pool32":
+        lab, rhs, _ = _config1()
+    else:
+        lab = synth.slosh_scene(64, 2000)
+        rhs = synth.rhs_normal(lab, 2001).astype(np.float32)
+    ores = oracle.jacobi_pcg(lab, rhs.astype(np.float64), tol=tol)
+    x, iters, relres, st = b.jacobi_pcg(_dev(lab, torch.uint8), _dev(rhs, torch.float32), tol=tol)
+    assert st == b.OK and relres < 1.2 * tol
+    h = ores["res_hist"] / ores["res_hist"][0]
+    if h[-1] < 0.99 * tol and h[-2] > 1.01 * tol:
+        assert iters == ores["iters"]
+    else:
+        assert (scene, tol) == ("slosh64", 1e-5) and abs(iters - ores["iters"]) <= 1
+    assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()), _remove_neumann_constants(lab, ores["x"])) <= 1e-5
 
 
 def test_error_statuses():
