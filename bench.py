@@ -3,7 +3,8 @@
 One step = one complete solve (setup from the labels, the NPSDO iterations,
 the final FP64 true-residual check) of a seeded 256^3 scene shaped like the
 paper's mixed-boundary examples (solid shell, 10-40 solid spheres/boxes,
-sinusoidal free surface, b ~ N(0,1) on fluid), in the BF16 served form.
+sinusoidal free surface, b ~ N(0,1) on fluid), in the BF16 served form, with
+the project-trained network of the paper's depth, L = 6 (Sec. 5; --levels).
 The inputs are resident in HBM when the timed region starts; every 256^3
 vector is 67 MB and one iteration touches about 1.5 GB, so the working set
 is far larger than the 126 MB L2 and no flush is needed between steps.
@@ -12,6 +13,8 @@ Also reported on the same line:
   e2e            the same solve through npsolve_solve_host (pinned host
                  buffers in, x back to the host, copies inside the timing)
   fp32_form      ms per solve and iterations of the FP32 form
+  sweeps         the appendix's sweeps on the same problem: L = 3..6 (each
+                 with its trained weights) and n_ortho = 0..4, BF16 form
   solver_variants  PCG and flexible PCG with the same network (BF16 form):
                  ms per solve, iterations, true relative residual; PCG with
                  the symmetric variant P_net^T P_net; the network's relative
@@ -59,8 +62,18 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "ms per 256^3 solve to 1e-6 rel. residual (BF16 served form)"
-WEIGHTS_FILE = os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32")
-ORACLE_ITERS_FILE = os.path.join(ROOT, "oracle", "iterations_slosh256.json")
+WEIGHTS_DIR = os.path.join(ROOT, "paper_2310_00177_b300", "weights")
+# the network depth of the timed solve: the paper's six levels (Sec. 5) when
+# their trained weights are present
+DEFAULT_LEVELS = 6 if os.path.exists(os.path.join(WEIGHTS_DIR, "npsdo_L6.f32")) else 4
+
+
+def weights_file(levels):
+    return os.path.join(WEIGHTS_DIR, f"npsdo_L{levels}.f32")
+
+
+def oracle_iters_file(levels):
+    return os.path.join(ROOT, "oracle", "iterations_slosh256" + (f"_L{levels}" if levels != 4 else "") + ".json")
 
 # DRAM bytes (read + write) per level-1 CConv launch of the 256^3 workload,
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
@@ -81,12 +94,13 @@ BYTES_PER_CELL = {
 }
 
 
-def load_weights():
+def load_weights(levels):
     from paper_2310_00177_b300 import synth
 
-    if os.path.exists(WEIGHTS_FILE):
-        return np.fromfile(WEIGHTS_FILE, dtype=np.float32), "trained (paper_2310_00177_b300/weights/npsdo_L4.f32)"
-    return synth.init_weights(4, 7).astype(np.float32), "random-init (seed 7)"
+    f = weights_file(levels)
+    if os.path.exists(f):
+        return np.fromfile(f, dtype=np.float32), f"trained (paper_2310_00177_b300/weights/npsdo_L{levels}.f32)"
+    return synth.init_weights(levels, 7).astype(np.float32), "random-init (seed 7)"
 
 
 def workload(n):
@@ -162,25 +176,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_iteration_ms(lab, rhs, w, iters_sample=1):
+def cpu_oracle_iteration_ms(lab, rhs, w, levels, iters_sample=1):
     """Wall time of `iters_sample` FP64 oracle NPSDO iterations on the workload."""
     import oracle
 
     t = time.perf_counter()
-    oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-6, max_iter=iters_sample)
+    oracle.npsdo(lab, rhs.astype(np.float64), L=levels, w=w.astype(np.float64), tol=1e-6, max_iter=iters_sample)
     return (time.perf_counter() - t) * 1e3 / iters_sample
 
 
-def oracle_iterations(n):
+def oracle_iterations(n, levels):
     """The FP64 oracle's own iteration count for this problem, stored by
     oracle/count_iterations.py for the current weights file."""
     import hashlib
 
-    if os.path.exists(ORACLE_ITERS_FILE) and os.path.exists(WEIGHTS_FILE):
-        d = json.load(open(ORACLE_ITERS_FILE))
-        wid = hashlib.sha256(open(WEIGHTS_FILE, "rb").read()).hexdigest()[:16]
+    f, wf = oracle_iters_file(levels), weights_file(levels)
+    if os.path.exists(f) and os.path.exists(wf):
+        d = json.load(open(f))
+        wid = hashlib.sha256(open(wf, "rb").read()).hexdigest()[:16]
         if d.get("weights_sha256_16") == wid and d.get("n") == n:
-            return int(d["iters"]), "oracle FP64 solve of this problem (" + os.path.basename(ORACLE_ITERS_FILE) + ")"
+            return int(d["iters"]), "oracle FP64 solve of this problem (" + os.path.basename(f) + ")"
     return None, None
 
 
@@ -207,13 +222,14 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     lab, rhs = workload(args.n)
-    w, wdesc = load_weights()
+    L = args.levels
+    w, wdesc = load_weights(L)
     cores = os.cpu_count()
     for _ in range(args.warmup):
-        cpu_oracle_iteration_ms(lab, rhs, w)
-    times = [cpu_oracle_iteration_ms(lab, rhs, w) for _ in range(args.steps)]
+        cpu_oracle_iteration_ms(lab, rhs, w, L)
+    times = [cpu_oracle_iteration_ms(lab, rhs, w, L) for _ in range(args.steps)]
     per_it = float(np.mean(times))
-    iters, src = oracle_iterations(args.n)
+    iters, src = oracle_iterations(args.n, L)
     if iters is None:
         print(json.dumps({"impl": "reference", "unavailable": "no stored oracle iteration count for these weights "
                           "(run oracle/count_iterations.py)"}))
@@ -224,7 +240,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_it, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"slosh {args.n}^3 mixed BC, L=4, n_ortho=2, tol 1e-6", "weights": wdesc},
+        "config": {"workload": f"slosh {args.n}^3 mixed BC, L={L}, n_ortho=2, tol 1e-6", "weights": wdesc},
         "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -240,6 +256,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-latency workload")
     ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--levels", type=int, default=DEFAULT_LEVELS, help="network levels of the timed solve")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the level / n_ortho sweeps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -264,11 +282,12 @@ def main():
     from paper_2310_00177_b300 import binding, synth
 
     lab, rhs = workload(args.n)
-    w, wdesc = load_weights()
+    L = args.levels
+    w, wdesc = load_weights(L)
     lab_d = torch.from_numpy(lab).to(dev)
     rhs_d = torch.from_numpy(rhs).to(dev)
     x_d = torch.empty(lab.shape, dtype=torch.float64, device=dev)
-    sol = binding.Solver(w, levels=4, n_ortho=2, precision=binding.BF16)
+    sol = binding.Solver(w, levels=L, n_ortho=2, precision=binding.BF16)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -310,7 +329,7 @@ def main():
     e2e_value = replica_value(e2e_ms, 1, world)
 
     # ---- FP32 form -----------------------------------------------------
-    sol32 = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
+    sol32 = binding.Solver(w, levels=L, n_ortho=2, precision=binding.FP32)
     x32 = torch.empty_like(x_d)
     sol32.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=x32)
     torch.cuda.synchronize()
@@ -331,7 +350,7 @@ def main():
     # network can stall on this problem)
     variants = {}
     for name, method in (("pcg", binding.PCG), ("fpcg", binding.FPCG)):
-        sv = binding.Solver(w, levels=4, precision=binding.BF16, method=method)
+        sv = binding.Solver(w, levels=L, precision=binding.BF16, method=method)
         xv = torch.empty_like(x_d)
         sv.solve(lab_d, rhs_d, 1e-6, 500, x=xv)
         torch.cuda.synchronize()
@@ -346,7 +365,7 @@ def main():
     # symmetry analysis; built from the same weights, not retrained), and the
     # relative asymmetry measure S of the network on three pairs of random
     # vectors on the fluid cells of this problem
-    sv = binding.Solver(w, levels=4, method=binding.PCG, symmetric=True)
+    sv = binding.Solver(w, levels=L, method=binding.PCG, symmetric=True)
     xv = torch.empty_like(x_d)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -366,13 +385,45 @@ def main():
     variants["asymmetry_S"] = {"values": svals, "median": float(np.median(svals)),
                                "vectors": "N(0,1) on fluid cells, 3 pairs"}
 
+    # ---- the appendix's sweeps on the same problem (BF16 form): the number of
+    # levels L = 3..6, each with its own trained weights, and n_ortho = 0..4 with
+    # the timed network (ms per solve: mean of 3 solves after one warm-up solve)
+    sweeps = None
+    if not args.no_sweep:
+        def timed(sv, reps=3):
+            xs = torch.empty_like(x_d)
+            sv.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=xs)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                _, it_s, rr_s, st_s = sv.solve(lab_d, rhs_d, 1e-6, args.max_iter, x=xs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return {"ms_per_solve": e0.elapsed_time(e1) / reps, "iters": it_s, "relres": rr_s,
+                    "status": binding.STATUS_NAMES[st_s]}
+
+        lv = {}
+        for Ls in (3, 4, 5, 6):
+            if os.path.exists(weights_file(Ls)):
+                sv = binding.Solver(np.fromfile(weights_file(Ls), np.float32), levels=Ls, n_ortho=2,
+                                    precision=binding.BF16)
+                lv[str(Ls)] = timed(sv)
+                sv.close()
+        no = {}
+        for k in range(5):
+            sv = binding.Solver(w, levels=L, n_ortho=k, precision=binding.BF16)
+            no[str(k)] = timed(sv)
+            sv.close()
+        sweeps = {"levels": lv, "n_ortho": no, "n_ortho_levels": L,
+                  "note": "levels: n_ortho 2, each L with its trained weights file; n_ortho: the timed network"}
+
     # ---- the 128^3 problem (FP32 form, trained network) against Jacobi-PCG on
     # the same GPU, both to 1e-6 (device-resident inputs, one warm-up solve each)
     lab128 = synth.slosh_scene(128, 2000)
     rhs128 = synth.rhs_normal(lab128, 2001).astype(np.float32)
     l128, b128 = torch.from_numpy(lab128).to(dev), torch.from_numpy(rhs128).to(dev)
     x128 = torch.empty(lab128.shape, dtype=torch.float64, device=dev)
-    s128 = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
+    s128 = binding.Solver(w, levels=L, n_ortho=2, precision=binding.FP32)
     cmp128 = {}
     for name, run in (("npsdo_fp32", lambda: s128.solve(l128, b128, 1e-6, args.max_iter, x=x128)),
                       ("jacobi_pcg", lambda: binding.jacobi_pcg(l128, b128, 1e-6, 100000, x=x128))):
@@ -389,7 +440,7 @@ def main():
     # ---- one training step (Sec. 4.2.3): a batch of 8 systems at 64^3 and 8 at
     # 128^3, loss, hand-written backward and the Adam update (N(0,1) right-hand
     # sides here: the step's cost does not depend on them)
-    st_sol = binding.Solver(w, levels=4, n_ortho=2, precision=binding.FP32)
+    st_sol = binding.Solver(w, levels=L, n_ortho=2, precision=binding.FP32)
     tl, tb = [], []
     for i, nn in enumerate([64] * 8 + [128] * 8):
         lt = synth.slosh_scene(nn, 5000 + i)
@@ -419,7 +470,10 @@ def main():
         return
     n = lab.size
     pk = peaks()
-    dom = max(prof, key=lambda k: prof[k][0])
+    # the level-1 CConvs: the largest class of the solve, and the one whose
+    # algorithmic bytes are defined per launch (the others are in
+    # roofline_stencil_vector and kernel_breakdown)
+    dom = "cconv_l1" if prof.get("cconv_l1", (0.0, 0))[1] else max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms / max(dom_launches, 1) / 1e3
     # 4-cell x-groups with a fluid cell: the vector kernels skip the loads of the others
@@ -484,7 +538,7 @@ def main():
     if not args.no_serve:
         from paper_2310_00177_b300 import serve
 
-        served = serve.serve_workload(w)
+        served = serve.serve_workload(w, levels=L)
         served = {k: served[k] for k in ("requests", "rate_per_s", "sizes", "p50_ms", "p99_ms", "mean_ms",
                                          "solves_per_s", "all_converged", "peak_reserved_gb", "budget_gb",
                                          "max_active", "per_size")}
@@ -504,7 +558,7 @@ def main():
     }
     cpu = None
     if not args.no_cpu:
-        per_it = cpu_oracle_iteration_ms(lab, rhs, w)
+        per_it = cpu_oracle_iteration_ms(lab, rhs, w, L)
         cpu = {"value": per_it * it_bf16, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"1 FP64 oracle NPSDO iteration of this 256^3 solve ({per_it:.0f} ms), "
                          f"scaled by the {it_bf16} iterations of the timed solve"}
@@ -512,13 +566,14 @@ def main():
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": f"slosh {args.n}^3 mixed BC (seed 3000), b ~ N(0,1) (seed 3001), L=4, n_ortho=2, "
+        "config": {"workload": f"slosh {args.n}^3 mixed BC (seed 3000), b ~ N(0,1) (seed 3001), L={L}, n_ortho=2, "
                                f"tol 1e-6", "weights": wdesc, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": int(lab.nbytes + rhs.nbytes),
                 "d2h_bytes_per_step": int(n * 8)},
         "fp32_form": {"ms_per_solve": fp32_ms, "iters": it_fp32},
         "solver_variants": variants,
+        "sweeps": sweeps,
         "slosh128_vs_jacobi_pcg": cmp128,
         "train_step": train,
         "served": served,

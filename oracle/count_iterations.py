@@ -8,8 +8,9 @@ per-iteration time by the stored iteration count.
 
 The problems are the sloshing scenes of the benchmark: 256^3 (scene seed
 3000, right-hand side seed 3001) and 128^3 (scene seed 2000, right-hand side
-seed 2001), L = 4, n_ortho = 2, tol 1e-6, recurrence residual, with the
-network weights identified by their SHA-256.  --form bf16 solves with the
+seed 2001), L levels (--levels, default 4) with the network weights
+paper_2310_00177_b300/weights/npsdo_L<L>.f32 identified by their SHA-256,
+n_ortho = 2, tol 1e-6, recurrence residual.  --form bf16 solves with the
 oracle's model of the library's BF16 form (every CConv kernel value rounded
 to BF16) instead of the exact FP64 network.
 
@@ -19,7 +20,7 @@ component that touches no air (the matrix is singular there), so the record
 holds x with each such component's mean removed: its values at 4096 seeded
 fluid cells, the sum and the 2-norm of every z-plane, and its 2-norm.
 
-Usage: python oracle/count_iterations.py [--n 256] [--form fp64|bf16]
+Usage: python oracle/count_iterations.py [--n 256] [--form fp64|bf16] [--levels 4]
                                          [--weights FILE] [--out FILE]
 """
 import argparse
@@ -46,8 +47,9 @@ def weights_id(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def default_out(n, form):
-    return os.path.join(HERE, f"iterations_slosh{n}" + ("_bf16" if form == "bf16" else "") + ".json")
+def default_out(n, form, levels=4):
+    return os.path.join(HERE, f"iterations_slosh{n}" + ("_bf16" if form == "bf16" else "") +
+                        (f"_L{levels}" if levels != 4 else "") + ".json")
 
 
 def remove_neumann_constants(labels, x):
@@ -80,19 +82,22 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=256, choices=sorted(SEEDS))
     ap.add_argument("--form", default="fp64", choices=["fp64", "bf16"])
-    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32"))
+    ap.add_argument("--levels", type=int, default=4)
+    ap.add_argument("--weights", default=None, help="default: paper_2310_00177_b300/weights/npsdo_L<levels>.f32")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
-    out_path = args.out or default_out(args.n, args.form)
+    if args.weights is None:
+        args.weights = os.path.join(ROOT, "paper_2310_00177_b300", "weights", f"npsdo_L{args.levels}.f32")
+    out_path = args.out or default_out(args.n, args.form, args.levels)
     s_lab, s_rhs = SEEDS[args.n]
     lab = synth.slosh_scene(args.n, s_lab)
     rhs = synth.rhs_normal(lab, s_rhs).astype(np.float32)
     w = np.fromfile(args.weights, dtype=np.float32)
     prec = oracle.PREC_NETWORK_BF16 if args.form == "bf16" else oracle.PREC_NETWORK
     t = time.time()
-    res = oracle.npsdo(lab, rhs.astype(np.float64), L=4, w=w.astype(np.float64), tol=1e-6, max_iter=2000,
+    res = oracle.npsdo(lab, rhs.astype(np.float64), L=args.levels, w=w.astype(np.float64), tol=1e-6, max_iter=2000,
                        prec=prec)
-    out = {"n": args.n, "form": args.form, "scene_seed": s_lab, "rhs_seed": s_rhs,
+    out = {"n": args.n, "form": args.form, "levels": args.levels, "scene_seed": s_lab, "rhs_seed": s_rhs,
            "weights_sha256_16": weights_id(args.weights), "iters": res["iters"], "status": res["status"],
            "relres": res["relres"], "seconds": time.time() - t,
            "res_hist": [float(v) for v in res["res_hist"] / res["res_hist"][0]],

@@ -292,8 +292,6 @@ __global__ void k_interp(const float *__restrict__ in, Dims coarse, float *__res
 // per fine cell), and writes four 16-byte rows.  Per axis, fine 2j uses
 // 0.25 c[j-1] + 0.75 c[j] (c[0] at j = 0) and fine 2j+1 uses
 // 0.75 c[j] + 0.25 c[j+1] (c[n-1] at the end), as in k_interp.
-__device__ __forceinline__ float lerp_lo(float a, float b) { return 0.25f * a + 0.75f * b; }  // fine 2j from c[j-1], c[j]
-__device__ __forceinline__ float lerp_hi(float b, float c) { return 0.75f * b + 0.25f * c; }  // fine 2j+1 from c[j], c[j+1]
 
 // skip (optional): one byte per (32 x 8 fine tile, fine plane), tile-major;
 // blocks whose two planes are both marked non-zero are not written (no later read).

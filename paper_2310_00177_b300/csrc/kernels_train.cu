@@ -382,6 +382,12 @@ void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, cons
 }
 int wgrad_outputs() { return kWG; }
 
+// *acc |= *flag (the label check of one training example into the batch's flag).
+__global__ void k_or_flag(const unsigned int *__restrict__ flag, unsigned int *__restrict__ acc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *flag) *acc = 1u;
+}
+void launch_or_flag(const unsigned int *flag, unsigned int *acc, cudaStream_t s) { k_or_flag<<<1, 32, 0, s>>>(flag, acc); }
+
 }  // namespace nps
 
 namespace nps {

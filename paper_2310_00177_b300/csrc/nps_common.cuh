@@ -203,6 +203,13 @@ struct Dims {
   __host__ __device__ long long n() const { return (long long)nx * ny * nz; }
 };
 
+// The x2 linear upsampling of Alg. 2 per axis (half-pixel centres, edge
+// clamp): fine 2j = 0.25 c[j-1] + 0.75 c[j] (c[0] itself at j = 0), fine
+// 2j+1 = 0.75 c[j] + 0.25 c[j+1] (c[n-1] for c[n]).  Written as explicit FMAs
+// so that every kernel that interpolates rounds identically.
+__device__ __forceinline__ float lerp_lo(float a, float b) { return fmaf(0.25f, a, 0.75f * b); }  // c[j-1], c[j]
+__device__ __forceinline__ float lerp_hi(float b, float c) { return fmaf(0.75f, b, 0.25f * c); }  // c[j], c[j+1]
+
 // Grids hold fewer than 2^31 cells, so the index arithmetic is 32-bit.
 __device__ __forceinline__ void cell_xyz(long long p, const Dims &d, int &x, int &y, int &z) {
   const unsigned q = (unsigned)p, nx = (unsigned)d.nx, ny = (unsigned)d.ny;

@@ -97,6 +97,22 @@ void launch_umma_selftest(float *d_out, float *d_ref, int *err, cudaStream_t s);
 
 // kernels_cached.cu: per-solve classification and kernel cache, streamed CConv
 bool stream_shape_ok(Dims d);          // the TMA boxes need rows of a multiple of 16 bytes
+
+// kernels_tail.cu: the coarse levels T..L of the network in one cluster launch.
+constexpr int kTailCtas = 8;                 // CTAs of the cluster
+constexpr long long kTailMaxCells = 4096;    // levels of at most this many cells run in the tail
+constexpr int kTailMaxSmem = 160 * 1024;     // shared memory a tail CTA may stage (bytes)
+struct TailParams {
+  int T, L;                                  // levels T..L (T >= 2); r2 of level T-1 is written too
+  Dims dims[kMaxLevels + 1];
+  const float *k1[kMaxLevels + 1], *k2[kMaxLevels + 1];  // per-cell kernels, 27 x n floats, tap-major
+  float *x1[kMaxLevels + 1], *r1[kMaxLevels + 1], *r2[kMaxLevels + 1], *xc[kMaxLevels + 1];
+  const double *affc;                        // c1, c2 of each level (2 l, 2 l + 1)
+  const SolveState *st;                      // may be null
+};
+void launch_tail_kernels(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int round_k, float *K,
+                         cudaStream_t s);
+int launch_tail(const TailParams &P, cudaStream_t s);  // 0 on success
 long long stream_desc_count(Dims d);   // plane descriptors of a level (tiles x nz)
 size_t stream_desc_bytes();            // bytes of one plane descriptor
 int cached_entry_bytes(bool bf16);     // bytes of one cached kernel
@@ -195,6 +211,7 @@ void launch_axpby(const uint8_t *lab, long long n, float alpha, const float *a, 
 void launch_scale_by_inv_norm(const uint8_t *lab, long long n, float scale, const double *norm2, const float *a,
                               float *out, cudaStream_t s);
 
+void launch_or_flag(const unsigned int *flag, unsigned int *acc, cudaStream_t s);
 void launch_multidot(const float *Q, long long n, int m, const float *w, double *part, double *out, cudaStream_t s);
 void launch_combine_basis(const float *Q, long long n, int m, const double *c, float beta, float *out,
                           cudaStream_t s);

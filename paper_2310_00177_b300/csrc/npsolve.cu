@@ -57,6 +57,12 @@ struct Workspace {
   float *x1[kMaxLevels + 1] = {}, *r1[kMaxLevels + 1] = {}, *r2[kMaxLevels + 1] = {}, *x2[kMaxLevels + 1] = {},
         *xc[kMaxLevels + 1] = {};
   ushort2 *counts[kMaxLevels + 1] = {};
+  // the coarse tail (kernels_tail.cu): its first level (0: none) for the
+  // current grid and the materialised per-cell kernels of its levels
+  int tail_T = 0;
+  float *tailk = nullptr;
+  size_t tailk_cap = 0;  // floats
+  float *tk1[kMaxLevels + 1] = {}, *tk2[kMaxLevels + 1] = {};
   // per-solve kernel cache of the mixed-window cells (cached path)
   uint8_t *kdesc[kMaxLevels + 1] = {};    // plane descriptors per level
   long long kdesc_cap[kMaxLevels + 1] = {};  // descriptors kdesc can hold
@@ -170,6 +176,9 @@ struct npsolve {
     float *gx[kMaxLevels + 1] = {}, *gx1[kMaxLevels + 1] = {};
     float *rm = nullptr, *tmp = nullptr, *tmp2 = nullptr, *res = nullptr, *gz = nullptr, *K = nullptr;
     double *part = nullptr, *out = nullptr;  // partials, and the reduced results (see train_backward)
+    double *outb = nullptr;                  // one reduced-results block per example of a batch
+    int outb_cap = 0;                        // examples outb holds
+    unsigned int *badb = nullptr;            // label-check flag accumulated over a batch
     std::vector<double> m, v;
     long long t = 0;
   } tr;
@@ -264,6 +273,7 @@ void free_ws(Workspace &w) {
     cudaFree(w.kdesc[l]);
   }
   for (int i = 0; i < (kMaxLevels + 1) * 2; ++i) cudaFree(w.kcache[i]);
+  cudaFree(w.tailk);
   cudaFree(w.ktotal);
   cudaFreeHost(w.h_ktotal);
   cudaFree(w.kskip);
@@ -497,12 +507,29 @@ int check_dims(npsolve *h, int nx, int ny, int nz) {
 // recompute path (image counts <= 64 are exact in BF16 up to level 3).
 bool tensor_level(const npsolve *h, int lvl) { return h->cfg.kernel_path == NPSOLVE_PATH_TENSOR && lvl <= 3; }
 // The cached path streams vector planes with TMA boxes, whose rows must be a
-// multiple of 16 bytes at every level; other shapes use the CUDA-core kernels.
-bool cached_path(const npsolve *h, Dims d1) {
-  if (h->cfg.kernel_path != NPSOLVE_PATH_CACHED) return false;
-  for (int l = 1; l <= h->cfg.levels; ++l)
-    if (!stream_shape_ok(level_dims(d1, l))) return false;
-  return true;
+// multiple of 16 bytes.  The decision is per level: a level whose rows are not
+// (a coarse level of a small or odd-sized grid, e.g. the 2^3 or 6^3 level of a
+// 6-level network on 64^3 or 192^3) runs on the CUDA-core kernels with a
+// separate pooling / combination, the other levels stay on the cached path.
+bool stream_shape_level(const npsolve *h, Dims d1, int l) {
+  return h->cfg.kernel_path == NPSOLVE_PATH_CACHED && l <= h->cfg.levels && stream_shape_ok(level_dims(d1, l));
+}
+// Level 1 on the cached path (the level-1 fusions, unit lists and setup).
+bool cached_path(const npsolve *h, Dims d1) { return stream_shape_level(h, d1, 1); }
+// The first level of the coarse tail (kernels_tail.cu) for this grid, 0 for
+// none: on the cached path, the first level from 2 on with at most
+// kTailMaxCells cells.  The levels from there on run in one cluster launch
+// inside solves and network evaluations, on their own materialised kernels.
+int tail_level(const npsolve *h, Dims d1) {
+  if (!cached_path(h, d1) || h->cfg.symmetric) return 0;
+  for (int l = 2; l <= h->cfg.levels; ++l)
+    if (level_dims(d1, l).n() <= kTailMaxCells) return l;
+  return 0;
+}
+// A level on the streamed cached kernels (not in the tail).
+bool stream_level(const npsolve *h, Dims d1, int l) {
+  const int T = tail_level(h, d1);
+  return stream_shape_level(h, d1, l) && !(T && l >= T);
 }
 
 // The recurrence step r_{k+1} = r_k - alpha q of an iteration is formed by the
@@ -573,7 +600,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   // symmetric variant applies the transpose to it), so no dots are taken here
   Workspace &w = h->ws;
   const int L = h->cfg.levels;
-  const bool cached = cached_path(h, d1);
+  const bool cached = cached_path(h, d1);  // level 1
   if (cached && !st) {
     // the cached stencil expects an input that is zero off fluid: inside a solve
     // r is, for a user-supplied vector zero it here
@@ -590,8 +617,12 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
   const StreamUnits ul2{w.ulist2, w.un2, w.uzc2};
   const StreamUnits *pl2 = lists && w.ulist2_ok ? &ul2 : nullptr;  // level 2 (L >= 3)
   const uint8_t *skip1 = lists ? w.ineed : nullptr;                // what the level-1 CConv2 does not read of r2
+  // levels T..L in one cluster launch (kernels_tail.cu), which also writes the
+  // interpolated input r2^(T-1) of the finer level's CConv2; not for the
+  // per-level inspection (it keeps no x2)
+  const int T = (!unfused && w.tail_T && w.tail_T == tail_level(h, d1)) ? w.tail_T : 0;
   // down pass: x1^l = CConv1^l(r1^l), r1^{l+1} = Pool(x1^l)
-  for (int l = 1; l < L; ++l) {
+  for (int l = 1; l < (T ? T : L); ++l) {
     const float *in = l == 1 ? r : w.r1[l];
     const float *vs = l == 1 ? vscale : nullptr;
     if (cached && l == 1 && st && fused_update(h, d1)) {
@@ -599,7 +630,7 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       const StreamUpdate up{{w.r, w.r_alt}, w.qring, kRing, w.part, w.part_cap, w.tickets + kTicketUpdate, w.hist, st};
       cconv_cached(h, d1, l, 1, w.r, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s, STREAM_MODE_ZERO_PURE,
                    nullptr, &up, pu1);
-    } else if (cached) {
+    } else if (stream_level(h, d1, l)) {
       cconv_cached(h, d1, l, 1, in, vs, w.x1[l], w.r1[l + 1], nullptr, nullptr, st, s,
                    l == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL, nullptr, nullptr,
                    l == 1 ? pu1 : (l == 2 ? pl2 : nullptr));
@@ -612,11 +643,30 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
       launch_pool(w.x1[l], level_dims(d1, l), w.r1[l + 1], st, s);
     }
   }
+  if (T) {
+    TailParams tp{};
+    tp.T = T;
+    tp.L = L;
+    for (int l = 1; l <= L; ++l) {
+      tp.dims[l] = level_dims(d1, l);
+      tp.k1[l] = w.tk1[l];
+      tp.k2[l] = w.tk2[l];
+      tp.x1[l] = w.x1[l];
+      tp.r1[l] = w.r1[l];
+      tp.r2[l] = w.r2[l];
+      tp.xc[l] = w.xc[l];
+    }
+    tp.affc = w.affc;
+    tp.st = st;
+    ProfScope ps(h, P_CCONV_COARSE, s);
+    h->launches += 1;
+    if (launch_tail(tp, s)) h->stream_err = true;
+  }
   // coarsest level: x^L = CConv1^L(r1^L)
-  {
+  if (!T) {
     const float *in = L == 1 ? r : w.r1[L];
     const float *vs = L == 1 ? vscale : nullptr;
-    if (cached)
+    if (stream_level(h, d1, L))
       cconv_cached(h, d1, L, 1, in, vs, w.x1[L], nullptr, nullptr, nullptr, st, s,
                    L == 1 ? STREAM_MODE_ZERO_PURE : STREAM_MODE_ALL);
     else if (tensor_level(h, L)) cconv_tc(h, lab, d1, L, 1, in, nullptr, vs, L == 1, w.x1[L], nullptr, st, s);
@@ -629,11 +679,13 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     return;
   }
   // up pass: r2^l = Interp(x^{l+1}); x2^l = CConv2^l(r2^l); x^l = c1 x1^l + c2 x2^l
-  for (int l = L - 1; l >= 1; --l) {
+  for (int l = (T ? T - 1 : L - 1); l >= 1; --l) {
     const float *coarse = (l + 1 == L) ? w.x1[L] : w.xc[l + 1];
     const double *c12 = w.affc + 2 * l;
-    if (cached && !unfused) {
-      {
+    const bool cached_l = stream_level(h, d1, l);
+    const bool interp_done = T && l == T - 1;  // the tail wrote r2^(T-1)
+    if (cached_l && !unfused) {
+      if (!interp_done) {
         ProfScope ps(h, P_INTERP, s);
         h->launches += 1;
         launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s, l == 1 ? skip1 : nullptr);
@@ -658,12 +710,12 @@ void run_network(npsolve *h, const uint8_t *lab, Dims d1, const float *r, const 
     } else if (tensor_level(h, l) && !unfused) {
       cconv_tc(h, lab, d1, l, 2, nullptr, coarse, nullptr, 0, w.x2[l], nullptr, st, s);
     } else {
-      {
+      if (!interp_done) {
         ProfScope ps(h, P_INTERP, s);
         h->launches += 1;
         launch_interp(coarse, level_dims(d1, l + 1), w.r2[l], st, s);
       }
-      if (cached) cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
+      if (cached_l) cconv_cached(h, d1, l, 2, w.r2[l], nullptr, w.x2[l], nullptr, nullptr, nullptr, st, s);
       else if (tensor_level(h, l))
         cconv_tc(h, lab, d1, l, 2, w.r2[l], nullptr, nullptr, 0, w.x2[l], nullptr, st, s);
       else cconv(h, lab, d1, l, 2, w.r2[l], nullptr, 0, w.x2[l], st, s);
@@ -698,9 +750,38 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
     launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
                h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s);
   h->launches += 1 + (L - 1) + 2 * (L - 1);
+  w.tail_T = tail_level(h, d1);
+  if (w.tail_T) {
+    // the coarse tail's per-cell kernels: CConv1 of levels T..L, CConv2 of T..L-1
+    size_t need = 0;
+    for (int l = w.tail_T; l <= L; ++l) need += (size_t)27 * level_dims(d1, l).n() * (l < L ? 2 : 1);
+    if (need > w.tailk_cap) {
+      if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old buffer
+      w.graph = nullptr;
+      CK(h, cudaStreamSynchronize(s));
+      if (w.tailk) w.bytes -= w.tailk_cap * sizeof(float) + 256;
+      cudaFree(w.tailk);
+      w.tailk = nullptr;
+      w.tailk_cap = 0;
+      CK(h, dalloc(&w.bytes, &w.tailk, need));
+      w.tailk_cap = need;
+    }
+    float *kp = w.tailk;
+    const int rk = h->cfg.precision == NPSOLVE_BF16 ? 1 : 0;
+    for (int l = w.tail_T; l <= L; ++l) {
+      const Dims dl = level_dims(d1, l);
+      for (int t = 0; t < (l < L ? 2 : 1); ++t) {
+        (t ? w.tk2 : w.tk1)[l] = kp;
+        launch_tail_kernels(nullptr, w.counts[l], dl, h->cw + l * 2 + t, rk, kp, s);
+        h->launches += 1;
+        kp += (size_t)27 * dl.n();
+      }
+    }
+  }
   if (cached_path(h, d1)) {
     const bool bf16 = h->cfg.precision == NPSOLVE_BF16;
     for (int l = 1; l <= L; ++l) {  // plane descriptors sized for this grid's shape
+      if (!stream_level(h, d1, l)) continue;
       const long long nd = stream_desc_count(level_dims(d1, l));
       if (nd > w.kdesc_cap[l]) {
         if (w.graph) cudaGraphExecDestroy(w.graph);  // the graph refers to the old buffers
@@ -742,7 +823,7 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       CK(h, cudaMalloc(&w.ineed, (size_t)nsk));
       w.kskip_cap = nsk;
     }
-    const bool lv2 = L >= 3;  // level 2 has a CConv1 and a CConv2
+    const bool lv2 = L >= 3 && stream_level(h, d1, 2);  // level 2 has a CConv1 and a CConv2
     const long long nsk2 = lv2 ? stream_desc_count(level_dims(d1, 2)) : 0;
     if (nsk2 > w.kskip2_cap) {
       if (w.graph) cudaGraphExecDestroy(w.graph);
@@ -764,12 +845,14 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
       w.kskip2_cap = nsk2;
     }
     CK(h, cudaMemsetAsync(w.ktotal, 0, sizeof(unsigned) * 2 * (kMaxLevels + 1), s));
-    for (int l = 1; l <= L; ++l)
+    for (int l = 1; l <= L; ++l) {
+      if (!stream_level(h, d1, l)) continue;
       launch_classify(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l),
                       1u << (3 * (l - 1)), w.kdesc[l], w.ktotal + 2 * l,
                       l == 1 ? w.kskip : (l == 2 && lv2 ? w.kskip2 : nullptr), l == 1 ? w.kmcount : nullptr,
                       h->num_sms, s);
-    h->launches += L;
+      h->launches += 1;
+    }
     CK(h, cudaMemcpyAsync(w.h_ktotal, w.ktotal, sizeof(unsigned) * 2 * (kMaxLevels + 1), cudaMemcpyDeviceToHost, s));
     CK(h, cudaMemcpyAsync(w.h_kskip + nsk, w.kskip, (size_t)nsk, cudaMemcpyDeviceToHost, s));
     CK(h, cudaMemcpyAsync(w.h_kmcount, w.kmcount, sizeof(uint16_t) * (size_t)nsk, cudaMemcpyDeviceToHost, s));
@@ -788,6 +871,7 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
     }
     CK(h, cudaStreamSynchronize(s));
     for (int l = 1; l <= L; ++l) {
+      if (!stream_level(h, d1, l)) continue;
       const int nblk = l < L ? 2 : 1;
       for (int t = 0; t < nblk; ++t) {
         const int idx = l * 2 + t;
@@ -904,7 +988,11 @@ int ensure_train(npsolve *h, Dims d1) {
 }
 
 // Forward of Alg. 2 on r (zeroed off fluid into tr.rm) with every
-// intermediate kept in the workspace; returns z in ws.z.
+// intermediate kept in the workspace; returns z in ws.z.  On the CUDA-core
+// kernels: training evaluates each image once, so the per-solve kernel cache
+// (classification, generation and its host synchronisation) does not pay.
+// The label check's flag is OR-ed into tr.badb, which the caller reads once
+// for the whole batch.  Enqueues only: no host synchronisation.
 int train_forward(npsolve *h, const uint8_t *lab, Dims d1, const float *r, cudaStream_t s) {
   int st = check_dims(h, d1.nx, d1.ny, d1.nz);
   if (st) return st;
@@ -912,21 +1000,54 @@ int train_forward(npsolve *h, const uint8_t *lab, Dims d1, const float *r, cudaS
   if (st) return st;
   st = ensure_train(h, d1);
   if (st) return st;
+  if (!h->tr.badb) {
+    CK(h, cudaMalloc(&h->tr.badb, sizeof(unsigned int)));
+    CK(h, cudaMemsetAsync(h->tr.badb, 0, sizeof(unsigned int), s));
+  }
+  const int path = h->cfg.kernel_path;
+  h->cfg.kernel_path = NPSOLVE_PATH_CUDA_CORE;
   st = setup_image(h, lab, d1, s, true);
+  if (!st) {
+    launch_or_flag(h->ws.bad, h->tr.badb, s);
+    launch_mask_copy(lab, d1.n(), r, h->tr.rm, s);
+    run_network(h, lab, d1, h->tr.rm, nullptr, h->ws.z, nullptr, s, true);
+  }
+  h->cfg.kernel_path = path;
   if (st) return st;
-  CK(h, cudaMemcpyAsync(h->ws.h_flag, h->ws.bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
-  CK(h, cudaStreamSynchronize(s));
-  if (h->ws.h_flag[0]) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
-  launch_mask_copy(lab, d1.n(), r, h->tr.rm, s);
-  run_network(h, lab, d1, h->tr.rm, nullptr, h->ws.z, nullptr, s, true);
   CK(h, cudaGetLastError());
   return NPSOLVE_OK;
 }
 
-// Reverse of Alg. 2 for the output cotangent gz (device), after train_forward.
-// Accumulates d<gz, z>/dw (raw blob layout, FP64) into gw; writes
-// d<gz, z>/dr into gr when gr != null.
-int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std::vector<double> &gw, float *gr,
+// Room for `count` examples' reduced results (tr.outb).
+int ensure_outb(npsolve *h, int count) {
+  auto &t = h->tr;
+  if (t.outb_cap >= count) return NPSOLVE_OK;
+  cudaFree(t.outb);
+  t.outb = nullptr;
+  t.outb_cap = 0;
+  CK(h, dalloc(nullptr, &t.outb, (size_t)count * (kMaxLevels + 1) * kTrOutPerLevel));
+  t.outb_cap = count;
+  return NPSOLVE_OK;
+}
+
+// Reads the batch's label-check flag (one host synchronisation, after the
+// batch's results were copied) and clears it.
+int check_batch_labels(npsolve *h, cudaStream_t s) {
+  if (!h->tr.badb) return NPSOLVE_OK;
+  unsigned int bad = 0;
+  CK(h, cudaMemcpyAsync(&bad, h->tr.badb, sizeof(bad), cudaMemcpyDeviceToHost, s));
+  CK(h, cudaMemsetAsync(h->tr.badb, 0, sizeof(unsigned int), s));
+  CK(h, cudaStreamSynchronize(s));
+  if (bad) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
+  return NPSOLVE_OK;
+}
+
+// Reverse of Alg. 2 for the output cotangent gz (device), after train_forward:
+// the folded weight gradients, the Aff dots and image statistics of every
+// level into `out` (device, (kMaxLevels + 1) x kTrOutPerLevel doubles, zeroed
+// here; fold_gradients turns them into the raw blob layout) and, when gr !=
+// null, d<gz, z>/dr into gr.  Enqueues only: no host synchronisation.
+int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, double *out, float *gr,
                    cudaStream_t s) {
   Workspace &w = h->ws;
   auto &t = h->tr;
@@ -934,13 +1055,8 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std
   const long long n1 = d1.n();
   auto lc = [&](int l) { return l == 1 ? nullptr : w.counts[l]; };
   auto ll = [&](int l) { return l == 1 ? lab : nullptr; };
-  double *out = t.out;
   auto O = [&](int l) { return out + (size_t)l * kTrOutPerLevel; };
-  // c1, c2 of every level on the host
-  std::vector<double> c12((kMaxLevels + 1) * 2, 0.0);
-  CK(h, cudaMemcpyAsync(c12.data(), w.affc, sizeof(double) * c12.size(), cudaMemcpyDeviceToHost, s));
   CK(h, cudaMemsetAsync(out, 0, sizeof(double) * (kMaxLevels + 1) * kTrOutPerLevel, s));
-  CK(h, cudaStreamSynchronize(s));
   for (int l = 1; l <= L; ++l) {
     const long long nl = level_dims(d1, l).n();
     CK(h, cudaMemsetAsync(t.gx[l], 0, sizeof(float) * nl, s));
@@ -954,8 +1070,8 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std
     const long long nl = dl.n();
     launch_dot2(t.gx[l], w.x1[l], w.x2[l], nl, t.part, O(l) + 2 * kWGOut, s);
     launch_aff_stats(ll(l), lc(l), dl, 1.0 / pow(8.0, l - 1), t.part, O(l) + 2 * kWGOut + 2, s);
-    launch_axpby(nullptr, nl, (float)c12[2 * l], t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);  // gx1 += c1 gx
-    launch_axpby(nullptr, nl, (float)c12[2 * l + 1], t.gx[l], 0.f, nullptr, t.tmp, s);  // g x2 = c2 gx
+    launch_axpby_dev(nullptr, nl, w.affc + 2 * l, t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);   // gx1 += c1 gx
+    launch_axpby_dev(nullptr, nl, w.affc + 2 * l + 1, t.gx[l], 0.f, nullptr, t.tmp, s);     // g x2 = c2 gx
     launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2 + 1, t.K, s);
     launch_cconv_wgrad(ll(l), lc(l), dl, w.r2[l], t.tmp, t.part, O(l) + kWGOut, s);
     launch_cconv_transpose(t.K, t.tmp, dl, t.tmp2, s);  // g r2
@@ -982,14 +1098,17 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std
     }
   }
   CK(h, cudaGetLastError());
-  std::vector<double> ho((size_t)(kMaxLevels + 1) * kTrOutPerLevel);
-  CK(h, cudaMemcpyAsync(ho.data(), out, sizeof(double) * ho.size(), cudaMemcpyDeviceToHost, s));
-  CK(h, cudaStreamSynchronize(s));
-  // folded gradients -> raw blob gradients
+  return NPSOLVE_OK;
+}
+
+// The folded gradients of one example's reduced results `ho` (host copy of a
+// train_backward output block) added into gw in the raw blob layout.
+void fold_gradients(const npsolve *h, const double *ho, std::vector<double> &gw) {
+  const int L = h->cfg.levels;
   const size_t per = 2 * kCConvParams + 2 * kAffParams;
   for (int l = 1; l <= L; ++l) {
     const double sc = 1.0 / pow(8.0, l - 1);
-    const double *Ol = ho.data() + (size_t)l * kTrOutPerLevel;
+    const double *Ol = ho + (size_t)l * kTrOutPerLevel;
     for (int type = 1; type <= (l < L ? 2 : 1); ++type) {
       const double *G = Ol + (type - 1) * kWGOut;
       const size_t base = (size_t)(l - 1) * per + (type == 2 ? kCConvParams : 0);
@@ -1018,7 +1137,6 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, std
       }
     }
   }
-  return NPSOLVE_OK;
 }
 
 // out = P_net^T g: the adjoint of the network z = mask_fluid(N(mask_fluid(r)))
@@ -1067,10 +1185,12 @@ void run_network_transpose(npsolve *h, const uint8_t *lab, Dims d1, const float 
   }
 }
 
-// Loss = || b - A P_net(I, b) || (Sec. 4.2.3) and its weight gradient
-// accumulated into gw (scaled by `weight`).
-int loss_grad_impl(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double *loss, std::vector<double> &gw,
-                   double weight, cudaStream_t s) {
+// Loss = || b - A P_net(I, b) || (Sec. 4.2.3) of one example and the
+// reduced results of its weight gradient, scaled by `weight`, into `out`
+// (device block of kTrOutPerLevel (kMaxLevels + 1) doubles; its last entry
+// receives ||b - A P_net(I, b)||^2).  Enqueues only.
+int loss_grad_enqueue(npsolve *h, const uint8_t *lab, Dims d1, const float *b, double weight, double *out,
+                      cudaStream_t s) {
   int st = train_forward(h, lab, d1, b, s);
   if (st) return st;
   auto &t = h->tr;
@@ -1082,11 +1202,12 @@ int loss_grad_impl(npsolve *h, const uint8_t *lab, Dims d1, const float *b, doub
   launch_lap(lab, d1, t.res, t.tmp2, s);                       // A res
   launch_scale_by_inv_norm(lab, n, (float)(-weight), nrm - 1, t.tmp2, t.gz, s);  // gz = -w A res / ||res||
   h->launches += 7;
-  double r2[2] = {0.0, 0.0};
-  CK(h, cudaMemcpyAsync(r2, nrm - 1, sizeof(r2), cudaMemcpyDeviceToHost, s));
-  CK(h, cudaStreamSynchronize(s));
-  *loss = sqrt(r2[0]);
-  return train_backward(h, lab, d1, t.gz, gw, nullptr, s);
+  st = train_backward(h, lab, d1, t.gz, out, nullptr, s);
+  if (st) return st;
+  // the squared loss into the block's last entry (train_backward zeroed the block)
+  CK(h, cudaMemcpyAsync(out + (size_t)(kMaxLevels + 1) * kTrOutPerLevel - 1, nrm - 1, sizeof(double),
+                        cudaMemcpyDeviceToDevice, s));
+  return NPSOLVE_OK;
 }
 
 // Enqueue one NPSDO iteration (Alg. 1 loop body) on stream s.
@@ -1447,6 +1568,8 @@ void npsolve_destroy(npsolve_t h) {
   cudaSetDevice(h->device);
   free_ws(h->ws);
   free_train(h);
+  cudaFree(h->tr.outb);
+  cudaFree(h->tr.badb);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   cudaFree(h->cw);
   cudaFree(h->aw);
@@ -1699,7 +1822,7 @@ long long npsolve_launch_count(npsolve_t h) { return h ? h->launches : 0; }
 size_t npsolve_workspace_bytes(npsolve_t h) { return h ? h->ws.bytes : 0; }
 
 long long npsolve_mixed_cells(npsolve_t h, int level) {
-  if (!h || level < 1 || level > h->cfg.levels || !h->ws.h_ktotal || !cached_path(h, h->ws.dims)) return -1;
+  if (!h || level < 1 || level > h->cfg.levels || !h->ws.h_ktotal || !stream_level(h, h->ws.dims, level)) return -1;
   return (long long)h->ws.h_ktotal[2 * level + 1];
 }
 
@@ -1744,11 +1867,43 @@ int npsolve_network_vjp(npsolve_t h, const uint8_t *labels, int nx, int ny, int 
   const Dims d1{nx, ny, nz};
   int st = train_forward(h, labels, d1, r, s);
   if (st) return st;
-  std::vector<double> gw(h->weights.size(), 0.0);
-  st = train_backward(h, labels, d1, gz, gw, grad_r, s);
+  st = ensure_outb(h, 1);
   if (st) return st;
+  st = train_backward(h, labels, d1, gz, h->tr.outb, grad_r, s);
+  if (st) return st;
+  std::vector<double> ho((size_t)(kMaxLevels + 1) * kTrOutPerLevel);
+  CK(h, cudaMemcpyAsync(ho.data(), h->tr.outb, sizeof(double) * ho.size(), cudaMemcpyDeviceToHost, s));
+  st = check_batch_labels(h, s);  // synchronises
+  if (st) return st;
+  std::vector<double> gw(h->weights.size(), 0.0);
+  fold_gradients(h, ho.data(), gw);
   for (size_t i = 0; i < gw.size(); ++i) grad_w_host[i] = (float)gw[i];
-  if (grad_r) CK(h, cudaStreamSynchronize(s));
+  return NPSOLVE_OK;
+}
+
+// The mean loss and weight gradient of a batch: every example enqueued into
+// its own results block, one copy and one host synchronisation at the end.
+int batch_loss_grad(npsolve *h, int batch, const uint8_t *const *labels, const int *dims, const float *const *b,
+                    double weight, cudaStream_t s, double *mean_loss, std::vector<double> &gw) {
+  int st = ensure_outb(h, batch);
+  if (st) return st;
+  const size_t blk = (size_t)(kMaxLevels + 1) * kTrOutPerLevel;
+  for (int i = 0; i < batch; ++i) {
+    if (!labels[i] || !b[i]) return fail(h, NPSOLVE_BAD_ARG, "null example pointer");
+    st = loss_grad_enqueue(h, labels[i], Dims{dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]}, b[i], weight,
+                           h->tr.outb + (size_t)i * blk, s);
+    if (st) return st;
+  }
+  std::vector<double> ho((size_t)batch * blk);
+  CK(h, cudaMemcpyAsync(ho.data(), h->tr.outb, sizeof(double) * ho.size(), cudaMemcpyDeviceToHost, s));
+  st = check_batch_labels(h, s);  // synchronises
+  if (st) return st;
+  double total = 0.0;
+  for (int i = 0; i < batch; ++i) {
+    fold_gradients(h, ho.data() + (size_t)i * blk, gw);
+    total += sqrt(ho[(size_t)i * blk + blk - 1]);
+  }
+  *mean_loss = total / batch;
   return NPSOLVE_OK;
 }
 
@@ -1758,7 +1913,8 @@ int npsolve_loss_grad(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz
   if (!labels || !b || !loss) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
   CK(h, cudaSetDevice(h->device));
   std::vector<double> gw(h->weights.size(), 0.0);
-  int st = loss_grad_impl(h, labels, Dims{nx, ny, nz}, b, loss, gw, 1.0, (cudaStream_t)stream);
+  const int dims[3] = {nx, ny, nz};
+  int st = batch_loss_grad(h, 1, &labels, dims, &b, 1.0, (cudaStream_t)stream, loss, gw);
   if (st) return st;
   if (grad_w_host)
     for (size_t i = 0; i < gw.size(); ++i) grad_w_host[i] = (float)gw[i];
@@ -1773,15 +1929,9 @@ int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, con
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nw = h->weights.size();
   std::vector<double> gw(nw, 0.0);
-  double total = 0.0;
-  for (int i = 0; i < batch; ++i) {
-    if (!labels[i] || !b[i]) return fail(h, NPSOLVE_BAD_ARG, "null example pointer");
-    double li = 0.0;
-    int st = loss_grad_impl(h, labels[i], Dims{dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]}, b[i], &li, gw,
-                            1.0 / batch, s);
-    if (st) return st;
-    total += li;
-  }
+  double mean_loss = 0.0;
+  int st = batch_loss_grad(h, batch, labels, dims, b, 1.0 / batch, s, &mean_loss, gw);
+  if (st) return st;
   // Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the raw weights, FP64 moments
   auto &t = h->tr;
   if (t.m.size() != nw) {
@@ -1799,7 +1949,7 @@ int npsolve_train_step(npsolve_t h, int batch, const uint8_t *const *labels, con
     t.v[k] = b2 * t.v[k] + (1.0 - b2) * g * g;
     h->weights[k] = (float)(h->weights[k] - lr * (t.m[k] / c1) / (sqrt(t.v[k] / c2) + eps));
   }
-  *loss = total / batch;
+  *loss = mean_loss;
   return upload_weights(h);
 }
 

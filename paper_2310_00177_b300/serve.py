@@ -124,7 +124,7 @@ def summarize(recs):
 
 
 def serve_workload(w, requests=512, rate=200.0, sizes=(64, 128, 192, 256), frames=6, budget_gb=150.0,
-                   max_active=8):
+                   max_active=8, levels=4):
     """Run the serving workload (seeded Poisson arrivals, mixed sizes, evolving
     frames, BF16 network, tol 1e-6, HBM-budget admission) on a fresh server
     and return the summary: p50 / p99 latency, solves per second, convergence
@@ -136,7 +136,7 @@ def serve_workload(w, requests=512, rate=200.0, sizes=(64, 128, 192, 256), frame
     reqs = synth.serving_requests(requests, rate, sizes=sizes)
     # every request returns its x to the host (a pinned array per request)
     x_pool = [pinned_like((r["n"],) * 3, np.float64) for r in reqs]
-    srv = binding.Server(w, precision=binding.BF16, hbm_budget_bytes=int(budget_gb * (1 << 30)),
+    srv = binding.Server(w, levels=levels, precision=binding.BF16, hbm_budget_bytes=int(budget_gb * (1 << 30)),
                          max_active=max_active)
     try:
         # grow every slot to the largest size once so that workspace growth is not timed
@@ -150,6 +150,7 @@ def serve_workload(w, requests=512, rate=200.0, sizes=(64, 128, 192, 256), frame
     out["sizes"] = list(sizes)
     out["budget_gb"] = budget_gb
     out["max_active"] = max_active
+    out["levels"] = levels
     out["warmup_requests"] = len(warm)
     return out
 
@@ -162,13 +163,14 @@ def main():
     ap.add_argument("--frames", type=int, default=6)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--levels", type=int, default=6)
     args = ap.parse_args()
     from paper_2310_00177_b300 import synth
 
-    wfile = os.path.join(ROOT, "paper_2310_00177_b300", "weights", "npsdo_L4.f32")
-    w = np.fromfile(wfile, dtype=np.float32) if os.path.exists(wfile) else synth.init_weights(4, 7)
+    wfile = os.path.join(ROOT, "paper_2310_00177_b300", "weights", f"npsdo_L{args.levels}.f32")
+    w = np.fromfile(wfile, dtype=np.float32) if os.path.exists(wfile) else synth.init_weights(args.levels, 7)
     out = serve_workload(w, args.requests, args.rate, tuple(int(s) for s in args.sizes.split(",")), args.frames,
-                         args.budget_gb, args.max_active)
+                         args.budget_gb, args.max_active, args.levels)
     print(json.dumps(out))
 
 

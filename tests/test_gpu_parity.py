@@ -409,3 +409,34 @@ def test_degenerate_scenes_through_host_buffers(scene):
     if scene == "single_cell":
         assert abs(xh[cell] - rhs[cell]) <= 1e-6 * abs(rhs[cell])
     s.close()
+
+
+@pytest.mark.parametrize("shape,L", [((64, 64, 64), 6), ((96, 96, 96), 6), ((48, 32, 40), 4)])
+def test_levels_with_short_rows_run_beside_the_cached_levels(shape, L):
+    # levels whose rows are not a multiple of 16 bytes (64^3 at L = 6: level 6
+    # is 2^3; 96^3: levels 5 and 6 are 6^3 and 3^3; 48 x 32 x 40 at L = 4:
+    # level 3 is 12 x 8 x 10, level 4 6 x 4 x 5) run on the CUDA-core kernels while the
+    # others stay on the cached path: the network against the oracle (FP32 form),
+    # and for 64^3 a whole solve (count under the margin rule, x to 1e-5)
+    b = _binding()
+    lab = synth.slosh_scene(shape[2], 90) if len(set(shape)) == 1 else \
+        np.random.default_rng(91).choice(np.array([0, 1, 2], np.uint8), size=shape, p=(0.2, 0.6, 0.2))
+    w = synth.init_weights(L, 92).astype(np.float32)
+    r = np.random.default_rng(93).standard_normal(lab.shape).astype(np.float32)
+    s = b.Solver(w, levels=L, n_ortho=2, precision=b.FP32)
+    z = s.apply_network(_dev(lab, torch.uint8), _dev(r, torch.float32)).cpu().numpy()
+    zo = oracle.network(lab, L, w.astype(np.float64), r.astype(np.float64))
+    assert _rel(z, zo) <= 1e-5
+    if shape == (64, 64, 64):
+        rhs = synth.rhs_normal(lab, 94).astype(np.float32)
+        ores = oracle.npsdo(lab, rhs.astype(np.float64), L=L, w=w.astype(np.float64), tol=1e-6, max_iter=1000)
+        x, iters, relres, st = s.solve(_dev(lab, torch.uint8), _dev(rhs, torch.float32), 1e-6, 1000)
+        h = ores["res_hist"] / ores["res_hist"][0]
+        assert st == b.OK and relres < 1e-6
+        if h[-1] < 0.95e-6 and h[-2] > 1.05e-6:
+            assert iters == ores["iters"]
+        else:
+            assert abs(iters - ores["iters"]) <= 1
+        assert _rel(_remove_neumann_constants(lab, x.cpu().numpy()),
+                    _remove_neumann_constants(lab, ores["x"])) <= 1e-5
+    s.close()
