@@ -79,7 +79,7 @@ def oracle_iters_file(levels):
 # from ncu (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the
 # CConv1 and CConv2 launches of one iteration, the summary kept in profiles/);
 # None when the kernel has changed since the counters were taken.
-TRAFFIC_L1 = (210.8e6 + 214.1e6) / 2
+TRAFFIC_L1 = (146.45e6 + 63.56e6 + 140.80e6 + 26.17e6) / 2
 
 # Algorithmic HBM bytes per fine cell for one launch of each kernel class
 # (inputs read once, outputs written once).

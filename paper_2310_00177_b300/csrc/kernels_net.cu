@@ -136,8 +136,10 @@ __device__ __forceinline__ bool keeps(int c, int o) { return !((o == 1 && (c & 1
 
 // 128 threads: the 128 counters are loaded into shared memory at once (one
 // load each), then 27 threads form the window sums.
+// stats (optional): the 54 window sums scaled by stat_scale, [0, 27) fluid and
+// [27, 54) air (the training backward's Aff image statistics).
 __global__ void k_aff_from_counts(const unsigned long long *__restrict__ gcnt, const AffW *a1, const AffW *a2,
-                                  long long n, double *out) {
+                                  long long n, double *out, double *stats, double stat_scale) {
   __shared__ unsigned long long cnt[128];
   __shared__ double t1[27], t2[27];
   const int l = threadIdx.x;
@@ -153,6 +155,10 @@ __global__ void k_aff_from_counts(const unsigned long long *__restrict__ gcnt, c
     }
     t1[l] = (double)a1->wf[l] * sf + (double)a1->wa[l] * sa;
     t2[l] = (double)a2->wf[l] * sf + (double)a2->wa[l] * sa;
+    if (stats) {
+      stats[l] = sf * stat_scale;
+      stats[27 + l] = sa * stat_scale;
+    }
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -439,7 +445,7 @@ void launch_pyramid(const uint8_t *lab, Dims d1, ushort2 *const *counts, int L, 
 }
 
 void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,
-                double *out, cudaStream_t s) {
+                double *out, cudaStream_t s, double *stats, double feature_scale) {
   ImgSrc im{lab, counts};
   if (counts) im.lab = nullptr;
   unsigned long long *cnt = (unsigned long long *)part;  // 128 counters in the reduction scratch
@@ -448,7 +454,7 @@ void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *
   long long g = (rows + 7) / 8;
   if (g > 148LL * 8) g = 148LL * 8;
   k_aff_counts<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(im, dm, cnt);
-  k_aff_from_counts<<<1, 128, 0, s>>>(cnt, a1, a2, dm.n(), out);
+  k_aff_from_counts<<<1, 128, 0, s>>>(cnt, a1, a2, dm.n(), out, stats, feature_scale / (27.0 * (double)dm.n()));
 }
 
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,

@@ -9,8 +9,11 @@
 // the input gradient is a deterministic gather, and the 27 x 55 weight
 // gradient accumulated per block in FP32 over 32-cell batches and reduced
 // across blocks in FP64 in a fixed order.
+#include <cuda_bf16.h>
+
 #include "nps_common.cuh"
 #include "nps_kernels.h"
+#include "umma.cuh"
 
 namespace nps {
 
@@ -157,6 +160,151 @@ __global__ void __launch_bounds__(256) k_cconv_wgrad(const uint8_t *__restrict__
     const int o = tid + k * 256;
     if (o < kWG) part[(size_t)blockIdx.x * kWG + o] = (double)acc[k];
   }
+}
+
+// The same weight gradient on the tcgen05 tensor cores, for levels whose
+// image counts are exact in BF16 (at most 256 fine cells per cell: levels
+// 1-3 here).  The contraction over cells is the MMA's K dimension:
+//   D[j][s * 32 + a] = sum_p F_j(p) gK_a^(s)(p)   (FP32 in TMEM)
+// with A = F (the 54 window counts and the bias 1 per cell, rows 55..127 zero)
+// and B = the kernel gradient gK_a(p) = g(p) v(p + a) split into three BF16
+// terms s (hi, mid, lo; their sum is the FP32 value to 2^-24 relative), both
+// K-major in shared memory in 128-cell chunks.  Thread t stages cell t of a
+// chunk (its window counts and 27 products, one pass over its 3 x 3 x 3
+// window); one thread issues the chunk's eight MMAs (K = 16 each) and commits
+// them to the buffer's mbarrier, while the CTA stages the next chunk into the
+// other buffer.  D accumulates over all of the CTA's chunks; at the end lane
+// j holds G[a][j] = D[j][a] + D[j][32 + a] + D[j][64 + a], written as the
+// CTA's partial in the layout of k_cconv_wgrad (reduced by k_wgrad_final).
+constexpr int kWgCells = 128;                      // cells per chunk (MMA K = 8 x 16)
+constexpr int kWgRowsA = 128;                      // MMA M: 55 feature rows, padded
+constexpr int kWgRowsB = 96;                       // MMA N: 3 BF16 terms x 32 taps
+constexpr int kWgSBO = (kWgCells / 8) * 128;       // bytes between 8-row groups (K-major, no swizzle)
+constexpr int kWgABytes = kWgRowsA * kWgCells * 2;  // 32 KB
+constexpr int kWgBBytes = kWgRowsB * kWgCells * 2;  // 24 KB
+constexpr int kWgBufBytes = kWgABytes + kWgBBytes;
+constexpr int kWgSmem = 2 * kWgBufBytes + 1024;     // two buffers + barriers (and 1 KB alignment slack)
+constexpr int kWgTmemCols = 128;
+
+// Byte offset of element (row, k) in a K-major, non-swizzled operand tile.
+__device__ __forceinline__ uint32_t wg_off(int row, int k) {
+  return (uint32_t)((row >> 3) * kWgSBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__global__ void __launch_bounds__(kWgCells) k_cconv_wgrad_tc(const uint8_t *__restrict__ lab,
+                                                             const ushort2 *__restrict__ counts, Dims d,
+                                                             const float *__restrict__ v, const float *__restrict__ g,
+                                                             double *__restrict__ part, int *err) {
+  using namespace umma;
+  extern __shared__ uint8_t wg_raw[];
+  uint8_t *sm = (uint8_t *)(((uintptr_t)wg_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *mbar = (uint64_t *)(sm + 2 * kWgBufBytes);
+  uint32_t *s_tmem = (uint32_t *)(mbar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // zero both buffers once: the padding rows are never written again
+  for (int i = tid; i < 2 * kWgBufBytes / 16; i += kWgCells) ((uint4 *)sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    tmem_alloc(s_tmem, kWgTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    fence_mbar_init();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t idesc = idesc_bf16(kWgRowsA, kWgRowsB);
+  const long long n = d.n();
+  const long long nch = (n + kWgCells - 1) / kWgCells;
+  uint32_t phase[2] = {0u, 0u};
+  int issued[2] = {0, 0};  // commits not yet waited for, per buffer
+  bool aborted = false;
+  int i = 0;
+  for (long long ch = blockIdx.x; ch < nch && !aborted; ch += gridDim.x, ++i) {
+    const int b = i & 1;
+    if (issued[b]) {  // the MMAs of two chunks ago read this buffer
+      const bool ok = mbar_wait_bounded(&mbar[b], phase[b], umma::kWaitNs);
+      if (__syncthreads_or(!ok)) {  // still outstanding: waited for once more below
+        aborted = true;
+        break;
+      }
+      phase[b] ^= 1u;
+      issued[b] = 0;
+    }
+    uint8_t *A = sm + b * kWgBufBytes, *B = A + kWgABytes;
+    const long long p = ch * kWgCells + tid;
+    float gp = 0.f;
+    int x = 0, y = 0, z = 0;
+    if (p < n) {
+      cell_xyz(p, d, x, y, z);
+      gp = g[p];
+    }
+#pragma unroll
+    for (int l = 0; l < 27; ++l) {
+      const float2 f = p < n ? feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1)
+                             : make_float2(0.f, 0.f);
+      *(__nv_bfloat16 *)(A + wg_off(l, tid)) = __float2bfloat16_rn(f.x);  // exact: counts <= 256
+      *(__nv_bfloat16 *)(A + wg_off(27 + l, tid)) = __float2bfloat16_rn(f.y);
+    }
+    *(__nv_bfloat16 *)(A + wg_off(54, tid)) = __float2bfloat16_rn(p < n ? 1.f : 0.f);
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+      const float gk = gp != 0.f ? gp * vec_at(v, d, x + a % 3 - 1, y + (a / 3) % 3 - 1, z + a / 9 - 1) : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(gk);
+      const float r1 = gk - __bfloat162float(hi);
+      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      *(__nv_bfloat16 *)(B + wg_off(a, tid)) = hi;
+      *(__nv_bfloat16 *)(B + wg_off(32 + a, tid)) = mid;
+      *(__nv_bfloat16 *)(B + wg_off(64 + a, tid)) = lo;
+    }
+    fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < kWgCells / 16; ++kk) {
+        const uint64_t ad = smem_desc_kmajor(smem_u32(A + kk * 256), 128, kWgSBO);
+        const uint64_t bd = smem_desc_kmajor(smem_u32(B + kk * 256), 128, kWgSBO);
+        mma_bf16_ss(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      }
+      umma_commit(&mbar[b]);
+    }
+    issued[b] = 1;
+  }
+  // the last commits of both buffers
+  for (int b = 0; b < 2; ++b)
+    if (issued[b]) {
+      const bool ok = mbar_wait_bounded(&mbar[b], phase[b], umma::kWaitNs);
+      if (!ok) aborted = true;
+    }
+  aborted = __syncthreads_or(aborted);
+  fence_after_sync();
+  if (aborted) {
+    if (tid == 0 && err) atomicExch(err, 1);
+  } else if (i == 0) {
+    for (int o = tid; o < kWG; o += kWgCells) part[(size_t)blockIdx.x * kWG + o] = 0.0;
+  } else {
+    uint32_t c[3][32];
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+#pragma unroll
+    for (int sgrp = 0; sgrp < 3; ++sgrp) tmem_ld32(tmem + lane_off + 32 * sgrp, c[sgrp]);
+    tmem_wait_ld();
+    if (tid < 55) {
+#pragma unroll
+      for (int a = 0; a < 27; ++a) {
+        const float s = (__uint_as_float(c[0][a]) + __uint_as_float(c[1][a])) + __uint_as_float(c[2][a]);
+        part[(size_t)blockIdx.x * kWG + a * 55 + tid] = (double)s;
+      }
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kWgTmemCols);
 }
 
 // Sum the block partials of k_cconv_wgrad (fixed order) into out[1485].
@@ -349,6 +497,25 @@ void launch_cconv_wgrad(const uint8_t *lab, const ushort2 *counts, Dims d, const
   const int nb = wgrad_blocks(d);
   k_cconv_wgrad<<<nb, 256, 0, s>>>(lab, counts, d, v, g, part);
   k_wgrad_final<<<(kWG + 255) / 256, 256, 0, s>>>(part, nb, out);
+}
+// The tensor-core weight gradient (levels with counts <= 256 per cell); `err`
+// is set if an MMA wait timed out.  Two CTAs per SM (112 KB of shared memory
+// and 128 TMEM columns each).
+void launch_cconv_wgrad_tc(const uint8_t *lab, const ushort2 *counts, Dims d, const float *v, const float *g,
+                           double *part, double *out, int *err, int num_sms, cudaStream_t s) {
+  static int configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !configured[dev]) {
+    cudaFuncSetAttribute(k_cconv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    configured[dev] = 1;
+  }
+  const long long nch = (d.n() + kWgCells - 1) / kWgCells;
+  long long nb = (long long)num_sms * 2;
+  if (nb > nch) nb = nch;
+  if (nb < 1) nb = 1;
+  k_cconv_wgrad_tc<<<(int)nb, kWgCells, kWgSmem, s>>>(lab, counts, d, v, g, part, err);
+  k_wgrad_final<<<(kWG + 255) / 256, 256, 0, s>>>(part, (int)nb, out);
 }
 void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s) {
   k_pool_adjoint_add<<<gridn(fine.n(), 256), 256, 0, s>>>(gc, fine, gf);

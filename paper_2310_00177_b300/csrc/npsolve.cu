@@ -91,6 +91,7 @@ struct Workspace {
   bool ulist2_ok = false;
   size_t part_cap = 0;        // doubles of part
   double *part = nullptr, *affc = nullptr, *relres = nullptr, *hist = nullptr;
+  double *affs = nullptr;     // per level: the 54 scaled image window sums of the Aff blocks
   int hist_cap = 0;
   SolveState *st = nullptr;
   unsigned *tickets = nullptr;  // last-block-done counters of the fused reduction kernels
@@ -289,6 +290,7 @@ void free_ws(Workspace &w) {
   cudaFreeHost(w.h_ulist2);
   cudaFree(w.part);
   cudaFree(w.affc);
+  cudaFree(w.affs);
   cudaFree(w.relres);
   cudaFree(w.hist);
   cudaFree(w.st);
@@ -353,6 +355,7 @@ int ensure_ws(npsolve *h, Dims d, int hist_cap) {
     w.part_cap = (size_t)kRedMaxBlocks * kMaxPartials + (size_t)(cap / 64) + 64;
     CK(h, dalloc(&w.bytes, &w.part, w.part_cap));
     CK(h, dalloc(&w.bytes, &w.affc, (size_t)(kMaxLevels + 1) * 2));
+  CK(h, dalloc(&w.bytes, &w.affs, (size_t)(kMaxLevels + 1) * 54));
     CK(h, dalloc(&w.bytes, &w.relres, 2));
     CK(h, dalloc(&w.bytes, &w.st, 1));
     CK(h, dalloc(&w.bytes, &w.tickets, 8));
@@ -748,7 +751,7 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
   }
   for (int l = 1; l < L; ++l)
     launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
-               h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s);
+               h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s, w.affs + 54 * l, 1.0 / pow(8.0, l - 1));
   h->launches += 1 + (L - 1) + 2 * (L - 1);
   w.tail_T = tail_level(h, d1);
   if (w.tail_T) {
@@ -1030,6 +1033,8 @@ int ensure_outb(npsolve *h, int count) {
   return NPSOLVE_OK;
 }
 
+int check_umma_err(npsolve *h);
+
 // Reads the batch's label-check flag (one host synchronisation, after the
 // batch's results were copied) and clears it.
 int check_batch_labels(npsolve *h, cudaStream_t s) {
@@ -1039,7 +1044,7 @@ int check_batch_labels(npsolve *h, cudaStream_t s) {
   CK(h, cudaMemsetAsync(h->tr.badb, 0, sizeof(unsigned int), s));
   CK(h, cudaStreamSynchronize(s));
   if (bad) return fail(h, NPSOLVE_BAD_LABELS, "labels must be 0 (solid), 1 (fluid) or 2 (air)");
-  return NPSOLVE_OK;
+  return check_umma_err(h);  // a tensor-core wait of the weight gradient that timed out
 }
 
 // Reverse of Alg. 2 for the output cotangent gz (device), after train_forward:
@@ -1056,6 +1061,13 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, dou
   auto lc = [&](int l) { return l == 1 ? nullptr : w.counts[l]; };
   auto ll = [&](int l) { return l == 1 ? lab : nullptr; };
   auto O = [&](int l) { return out + (size_t)l * kTrOutPerLevel; };
+  // the weight-gradient contraction on the tensor cores where the level's image
+  // counts are exact in BF16 (at most 256 fine cells per cell: levels 1-3), on
+  // CUDA cores beyond
+  auto wgrad = [&](int l, Dims dl, const float *v, const float *g, double *dst) {
+    if (l <= 3) launch_cconv_wgrad_tc(ll(l), lc(l), dl, v, g, t.part, dst, h->umma_err, h->num_sms, s);
+    else launch_cconv_wgrad(ll(l), lc(l), dl, v, g, t.part, dst, s);
+  };
   CK(h, cudaMemsetAsync(out, 0, sizeof(double) * (kMaxLevels + 1) * kTrOutPerLevel, s));
   for (int l = 1; l <= L; ++l) {
     const long long nl = level_dims(d1, l).n();
@@ -1069,11 +1081,12 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, dou
     const Dims dl = level_dims(d1, l);
     const long long nl = dl.n();
     launch_dot2(t.gx[l], w.x1[l], w.x2[l], nl, t.part, O(l) + 2 * kWGOut, s);
-    launch_aff_stats(ll(l), lc(l), dl, 1.0 / pow(8.0, l - 1), t.part, O(l) + 2 * kWGOut + 2, s);
+    // the image statistics of Aff's weight gradient: the exact window sums of the setup
+    CK(h, cudaMemcpyAsync(O(l) + 2 * kWGOut + 2, w.affs + 54 * l, 54 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     launch_axpby_dev(nullptr, nl, w.affc + 2 * l, t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);   // gx1 += c1 gx
     launch_axpby_dev(nullptr, nl, w.affc + 2 * l + 1, t.gx[l], 0.f, nullptr, t.tmp, s);     // g x2 = c2 gx
     launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2 + 1, t.K, s);
-    launch_cconv_wgrad(ll(l), lc(l), dl, w.r2[l], t.tmp, t.part, O(l) + kWGOut, s);
+    wgrad(l, dl, w.r2[l], t.tmp, O(l) + kWGOut);
     launch_cconv_transpose(t.K, t.tmp, dl, t.tmp2, s);  // g r2
     launch_interp_adjoint_add(t.tmp2, level_dims(d1, l + 1), (l + 1 == L) ? t.gx1[L] : t.gx[l + 1], s);
     h->launches += 11;
@@ -1083,7 +1096,7 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, dou
     const Dims dl = level_dims(d1, l);
     const float *v = l == 1 ? t.rm : w.r1[l];
     launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2, t.K, s);
-    launch_cconv_wgrad(ll(l), lc(l), dl, v, t.gx1[l], t.part, O(l), s);
+    wgrad(l, dl, v, t.gx1[l], O(l));
     h->launches += 3;
     if (l > 1 || gr) {
       launch_cconv_transpose(t.K, t.gx1[l], dl, t.tmp, s);  // g r1^l
