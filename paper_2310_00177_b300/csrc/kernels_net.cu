@@ -171,6 +171,121 @@ __global__ void k_aff_from_counts(const unsigned long long *__restrict__ gcnt, c
   out[1] = a2->bconst + s2 / (27.0 * (double)n);
 }
 
+// The Aff blocks of every level (1..L-1) in two launches: the boundary-class
+// counts of all levels (blockIdx.y = level - 1; level 1 reads four labels per
+// lane), then one block per level forms c1, c2 and, optionally, the training
+// statistics, with the arithmetic of k_aff_counts / k_aff_from_counts.
+__device__ __forceinline__ void aff_count_cell(uint32_t f, uint32_t a, int cls, unsigned long long &inf,
+                                               unsigned long long &ina, unsigned long long *sc) {
+  if (cls == 0) {
+    inf += f;
+    ina += a;
+  } else {
+    if (f) atomicAdd(&sc[2 * cls], (unsigned long long)f);
+    if (a) atomicAdd(&sc[2 * cls + 1], (unsigned long long)a);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_aff_counts_all(const __grid_constant__ AffAll A) {
+  __shared__ unsigned long long sc[128];
+  const int lvl = blockIdx.y + 1;
+  const Dims dm = A.dims[lvl];
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) sc[i] = 0ull;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long rows = (long long)dm.ny * dm.nz;
+  unsigned long long inf = 0ull, ina = 0ull;
+  const bool vec = lvl == 1 && (dm.nx & 3) == 0;
+  for (long long r = (long long)blockIdx.x * nw + warp; r < rows; r += (long long)gridDim.x * nw) {
+    const int y = (int)(r % dm.ny), z = (int)(r / dm.ny);
+    const int cyz = 4 * edge_class(y, dm.ny) + 16 * edge_class(z, dm.nz);
+    const long long base = r * dm.nx;
+    if (vec) {
+      for (int x4 = lane; x4 < (dm.nx >> 2); x4 += 32) {
+        const uchar4 l4 = *reinterpret_cast<const uchar4 *>(A.lab + base + 4 * x4);
+        const uint8_t ls[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          aff_count_cell(ls[e] == kFluid, ls[e] == kAir, cyz + edge_class(4 * x4 + e, dm.nx), inf, ina, sc);
+      }
+    } else {
+      for (int x = lane; x < dm.nx; x += 32) {
+        uint32_t f, a;
+        if (lvl == 1) {
+          const uint8_t l = A.lab[base + x];
+          f = l == kFluid;
+          a = l == kAir;
+        } else {
+          const ushort2 c = A.counts[lvl][base + x];
+          f = c.x;
+          a = c.y;
+        }
+        aff_count_cell(f, a, cyz + edge_class(x, dm.nx), inf, ina, sc);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    inf += __shfl_down_sync(0xffffffffu, inf, o);
+    ina += __shfl_down_sync(0xffffffffu, ina, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&sc[0], inf);
+    atomicAdd(&sc[1], ina);
+  }
+  __syncthreads();
+  unsigned long long *cnt = A.cnt + 128 * lvl;
+  for (int i = threadIdx.x; i < 128; i += blockDim.x)
+    if (sc[i]) atomicAdd(&cnt[i], sc[i]);
+}
+
+__global__ void k_aff_from_counts_all(const __grid_constant__ AffAll A) {
+  const int lvl = blockIdx.x + 1;
+  __shared__ unsigned long long cnt[128];
+  __shared__ double t1[27], t2[27];
+  const AffW *a1 = A.aw + 2 * lvl, *a2 = A.aw + 2 * lvl + 1;
+  const long long n = A.dims[lvl].n();
+  double *stats = A.stats ? A.stats + 54 * lvl : nullptr;
+  const double stat_scale = ldexp(1.0, -3 * (lvl - 1)) / (27.0 * (double)n);  // 1 / (8^(lvl-1) 27 n)
+  const int l = threadIdx.x;
+  cnt[l] = A.cnt[128 * lvl + l];
+  __syncthreads();
+  if (l < 27) {
+    const int ox = l % 3 - 1, oy = (l / 3) % 3 - 1, oz = l / 9 - 1;
+    double sf = 0.0, sa = 0.0;  // exact: integer counts below 2^53
+    for (int c = 0; c < 64; ++c) {
+      if (!(keeps(c & 3, ox) && keeps((c >> 2) & 3, oy) && keeps(c >> 4, oz))) continue;
+      sf += (double)cnt[2 * c];
+      sa += (double)cnt[2 * c + 1];
+    }
+    t1[l] = (double)a1->wf[l] * sf + (double)a1->wa[l] * sa;
+    t2[l] = (double)a2->wf[l] * sf + (double)a2->wa[l] * sa;
+    if (stats) {
+      stats[l] = sf * stat_scale;
+      stats[27 + l] = sa * stat_scale;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = 0; i < 27; ++i) {
+    s1 += t1[i];
+    s2 += t2[i];
+  }
+  A.out[2 * lvl] = a1->bconst + s1 / (27.0 * (double)n);
+  A.out[2 * lvl + 1] = a2->bconst + s2 / (27.0 * (double)n);
+}
+
+void launch_aff_all(const AffAll &A, cudaStream_t s) {
+  if (A.L < 2) return;
+  cudaMemsetAsync(A.cnt, 0, sizeof(unsigned long long) * 128 * A.L, s);
+  const long long rows = (long long)A.dims[1].ny * A.dims[1].nz;
+  long long g = (rows + 7) / 8;
+  if (g > 148LL * 8) g = 148LL * 8;
+  k_aff_counts_all<<<dim3((unsigned)(g < 1 ? 1 : g), (unsigned)(A.L - 1)), 256, 0, s>>>(A);
+  k_aff_from_counts_all<<<A.L - 1, 128, 0, s>>>(A);
+}
+
 // ---------------------------------------------------------------------------
 // CConv on CUDA cores (FP32):
 //   K_a(p) = bp[a] + sum_l (wf[a][l] nF(p+l) + wa[a][l] nA(p+l))

@@ -49,6 +49,20 @@ int pcg_k_offset();
 
 // kernels_net.cu
 void launch_pyramid(const uint8_t *lab, Dims d1, ushort2 *const *counts, int L, cudaStream_t s);
+// The Aff coefficients (and training statistics) of levels 1..L-1 in two
+// launches: out[2 l], out[2 l + 1] = c1, c2 of level l; stats (may be null)
+// + 54 l the 54 window sums scaled by 1 / (8^(l-1) 27 n_l); cnt: 128 L
+// counters of scratch.
+struct AffAll {
+  const uint8_t *lab;
+  const ushort2 *counts[kMaxLevels + 1];
+  Dims dims[kMaxLevels + 1];
+  const AffW *aw;
+  double *out, *stats;
+  unsigned long long *cnt;
+  int L;
+};
+void launch_aff_all(const AffAll &A, cudaStream_t s);
 // Aff coefficients c1, c2 of a level into out[0..1]; with stats != null also the
 // 54 image window sums scaled by feature_scale / (27 n) (training statistics).
 void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,

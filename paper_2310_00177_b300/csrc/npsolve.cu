@@ -749,10 +749,21 @@ int setup_image(npsolve *h, const uint8_t *lab, Dims d1, cudaStream_t s, bool ch
     launch_lap_codes(lab, d1, w.lapcode, w.gmask, s);
     h->launches += 2;
   }
-  for (int l = 1; l < L; ++l)
-    launch_aff(l == 1 ? lab : nullptr, l == 1 ? nullptr : w.counts[l], level_dims(d1, l), h->aw + l * 2,
-               h->aw + l * 2 + 1, w.part, w.affc + 2 * l, s, w.affs + 54 * l, 1.0 / pow(8.0, l - 1));
-  h->launches += 1 + (L - 1) + 2 * (L - 1);
+  {
+    AffAll aa{};
+    aa.lab = lab;
+    for (int l = 1; l <= L; ++l) {
+      aa.counts[l] = l == 1 ? nullptr : w.counts[l];
+      aa.dims[l] = level_dims(d1, l);
+    }
+    aa.aw = h->aw;
+    aa.out = w.affc;
+    aa.stats = w.affs;
+    aa.cnt = (unsigned long long *)w.part;  // 128 L counters of the reduction scratch
+    aa.L = L;
+    launch_aff_all(aa, s);
+  }
+  h->launches += 1 + (L - 1) + (L > 1 ? 2 : 0);
   w.tail_T = tail_level(h, d1);
   if (w.tail_T) {
     // the coarse tail's per-cell kernels: CConv1 of levels T..L, CConv2 of T..L-1

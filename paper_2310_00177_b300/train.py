@@ -31,6 +31,12 @@ After each stage the weights are written as raw FP32
 (npsolve_weight_count(L) values) to <out-dir>/npsdo_L<L>.f32 with a JSON log
 beside them (loss history, the iteration counts of the 256^3 / 128^3 / 64^3
 evaluation problems in both precision forms).
+
+--time-steps K times K training steps instead (after one untimed step) on a
+fixed batch of 8 seeded 64^3 and 8 seeded 128^3 sloshing systems with N(0, 1)
+right-hand sides (the cost of a step does not depend on them) at lr 1e-30, so
+that the weights stay as they are; --levels picks the network (its trained
+weights when present).
 """
 from __future__ import annotations
 
@@ -163,6 +169,34 @@ def train_stage(w0, L, minutes, lr0, pools, per_batch, rng, log_every=50):
     return w, hist, time.time() - t1
 
 
+def time_steps(steps, L, dev):
+    """ms per training step on the fixed timing batch (--time-steps)."""
+    import torch
+
+    from paper_2310_00177_b300 import binding, synth
+
+    f = os.path.join(ROOT, "paper_2310_00177_b300", "weights", f"npsdo_L{L}.f32")
+    w = np.fromfile(f, np.float32) if os.path.exists(f) else synth.init_weights(L, 7).astype(np.float32)
+    sol = binding.Solver(w, levels=L, n_ortho=2, precision=binding.FP32)
+    labs, bs = [], []
+    for i, n in enumerate([64] * 8 + [128] * 8):
+        lab = synth.slosh_scene(n, 5000 + i)
+        b = synth.rhs_normal(lab, 6000 + i).astype(np.float32)
+        b /= max(float(np.linalg.norm(b)), 1e-30)
+        labs.append(torch.from_numpy(lab).to(dev))
+        bs.append(torch.from_numpy(b).to(dev))
+    sol.train_step(labs, bs, lr=1e-30)
+    out = []
+    for _ in range(steps):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        loss = sol.train_step(labs, bs, lr=1e-30)
+        torch.cuda.synchronize(dev)
+        out.append((time.perf_counter() - t) * 1e3)
+    sol.close()
+    print(json.dumps({"levels": L, "batch": "8 x 64^3 + 8 x 128^3", "ms_per_step": out, "loss": loss}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--stages", default="4:8", help="comma-separated L:minutes[:scratch]")
@@ -177,6 +211,8 @@ def main():
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "paper_2310_00177_b300", "weights"))
     ap.add_argument("--seed", type=int, default=4000)
     ap.add_argument("--no-eval", action="store_true")
+    ap.add_argument("--time-steps", type=int, default=0, help="only time this many steps on the timing batch")
+    ap.add_argument("--levels", type=int, default=6, help="network depth of --time-steps")
     args = ap.parse_args()
 
     import torch
@@ -184,6 +220,9 @@ def main():
     from paper_2310_00177_b300 import synth
 
     dev = torch.device("cuda", 0)
+    if args.time_steps:
+        time_steps(args.time_steps, args.levels, dev)
+        return
     t0 = time.time()
     pool_s = make_pool(args.small, args.systems, args.rhs, args.rhs_mode, args.seed, dev)
     t_s = time.time() - t0
