@@ -20,7 +20,10 @@
  * a DEVICE pointer on the current CUDA device, owned by the caller, and must
  * stay valid until the call returns (all calls are synchronous with respect
  * to the host; work is issued on `stream`, a cudaStream_t, 0 = legacy default
- * stream).  The handle owns its scratch memory (Krylov state, image pyramid,
+ * stream).  Device arrays are accessed with 8- and 16-byte vector loads and
+ * stores, so every device pointer must be 16-byte aligned (cudaMalloc and
+ * framework allocators return far larger alignments; an offset view into one
+ * may not be): a misaligned one is rejected with NPSOLVE_BAD_ARG.  The handle owns its scratch memory (Krylov state, image pyramid,
  * network intermediates), allocates it on first use for a grid size, reuses
  * it for equal or smaller grids, and frees it in npsolve_destroy.  There is
  * no CPU fallback: without a usable sm_103a device every call fails with

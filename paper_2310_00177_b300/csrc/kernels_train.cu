@@ -5,11 +5,14 @@
 //   input gradient   gv(q) = sum_a K_a(q - a) g(q - a)          (gather form)
 //   kernel gradient  gK_a(p) = g(p) v(p + a)
 //   weight gradient  gW'[a][j] = sum_p gK_a(p) F_j(p),  F = (nF window, nA window, 1)
-// with K materialised per cell (the same FP32 arithmetic as the forward) so
-// the input gradient is a deterministic gather, and the 27 x 55 weight
-// gradient accumulated per block in FP32 over 32-cell batches and reduced
-// across blocks in FP64 in a fixed order.
+// with K stored per cell by the training forward (k_cconv_store_K) so the
+// input gradient is a deterministic gather, and the 27 x 55 weight gradient a
+// [27 x P] . [P x 55] contraction over the cells: on the tcgen05 tensor cores
+// where the level's image counts are exact in BF16 (k_cconv_wgrad_tc), on
+// CUDA cores in FP32 32-cell batches beyond (k_cconv_wgrad); block partials
+// reduced in FP64 in a fixed order.
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include "nps_common.cuh"
 #include "nps_kernels.h"
@@ -72,6 +75,148 @@ __global__ void __launch_bounds__(128) k_materialize_K(const uint8_t *__restrict
       for (int l = 0; l < 27; ++l) k = fmaf(sw.wf[a][l], nf[l], fmaf(sw.wa[a][l], na[l], k));
       K[p * 27 + a] = k;
     }
+  }
+}
+
+// Training forward of one CConv block: out(p) = sum_a K_a(p) v(p + a), the
+// per-cell kernels stored to K[p][a] for the backward.  A window that is all
+// one pure class (all solid, all fluid or all air, the grid's outside solid)
+// takes that class's constant kernel (computed once on the host, as the
+// solve's cached path does); any other window computes K_a(p) as the solve's
+// CUDA-core CConv does (the same FMA order; rounded to BF16 when RK).  The
+// folded weights are a kernel parameter (uniform constant operands of the
+// FMAs, no shared-memory load per FMA), and a warp whose 32 windows are all
+// pure skips the FMA chain.  A warp owns 32 consecutive cells; with ROWS (nx a
+// multiple of 32) they are 32 cells of one grid row and the warp loads each of
+// the nine window rows once, coalesced, taking the x-1 and x+1 taps from the
+// neighbouring lanes.  Each warp's 32 x 27 kernels go out through shared
+// memory as contiguous stores.
+struct PureK {
+  float k[3][27];  // the constant kernels of pure solid, fluid and air windows
+};
+constexpr int kSKWarps = 4;
+
+// One window cell's features and input value (0 outside the grid; the input
+// zeroed off fluid when mask_input).
+__device__ __forceinline__ void window_cell(const uint8_t *lab, const ushort2 *counts, const float *v, long long q,
+                                            int mask_input, float &f, float &a, float &val) {
+  if (lab) {
+    const uint8_t l = lab[q];
+    f = l == kFluid ? 1.f : 0.f;
+    a = l == kAir ? 1.f : 0.f;
+  } else {
+    const ushort2 c = counts[q];
+    f = (float)c.x;
+    a = (float)c.y;
+  }
+  val = v[q];
+  if (mask_input && f == 0.f) val = 0.f;  // level 1: f == 1 exactly on fluid
+}
+
+template <bool RK, bool ROWS>
+__global__ void __launch_bounds__(kSKWarps * 32) k_cconv_store_K(const uint8_t *__restrict__ lab,
+                                                                 const ushort2 *__restrict__ counts, Dims d,
+                                                                 const __grid_constant__ CConvW w,
+                                                                 const __grid_constant__ PureK pk, float full,
+                                                                 const float *__restrict__ v, int mask_input,
+                                                                 float *__restrict__ K, float *__restrict__ out) {
+  __shared__ float sk[kSKWarps][32 * 27];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long n = d.n();
+  const long long ntiles = (n + 31) / 32;
+  for (long long wt = (long long)blockIdx.x * kSKWarps + warp; wt < ntiles; wt += (long long)gridDim.x * kSKWarps) {
+    const long long p = wt * 32 + lane;
+    const bool act = p < n;
+    float nf[27], na[27], vv[27];
+    if (ROWS) {  // n is a multiple of 32: every lane is active
+      int x0, y, z;
+      cell_xyz(wt * 32, d, x0, y, z);
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {  // window row dy = r % 3 - 1, dz = r / 3 - 1
+        const int yy = y + r % 3 - 1, zz = z + r / 3 - 1;
+        float cf = 0.f, ca = 0.f, cv = 0.f, hf = 0.f, ha = 0.f, hv = 0.f;
+        if (yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz) {  // the same for the whole warp
+          const long long rb = ((long long)zz * d.ny + yy) * d.nx;
+          window_cell(lab, counts, v, rb + x0 + lane, mask_input, cf, ca, cv);
+          const int hx = lane == 0 ? x0 - 1 : x0 + 32;  // the halo columns, read by lanes 0 and 31
+          if ((lane == 0 || lane == 31) && hx >= 0 && hx < d.nx)
+            window_cell(lab, counts, v, rb + hx, mask_input, hf, ha, hv);
+        }
+        float lf = __shfl_up_sync(0xffffffffu, cf, 1), la = __shfl_up_sync(0xffffffffu, ca, 1);
+        float lv = __shfl_up_sync(0xffffffffu, cv, 1);
+        float rf = __shfl_down_sync(0xffffffffu, cf, 1), ra = __shfl_down_sync(0xffffffffu, ca, 1);
+        float rv = __shfl_down_sync(0xffffffffu, cv, 1);
+        if (lane == 0) {
+          lf = hf;
+          la = ha;
+          lv = hv;
+        }
+        if (lane == 31) {
+          rf = hf;
+          ra = ha;
+          rv = hv;
+        }
+        nf[3 * r] = lf;
+        na[3 * r] = la;
+        vv[3 * r] = lv;
+        nf[3 * r + 1] = cf;
+        na[3 * r + 1] = ca;
+        vv[3 * r + 1] = cv;
+        nf[3 * r + 2] = rf;
+        na[3 * r + 2] = ra;
+        vv[3 * r + 2] = rv;
+      }
+    } else if (act) {
+      int x, y, z;
+      cell_xyz(p, d, x, y, z);
+#pragma unroll
+      for (int t = 0; t < 27; ++t) {
+        const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
+        nf[t] = na[t] = vv[t] = 0.f;
+        if (xx >= 0 && yy >= 0 && zz >= 0 && xx < d.nx && yy < d.ny && zz < d.nz)
+          window_cell(lab, counts, v, ((long long)zz * d.ny + yy) * d.nx + xx, mask_input, nf[t], na[t], vv[t]);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 27; ++t) nf[t] = na[t] = vv[t] = 0.f;
+    }
+    // 0 pure solid, 1 pure fluid, 2 pure air, -1 mixed (lanes past the end: solid)
+    bool all_s = true, all_f = true, all_a = true;
+#pragma unroll
+    for (int t = 0; t < 27; ++t) {
+      all_s &= nf[t] == 0.f && na[t] == 0.f;
+      all_f &= nf[t] == full;
+      all_a &= na[t] == full;
+    }
+    const int cls = all_f ? 1 : (all_a ? 2 : (all_s ? 0 : -1));
+    const int c = cls < 0 ? 0 : cls;
+    float acc = 0.f;
+    if (__all_sync(0xffffffffu, cls >= 0)) {
+#pragma unroll
+      for (int a = 0; a < 27; ++a) {
+        const float k = c == 1 ? pk.k[1][a] : (c == 2 ? pk.k[2][a] : pk.k[0][a]);
+        acc = fmaf(k, vv[a], acc);
+        sk[warp][lane * 27 + a] = k;  // stride 27 (odd): no bank conflicts
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 27; ++a) {
+        float k = w.bp[a];
+#pragma unroll
+        for (int l = 0; l < 27; ++l) k = fmaf(w.wf[a][l], nf[l], fmaf(w.wa[a][l], na[l], k));
+        if (RK) k = __bfloat162float(__float2bfloat16_rn(k));
+        if (cls >= 0) k = c == 1 ? pk.k[1][a] : (c == 2 ? pk.k[2][a] : pk.k[0][a]);
+        acc = fmaf(k, vv[a], acc);
+        sk[warp][lane * 27 + a] = k;
+      }
+    }
+    if (act) out[p] = acc;
+    __syncwarp();
+    const long long lim = (n - wt * 32) * 27;  // floats of this tile inside the grid
+    float *dst = K + wt * 32 * 27;
+    for (int i = lane; i < 32 * 27; i += 32)
+      if (i < lim) dst[i] = sk[warp][i];
+    __syncwarp();
   }
 }
 
@@ -177,6 +322,10 @@ __global__ void __launch_bounds__(256) k_cconv_wgrad(const uint8_t *__restrict__
 // j holds G[a][j] = D[j][a] + D[j][32 + a] + D[j][64 + a], written as the
 // CTA's partial in the layout of k_cconv_wgrad (reduced by k_wgrad_final).
 constexpr int kWgCells = 128;                      // cells per chunk (MMA K = 8 x 16)
+// threads: the 144 staging tasks of a chunk of runs (16 runs x 9 window rows)
+// one each; the per-cell staging uses the first 128, the epilogue warps 0-1
+// (TMEM lanes 0-63 hold the 55 feature rows)
+constexpr int kWgThreads = 160;
 constexpr int kWgRowsA = 128;                      // MMA M: 55 feature rows, padded
 constexpr int kWgRowsB = 96;                       // MMA N: 3 BF16 terms x 32 taps
 constexpr int kWgSBO = (kWgCells / 8) * 128;       // bytes between 8-row groups (K-major, no swizzle)
@@ -191,7 +340,165 @@ __device__ __forceinline__ uint32_t wg_off(int row, int k) {
   return (uint32_t)((row >> 3) * kWgSBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
-__global__ void __launch_bounds__(kWgCells) k_cconv_wgrad_tc(const uint8_t *__restrict__ lab,
+// The three BF16 terms hi + mid + lo of two FP32 values (hi = bf16(x),
+// mid = bf16(x - hi), lo = bf16(x - hi - mid)), packed in pairs.
+__device__ __forceinline__ void split3_pair(float a, float b, uint32_t &hi, uint32_t &mid, uint32_t &lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float ra = a - __low2float(h), rb = b - __high2float(h);
+  const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(ra - __low2float(m), rb - __high2float(m));
+  hi = *(const uint32_t *)&h;
+  mid = *(const uint32_t *)&m;
+  lo = *(const uint32_t *)&l;
+}
+
+__device__ __forceinline__ uint32_t bf16_bits_of_count(uint32_t c) {  // exact: c <= 256
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)c));
+}
+
+// Operand staging of one 128-cell chunk when nx % 8 == 0 (and the sources are
+// aligned for vector loads): the chunk is 16 runs of 8 consecutive cells of
+// one grid row.  A task is one run and one (dy, dz) row of the 3 x 3 x 3
+// window: it loads the ten labels / counts and input values x0-1 .. x0+8 of
+// that row and the run's eight cotangents, and writes the taps dx = -1, 0, 1
+// of both feature channels and of the three BF16 terms of gK, each one
+// 16-byte row of the K-major operands.  The values are those of the per-cell
+// staging, bit for bit.
+__device__ __forceinline__ void wg_stage_runs(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                              const Dims &d, const float *__restrict__ v,
+                                              const float *__restrict__ g, long long ch, uint8_t *A, uint8_t *B,
+                                              int tid) {
+  const long long n = d.n();
+  for (int task = tid; task < (kWgCells / 8) * 9; task += kWgThreads) {
+    const int run = task / 9, r = task - run * 9;
+    const long long p0 = ch * kWgCells + run * 8;
+    const bool valid = p0 < n;  // n is a multiple of 8
+    int x0 = 0, y = 0, z = 0;
+    if (valid) cell_xyz(p0, d, x0, y, z);
+    const int yy = y + r % 3 - 1, zz = z + r / 3 - 1;
+    const bool rowin = valid && yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz;
+    const long long rb = rowin ? ((long long)zz * d.ny + yy) * d.nx + x0 : 0;  // cell x0 of the row
+    const bool has_l = rowin && x0 > 0, has_r = rowin && x0 + 8 < d.nx;
+    // the fluid and air features at x0-1 .. x0+8 as BF16 bits (0 outside the grid)
+    uint32_t hf[10], ha[10];
+    if (lab) {
+      uint2 mid = make_uint2(0u, 0u);
+      if (rowin) mid = *(const uint2 *)(lab + rb);
+      const uint32_t el = has_l ? lab[rb - 1] : 0u, er = has_r ? lab[rb + 8] : 0u;
+      hf[0] = el == kFluid ? 0x3F80u : 0u;
+      ha[0] = el == kAir ? 0x3F80u : 0u;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const uint32_t c = ((i < 4 ? mid.x : mid.y) >> (8 * (i & 3))) & 0xFFu;
+        hf[1 + i] = c == kFluid ? 0x3F80u : 0u;
+        ha[1 + i] = c == kAir ? 0x3F80u : 0u;
+      }
+      hf[9] = er == kFluid ? 0x3F80u : 0u;
+      ha[9] = er == kAir ? 0x3F80u : 0u;
+    } else {
+      uint4 q0 = make_uint4(0u, 0u, 0u, 0u), q1 = q0;
+      if (rowin) {
+        q0 = *(const uint4 *)(counts + rb);
+        q1 = *(const uint4 *)(counts + rb + 4);
+      }
+      const uint32_t el = has_l ? *(const uint32_t *)(counts + rb - 1) : 0u;
+      const uint32_t er = has_r ? *(const uint32_t *)(counts + rb + 8) : 0u;
+      const uint32_t wv[10] = {el, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, er};
+#pragma unroll
+      for (int i = 0; i < 10; ++i) {
+        hf[i] = bf16_bits_of_count(wv[i] & 0xFFFFu);
+        ha[i] = bf16_bits_of_count(wv[i] >> 16);
+      }
+    }
+    // the input at x0-1 .. x0+8 and the run's cotangents
+    float vr[10], gp[8];
+    {
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, g0 = a0, g1 = a0;
+      if (rowin) {
+        a0 = *(const float4 *)(v + rb);
+        a1 = *(const float4 *)(v + rb + 4);
+      }
+      if (valid) {
+        g0 = *(const float4 *)(g + p0);
+        g1 = *(const float4 *)(g + p0 + 4);
+      }
+      vr[0] = has_l ? v[rb - 1] : 0.f;
+      vr[1] = a0.x; vr[2] = a0.y; vr[3] = a0.z; vr[4] = a0.w;
+      vr[5] = a1.x; vr[6] = a1.y; vr[7] = a1.z; vr[8] = a1.w;
+      vr[9] = has_r ? v[rb + 8] : 0.f;
+      gp[0] = g0.x; gp[1] = g0.y; gp[2] = g0.z; gp[3] = g0.w;
+      gp[4] = g1.x; gp[5] = g1.y; gp[6] = g1.z; gp[7] = g1.w;
+    }
+    const uint32_t col = (uint32_t)run * 8;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {  // dx = k - 1: tap a = 3 r + k
+      const int a = 3 * r + k;
+      uint4 f, q, hi, md, lo;
+      f.x = hf[k] | (hf[k + 1] << 16);
+      f.y = hf[k + 2] | (hf[k + 3] << 16);
+      f.z = hf[k + 4] | (hf[k + 5] << 16);
+      f.w = hf[k + 6] | (hf[k + 7] << 16);
+      q.x = ha[k] | (ha[k + 1] << 16);
+      q.y = ha[k + 2] | (ha[k + 3] << 16);
+      q.z = ha[k + 4] | (ha[k + 5] << 16);
+      q.w = ha[k + 6] | (ha[k + 7] << 16);
+      *(uint4 *)(A + wg_off(a, col)) = f;
+      *(uint4 *)(A + wg_off(27 + a, col)) = q;
+      float gk[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) gk[i] = gp[i] != 0.f ? gp[i] * vr[i + k] : 0.f;
+      split3_pair(gk[0], gk[1], hi.x, md.x, lo.x);
+      split3_pair(gk[2], gk[3], hi.y, md.y, lo.y);
+      split3_pair(gk[4], gk[5], hi.z, md.z, lo.z);
+      split3_pair(gk[6], gk[7], hi.w, md.w, lo.w);
+      *(uint4 *)(B + wg_off(a, col)) = hi;
+      *(uint4 *)(B + wg_off(32 + a, col)) = md;
+      *(uint4 *)(B + wg_off(64 + a, col)) = lo;
+    }
+    if (r == 0) {  // the constant feature of the bias
+      const uint32_t one = valid ? 0x3F803F80u : 0u;
+      *(uint4 *)(A + wg_off(54, col)) = make_uint4(one, one, one, one);
+    }
+  }
+}
+
+// Operand staging of one 128-cell chunk, one cell per thread (any grid).
+__device__ __forceinline__ void wg_stage_cells(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                               const Dims &d, const float *__restrict__ v,
+                                               const float *__restrict__ g, long long ch, uint8_t *A, uint8_t *B,
+                                               int tid) {
+  if (tid >= kWgCells) return;
+  const long long n = d.n();
+  const long long p = ch * kWgCells + tid;
+  float gp = 0.f;
+  int x = 0, y = 0, z = 0;
+  if (p < n) {
+    cell_xyz(p, d, x, y, z);
+    gp = g[p];
+  }
+#pragma unroll
+  for (int l = 0; l < 27; ++l) {
+    const float2 f = p < n ? feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1)
+                           : make_float2(0.f, 0.f);
+    *(__nv_bfloat16 *)(A + wg_off(l, tid)) = __float2bfloat16_rn(f.x);  // exact: counts <= 256
+    *(__nv_bfloat16 *)(A + wg_off(27 + l, tid)) = __float2bfloat16_rn(f.y);
+  }
+  *(__nv_bfloat16 *)(A + wg_off(54, tid)) = __float2bfloat16_rn(p < n ? 1.f : 0.f);
+#pragma unroll
+  for (int a = 0; a < 27; ++a) {
+    const float gk = gp != 0.f ? gp * vec_at(v, d, x + a % 3 - 1, y + (a / 3) % 3 - 1, z + a / 9 - 1) : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(gk);
+    const float r1 = gk - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    *(__nv_bfloat16 *)(B + wg_off(a, tid)) = hi;
+    *(__nv_bfloat16 *)(B + wg_off(32 + a, tid)) = mid;
+    *(__nv_bfloat16 *)(B + wg_off(64 + a, tid)) = lo;
+  }
+}
+
+template <bool RUNS>
+__global__ void __launch_bounds__(kWgThreads) k_cconv_wgrad_tc(const uint8_t *__restrict__ lab,
                                                              const ushort2 *__restrict__ counts, Dims d,
                                                              const float *__restrict__ v, const float *__restrict__ g,
                                                              double *__restrict__ part, int *err) {
@@ -202,7 +509,7 @@ __global__ void __launch_bounds__(kWgCells) k_cconv_wgrad_tc(const uint8_t *__re
   uint32_t *s_tmem = (uint32_t *)(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   // zero both buffers once: the padding rows are never written again
-  for (int i = tid; i < 2 * kWgBufBytes / 16; i += kWgCells) ((uint4 *)sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < 2 * kWgBufBytes / 16; i += kWgThreads) ((uint4 *)sm)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
     tmem_alloc(s_tmem, kWgTmemCols);
     tmem_relinquish();
@@ -235,32 +542,8 @@ __global__ void __launch_bounds__(kWgCells) k_cconv_wgrad_tc(const uint8_t *__re
       issued[b] = 0;
     }
     uint8_t *A = sm + b * kWgBufBytes, *B = A + kWgABytes;
-    const long long p = ch * kWgCells + tid;
-    float gp = 0.f;
-    int x = 0, y = 0, z = 0;
-    if (p < n) {
-      cell_xyz(p, d, x, y, z);
-      gp = g[p];
-    }
-#pragma unroll
-    for (int l = 0; l < 27; ++l) {
-      const float2 f = p < n ? feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1)
-                             : make_float2(0.f, 0.f);
-      *(__nv_bfloat16 *)(A + wg_off(l, tid)) = __float2bfloat16_rn(f.x);  // exact: counts <= 256
-      *(__nv_bfloat16 *)(A + wg_off(27 + l, tid)) = __float2bfloat16_rn(f.y);
-    }
-    *(__nv_bfloat16 *)(A + wg_off(54, tid)) = __float2bfloat16_rn(p < n ? 1.f : 0.f);
-#pragma unroll
-    for (int a = 0; a < 27; ++a) {
-      const float gk = gp != 0.f ? gp * vec_at(v, d, x + a % 3 - 1, y + (a / 3) % 3 - 1, z + a / 9 - 1) : 0.f;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(gk);
-      const float r1 = gk - __bfloat162float(hi);
-      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-      *(__nv_bfloat16 *)(B + wg_off(a, tid)) = hi;
-      *(__nv_bfloat16 *)(B + wg_off(32 + a, tid)) = mid;
-      *(__nv_bfloat16 *)(B + wg_off(64 + a, tid)) = lo;
-    }
+    if (RUNS) wg_stage_runs(lab, counts, d, v, g, ch, A, B, tid);
+    else wg_stage_cells(lab, counts, d, v, g, ch, A, B, tid);
     fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
     fence_before_sync();
     __syncthreads();
@@ -287,8 +570,8 @@ __global__ void __launch_bounds__(kWgCells) k_cconv_wgrad_tc(const uint8_t *__re
   if (aborted) {
     if (tid == 0 && err) atomicExch(err, 1);
   } else if (i == 0) {
-    for (int o = tid; o < kWG; o += kWgCells) part[(size_t)blockIdx.x * kWG + o] = 0.0;
-  } else {
+    for (int o = tid; o < kWG; o += kWgThreads) part[(size_t)blockIdx.x * kWG + o] = 0.0;
+  } else if (warp < 2) {
     uint32_t c[3][32];
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
 #pragma unroll
@@ -307,12 +590,25 @@ __global__ void __launch_bounds__(kWgCells) k_cconv_wgrad_tc(const uint8_t *__re
   if (warp == 0) tmem_dealloc(tmem, kWgTmemCols);
 }
 
-// Sum the block partials of k_cconv_wgrad (fixed order) into out[1485].
-__global__ void k_wgrad_final(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < kWG; o += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * kWG + o];
-    out[o] = s;
+// Sum the block partials of the weight gradient into out[1485] in a fixed
+// order: a CTA takes 32 consecutive outputs, its warp i the blocks i, i + 8,
+// ..., and the eight warp sums are added in order.
+constexpr int kWFSlices = 8;
+__global__ void __launch_bounds__(kWFSlices * 32) k_wgrad_final(const double *__restrict__ part, int nblocks,
+                                                                double *__restrict__ out) {
+  __shared__ double sm[kWFSlices][32];
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (o < kWG)
+    for (int b = sl; b < nblocks; b += kWFSlices) s += part[(size_t)b * kWG + o];
+  sm[sl][lane] = s;
+  __syncthreads();
+  if (sl == 0 && o < kWG) {
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < kWFSlices; ++i) t += sm[i][lane];
+    out[o] = t;
   }
 }
 
@@ -484,6 +780,22 @@ void launch_materialize_K(const uint8_t *lab, const ushort2 *counts, Dims d, con
                           cudaStream_t s) {
   k_materialize_K<<<gridn(d.n(), 128), 128, 0, s>>>(lab, counts, d, w, K);
 }
+void launch_cconv_store_K(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW &w, const float *kpure,
+                          float full, const float *v, int mask_input, int round_k, float *K, float *out,
+                          cudaStream_t s) {
+  const long long tiles = (d.n() + 31) / 32;
+  long long g = (tiles + kSKWarps - 1) / kSKWarps;
+  if (g > 148LL * 16) g = 148LL * 16;
+  if (g < 1) g = 1;
+  PureK pk;
+  memcpy(&pk, kpure, sizeof(pk));
+  auto go = [&](auto kern) {
+    kern<<<(int)g, kSKWarps * 32, 0, s>>>(lab, counts, d, w, pk, full, v, mask_input, K, out);
+  };
+  const bool rows = d.nx % 32 == 0;  // a warp's 32 cells in one grid row
+  if (round_k) rows ? go(k_cconv_store_K<true, true>) : go(k_cconv_store_K<true, false>);
+  else rows ? go(k_cconv_store_K<false, true>) : go(k_cconv_store_K<false, false>);
+}
 void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s) {
   k_cconv_transpose<<<gridn(d.n(), 256), 256, 0, s>>>(K, g, d, gv);
 }
@@ -496,7 +808,7 @@ void launch_cconv_wgrad(const uint8_t *lab, const ushort2 *counts, Dims d, const
                         double *part, double *out, cudaStream_t s) {
   const int nb = wgrad_blocks(d);
   k_cconv_wgrad<<<nb, 256, 0, s>>>(lab, counts, d, v, g, part);
-  k_wgrad_final<<<(kWG + 255) / 256, 256, 0, s>>>(part, nb, out);
+  k_wgrad_final<<<(kWG + 31) / 32, kWFSlices * 32, 0, s>>>(part, nb, out);
 }
 // The tensor-core weight gradient (levels with counts <= 256 per cell); `err`
 // is set if an MMA wait timed out.  Two CTAs per SM (112 KB of shared memory
@@ -507,15 +819,21 @@ void launch_cconv_wgrad_tc(const uint8_t *lab, const ushort2 *counts, Dims d, co
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaFuncSetAttribute(k_cconv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    cudaFuncSetAttribute(k_cconv_wgrad_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    cudaFuncSetAttribute(k_cconv_wgrad_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
     configured[dev] = 1;
   }
   const long long nch = (d.n() + kWgCells - 1) / kWgCells;
   long long nb = (long long)num_sms * 2;
   if (nb > nch) nb = nch;
   if (nb < 1) nb = 1;
-  k_cconv_wgrad_tc<<<(int)nb, kWgCells, kWgSmem, s>>>(lab, counts, d, v, g, part, err);
-  k_wgrad_final<<<(kWG + 255) / 256, 256, 0, s>>>(part, (int)nb, out);
+  // runs of 8 cells: rows of a multiple of 8 cells, and sources aligned for
+  // the 8- and 16-byte loads (the level buffers are; user labels may not be)
+  const bool runs = d.nx % 8 == 0 && ((uintptr_t)lab % 8) == 0 && ((uintptr_t)counts % 16) == 0 &&
+                    ((uintptr_t)v % 16) == 0 && ((uintptr_t)g % 16) == 0;
+  if (runs) k_cconv_wgrad_tc<true><<<(int)nb, kWgThreads, kWgSmem, s>>>(lab, counts, d, v, g, part, err);
+  else k_cconv_wgrad_tc<false><<<(int)nb, kWgThreads, kWgSmem, s>>>(lab, counts, d, v, g, part, err);
+  k_wgrad_final<<<(kWG + 31) / 32, kWFSlices * 32, 0, s>>>(part, (int)nb, out);
 }
 void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s) {
   k_pool_adjoint_add<<<gridn(fine.n(), 256), 256, 0, s>>>(gc, fine, gf);

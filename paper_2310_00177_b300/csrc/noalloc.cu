@@ -134,6 +134,8 @@ __global__ void k_relres_final_na(const double *part, int nblocks, double *out) 
 extern "C" int npsolve_true_residual_noalloc(const uint8_t *labels, int nx, int ny, int nz, const float *b,
                                              const double *x, double *rel_residual, void *stream) {
   if (!labels || !b || !x || !rel_residual) return na_fail(NPSOLVE_BAD_ARG, "null pointer argument");
+  if ((((uintptr_t)labels | (uintptr_t)b | (uintptr_t)x) & 15u) != 0)
+    return na_fail(NPSOLVE_BAD_ARG, "device pointers must be 16-byte aligned");
   if (nx < 1 || ny < 1 || nz < 1) return na_fail(NPSOLVE_BAD_DIMS, "bad dims %dx%dx%d", nx, ny, nz);
   const long long n = (long long)nx * ny * nz;
   if (n > kNoAllocMaxCells)

@@ -209,6 +209,13 @@ void launch_mask_copy(const uint8_t *lab, long long n, const float *in, float *o
 // kernels_train.cu
 void launch_materialize_K(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, float *K,
                           cudaStream_t s);
+// Training forward of one CConv block with the weights as kernel parameters;
+// the per-cell kernels go to K[p][27] for the backward.  kpure (host, 81
+// floats): the kernels of pure solid, fluid and air windows; full: the count
+// of a pure cell of the level (8^(l-1)).
+void launch_cconv_store_K(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW &w, const float *kpure,
+                          float full, const float *v, int mask_input, int round_k, float *K, float *out,
+                          cudaStream_t s);
 void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s);
 int wgrad_blocks(Dims d);
 int wgrad_outputs();

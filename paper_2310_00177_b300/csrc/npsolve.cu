@@ -23,6 +23,7 @@
 #include <random>
 #include <algorithm>
 #include <string>
+#include <initializer_list>
 #include <vector>
 
 #include "../../include/npsolve.h"
@@ -150,6 +151,7 @@ struct npsolve {
   int device = 0;
   std::vector<float> weights;      // host copy of the flat blob
   CConvW *cw = nullptr;            // [(kMaxLevels+1)*2], index lvl*2 + (type-1)
+  std::vector<CConvW> cw_host;     // the same on the host (kernel parameters of the training forward)
   uint8_t *uw = nullptr;           // tensor-core W splits, [(kMaxLevels+1)*2][umma_weight_bytes(3)]
   float *uni = nullptr;            // uniform-window kernel terms Bp, SWf, SWa: [(kMaxLevels+1)*2][81]
   std::vector<float> uni_host;     // the same on the host
@@ -176,6 +178,12 @@ struct npsolve {
     long long cap = 0;
     float *gx[kMaxLevels + 1] = {}, *gx1[kMaxLevels + 1] = {};
     float *rm = nullptr, *tmp = nullptr, *tmp2 = nullptr, *res = nullptr, *gz = nullptr, *K = nullptr;
+    // the per-cell kernels of every CConv of the last training forward, K[p][a]
+    // per block (slot lvl*2 + type-1), kept for the backward
+    float *kall = nullptr;
+    long long kall_cap = 0;  // floats
+    float *kslot[(kMaxLevels + 1) * 2] = {};
+    bool kstore = false;     // cconv() computes and stores the kernels (training forward)
     double *part = nullptr, *out = nullptr;  // partials, and the reduced results (see train_backward)
     double *outb = nullptr;                  // one reduced-results block per example of a batch
     int outb_cap = 0;                        // examples outb holds
@@ -186,6 +194,17 @@ struct npsolve {
 };
 
 namespace {
+
+// The kernels read and write device arrays with 8- and 16-byte vector
+// accesses, so every device pointer argument must be 16-byte aligned (cudaMalloc
+// and framework allocators return blocks aligned far beyond that; an offset
+// view into one may not be).  True if one of `ps` is not.
+bool misaligned16(std::initializer_list<const void *> ps) {
+  for (const void *p : ps)
+    if (((uintptr_t)p & 15u) != 0) return true;
+  return false;
+}
+constexpr const char *kAlignMsg = "device pointers must be 16-byte aligned";
 
 int fail(npsolve *h, int code, const char *fmt, ...) {
   char buf[512];
@@ -491,6 +510,7 @@ int upload_weights(npsolve *h) {
     h->kfix_host = kfix;
   }
   CK(h, cudaMemcpy(h->cw, cw.data(), cw.size() * sizeof(CConvW), cudaMemcpyHostToDevice));
+  h->cw_host = cw;
   CK(h, cudaMemcpy(h->aw, aw.data(), aw.size() * sizeof(AffW), cudaMemcpyHostToDevice));
   return NPSOLVE_OK;
 }
@@ -551,6 +571,12 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
   const int idx = lvl * 2 + (type - 1);
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
+  if (h->tr.kstore) {  // training forward: no input scale, no solve state
+    launch_cconv_store_K(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw_host[idx],
+                         h->kfix_host.data() + (size_t)idx * 81, (float)ldexp(1.0, 3 * (lvl - 1)), in, mask_input,
+                         h->cfg.precision == NPSOLVE_BF16 ? 1 : 0, h->tr.kslot[idx], out, s);
+    return;
+  }
   launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw + idx, in, vscale,
                    mask_input, h->cfg.precision == NPSOLVE_BF16 ? 1 : 0, out, st, s);
 }
@@ -967,6 +993,9 @@ void free_train(npsolve *h) {
   cudaFree(t.res);
   cudaFree(t.gz);
   cudaFree(t.K);
+  cudaFree(t.kall);
+  t.kall = nullptr;
+  t.kall_cap = 0;
   cudaFree(t.part);
   cudaFree(t.out);
   t.rm = t.tmp = t.tmp2 = t.res = t.gz = t.K = nullptr;
@@ -1018,13 +1047,35 @@ int train_forward(npsolve *h, const uint8_t *lab, Dims d1, const float *r, cudaS
     CK(h, cudaMalloc(&h->tr.badb, sizeof(unsigned int)));
     CK(h, cudaMemsetAsync(h->tr.badb, 0, sizeof(unsigned int), s));
   }
+  {
+    // room for the per-cell kernels of every CConv block
+    auto &t = h->tr;
+    const int L = h->cfg.levels;
+    long long need = 0;
+    for (int l = 1; l <= L; ++l) need += (l < L ? 2 : 1) * level_dims(d1, l).n() * 27;
+    if (need > t.kall_cap) {
+      cudaFree(t.kall);
+      t.kall = nullptr;
+      t.kall_cap = 0;
+      CK(h, dalloc(nullptr, &t.kall, (size_t)need));
+      t.kall_cap = need;
+    }
+    long long off = 0;
+    for (int l = 1; l <= L; ++l)
+      for (int ty = 0; ty < (l < L ? 2 : 1); ++ty) {
+        t.kslot[l * 2 + ty] = t.kall + off;
+        off += level_dims(d1, l).n() * 27;
+      }
+  }
   const int path = h->cfg.kernel_path;
   h->cfg.kernel_path = NPSOLVE_PATH_CUDA_CORE;
   st = setup_image(h, lab, d1, s, true);
   if (!st) {
     launch_or_flag(h->ws.bad, h->tr.badb, s);
     launch_mask_copy(lab, d1.n(), r, h->tr.rm, s);
+    h->tr.kstore = true;
     run_network(h, lab, d1, h->tr.rm, nullptr, h->ws.z, nullptr, s, true);
+    h->tr.kstore = false;
   }
   h->cfg.kernel_path = path;
   if (st) return st;
@@ -1096,21 +1147,19 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, dou
     CK(h, cudaMemcpyAsync(O(l) + 2 * kWGOut + 2, w.affs + 54 * l, 54 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     launch_axpby_dev(nullptr, nl, w.affc + 2 * l, t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);   // gx1 += c1 gx
     launch_axpby_dev(nullptr, nl, w.affc + 2 * l + 1, t.gx[l], 0.f, nullptr, t.tmp, s);     // g x2 = c2 gx
-    launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2 + 1, t.K, s);
     wgrad(l, dl, w.r2[l], t.tmp, O(l) + kWGOut);
-    launch_cconv_transpose(t.K, t.tmp, dl, t.tmp2, s);  // g r2
+    launch_cconv_transpose(t.kslot[l * 2 + 1], t.tmp, dl, t.tmp2, s);  // g r2 (the forward's kernels)
     launch_interp_adjoint_add(t.tmp2, level_dims(d1, l + 1), (l + 1 == L) ? t.gx1[L] : t.gx[l + 1], s);
-    h->launches += 11;
+    h->launches += 10;
   }
   // down pass in reverse: CConv1 and pooling
   for (int l = L; l >= 1; --l) {
     const Dims dl = level_dims(d1, l);
     const float *v = l == 1 ? t.rm : w.r1[l];
-    launch_materialize_K(ll(l), lc(l), dl, h->cw + l * 2, t.K, s);
     wgrad(l, dl, v, t.gx1[l], O(l));
-    h->launches += 3;
+    h->launches += 2;
     if (l > 1 || gr) {
-      launch_cconv_transpose(t.K, t.gx1[l], dl, t.tmp, s);  // g r1^l
+      launch_cconv_transpose(t.kslot[l * 2], t.gx1[l], dl, t.tmp, s);  // g r1^l
       h->launches += 1;
       if (l > 1) {
         launch_pool_adjoint_add(t.tmp, level_dims(d1, l - 1), t.gx1[l - 1], s);
@@ -1341,6 +1390,7 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
                double *x_host = nullptr) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!lab || !b || !x || !iters || !rel_residual) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({lab, b, x})) return fail(h, NPSOLVE_BAD_ARG, kAlignMsg);
   if (!(tol > 0.0) || !isfinite(tol)) return fail(h, NPSOLVE_BAD_ARG, "tolerance must be finite and > 0");
   if (max_iter < 0) return fail(h, NPSOLVE_BAD_ARG, "max_iter must be >= 0");
   int st = check_dims(h, nx, ny, nz);
@@ -1655,6 +1705,7 @@ int npsolve_network_intermediate(npsolve_t h, const uint8_t *labels, int nx, int
                                  int level, int which, float *out, double *c12_host, void *stream) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!labels || !r || !out) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, r, out})) return fail(h, NPSOLVE_BAD_ARG, kAlignMsg);
   const int L = h->cfg.levels;
   if (level < 0 || level > L || which < 0 || which > 4) return fail(h, NPSOLVE_BAD_ARG, "bad level/which");
   int st = check_dims(h, nx, ny, nz);
@@ -1720,6 +1771,7 @@ int npsolve_network_transpose(npsolve_t h, const uint8_t *labels, int nx, int ny
                               void *stream) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!labels || !g || !out) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, g, out})) return fail(h, NPSOLVE_BAD_ARG, kAlignMsg);
   cudaStream_t s = (cudaStream_t)stream;
   const Dims d1{nx, ny, nz};
   int st = symmetry_setup(h, labels, d1, s);
@@ -1734,6 +1786,7 @@ int npsolve_asymmetry(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz
                       void *stream, double *S, double *dots_host) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!labels || !x || !y || !S) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, x, y})) return fail(h, NPSOLVE_BAD_ARG, kAlignMsg);
   cudaStream_t s = (cudaStream_t)stream;
   const Dims d1{nx, ny, nz};
   int st = symmetry_setup(h, labels, d1, s);
@@ -1760,6 +1813,7 @@ int npsolve_asymmetry(npsolve_t h, const uint8_t *labels, int nx, int ny, int nz
 
 int npsolve_apply_laplacian(const uint8_t *labels, int nx, int ny, int nz, const float *d, float *q, void *stream) {
   if (!labels || !d || !q) return fail(nullptr, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, d, q})) return fail(nullptr, NPSOLVE_BAD_ARG, kAlignMsg);
   if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
     return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
   launch_lap(labels, Dims{nx, ny, nz}, d, q, (cudaStream_t)stream);
@@ -1771,6 +1825,7 @@ int npsolve_apply_laplacian(const uint8_t *labels, int nx, int ny, int nz, const
 int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const float *b, const double *x,
                           double *rel_residual, void *stream) {
   if (!labels || !b || !x || !rel_residual) return fail(nullptr, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, b, x})) return fail(nullptr, NPSOLVE_BAD_ARG, kAlignMsg);
   if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
     return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1789,6 +1844,7 @@ int npsolve_true_residual(const uint8_t *labels, int nx, int ny, int nz, const f
 int npsolve_jacobi_pcg(const uint8_t *labels, int nx, int ny, int nz, const float *b, double tol, int max_iter,
                        void *stream, double *x, int *iters, double *rel_residual) {
   if (!labels || !b || !x || !iters || !rel_residual) return fail(nullptr, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, b, x})) return fail(nullptr, NPSOLVE_BAD_ARG, kAlignMsg);
   if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
     return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
   if (!(tol > 0.0) || max_iter < 0) return fail(nullptr, NPSOLVE_BAD_ARG, "bad tol/max_iter");
@@ -1886,6 +1942,7 @@ int npsolve_network_vjp(npsolve_t h, const uint8_t *labels, int nx, int ny, int 
                         float *grad_w_host, float *grad_r, void *stream) {
   if (!h) return fail(nullptr, NPSOLVE_BAD_ARG, "null handle");
   if (!labels || !r || !gz || !grad_w_host) return fail(h, NPSOLVE_BAD_ARG, "null pointer argument");
+  if (misaligned16({labels, r, gz, grad_r})) return fail(h, NPSOLVE_BAD_ARG, kAlignMsg);
   CK(h, cudaSetDevice(h->device));
   cudaStream_t s = (cudaStream_t)stream;
   const Dims d1{nx, ny, nz};
@@ -1914,6 +1971,7 @@ int batch_loss_grad(npsolve *h, int batch, const uint8_t *const *labels, const i
   const size_t blk = (size_t)(kMaxLevels + 1) * kTrOutPerLevel;
   for (int i = 0; i < batch; ++i) {
     if (!labels[i] || !b[i]) return fail(h, NPSOLVE_BAD_ARG, "null example pointer");
+    if (misaligned16({labels[i], b[i]})) return fail(h, NPSOLVE_BAD_ARG, kAlignMsg);
     st = loss_grad_enqueue(h, labels[i], Dims{dims[3 * i], dims[3 * i + 1], dims[3 * i + 2]}, b[i], weight,
                            h->tr.outb + (size_t)i * blk, s);
     if (st) return st;
@@ -2036,6 +2094,7 @@ int npsolve_lanczos_rhs(const uint8_t *labels, int nx, int ny, int nz, const flo
                         unsigned long long seed, float *out, double *ritz_values_host, void *stream) {
   if (!labels || !start || !out || m < 2 || m > kMaxLanczos || k < 1 || k > m || count < 0)
     return fail(nullptr, NPSOLVE_BAD_ARG, "bad argument");
+  if (misaligned16({labels, start, out})) return fail(nullptr, NPSOLVE_BAD_ARG, kAlignMsg);
   if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > (1LL << 31) - 1)
     return fail(nullptr, NPSOLVE_BAD_DIMS, "bad dims");
   cudaStream_t s = (cudaStream_t)stream;

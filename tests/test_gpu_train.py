@@ -1,8 +1,10 @@
 """The hand-written backward (reverse of Alg. 2) and the training loss of
 Sec. 4.2.3 on the GPU against the FP64 oracle and finite differences.
 
-Tolerances: the GPU backward accumulates FP32 products per 32-cell batch and
-FP64 across blocks; for a 16^3 grid each weight-gradient entry is a sum of
+Tolerances: the GPU backward accumulates the weight gradient in FP32 (on the
+tensor cores for levels 1-3: the kernel gradient as three BF16 terms, exact
+features, FP32 accumulation per CTA; FP32 CUDA-core batches beyond) and in
+FP64 across CTAs; for a 16^3 grid each weight-gradient entry is a sum of
 O(10^4) products, so its rounding error is ~sqrt(10^4) eps32 ~ 1e-5 of the sum
 of magnitudes.  Norm-wise relative error <= 1e-4 and element-wise
 <= 1e-4 * max|g| against the FP64 oracle gradient.  The finite-difference
@@ -37,7 +39,11 @@ def _rng_labels(shape, seed, p=(0.2, 0.6, 0.2)):
     return rng.choice(np.array([0, 1, 2], np.uint8), size=shape, p=p)
 
 
-@pytest.mark.parametrize("shape,L", [((16, 16, 16), 4), ((8, 16, 24), 3), ((8, 8, 8), 1), ((16, 8, 16), 2)])
+# (nz, ny, nx): rows of a multiple of 8 cells take the 8-cell-run operand
+# staging of the tensor-core weight gradient, others the per-cell one; the
+# last two span tens of 128-cell chunks, 10 x 22 x 24 with a partial last one
+@pytest.mark.parametrize("shape,L", [((16, 16, 16), 4), ((8, 16, 24), 3), ((8, 8, 8), 1), ((16, 8, 16), 2),
+                                     ((10, 22, 24), 2), ((16, 24, 40), 3)])
 def test_network_vjp_matches_oracle_backward(shape, L):
     b = _b()
     lab = _rng_labels(shape, 61) if shape != (16, 16, 16) else synth.pool_scene(16, 62)
@@ -51,6 +57,32 @@ def test_network_vjp_matches_oracle_backward(shape, L):
     assert _rel(gw, ogw) <= 1e-4
     assert np.abs(gw - ogw).max() <= 1e-4 * np.abs(ogw).max()
     assert _rel(gr.cpu().numpy(), ogr) <= 1e-5
+    s.close()
+
+
+def test_misaligned_device_pointers_are_rejected():
+    """The kernels use 8- and 16-byte vector accesses: an offset view is
+    refused at the boundary, before anything is launched on it."""
+    b = _b()
+    shape = (8, 8, 8)
+    lab = synth.pool_scene(8, 62)
+    n = lab.size
+    big = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+    big[1:n + 1] = _dev(lab.ravel(), torch.uint8)
+    lab_off = big[1:n + 1].view(shape)
+    assert lab_off.data_ptr() % 16 == 1 and lab_off.is_contiguous()
+    rng = np.random.default_rng(5)
+    r = _dev(rng.standard_normal(shape), torch.float32)
+    s = b.Solver(synth.init_weights(2, 7).astype(np.float32), levels=2)
+    with pytest.raises(b.NpsolveError, match="16-byte aligned"):
+        s.solve(lab_off, r, 1e-6, 10)
+    with pytest.raises(b.NpsolveError, match="16-byte aligned"):
+        s.network_vjp(lab_off, r, r)
+    with pytest.raises(b.NpsolveError, match="16-byte aligned"):
+        s.train_step([lab_off], [r], lr=1e-3)
+    # the handle still works with aligned arguments
+    _, it, rr, st = s.solve(_dev(lab, torch.uint8), r, 1e-6, 200)
+    assert st == b.OK and rr < 1e-6
     s.close()
 
 
