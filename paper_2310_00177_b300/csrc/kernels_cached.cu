@@ -214,86 +214,96 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // fluid or all pure air (solid outside the grid): with one class bit per cell
 // (1 pure solid, 2 pure fluid, 4 pure air, 8 anything else) that is a window
 // OR of 1, 2 or 4.  The OR is separable: along x by lane shuffles (the two
-// halo columns loaded by the edge lanes), along y through shared memory (the
-// two halo rows by the edge warps), along z by keeping the last two planes'
-// 3x3 ORs in registers, so each cell's class is loaded about 1.3 times per
-// plane instead of 27 times.
+// halo columns loaded by the edge lanes), along y through shared memory, along
+// z by keeping the last two planes' 3x3 ORs in registers, so each cell's class
+// is loaded about 1.3 times instead of 27 times.  Ten warps, one per row
+// y0-1 .. y0+8 (the two halo rows included, so that every warp loads one row
+// per plane), and each thread's loads for the next plane are issued before
+// the current plane's barrier.
 // ---------------------------------------------------------------------------
+// The class bit of a cell, and bit 4 set if it holds fluid (level 1: its
+// label; coarser levels: a non-zero fluid count).
 __device__ __forceinline__ uint32_t class_bit(const uint8_t *lab, const ushort2 *counts, const Dims &d, int x, int y,
                                               int z, uint32_t kF, uint32_t kA) {
   if ((unsigned)x >= (unsigned)d.nx || (unsigned)y >= (unsigned)d.ny || (unsigned)z >= (unsigned)d.nz) return 1u;
   const uint32_t p = ((uint32_t)z * (uint32_t)d.ny + (uint32_t)y) * (uint32_t)d.nx + (uint32_t)x;  // n < 2^31
   if (lab) {
     const uint8_t l = __ldg(lab + p);
-    return l == kFluid ? 2u : (l == kAir ? 4u : 1u);  // level 1: every cell is pure
+    return l == kFluid ? 2u | 16u : (l == kAir ? 4u : 1u);  // level 1: every cell is pure
   }
   const ushort2 c = counts[p];
   const uint32_t k = (uint32_t)c.x | ((uint32_t)c.y << 16);
-  return k == 0u ? 1u : (k == kF ? 2u : (k == kA ? 4u : 8u));
+  const uint32_t b = k == 0u ? 1u : (k == kF ? 2u : (k == kA ? 4u : 8u));
+  return b | (c.x > 0 ? 16u : 0u);
 }
 
-__global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
-                                                 Dims d, uint32_t full, int zcc, PlaneDesc *__restrict__ desc,
-                                                 unsigned *__restrict__ totals, uint8_t *__restrict__ skip,
-                                                 uint16_t *__restrict__ mcount) {
+constexpr int CLW = TY + 2;    // classification warps: rows y0-1 .. y0+8
+constexpr int CLT = CLW * 32;  // classification threads
+
+__global__ void __launch_bounds__(CLT) k_classify(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                                  Dims d, uint32_t full, int zcc, PlaneDesc *__restrict__ desc,
+                                                  unsigned *__restrict__ totals, uint8_t *__restrict__ skip,
+                                                  uint16_t *__restrict__ mcount) {
   __shared__ uint32_t sd[ZCG][DWORDS];
-  __shared__ uint8_t rows[2][TY + 2][TX];  // x-ORed class bits of rows y0-1 .. y0+8 of one plane, two buffers
+  __shared__ uint8_t rows[2][CLW][TX];  // x-ORed class bits of rows y0-1 .. y0+8 of one plane, two buffers
   __shared__ uint32_t sbase;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntx = (d.nx + TX - 1) / TX, nty = (d.ny + TY - 1) / TY, nch = (d.nz + zcc - 1) / zcc;
   const int ntiles = ntx * nty;
   const long long units = (long long)ntiles * nch;
   const uint32_t kF = full, kA = full << 16;
+  const bool interior = warp >= 1 && warp <= TY;  // rows y0 .. y0+7: the tile's cells
   for (long long u = blockIdx.x; u < units; u += gridDim.x) {
     const int t = (int)(u % ntiles), c = (int)(u / ntiles);
     const int x0 = (t % ntx) * TX, y0 = (t / ntx) * TY;
-    const int x = x0 + lane, y = y0 + warp;
+    const int x = x0 + lane, y = y0 + warp - 1;  // this warp's row
     const int zs = c * zcc, nzu = min(zcc, d.nz - zs);
-    const bool inside = x < d.nx && y < d.ny;
-    uint32_t own = 0u;  // this thread's class bit in the plane of the last row_or(y, .)
-    // the OR of row yy's class bits over x-1 .. x+1 (plane z)
-    auto row_or = [&](int yy, int z) -> uint32_t {
-      const uint32_t b = class_bit(lab, counts, d, x, yy, z, kF, kA);
-      if (yy == y) own = b;
+    const bool inside = interior && x < d.nx && y < d.ny;
+    // the raw bits of this thread's column and (lanes 0 and 31) of its halo column in plane z
+    auto load_row = [&](int z, uint32_t &b, uint32_t &e) {
+      b = class_bit(lab, counts, d, x, y, z, kF, kA);
+      e = 1u;
+      if (lane == 0) e = class_bit(lab, counts, d, x - 1, y, z, kF, kA);
+      else if (lane == 31) e = class_bit(lab, counts, d, x + 1, y, z, kF, kA);
+    };
+    uint32_t bn, en;
+    load_row(zs - 1, bn, en);
+    uint32_t pm = 0u, p0 = 0u, own = 0u;  // 3x3 ORs of planes z-2, z-1; class bits of this cell in plane z-1
+    for (int st = 0; st < nzu + 2; ++st) {  // plane zs - 1 + st
+      const uint32_t b = bn, e = en;
+      if (st + 1 < nzu + 2) load_row(zs + st, bn, en);  // the next plane, in flight across the barrier
       uint32_t left = __shfl_up_sync(0xffffffffu, b, 1), right = __shfl_down_sync(0xffffffffu, b, 1);
-      if (lane == 0) left = class_bit(lab, counts, d, x - 1, yy, z, kF, kA);
-      if (lane == 31) right = class_bit(lab, counts, d, x + 1, yy, z, kF, kA);
-      return b | left | right;
-    };
-    // the OR over the 3 x 3 (x, y) neighbourhood of this thread's cell in plane z
-    // (one barrier per plane: the two buffers alternate between calls)
-    auto plane = [&](int z, int buf) -> uint32_t {
-      rows[buf][warp + 1][lane] = (uint8_t)row_or(y, z);
-      if (warp == 0) rows[buf][0][lane] = (uint8_t)row_or(y0 - 1, z);
-      if (warp == TY - 1) rows[buf][TY + 1][lane] = (uint8_t)row_or(y0 + TY, z);
+      if (lane == 0) left = e;
+      if (lane == 31) right = e;
+      const int buf = st & 1;
+      rows[buf][warp][lane] = (uint8_t)((b | left | right) & 15u);
       __syncthreads();
-      return (uint32_t)(rows[buf][warp][lane] | rows[buf][warp + 1][lane] | rows[buf][warp + 2][lane]);
-    };
-    uint32_t pm = plane(zs - 1, 0), p0 = plane(zs, 1);
-    for (int j = 0; j < nzu; ++j) {
-      const uint32_t o0 = own;  // class bit of this thread's cell in plane z
-      const uint32_t pp = plane(zs + j + 1, j & 1);
-      const uint32_t wor = pm | p0 | pp;
-      const bool pure = wor == 1u || wor == 2u || wor == 4u;
-      const bool mixed = inside && !pure, fl = inside && wor == 2u, ai = inside && wor == 4u;
-      // the cell holds fluid: level 1 its label, coarser levels a non-zero fluid count
-      const bool self = inside && (lab != nullptr ? o0 == 2u
-                                                  : (o0 == 2u || (o0 == 8u && counts[((size_t)(zs + j) * d.ny + y) *
-                                                                                       d.nx + x].x > 0)));
-      const uint32_t bm = __ballot_sync(0xffffffffu, mixed), bf = __ballot_sync(0xffffffffu, fl);
-      const uint32_t ba = __ballot_sync(0xffffffffu, ai), bs = __ballot_sync(0xffffffffu, self);
-      if (lane == 0) {
-        sd[j][4 * warp] = bm;
-        sd[j][4 * warp + 1] = bf;
-        sd[j][4 * warp + 2] = ba;
-        sd[j][4 * warp + 3] = bs;
+      if (interior) {
+        const uint32_t pp = (uint32_t)(rows[buf][warp - 1][lane] | rows[buf][warp][lane] | rows[buf][warp + 1][lane]);
+        if (st >= 2) {
+          const int j = st - 2;  // plane zs + j: window OR over planes zs+j-1 .. zs+j+1
+          const uint32_t wor = pm | p0 | pp;
+          const bool pure = wor == 1u || wor == 2u || wor == 4u;
+          const bool mixed = inside && !pure, fl = inside && wor == 2u, ai = inside && wor == 4u;
+          const bool self = inside && (own & 16u) != 0u;  // the cell holds fluid
+          const uint32_t bm = __ballot_sync(0xffffffffu, mixed), bf = __ballot_sync(0xffffffffu, fl);
+          const uint32_t ba = __ballot_sync(0xffffffffu, ai), bs = __ballot_sync(0xffffffffu, self);
+          if (lane == 0) {
+            const int w = warp - 1;
+            sd[j][4 * w] = bm;
+            sd[j][4 * w + 1] = bf;
+            sd[j][4 * w + 2] = ba;
+            sd[j][4 * w + 3] = bs;
+          }
+        }
+        pm = p0;
+        p0 = pp;
       }
-      pm = p0;
-      p0 = pp;
+      own = b;
     }
     __syncthreads();
     // per plane (one thread each): mixed count, block size, row ranks, patch classes
-    for (int j = threadIdx.x; j < nzu; j += NT) {
+    for (int j = threadIdx.x; j < nzu; j += CLT) {
       uint32_t m = 0, rb[2] = {0u, 0u};
       for (int w = 0; w < TY; ++w) {
         rb[w >> 2] |= m << (8 * (w & 3));
@@ -338,7 +348,7 @@ __global__ void __launch_bounds__(NT) k_classify(const uint8_t *__restrict__ lab
     }
     __syncthreads();
     uint32_t *dst = (uint32_t *)(desc + (size_t)t * d.nz + zs);
-    for (int i = threadIdx.x; i < nzu * DWORDS; i += NT) {
+    for (int i = threadIdx.x; i < nzu * DWORDS; i += CLT) {
       uint32_t v = sd[i / DWORDS][i % DWORDS];
       if (i % DWORDS == 4 * TY) v += sbase;
       dst[i] = v;
@@ -452,6 +462,14 @@ __device__ __forceinline__ uint32_t image_code_bf16(const uint8_t *lab, const us
 
 constexpr int kGenTmemCols = 64;  // A: columns [0, 32), D: [32, 64)
 constexpr int GT = 128;           // threads of the tensor-core generator: one per TMEM lane / MMA row
+constexpr int kWinRow = TX + 2, kWinPlane = (TY + 2) * kWinRow;  // the label window of a unit (level 1)
+constexpr int kWinBytes = ((ZCG + 2) * kWinPlane + 15) & ~15;
+// dynamic shared memory of the generator: W splits of both blocks, the unit's
+// plane descriptors, its cache-entry map and label window (+ alignment slack)
+template <int NSPLIT>
+constexpr int gen_smem_bytes() {
+  return 2 * NSPLIT * umma::kBBytes + ZCG * (int)sizeof(PlaneDesc) + ZCG * NT * 2 + kWinBytes + 1024;
+}
 
 template <int NSPLIT, bool BF16>
 __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
@@ -461,12 +479,15 @@ __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ 
                                                     uint32_t *__restrict__ cache1, int zcc, int *err) {
   using namespace umma;
   constexpr int KW = BF16 ? 14 : 27;
-  __shared__ __align__(1024) uint8_t sW[2][NSPLIT * kBBytes];
-  __shared__ PlaneDesc sd[ZCG];
-  __shared__ uint16_t cell_of[ZCG * NT];  // unit-local cache entry -> plane << 8 | cell (0xFFFF: padding)
+  extern __shared__ uint8_t gen_raw[];
+  uint8_t *gsm = (uint8_t *)(((uintptr_t)gen_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t(*sW)[NSPLIT * kBBytes] = reinterpret_cast<uint8_t(*)[NSPLIT * kBBytes]>(gsm);
+  PlaneDesc *sd = (PlaneDesc *)(gsm + 2 * NSPLIT * kBBytes);
+  uint16_t *cell_of = (uint16_t *)(sd + ZCG);  // unit-local cache entry -> plane << 8 | cell (0xFFFF: padding)
+  uint8_t *win = (uint8_t *)(cell_of + ZCG * NT);  // level 1: labels of planes zs-1 .., rows y0-1 .., x0-1 ..
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t s_tmem;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   {
     const uint4 *src0 = (const uint4 *)w0;
     const uint4 *src1 = (const uint4 *)w1;
@@ -510,6 +531,35 @@ __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ 
     const uint32_t base = sd[0].off;
     const int total = (int)(sd[nzu - 1].off + sd[nzu - 1].cpad - base);  // entries of the unit, padding included
     if (total > 0) {
+      if (lab) {
+        // the unit's label window (solid outside the grid): a warp takes rows warp, warp + 4, ...; lane c loads
+        // column c and lanes 0, 1 also columns 32, 33; eight rows' loads are in flight before their stores
+        constexpr int kNW = GT / 32, kBatch = 8;
+        const int nrows = (nzu + 2) * (TY + 2);
+        for (int r0 = warp; r0 < nrows; r0 += kBatch * kNW) {
+          uint32_t v0[kBatch], v1[kBatch];
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            const int rr = r0 + k * kNW;
+            v0[k] = v1[k] = (uint32_t)kSolid;
+            const int gz = zs - 1 + rr / (TY + 2), gy = y0 - 1 + rr % (TY + 2);
+            if (rr < nrows && gz >= 0 && gz < d.nz && gy >= 0 && gy < d.ny) {
+              const long long rb = ((long long)gz * d.ny + gy) * d.nx;
+              const int gx = x0 - 1 + lane, gx2 = x0 + 31 + lane;
+              if (gx >= 0 && gx < d.nx) v0[k] = __ldg(lab + rb + gx);
+              if (lane < 2 && gx2 < d.nx) v1[k] = __ldg(lab + rb + gx2);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < kBatch; ++k) {
+            const int rr = r0 + k * kNW;
+            if (rr < nrows) {
+              win[rr * kWinRow + lane] = (uint8_t)v0[k];
+              if (lane < 2) win[rr * kWinRow + 32 + lane] = (uint8_t)v1[k];
+            }
+          }
+        }
+      }
       for (int i = tid; i < total; i += GT) cell_of[i] = 0xFFFFu;
       __syncthreads();
       for (int j = 0; j < nzu; ++j) {
@@ -533,11 +583,20 @@ __global__ void __launch_bounds__(GT) k_generate_tc(const uint8_t *__restrict__ 
           j = (int)(e >> 8);
           const int cell = (int)(e & 255u);
           const int x = x0 + (cell & 31), y = y0 + (cell >> 5), z = zs + j;
-          uint32_t win[27];
+          uint32_t wc[27];
+          if (lab) {
+            const uint8_t *w0p = win + (j + 1) * kWinPlane + ((cell >> 5) + 1) * kWinRow + (cell & 31) + 1;
 #pragma unroll
-          for (int l = 0; l < 27; ++l)
-            win[l] = image_code_bf16(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
-          build_feature_words(win, fw);
+            for (int l = 0; l < 27; ++l) {
+              const uint8_t lb = w0p[(l / 9 - 1) * kWinPlane + ((l / 3) % 3 - 1) * kWinRow + (l % 3 - 1)];
+              wc[l] = lb == kFluid ? 0x00003F80u : (lb == kAir ? 0x3F800000u : 0u);
+            }
+          } else {
+#pragma unroll
+            for (int l = 0; l < 27; ++l)
+              wc[l] = image_code_bf16(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
+          }
+          build_feature_words(wc, fw);
         } else {
 #pragma unroll
           for (int q = 0; q < 32; ++q) fw[q] = 0u;
@@ -1465,8 +1524,8 @@ void launch_classify(const uint8_t *lab, const ushort2 *counts, Dims d, uint32_t
                      uint8_t *skip, uint16_t *mcount, int num_sms, cudaStream_t s) {
   const int zc = setup_chunk(d, num_sms);
   const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
-  k_classify<<<grid_for_units(units, num_sms * 8), NT, 0, s>>>(lab, counts, d, full, zc, (PlaneDesc *)desc, totals,
-                                                                 skip, mcount);
+  k_classify<<<grid_for_units(units, num_sms * 8), CLT, 0, s>>>(lab, counts, d, full, zc, (PlaneDesc *)desc, totals,
+                                                                  skip, mcount);
 }
 
 void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW *w, int nblk,
@@ -1476,16 +1535,26 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
   if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3); units within the classification's
     const int zc = setup_chunk(d, num_sms);
     const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
-    const int g = grid_for_units(units, num_sms * 7);  // 7 CTAs per SM: 448 of the 512 TMEM columns
+    // 5 (BF16 form) or 3 CTAs per SM by shared memory, 64 TMEM columns each
+    const int g = grid_for_units(units, num_sms * (nsplit == 1 ? 5 : 3));
+    static int configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !configured[dev]) {
+      cudaFuncSetAttribute(k_generate_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes<1>());
+      cudaFuncSetAttribute(k_generate_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes<3>());
+      cudaFuncSetAttribute(k_generate_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes<3>());
+      configured[dev] = 1;
+    }
     if (nsplit == 1)
-      k_generate_tc<1, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
-                                              (uint32_t *)cache1, zc, err);
+      k_generate_tc<1, true><<<g, GT, gen_smem_bytes<1>(), s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd,
+                                                                (uint32_t *)cache0, (uint32_t *)cache1, zc, err);
     else if (bf16)
-      k_generate_tc<3, true><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
-                                              (uint32_t *)cache1, zc, err);
+      k_generate_tc<3, true><<<g, GT, gen_smem_bytes<3>(), s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd,
+                                                                (uint32_t *)cache0, (uint32_t *)cache1, zc, err);
     else
-      k_generate_tc<3, false><<<g, GT, 0, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
-                                               (uint32_t *)cache1, zc, err);
+      k_generate_tc<3, false><<<g, GT, gen_smem_bytes<3>(), s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd,
+                                                                 (uint32_t *)cache0, (uint32_t *)cache1, zc, err);
     return;
   }
   const int g = grid_for_units((long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * d.nz, num_sms * 8);
