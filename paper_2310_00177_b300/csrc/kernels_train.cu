@@ -113,6 +113,80 @@ __device__ __forceinline__ void window_cell(const uint8_t *lab, const ushort2 *c
   if (mask_input && f == 0.f) val = 0.f;  // level 1: f == 1 exactly on fluid
 }
 
+// The window (features and input) of the 32 cells x0 .. x0+31 of one grid row,
+// lane i holding cell x0+i's: each of the nine window rows is loaded once,
+// coalesced, the x-1 and x+1 taps taken from the neighbouring lanes (lanes 0
+// and 31 load the halo columns).
+__device__ __forceinline__ void window_rows(const uint8_t *lab, const ushort2 *counts, const float *v, const Dims &d,
+                                            int mask_input, long long p0, int lane, float (&nf)[27], float (&na)[27],
+                                            float (&vv)[27]) {
+  int x0, y, z;
+  cell_xyz(p0, d, x0, y, z);
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {  // window row dy = r % 3 - 1, dz = r / 3 - 1
+    const int yy = y + r % 3 - 1, zz = z + r / 3 - 1;
+    float cf = 0.f, ca = 0.f, cv = 0.f, hf = 0.f, ha = 0.f, hv = 0.f;
+    if (yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz) {  // the same for the whole warp
+      const long long rb = ((long long)zz * d.ny + yy) * d.nx;
+      window_cell(lab, counts, v, rb + x0 + lane, mask_input, cf, ca, cv);
+      const int hx = lane == 0 ? x0 - 1 : x0 + 32;  // the halo columns, read by lanes 0 and 31
+      if ((lane == 0 || lane == 31) && hx >= 0 && hx < d.nx)
+        window_cell(lab, counts, v, rb + hx, mask_input, hf, ha, hv);
+    }
+    float lf = __shfl_up_sync(0xffffffffu, cf, 1), la = __shfl_up_sync(0xffffffffu, ca, 1);
+    float lv = __shfl_up_sync(0xffffffffu, cv, 1);
+    float rf = __shfl_down_sync(0xffffffffu, cf, 1), ra = __shfl_down_sync(0xffffffffu, ca, 1);
+    float rv = __shfl_down_sync(0xffffffffu, cv, 1);
+    if (lane == 0) {
+      lf = hf;
+      la = ha;
+      lv = hv;
+    }
+    if (lane == 31) {
+      rf = hf;
+      ra = ha;
+      rv = hv;
+    }
+    nf[3 * r] = lf;
+    na[3 * r] = la;
+    vv[3 * r] = lv;
+    nf[3 * r + 1] = cf;
+    na[3 * r + 1] = ca;
+    vv[3 * r + 1] = cv;
+    nf[3 * r + 2] = rf;
+    na[3 * r + 2] = ra;
+    vv[3 * r + 2] = rv;
+  }
+}
+
+// 0 pure solid, 1 pure fluid, 2 pure air, -1 anything else (a cell of a pure
+// class has count `full` of it: 1 at level 1, 8^(l-1) at level l).
+__device__ __forceinline__ int window_class(const float (&nf)[27], const float (&na)[27], float full) {
+  bool all_s = true, all_f = true, all_a = true;
+#pragma unroll
+  for (int t = 0; t < 27; ++t) {
+    all_s &= nf[t] == 0.f && na[t] == 0.f;
+    all_f &= nf[t] == full;
+    all_a &= na[t] == full;
+  }
+  return all_f ? 1 : (all_a ? 2 : (all_s ? 0 : -1));
+}
+
+__device__ __forceinline__ float pure_k(const PureK &pk, int c, int a) {
+  return c == 1 ? pk.k[1][a] : (c == 2 ? pk.k[2][a] : pk.k[0][a]);
+}
+
+// A warp's 32 x 27 kernels (staged in shared memory at stride 27, odd: no bank
+// conflicts) out to K as contiguous stores.
+__device__ __forceinline__ void store_tile_K(const float *sk, long long wt, long long n, int lane, float *K) {
+  __syncwarp();
+  const long long lim = (n - wt * 32) * 27;  // floats of this tile inside the grid
+  float *dst = K + wt * 32 * 27;
+  for (int i = lane; i < 32 * 27; i += 32)
+    if (i < lim) dst[i] = sk[i];
+  __syncwarp();
+}
+
 template <bool RK, bool ROWS>
 __global__ void __launch_bounds__(kSKWarps * 32) k_cconv_store_K(const uint8_t *__restrict__ lab,
                                                                  const ushort2 *__restrict__ counts, Dims d,
@@ -129,43 +203,7 @@ __global__ void __launch_bounds__(kSKWarps * 32) k_cconv_store_K(const uint8_t *
     const bool act = p < n;
     float nf[27], na[27], vv[27];
     if (ROWS) {  // n is a multiple of 32: every lane is active
-      int x0, y, z;
-      cell_xyz(wt * 32, d, x0, y, z);
-#pragma unroll
-      for (int r = 0; r < 9; ++r) {  // window row dy = r % 3 - 1, dz = r / 3 - 1
-        const int yy = y + r % 3 - 1, zz = z + r / 3 - 1;
-        float cf = 0.f, ca = 0.f, cv = 0.f, hf = 0.f, ha = 0.f, hv = 0.f;
-        if (yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz) {  // the same for the whole warp
-          const long long rb = ((long long)zz * d.ny + yy) * d.nx;
-          window_cell(lab, counts, v, rb + x0 + lane, mask_input, cf, ca, cv);
-          const int hx = lane == 0 ? x0 - 1 : x0 + 32;  // the halo columns, read by lanes 0 and 31
-          if ((lane == 0 || lane == 31) && hx >= 0 && hx < d.nx)
-            window_cell(lab, counts, v, rb + hx, mask_input, hf, ha, hv);
-        }
-        float lf = __shfl_up_sync(0xffffffffu, cf, 1), la = __shfl_up_sync(0xffffffffu, ca, 1);
-        float lv = __shfl_up_sync(0xffffffffu, cv, 1);
-        float rf = __shfl_down_sync(0xffffffffu, cf, 1), ra = __shfl_down_sync(0xffffffffu, ca, 1);
-        float rv = __shfl_down_sync(0xffffffffu, cv, 1);
-        if (lane == 0) {
-          lf = hf;
-          la = ha;
-          lv = hv;
-        }
-        if (lane == 31) {
-          rf = hf;
-          ra = ha;
-          rv = hv;
-        }
-        nf[3 * r] = lf;
-        na[3 * r] = la;
-        vv[3 * r] = lv;
-        nf[3 * r + 1] = cf;
-        na[3 * r + 1] = ca;
-        vv[3 * r + 1] = cv;
-        nf[3 * r + 2] = rf;
-        na[3 * r + 2] = ra;
-        vv[3 * r + 2] = rv;
-      }
+      window_rows(lab, counts, v, d, mask_input, wt * 32, lane, nf, na, vv);
     } else if (act) {
       int x, y, z;
       cell_xyz(p, d, x, y, z);
@@ -178,25 +216,17 @@ __global__ void __launch_bounds__(kSKWarps * 32) k_cconv_store_K(const uint8_t *
       }
     } else {
 #pragma unroll
-      for (int t = 0; t < 27; ++t) nf[t] = na[t] = vv[t] = 0.f;
+      for (int t = 0; t < 27; ++t) nf[t] = na[t] = vv[t] = 0.f;  // lanes past the end: solid
     }
-    // 0 pure solid, 1 pure fluid, 2 pure air, -1 mixed (lanes past the end: solid)
-    bool all_s = true, all_f = true, all_a = true;
-#pragma unroll
-    for (int t = 0; t < 27; ++t) {
-      all_s &= nf[t] == 0.f && na[t] == 0.f;
-      all_f &= nf[t] == full;
-      all_a &= na[t] == full;
-    }
-    const int cls = all_f ? 1 : (all_a ? 2 : (all_s ? 0 : -1));
+    const int cls = window_class(nf, na, full);
     const int c = cls < 0 ? 0 : cls;
     float acc = 0.f;
     if (__all_sync(0xffffffffu, cls >= 0)) {
 #pragma unroll
       for (int a = 0; a < 27; ++a) {
-        const float k = c == 1 ? pk.k[1][a] : (c == 2 ? pk.k[2][a] : pk.k[0][a]);
+        const float k = pure_k(pk, c, a);
         acc = fmaf(k, vv[a], acc);
-        sk[warp][lane * 27 + a] = k;  // stride 27 (odd): no bank conflicts
+        sk[warp][lane * 27 + a] = k;
       }
     } else {
 #pragma unroll
@@ -205,19 +235,133 @@ __global__ void __launch_bounds__(kSKWarps * 32) k_cconv_store_K(const uint8_t *
 #pragma unroll
         for (int l = 0; l < 27; ++l) k = fmaf(w.wf[a][l], nf[l], fmaf(w.wa[a][l], na[l], k));
         if (RK) k = __bfloat162float(__float2bfloat16_rn(k));
-        if (cls >= 0) k = c == 1 ? pk.k[1][a] : (c == 2 ? pk.k[2][a] : pk.k[0][a]);
+        if (cls >= 0) k = pure_k(pk, c, a);
         acc = fmaf(k, vv[a], acc);
         sk[warp][lane * 27 + a] = k;
       }
     }
     if (act) out[p] = acc;
-    __syncwarp();
-    const long long lim = (n - wt * 32) * 27;  // floats of this tile inside the grid
-    float *dst = K + wt * 32 * 27;
-    for (int i = lane; i < 32 * 27; i += 32)
-      if (i < lim) dst[i] = sk[warp][i];
-    __syncwarp();
+    store_tile_K(sk[warp], wt, n, lane, K);
   }
+}
+
+// The same block on the tcgen05 tensor cores, for levels whose image counts
+// are exact in BF16 (at most 256 fine cells per cell) and rows of a multiple
+// of 32 cells.  A CTA takes 128 cells (four 32-cell row runs, one per warp,
+// loaded as in window_rows); each thread writes its cell's 64 BF16 features
+// (the exact counts, the bias 1) into TMEM as the MMA's A rows, one thread
+// issues the contraction with the folded weights split into `nsplit` BF16
+// terms (K-major in shared memory, the solve's kernel-generation layout), and
+// the FP32 result comes back per cell from TMEM: the kernels of windows that
+// are not pure, the same values as the solve's tensor-core generation.  Pure
+// windows take their class kernel; BF16 rounding (RK), the output sum and the
+// stores are those of k_cconv_store_K.  A timed-out MMA wait sets *err.
+constexpr int kSTCells = 128;
+template <bool RK>
+__global__ void __launch_bounds__(kSTCells) k_cconv_store_K_tc(const uint8_t *__restrict__ lab,
+                                                               const ushort2 *__restrict__ counts, Dims d,
+                                                               const uint8_t *__restrict__ wsplit, int nsplit,
+                                                               const __grid_constant__ PureK pk, float full,
+                                                               const float *__restrict__ v, int mask_input,
+                                                               float *__restrict__ K, float *__restrict__ out,
+                                                               int *err) {
+  using namespace umma;
+  __shared__ __align__(1024) uint8_t sW[3 * kBBytes];
+  __shared__ float sk[kSTCells / 32][32 * 27];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < nsplit * kBBytes / 16; i += kSTCells) ((uint4 *)sW)[i] = ((const uint4 *)wsplit)[i];
+  if (warp == 0) {
+    tmem_alloc(&s_tmem, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_mbar_init();
+  }
+  fence_proxy_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t idesc = idesc_bf16(kTileM, kN);
+  const long long n = d.n();  // a multiple of 32
+  const long long nch = (n + kSTCells - 1) / kSTCells;
+  uint32_t phase = 0u;
+  bool aborted = false, issued = false;
+  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long long wt = ch * (kSTCells / 32) + warp;  // this warp's 32-cell run
+    const long long p = wt * 32 + lane;
+    const bool act = wt * 32 < n;
+    float nf[27], na[27], vv[27];
+    uint32_t fw[32];
+    int cls = 0;
+    if (act) {
+      window_rows(lab, counts, v, d, mask_input, wt * 32, lane, nf, na, vv);
+      cls = window_class(nf, na, full);
+      uint32_t wc[27];
+#pragma unroll
+      for (int l = 0; l < 27; ++l)
+        wc[l] = bf16_bits_small((unsigned)nf[l]) | (bf16_bits_small((unsigned)na[l]) << 16);
+      build_feature_words(wc, fw);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 27; ++t) nf[t] = na[t] = vv[t] = 0.f;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) fw[q] = 0u;
+    }
+    tmem_st32(tmem + lane_off, fw);
+    tmem_wait_st();
+    fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      for (int sp = 0; sp < nsplit; ++sp)
+#pragma unroll
+        for (int kk = 0; kk < kK / 16; ++kk) {
+          const uint64_t bd = smem_desc_kmajor(smem_u32(sW + sp * kBBytes + kk * 2 * kLBO), kLBO, kSBO);
+          mma_bf16_ts(tmem + 32, tmem + kk * 8, bd, idesc, (sp | kk) != 0);
+        }
+      umma_commit(&mbar);
+    }
+    issued = true;
+    const bool ok = mbar_wait_bounded(&mbar, phase, kWaitNs);
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
+    phase ^= 1u;
+    issued = false;
+    fence_after_sync();
+    uint32_t kr[32];
+    tmem_ld32(tmem + 32 + lane_off, kr);
+    tmem_wait_ld();
+    const int c = cls < 0 ? 0 : cls;
+    float acc = 0.f;
+#pragma unroll
+    for (int a = 0; a < 27; ++a) {
+      float k = __uint_as_float(kr[a]);
+      if (RK) k = __bfloat162float(__float2bfloat16_rn(k));
+      if (cls >= 0) k = pure_k(pk, c, a);
+      acc = fmaf(k, vv[a], acc);
+      sk[warp][lane * 27 + a] = k;
+    }
+    if (act) {
+      out[p] = acc;
+      store_tile_K(sk[warp], wt, n, lane, K);
+    }
+    // the next chunk's MMAs are issued after its barrier, which every thread
+    // reaches only after its TMEM load above has completed
+  }
+  if (aborted) {
+    if (tid == 0 && err) atomicExch(err, 1);
+    if (issued) (void)mbar_wait_bounded(&mbar, phase, kWaitNs);  // the MMAs possibly still in flight
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
 // gv(q) = sum_a K_a(q - a) g(q - a) over neighbours p = q - a inside the grid.
@@ -795,6 +939,22 @@ void launch_cconv_store_K(const uint8_t *lab, const ushort2 *counts, Dims d, con
   const bool rows = d.nx % 32 == 0;  // a warp's 32 cells in one grid row
   if (round_k) rows ? go(k_cconv_store_K<true, true>) : go(k_cconv_store_K<true, false>);
   else rows ? go(k_cconv_store_K<false, true>) : go(k_cconv_store_K<false, false>);
+}
+void launch_cconv_store_K_tc(const uint8_t *lab, const ushort2 *counts, Dims d, const uint8_t *wsplit, int nsplit,
+                             const float *kpure, float full, const float *v, int mask_input, int round_k, float *K,
+                             float *out, int *err, int num_sms, cudaStream_t s) {
+  const long long nch = (d.n() + kSTCells - 1) / kSTCells;
+  long long g = (long long)num_sms * 4;  // up to four CTAs per SM by registers; 64 TMEM columns each
+  if (g > nch) g = nch;
+  if (g < 1) g = 1;
+  PureK pk;
+  memcpy(&pk, kpure, sizeof(pk));
+  if (round_k)
+    k_cconv_store_K_tc<true><<<(int)g, kSTCells, 0, s>>>(lab, counts, d, wsplit, nsplit, pk, full, v, mask_input, K,
+                                                          out, err);
+  else
+    k_cconv_store_K_tc<false><<<(int)g, kSTCells, 0, s>>>(lab, counts, d, wsplit, nsplit, pk, full, v, mask_input, K,
+                                                           out, err);
 }
 void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s) {
   k_cconv_transpose<<<gridn(d.n(), 256), 256, 0, s>>>(K, g, d, gv);

@@ -216,6 +216,12 @@ void launch_materialize_K(const uint8_t *lab, const ushort2 *counts, Dims d, con
 void launch_cconv_store_K(const uint8_t *lab, const ushort2 *counts, Dims d, const CConvW &w, const float *kpure,
                           float full, const float *v, int mask_input, int round_k, float *K, float *out,
                           cudaStream_t s);
+// The same on the tensor cores (levels with counts <= 256 per cell, nx a
+// multiple of 32): wsplit (device) the block's folded weights in `nsplit` BF16
+// terms, the solve's kernel-generation layout; *err set if an MMA wait timed out.
+void launch_cconv_store_K_tc(const uint8_t *lab, const ushort2 *counts, Dims d, const uint8_t *wsplit, int nsplit,
+                             const float *kpure, float full, const float *v, int mask_input, int round_k, float *K,
+                             float *out, int *err, int num_sms, cudaStream_t s);
 void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s);
 int wgrad_blocks(Dims d);
 int wgrad_outputs();

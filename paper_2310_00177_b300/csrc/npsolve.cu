@@ -572,9 +572,16 @@ void cconv(npsolve *h, const uint8_t *lab, Dims d1, int lvl, int type, const flo
   ProfScope ps(h, lvl == 1 ? P_CCONV_L1 : P_CCONV_COARSE, s);
   h->launches += 1;
   if (h->tr.kstore) {  // training forward: no input scale, no solve state
-    launch_cconv_store_K(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw_host[idx],
-                         h->kfix_host.data() + (size_t)idx * 81, (float)ldexp(1.0, 3 * (lvl - 1)), in, mask_input,
-                         h->cfg.precision == NPSOLVE_BF16 ? 1 : 0, h->tr.kslot[idx], out, s);
+    const uint8_t *ll = lvl == 1 ? lab : nullptr;
+    const ushort2 *lc = lvl == 1 ? nullptr : w.counts[lvl];
+    const float *kpure = h->kfix_host.data() + (size_t)idx * 81;
+    const float full = (float)ldexp(1.0, 3 * (lvl - 1));
+    const int rk = h->cfg.precision == NPSOLVE_BF16 ? 1 : 0;
+    if (lvl <= 3 && dl.nx % 32 == 0)  // counts exact in BF16, rows of whole warps: the tensor cores
+      launch_cconv_store_K_tc(ll, lc, dl, h->uw + (size_t)idx * umma_weight_bytes(3), h->nsplit, kpure, full, in,
+                              mask_input, rk, h->tr.kslot[idx], out, h->umma_err, h->num_sms, s);
+    else
+      launch_cconv_store_K(ll, lc, dl, h->cw_host[idx], kpure, full, in, mask_input, rk, h->tr.kslot[idx], out, s);
     return;
   }
   launch_cconv_f32(lvl == 1 ? lab : nullptr, lvl == 1 ? nullptr : w.counts[lvl], dl, h->cw + idx, in, vscale,
