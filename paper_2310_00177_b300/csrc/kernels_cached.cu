@@ -465,10 +465,9 @@ constexpr int GT = 128;           // threads of the tensor-core generator: one p
 constexpr int kWinRow = TX + 2, kWinPlane = (TY + 2) * kWinRow;  // the label window of a unit (level 1)
 constexpr int kWinBytes = ((ZCG + 2) * kWinPlane + 15) & ~15;
 // dynamic shared memory of the generator: W splits of both blocks, the unit's
-// plane descriptors, its cache-entry map and label window (+ alignment slack)
-template <int NSPLIT>
-constexpr int gen_smem_bytes() {
-  return 2 * NSPLIT * umma::kBBytes + ZCG * (int)sizeof(PlaneDesc) + ZCG * NT * 2 + kWinBytes + 1024;
+// plane descriptors, its cache-entry map and (level 1) label window, + alignment slack
+constexpr int gen_smem_bytes(int nsplit, bool window) {
+  return 2 * nsplit * umma::kBBytes + ZCG * (int)sizeof(PlaneDesc) + ZCG * NT * 2 + (window ? kWinBytes : 0) + 1024;
 }
 
 template <int NSPLIT, bool BF16>
@@ -1535,26 +1534,31 @@ void launch_generate(bool bf16, const uint8_t *lab, const ushort2 *counts, Dims 
   if (wsplit0) {  // tensor cores: image counts exact in BF16 (levels <= 3); units within the classification's
     const int zc = setup_chunk(d, num_sms);
     const long long units = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * ((d.nz + zc - 1) / zc);
-    // 5 (BF16 form) or 3 CTAs per SM by shared memory, 64 TMEM columns each
-    const int g = grid_for_units(units, num_sms * (nsplit == 1 ? 5 : 3));
+    // CTAs per SM by shared memory (at most 7 by TMEM: 64 columns each): the level-1
+    // label window takes 11.3 KB more
+    const bool window = lab != nullptr;
+    const int smem = gen_smem_bytes(nsplit, window);
+    const int per_sm = std::min(7, (227 * 1024) / (smem + 1024));
+    const int g = grid_for_units(units, num_sms * per_sm);
     static int configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !configured[dev]) {
-      cudaFuncSetAttribute(k_generate_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes<1>());
-      cudaFuncSetAttribute(k_generate_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes<3>());
-      cudaFuncSetAttribute(k_generate_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes<3>());
+      cudaFuncSetAttribute(k_generate_tc<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes(1, true));
+      cudaFuncSetAttribute(k_generate_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gen_smem_bytes(3, true));
+      cudaFuncSetAttribute(k_generate_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           gen_smem_bytes(3, true));
       configured[dev] = 1;
     }
     if (nsplit == 1)
-      k_generate_tc<1, true><<<g, GT, gen_smem_bytes<1>(), s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd,
-                                                                (uint32_t *)cache0, (uint32_t *)cache1, zc, err);
+      k_generate_tc<1, true><<<g, GT, smem, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+                                                 (uint32_t *)cache1, zc, err);
     else if (bf16)
-      k_generate_tc<3, true><<<g, GT, gen_smem_bytes<3>(), s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd,
-                                                                (uint32_t *)cache0, (uint32_t *)cache1, zc, err);
+      k_generate_tc<3, true><<<g, GT, smem, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+                                                 (uint32_t *)cache1, zc, err);
     else
-      k_generate_tc<3, false><<<g, GT, gen_smem_bytes<3>(), s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd,
-                                                                 (uint32_t *)cache0, (uint32_t *)cache1, zc, err);
+      k_generate_tc<3, false><<<g, GT, smem, s>>>(lab, counts, d, wsplit0, wsplit1, nblk, pd, (uint32_t *)cache0,
+                                                  (uint32_t *)cache1, zc, err);
     return;
   }
   const int g = grid_for_units((long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY) * d.nz, num_sms * 8);

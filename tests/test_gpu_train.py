@@ -40,10 +40,14 @@ def _rng_labels(shape, seed, p=(0.2, 0.6, 0.2)):
 
 
 # (nz, ny, nx): rows of a multiple of 8 cells take the 8-cell-run operand
-# staging of the tensor-core weight gradient, others the per-cell one; the
-# last two span tens of 128-cell chunks, 10 x 22 x 24 with a partial last one
+# staging of the tensor-core weight gradient, others the per-cell one; 10 x 22
+# x 24 and 16 x 24 x 40 span tens of 128-cell chunks, the first with a partial
+# last one.  Rows of a multiple of 32 cells take the forward on the tensor
+# cores at levels 1-3 (4 x 8 x 64: levels 1 and 2; 8 x 8 x 256: levels 1-3)
+# and the CUDA-core forward with row loads beyond (8 x 8 x 256: level 4, 32
+# cells wide); the rest the CUDA-core forward with per-cell loads.
 @pytest.mark.parametrize("shape,L", [((16, 16, 16), 4), ((8, 16, 24), 3), ((8, 8, 8), 1), ((16, 8, 16), 2),
-                                     ((10, 22, 24), 2), ((16, 24, 40), 3)])
+                                     ((10, 22, 24), 2), ((16, 24, 40), 3), ((4, 8, 64), 2), ((8, 8, 256), 4)])
 def test_network_vjp_matches_oracle_backward(shape, L):
     b = _b()
     lab = _rng_labels(shape, 61) if shape != (16, 16, 16) else synth.pool_scene(16, 62)
