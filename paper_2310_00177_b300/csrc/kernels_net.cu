@@ -84,97 +84,19 @@ __device__ __forceinline__ float2 img_at(const ImgSrc &im, const Dims &dm, int x
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int edge_class(int q, int n) { return (q == 0 ? 1 : 0) | (q == n - 1 ? 2 : 0); }
 
-__global__ void __launch_bounds__(256) k_aff_counts(ImgSrc im, Dims dm, unsigned long long *__restrict__ cnt) {
-  __shared__ unsigned long long sc[128];  // [boundary class 64][channel 2]
-  for (int i = threadIdx.x; i < 128; i += blockDim.x) sc[i] = 0ull;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long rows = (long long)dm.ny * dm.nz;
-  unsigned long long inf = 0ull, ina = 0ull;  // interior cells of this thread
-  for (long long r = (long long)blockIdx.x * nw + warp; r < rows; r += (long long)gridDim.x * nw) {
-    const int y = (int)(r % dm.ny), z = (int)(r / dm.ny);
-    const int cyz = 4 * edge_class(y, dm.ny) + 16 * edge_class(z, dm.nz);
-    const long long base = r * dm.nx;
-    for (int x = lane; x < dm.nx; x += 32) {
-      uint32_t f, a;
-      if (im.lab) {
-        const uint8_t l = im.lab[base + x];
-        f = l == kFluid;
-        a = l == kAir;
-      } else {
-        const ushort2 c = im.counts[base + x];
-        f = c.x;
-        a = c.y;
-      }
-      const int cls = cyz + edge_class(x, dm.nx);
-      if (cls == 0) {
-        inf += f;
-        ina += a;
-      } else {
-        if (f) atomicAdd(&sc[2 * cls], (unsigned long long)f);
-        if (a) atomicAdd(&sc[2 * cls + 1], (unsigned long long)a);
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    inf += __shfl_down_sync(0xffffffffu, inf, o);
-    ina += __shfl_down_sync(0xffffffffu, ina, o);
-  }
-  if (lane == 0) {
-    atomicAdd(&sc[0], inf);
-    atomicAdd(&sc[1], ina);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 128; i += blockDim.x)
-    if (sc[i]) atomicAdd(&cnt[i], sc[i]);
-}
-
 // A cell of boundary class c (bit 0: first plane, bit 1: last plane) along an
 // axis stays inside the window sum of offset o unless o pushes it out.
 __device__ __forceinline__ bool keeps(int c, int o) { return !((o == 1 && (c & 1)) || (o == -1 && (c & 2))); }
 
-// 128 threads: the 128 counters are loaded into shared memory at once (one
-// load each), then 27 threads form the window sums.
-// stats (optional): the 54 window sums scaled by stat_scale, [0, 27) fluid and
-// [27, 54) air (the training backward's Aff image statistics).
-__global__ void k_aff_from_counts(const unsigned long long *__restrict__ gcnt, const AffW *a1, const AffW *a2,
-                                  long long n, double *out, double *stats, double stat_scale) {
-  __shared__ unsigned long long cnt[128];
-  __shared__ double t1[27], t2[27];
-  const int l = threadIdx.x;
-  cnt[l] = gcnt[l];
-  __syncthreads();
-  if (l < 27) {
-    const int ox = l % 3 - 1, oy = (l / 3) % 3 - 1, oz = l / 9 - 1;
-    double sf = 0.0, sa = 0.0;  // exact: integer counts below 2^53
-    for (int c = 0; c < 64; ++c) {
-      if (!(keeps(c & 3, ox) && keeps((c >> 2) & 3, oy) && keeps(c >> 4, oz))) continue;
-      sf += (double)cnt[2 * c];
-      sa += (double)cnt[2 * c + 1];
-    }
-    t1[l] = (double)a1->wf[l] * sf + (double)a1->wa[l] * sa;
-    t2[l] = (double)a2->wf[l] * sf + (double)a2->wa[l] * sa;
-    if (stats) {
-      stats[l] = sf * stat_scale;
-      stats[27 + l] = sa * stat_scale;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double s1 = 0.0, s2 = 0.0;
-  for (int i = 0; i < 27; ++i) {
-    s1 += t1[i];
-    s2 += t2[i];
-  }
-  out[0] = a1->bconst + s1 / (27.0 * (double)n);
-  out[1] = a2->bconst + s2 / (27.0 * (double)n);
-}
-
-// The Aff blocks of every level (1..L-1) in two launches: the boundary-class
-// counts of all levels (blockIdx.y = level - 1; level 1 reads four labels per
-// lane), then one block per level forms c1, c2 and, optionally, the training
-// statistics, with the arithmetic of k_aff_counts / k_aff_from_counts.
+// The Aff blocks of every level (1..L-1) in two launches.  k_aff_counts_all:
+// the boundary-class counts of all levels (blockIdx.y = level - 1; a warp per
+// grid row, level 1 reading four labels per lane), interior cells summed per
+// thread, the other 63 classes in shared memory, one global atomic per class.
+// k_aff_from_counts_all: one block of 128 threads per level loads the 128
+// counters, 27 threads form the window sums of their offsets (exact: integer
+// counts below 2^53) and the weighted FP64 terms, thread 0 sums them in a fixed
+// order into c1, c2; optionally the 54 window sums scaled by 1 / (8^(l-1) 27 n)
+// (fluid [0, 27), air [27, 54)) for the training backward's Aff gradient.
 __device__ __forceinline__ void aff_count_cell(uint32_t f, uint32_t a, int cls, unsigned long long &inf,
                                                unsigned long long &ina, unsigned long long *sc) {
   if (cls == 0) {
@@ -557,19 +479,6 @@ void launch_pyramid(const uint8_t *lab, Dims d1, ushort2 *const *counts, int L, 
     else k_pyramid_next<<<grid_for(nc, 256), 256, 0, s>>>(counts[l - 1], d, counts[l]);
     d = Dims{d.nx / 2, d.ny / 2, d.nz / 2};
   }
-}
-
-void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,
-                double *out, cudaStream_t s, double *stats, double feature_scale) {
-  ImgSrc im{lab, counts};
-  if (counts) im.lab = nullptr;
-  unsigned long long *cnt = (unsigned long long *)part;  // 128 counters in the reduction scratch
-  cudaMemsetAsync(cnt, 0, 128 * sizeof(unsigned long long), s);
-  const long long rows = (long long)dm.ny * dm.nz;
-  long long g = (rows + 7) / 8;
-  if (g > 148LL * 8) g = 148LL * 8;
-  k_aff_counts<<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(im, dm, cnt);
-  k_aff_from_counts<<<1, 128, 0, s>>>(cnt, a1, a2, dm.n(), out, stats, feature_scale / (27.0 * (double)dm.n()));
 }
 
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,

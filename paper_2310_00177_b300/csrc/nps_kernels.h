@@ -63,10 +63,6 @@ struct AffAll {
   int L;
 };
 void launch_aff_all(const AffAll &A, cudaStream_t s);
-// Aff coefficients c1, c2 of a level into out[0..1]; with stats != null also the
-// 54 image window sums scaled by feature_scale / (27 n) (training statistics).
-void launch_aff(const uint8_t *lab, const ushort2 *counts, Dims dm, const AffW *a1, const AffW *a2, double *part,
-                double *out, cudaStream_t s, double *stats = nullptr, double feature_scale = 1.0);
 void launch_cconv_f32(const uint8_t *lab, const ushort2 *counts, Dims dm, const CConvW *w, const float *v,
                       const float *vscale, int mask_input, int round_k, float *out, const SolveState *st,
                       cudaStream_t s);
@@ -231,8 +227,6 @@ void launch_cconv_wgrad_tc(const uint8_t *lab, const ushort2 *counts, Dims d, co
                            double *part, double *out, int *err, int num_sms, cudaStream_t s);
 void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s);
 void launch_interp_adjoint_add(const float *gfine, Dims coarse, float *gc, cudaStream_t s);
-void launch_aff_stats(const uint8_t *lab, const ushort2 *counts, Dims d, double feature_scale, double *part,
-                      double *out, cudaStream_t s);
 void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
                  cudaStream_t s);
 void launch_axpby_dev(const uint8_t *lab, long long n, const double *alpha, const float *a, float beta,
