@@ -301,10 +301,12 @@ __global__ void __launch_bounds__(kSTCells) k_cconv_store_K_tc(const uint8_t *__
     if (act) {
       window_rows(lab, counts, v, d, mask_input, wt * 32, lane, nf, na, vv);
       cls = window_class(nf, na, full);
-      uint32_t wc[27];
+      uint32_t wc[27];  // (fluid, air) of each window cell as a BF16 pair: exact, the counts are at most 256
 #pragma unroll
-      for (int l = 0; l < 27; ++l)
-        wc[l] = bf16_bits_small((unsigned)nf[l]) | (bf16_bits_small((unsigned)na[l]) << 16);
+      for (int l = 0; l < 27; ++l) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(nf[l], na[l]);
+        wc[l] = *reinterpret_cast<const uint32_t *>(&h);
+      }
       build_feature_words(wc, fw);
     } else {
 #pragma unroll
@@ -818,51 +820,6 @@ __global__ void k_interp_adjoint_add(const float *__restrict__ gfine, Dims coars
   }
 }
 
-// Aff gradient statistics: S[c][l] = (1/(27 n)) sum_p I_c(p + l) for the
-// channels c = fluid, air (the solid one is 1/27 - S_fluid - S_air, the
-// channels summing to one, padding included); block partials of the 54 sums
-// with a fixed-order reduction (per warp by shuffles, then across warps).
-__global__ void __launch_bounds__(kRedThreads) k_aff_stats(const uint8_t *__restrict__ lab,
-                                                           const ushort2 *__restrict__ counts, Dims d, float inv,
-                                                           double *__restrict__ part) {
-  __shared__ double sm[kRedThreads / 32][54];
-  float acc[54];
-#pragma unroll
-  for (int i = 0; i < 54; ++i) acc[i] = 0.f;
-  const long long n = d.n();
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    int x, y, z;
-    cell_xyz(p, d, x, y, z);
-#pragma unroll
-    for (int l = 0; l < 27; ++l) {
-      const float2 f = feat_at(lab, counts, d, x + l % 3 - 1, y + (l / 3) % 3 - 1, z + l / 9 - 1);
-      acc[l] += f.x;
-      acc[27 + l] += f.y;
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 54; ++i) {
-    double v = (double)acc[i] * inv;
-    v = warp_sum(v);
-    if (lane == 0) sm[warp][i] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 54) {
-    double t = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) t += sm[w][threadIdx.x];
-    part[(size_t)blockIdx.x * 54 + threadIdx.x] = t;
-  }
-}
-
-__global__ void k_aff_stats_final(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
-  const int o = threadIdx.x;
-  if (o >= 54) return;
-  double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * 54 + o];
-  out[o] = s;
-}
-
 // Plain dot product partials (deterministic, FP64 above the thread).
 __global__ void __launch_bounds__(kRedThreads) k_dot2(const float *__restrict__ a, const float *__restrict__ b,
                                                       const float *__restrict__ c, long long n,
@@ -1000,12 +957,6 @@ void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t
 }
 void launch_interp_adjoint_add(const float *gfine, Dims coarse, float *gc, cudaStream_t s) {
   k_interp_adjoint_add<<<gridn(coarse.n(), 256), 256, 0, s>>>(gfine, coarse, gc);
-}
-void launch_aff_stats(const uint8_t *lab, const ushort2 *counts, Dims d, double feature_scale, double *part,
-                      double *out, cudaStream_t s) {
-  const int nb = red_blocks(d.n());
-  k_aff_stats<<<nb, kRedThreads, 0, s>>>(lab, counts, d, (float)(feature_scale / (27.0 * (double)d.n())), part);
-  k_aff_stats_final<<<1, 64, 0, s>>>(part, nb, out);
 }
 void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
                  cudaStream_t s) {
