@@ -505,106 +505,127 @@ __device__ __forceinline__ uint32_t bf16_bits_of_count(uint32_t c) {  // exact: 
 // Operand staging of one 128-cell chunk when nx % 8 == 0 (and the sources are
 // aligned for vector loads): the chunk is 16 runs of 8 consecutive cells of
 // one grid row.  A task is one run and one (dy, dz) row of the 3 x 3 x 3
-// window: it loads the ten labels / counts and input values x0-1 .. x0+8 of
-// that row and the run's eight cotangents, and writes the taps dx = -1, 0, 1
-// of both feature channels and of the three BF16 terms of gK, each one
-// 16-byte row of the K-major operands.  The values are those of the per-cell
-// staging, bit for bit.
-__device__ __forceinline__ void wg_stage_runs(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
-                                              const Dims &d, const float *__restrict__ v,
-                                              const float *__restrict__ g, long long ch, uint8_t *A, uint8_t *B,
-                                              int tid) {
+// window, one per thread (144 tasks, kWgThreads >= 144): wg_load_run issues its
+// loads -- the ten labels / counts and input values x0-1 .. x0+8 of that row and
+// the run's eight cotangents -- and wg_store_run writes the taps dx = -1, 0, 1
+// of both feature channels and of the three BF16 terms of gK, each one 16-byte
+// row of the K-major operands.  (Issuing the next chunk's loads before this
+// chunk's stores was measured: no faster, 128 registers instead of 104.)  The
+// values are those of the per-cell staging, bit for bit.
+struct WgRaw {
+  uint4 i0, i1;         // labels (i0.x, i0.y: 8 bytes) or counts (8 ushort2) of x0 .. x0+7
+  uint32_t el, er;      // the same at x0-1 and x0+8 (0 outside the grid)
+  float4 a0, a1, g0, g1;  // input at x0 .. x0+7; cotangents of the run
+  float vl, vr;         // input at x0-1 and x0+8
+  int run, r;           // r < 0: no task
+  bool valid;
+};
+static_assert(kWgThreads >= (kWgCells / 8) * 9, "one staging task per thread");
+
+__device__ __forceinline__ WgRaw wg_load_run(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
+                                             const Dims &d, const float *__restrict__ v,
+                                             const float *__restrict__ g, long long ch, int tid) {
+  WgRaw w;
+  w.i0 = w.i1 = make_uint4(0u, 0u, 0u, 0u);
+  w.el = w.er = 0u;
+  w.a0 = w.a1 = w.g0 = w.g1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  w.vl = w.vr = 0.f;
+  w.run = tid / 9;
+  w.r = tid < (kWgCells / 8) * 9 ? tid - w.run * 9 : -1;
+  w.valid = false;
+  if (w.r < 0) return w;
   const long long n = d.n();
-  for (int task = tid; task < (kWgCells / 8) * 9; task += kWgThreads) {
-    const int run = task / 9, r = task - run * 9;
-    const long long p0 = ch * kWgCells + run * 8;
-    const bool valid = p0 < n;  // n is a multiple of 8
-    int x0 = 0, y = 0, z = 0;
-    if (valid) cell_xyz(p0, d, x0, y, z);
-    const int yy = y + r % 3 - 1, zz = z + r / 3 - 1;
-    const bool rowin = valid && yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz;
-    const long long rb = rowin ? ((long long)zz * d.ny + yy) * d.nx + x0 : 0;  // cell x0 of the row
-    const bool has_l = rowin && x0 > 0, has_r = rowin && x0 + 8 < d.nx;
-    // the fluid and air features at x0-1 .. x0+8 as BF16 bits (0 outside the grid)
-    uint32_t hf[10], ha[10];
-    if (lab) {
-      uint2 mid = make_uint2(0u, 0u);
-      if (rowin) mid = *(const uint2 *)(lab + rb);
-      const uint32_t el = has_l ? lab[rb - 1] : 0u, er = has_r ? lab[rb + 8] : 0u;
-      hf[0] = el == kFluid ? 0x3F80u : 0u;
-      ha[0] = el == kAir ? 0x3F80u : 0u;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t c = ((i < 4 ? mid.x : mid.y) >> (8 * (i & 3))) & 0xFFu;
-        hf[1 + i] = c == kFluid ? 0x3F80u : 0u;
-        ha[1 + i] = c == kAir ? 0x3F80u : 0u;
-      }
-      hf[9] = er == kFluid ? 0x3F80u : 0u;
-      ha[9] = er == kAir ? 0x3F80u : 0u;
-    } else {
-      uint4 q0 = make_uint4(0u, 0u, 0u, 0u), q1 = q0;
-      if (rowin) {
-        q0 = *(const uint4 *)(counts + rb);
-        q1 = *(const uint4 *)(counts + rb + 4);
-      }
-      const uint32_t el = has_l ? *(const uint32_t *)(counts + rb - 1) : 0u;
-      const uint32_t er = has_r ? *(const uint32_t *)(counts + rb + 8) : 0u;
-      const uint32_t wv[10] = {el, q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, er};
-#pragma unroll
-      for (int i = 0; i < 10; ++i) {
-        hf[i] = bf16_bits_of_count(wv[i] & 0xFFFFu);
-        ha[i] = bf16_bits_of_count(wv[i] >> 16);
-      }
+  const long long p0 = ch * kWgCells + w.run * 8;
+  w.valid = p0 < n;  // n is a multiple of 8
+  int x0 = 0, y = 0, z = 0;
+  if (w.valid) cell_xyz(p0, d, x0, y, z);
+  const int yy = y + w.r % 3 - 1, zz = z + w.r / 3 - 1;
+  const bool rowin = w.valid && yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz;
+  const long long rb = rowin ? ((long long)zz * d.ny + yy) * d.nx + x0 : 0;  // cell x0 of the row
+  const bool has_l = rowin && x0 > 0, has_r = rowin && x0 + 8 < d.nx;
+  if (lab) {
+    if (rowin) {
+      const uint2 m = *(const uint2 *)(lab + rb);
+      w.i0.x = m.x;
+      w.i0.y = m.y;
     }
-    // the input at x0-1 .. x0+8 and the run's cotangents
-    float vr[10], gp[8];
-    {
-      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0, g0 = a0, g1 = a0;
-      if (rowin) {
-        a0 = *(const float4 *)(v + rb);
-        a1 = *(const float4 *)(v + rb + 4);
-      }
-      if (valid) {
-        g0 = *(const float4 *)(g + p0);
-        g1 = *(const float4 *)(g + p0 + 4);
-      }
-      vr[0] = has_l ? v[rb - 1] : 0.f;
-      vr[1] = a0.x; vr[2] = a0.y; vr[3] = a0.z; vr[4] = a0.w;
-      vr[5] = a1.x; vr[6] = a1.y; vr[7] = a1.z; vr[8] = a1.w;
-      vr[9] = has_r ? v[rb + 8] : 0.f;
-      gp[0] = g0.x; gp[1] = g0.y; gp[2] = g0.z; gp[3] = g0.w;
-      gp[4] = g1.x; gp[5] = g1.y; gp[6] = g1.z; gp[7] = g1.w;
+    if (has_l) w.el = lab[rb - 1];
+    if (has_r) w.er = lab[rb + 8];
+  } else {
+    if (rowin) {
+      w.i0 = *(const uint4 *)(counts + rb);
+      w.i1 = *(const uint4 *)(counts + rb + 4);
     }
-    const uint32_t col = (uint32_t)run * 8;
+    if (has_l) w.el = *(const uint32_t *)(counts + rb - 1);
+    if (has_r) w.er = *(const uint32_t *)(counts + rb + 8);
+  }
+  if (rowin) {
+    w.a0 = *(const float4 *)(v + rb);
+    w.a1 = *(const float4 *)(v + rb + 4);
+  }
+  if (w.valid) {
+    w.g0 = *(const float4 *)(g + p0);
+    w.g1 = *(const float4 *)(g + p0 + 4);
+  }
+  if (has_l) w.vl = v[rb - 1];
+  if (has_r) w.vr = v[rb + 8];
+  return w;
+}
+
+__device__ __forceinline__ void wg_store_run(const WgRaw &w, bool labels, uint8_t *A, uint8_t *B) {
+  if (w.r < 0) return;
+  // the fluid and air features at x0-1 .. x0+8 as BF16 bits (0 outside the grid)
+  uint32_t hf[10], ha[10];
+  if (labels) {
+    hf[0] = w.el == kFluid ? 0x3F80u : 0u;
+    ha[0] = w.el == kAir ? 0x3F80u : 0u;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {  // dx = k - 1: tap a = 3 r + k
-      const int a = 3 * r + k;
-      uint4 f, q, hi, md, lo;
-      f.x = hf[k] | (hf[k + 1] << 16);
-      f.y = hf[k + 2] | (hf[k + 3] << 16);
-      f.z = hf[k + 4] | (hf[k + 5] << 16);
-      f.w = hf[k + 6] | (hf[k + 7] << 16);
-      q.x = ha[k] | (ha[k + 1] << 16);
-      q.y = ha[k + 2] | (ha[k + 3] << 16);
-      q.z = ha[k + 4] | (ha[k + 5] << 16);
-      q.w = ha[k + 6] | (ha[k + 7] << 16);
-      *(uint4 *)(A + wg_off(a, col)) = f;
-      *(uint4 *)(A + wg_off(27 + a, col)) = q;
-      float gk[8];
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t c = ((i < 4 ? w.i0.x : w.i0.y) >> (8 * (i & 3))) & 0xFFu;
+      hf[1 + i] = c == kFluid ? 0x3F80u : 0u;
+      ha[1 + i] = c == kAir ? 0x3F80u : 0u;
+    }
+    hf[9] = w.er == kFluid ? 0x3F80u : 0u;
+    ha[9] = w.er == kAir ? 0x3F80u : 0u;
+  } else {
+    const uint32_t wv[10] = {w.el, w.i0.x, w.i0.y, w.i0.z, w.i0.w, w.i1.x, w.i1.y, w.i1.z, w.i1.w, w.er};
 #pragma unroll
-      for (int i = 0; i < 8; ++i) gk[i] = gp[i] != 0.f ? gp[i] * vr[i + k] : 0.f;
-      split3_pair(gk[0], gk[1], hi.x, md.x, lo.x);
-      split3_pair(gk[2], gk[3], hi.y, md.y, lo.y);
-      split3_pair(gk[4], gk[5], hi.z, md.z, lo.z);
-      split3_pair(gk[6], gk[7], hi.w, md.w, lo.w);
-      *(uint4 *)(B + wg_off(a, col)) = hi;
-      *(uint4 *)(B + wg_off(32 + a, col)) = md;
-      *(uint4 *)(B + wg_off(64 + a, col)) = lo;
+    for (int i = 0; i < 10; ++i) {
+      hf[i] = bf16_bits_of_count(wv[i] & 0xFFFFu);
+      ha[i] = bf16_bits_of_count(wv[i] >> 16);
     }
-    if (r == 0) {  // the constant feature of the bias
-      const uint32_t one = valid ? 0x3F803F80u : 0u;
-      *(uint4 *)(A + wg_off(54, col)) = make_uint4(one, one, one, one);
-    }
+  }
+  const float vr[10] = {w.vl, w.a0.x, w.a0.y, w.a0.z, w.a0.w, w.a1.x, w.a1.y, w.a1.z, w.a1.w, w.vr};
+  const float gp[8] = {w.g0.x, w.g0.y, w.g0.z, w.g0.w, w.g1.x, w.g1.y, w.g1.z, w.g1.w};
+  const uint32_t col = (uint32_t)w.run * 8;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {  // dx = k - 1: tap a = 3 r + k
+    const int a = 3 * w.r + k;
+    uint4 f, q, hi, md, lo;
+    f.x = hf[k] | (hf[k + 1] << 16);
+    f.y = hf[k + 2] | (hf[k + 3] << 16);
+    f.z = hf[k + 4] | (hf[k + 5] << 16);
+    f.w = hf[k + 6] | (hf[k + 7] << 16);
+    q.x = ha[k] | (ha[k + 1] << 16);
+    q.y = ha[k + 2] | (ha[k + 3] << 16);
+    q.z = ha[k + 4] | (ha[k + 5] << 16);
+    q.w = ha[k + 6] | (ha[k + 7] << 16);
+    *(uint4 *)(A + wg_off(a, col)) = f;
+    *(uint4 *)(A + wg_off(27 + a, col)) = q;
+    float gk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gk[i] = gp[i] != 0.f ? gp[i] * vr[i + k] : 0.f;
+    split3_pair(gk[0], gk[1], hi.x, md.x, lo.x);
+    split3_pair(gk[2], gk[3], hi.y, md.y, lo.y);
+    split3_pair(gk[4], gk[5], hi.z, md.z, lo.z);
+    split3_pair(gk[6], gk[7], hi.w, md.w, lo.w);
+    *(uint4 *)(B + wg_off(a, col)) = hi;
+    *(uint4 *)(B + wg_off(32 + a, col)) = md;
+    *(uint4 *)(B + wg_off(64 + a, col)) = lo;
+  }
+  if (w.r == 0) {  // the constant feature of the bias
+    const uint32_t one = w.valid ? 0x3F803F80u : 0u;
+    *(uint4 *)(A + wg_off(54, col)) = make_uint4(one, one, one, one);
   }
 }
 
@@ -688,7 +709,7 @@ __global__ void __launch_bounds__(kWgThreads) k_cconv_wgrad_tc(const uint8_t *__
       issued[b] = 0;
     }
     uint8_t *A = sm + b * kWgBufBytes, *B = A + kWgABytes;
-    if (RUNS) wg_stage_runs(lab, counts, d, v, g, ch, A, B, tid);
+    if (RUNS) wg_store_run(wg_load_run(lab, counts, d, v, g, ch, tid), lab != nullptr, A, B);
     else wg_stage_cells(lab, counts, d, v, g, ch, A, B, tid);
     fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
     fence_before_sync();
@@ -832,6 +853,34 @@ __global__ void __launch_bounds__(kRedThreads) k_dot2(const float *__restrict__ 
   block_sum_store<2>(v, part + (size_t)blockIdx.x * 2);
 }
 
+// The pairs of dots of several levels in two launches (blockIdx.y = the level's
+// index; each level with the block count, grid stride and fixed-order partial
+// sum of k_dot2 / k_dot2_final, so the results are those of a launch per level).
+__global__ void __launch_bounds__(kRedThreads) k_dot2_levels(const __grid_constant__ Dot2Levels D,
+                                                             double *__restrict__ part) {
+  const int l = D.l0 + blockIdx.y;
+  const int nb = D.nb[l];
+  if ((int)blockIdx.x >= nb) return;  // the whole block
+  const float *__restrict__ a = D.a[l], *__restrict__ b = D.b[l], *__restrict__ c = D.c[l];
+  const long long n = D.n[l];
+  double v[2] = {0.0, 0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)nb * blockDim.x) {
+    v[0] += (double)a[p] * b[p];
+    if (c) v[1] += (double)a[p] * c[p];
+  }
+  block_sum_store<2>(v, part + ((size_t)blockIdx.y * kRedMaxBlocks + blockIdx.x) * 2);
+}
+__global__ void k_dot2_levels_final(const __grid_constant__ Dot2Levels D, const double *part) {
+  const int l = D.l0 + blockIdx.x;
+  double t[2];
+  reduce_partials<2>(part + (size_t)blockIdx.x * kRedMaxBlocks * 2, D.nb[l], t);
+  if (threadIdx.x == 0) {
+    D.out[l][0] = t[0];
+    D.out[l][1] = t[1];
+  }
+  if (D.stats_src[l] && threadIdx.x < 54) D.stats_dst[l][threadIdx.x] = D.stats_src[l][threadIdx.x];
+}
+
 __global__ void k_dot2_final(const double *part, int nblocks, double *out) {
   double t[2];
   reduce_partials<2>(part, nblocks, t);
@@ -957,6 +1006,17 @@ void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t
 }
 void launch_interp_adjoint_add(const float *gfine, Dims coarse, float *gc, cudaStream_t s) {
   k_interp_adjoint_add<<<gridn(coarse.n(), 256), 256, 0, s>>>(gfine, coarse, gc);
+}
+void launch_dot2_levels(const Dot2Levels &D, double *part, cudaStream_t s) {
+  if (D.count < 1) return;
+  Dot2Levels P = D;
+  int nbmax = 1;
+  for (int i = 0; i < D.count; ++i) {
+    P.nb[D.l0 + i] = red_blocks(D.n[D.l0 + i]);
+    if (P.nb[D.l0 + i] > nbmax) nbmax = P.nb[D.l0 + i];
+  }
+  k_dot2_levels<<<dim3((unsigned)nbmax, (unsigned)D.count), kRedThreads, 0, s>>>(P, part);
+  k_dot2_levels_final<<<D.count, kRedThreads, 0, s>>>(P, part);
 }
 void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
                  cudaStream_t s) {

@@ -227,6 +227,19 @@ void launch_cconv_wgrad_tc(const uint8_t *lab, const ushort2 *counts, Dims d, co
                            double *part, double *out, int *err, int num_sms, cudaStream_t s);
 void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s);
 void launch_interp_adjoint_add(const float *gfine, Dims coarse, float *gc, cudaStream_t s);
+// Dots a.b and a.c (c optional) of the levels l0 .. l0+count-1 in two launches;
+// part holds count x kRedMaxBlocks x 2 doubles; out[l] receives the pair; when
+// stats_src[l] is set, its 54 doubles are copied to stats_dst[l] as well.
+struct Dot2Levels {
+  const float *a[kMaxLevels + 1], *b[kMaxLevels + 1], *c[kMaxLevels + 1];
+  long long n[kMaxLevels + 1];
+  double *out[kMaxLevels + 1];
+  const double *stats_src[kMaxLevels + 1];
+  double *stats_dst[kMaxLevels + 1];
+  int nb[kMaxLevels + 1];  // set by the launcher
+  int l0, count;
+};
+void launch_dot2_levels(const Dot2Levels &D, double *part, cudaStream_t s);
 void launch_dot2(const float *a, const float *b, const float *c, long long n, double *part, double *out,
                  cudaStream_t s);
 void launch_axpby_dev(const uint8_t *lab, long long n, const double *alpha, const float *a, float beta,

@@ -1149,15 +1149,30 @@ int train_backward(npsolve *h, const uint8_t *lab, Dims d1, const float *gz, dou
   for (int l = 1; l < L; ++l) {
     const Dims dl = level_dims(d1, l);
     const long long nl = dl.n();
-    launch_dot2(t.gx[l], w.x1[l], w.x2[l], nl, t.part, O(l) + 2 * kWGOut, s);
-    // the image statistics of Aff's weight gradient: the exact window sums of the setup
-    CK(h, cudaMemcpyAsync(O(l) + 2 * kWGOut + 2, w.affs + 54 * l, 54 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     launch_axpby_dev(nullptr, nl, w.affc + 2 * l, t.gx[l], 1.f, t.gx1[l], t.gx1[l], s);   // gx1 += c1 gx
     launch_axpby_dev(nullptr, nl, w.affc + 2 * l + 1, t.gx[l], 0.f, nullptr, t.tmp, s);     // g x2 = c2 gx
     wgrad(l, dl, w.r2[l], t.tmp, O(l) + kWGOut);
     launch_cconv_transpose(t.kslot[l * 2 + 1], t.tmp, dl, t.tmp2, s);  // g r2 (the forward's kernels)
     launch_interp_adjoint_add(t.tmp2, level_dims(d1, l + 1), (l + 1 == L) ? t.gx1[L] : t.gx[l + 1], s);
-    h->launches += 10;
+    h->launches += 6;
+  }
+  if (L > 1) {
+    // Aff's weight gradient of every level, now that every gx[l] is final: the dots gx.x1, gx.x2 and the
+    // image statistics (the exact window sums of the setup), in two launches
+    Dot2Levels D{};
+    D.l0 = 1;
+    D.count = L - 1;
+    for (int l = 1; l < L; ++l) {
+      D.a[l] = t.gx[l];
+      D.b[l] = w.x1[l];
+      D.c[l] = w.x2[l];
+      D.n[l] = level_dims(d1, l).n();
+      D.out[l] = O(l) + 2 * kWGOut;
+      D.stats_src[l] = w.affs + 54 * l;
+      D.stats_dst[l] = O(l) + 2 * kWGOut + 2;
+    }
+    launch_dot2_levels(D, t.part, s);
+    h->launches += 2;
   }
   // down pass in reverse: CConv1 and pooling
   for (int l = L; l >= 1; --l) {
