@@ -460,11 +460,12 @@ __global__ void __launch_bounds__(256) k_cconv_wgrad(const uint8_t *__restrict__
 // with A = F (the 54 window counts and the bias 1 per cell, rows 55..127 zero)
 // and B = the kernel gradient gK_a(p) = g(p) v(p + a) split into three BF16
 // terms s (hi, mid, lo; their sum is the FP32 value to 2^-24 relative), both
-// K-major in shared memory in 128-cell chunks.  Thread t stages cell t of a
-// chunk (its window counts and 27 products, one pass over its 3 x 3 x 3
-// window); one thread issues the chunk's eight MMAs (K = 16 each) and commits
-// them to the buffer's mbarrier, while the CTA stages the next chunk into the
-// other buffer.  D accumulates over all of the CTA's chunks; at the end lane
+// K-major in shared memory in 128-cell chunks.  The threads stage a chunk in
+// runs of 8 cells (rows of a multiple of 8 cells: wg_load_run / wg_store_run)
+// or one cell each (any grid: wg_stage_cells, the window counts and 27
+// products of its 3 x 3 x 3 window); one thread issues the chunk's eight MMAs
+// (K = 16 each) and commits them to the buffer's mbarrier, while the CTA stages
+// the next chunk into the other buffer.  D accumulates over all of the CTA's chunks; at the end lane
 // j holds G[a][j] = D[j][a] + D[j][32 + a] + D[j][64 + a], written as the
 // CTA's partial in the layout of k_cconv_wgrad (reduced by k_wgrad_final).
 constexpr int kWgCells = 128;                      // cells per chunk (MMA K = 8 x 16)
