@@ -1010,6 +1010,14 @@ void free_train(npsolve *h) {
   t.cap = 0;
 }
 
+// The per-cell kernels of one block for the network transpose (t.cap x 27
+// floats), allocated only by the paths that run it, before any graph capture.
+int ensure_transpose_K(npsolve *h) {
+  auto &t = h->tr;
+  if (!t.K) CK(h, dalloc(nullptr, &t.K, (size_t)t.cap * 27));
+  return NPSOLVE_OK;
+}
+
 int ensure_train(npsolve *h, Dims d1) {
   auto &t = h->tr;
   const long long n = d1.n();
@@ -1030,7 +1038,6 @@ int ensure_train(npsolve *h, Dims d1) {
   CK(h, dalloc(nullptr, &t.tmp2, (size_t)n));
   CK(h, dalloc(nullptr, &t.res, (size_t)n));
   CK(h, dalloc(nullptr, &t.gz, (size_t)n));
-  CK(h, dalloc(nullptr, &t.K, (size_t)n * 27));
   CK(h, dalloc(nullptr, &t.part, (size_t)148 * 4 * kWGOut + (size_t)kRedMaxBlocks * 64));
   CK(h, dalloc(nullptr, &t.out, (size_t)(kMaxLevels + 1) * kTrOutPerLevel));
   t.cap = n;
@@ -1424,6 +1431,8 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
   if (h->cfg.symmetric) {  // the transpose pass of P_sym uses the train workspace
     st = ensure_train(h, d1);
     if (st) return st;
+    st = ensure_transpose_K(h);
+    if (st) return st;
   }
   Workspace &w = h->ws;
   {
@@ -1780,6 +1789,8 @@ static int symmetry_setup(npsolve *h, const uint8_t *labels, Dims d1, cudaStream
   st = ensure_ws(h, d1, 1);
   if (st) return st;
   st = ensure_train(h, d1);
+  if (st) return st;
+  st = ensure_transpose_K(h);
   if (st) return st;
   st = setup_image(h, labels, d1, s, true);
   if (st) return st;
