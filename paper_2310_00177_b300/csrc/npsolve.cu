@@ -1480,7 +1480,27 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
     // Replay the captured iterations until the device flags completion or the
     // cap is reached.  The state copy of batch i is read only after batch i+1
     // has been queued, so the GPU does not wait for the host between batches.
+    // Once the residual's rate of decrease says that the batch just queued is
+    // likely to converge, its state is read before anything more is queued:
+    // that costs one short host wait, where a batch queued past convergence
+    // replays kPollEvery iterations whose kernels return at once.
     int nb = 0;
+    int rate_k = -1;       // the iteration count and ||r||^2 of an earlier state read
+    double rate_r2 = 0.0;
+    bool near = false;     // from the first prediction on, every batch's state is read before the next is queued
+    auto near_convergence = [&](const SolveState &c) {
+      bool close = false;
+      if (rate_k >= 0 && c.k > rate_k && rate_r2 > 0.0 && c.rnorm2 > 0.0) {
+        const double per_iter = pow(c.rnorm2 / rate_r2, 1.0 / (double)(c.k - rate_k));  // of ||r||^2
+        // within a factor 10 of the tolerance after the queued batch: stop looking ahead
+        close = per_iter < 1.0 && c.rnorm2 * pow(per_iter, (double)kPollEvery) < 100.0 * c.eps2;
+      }
+      if (c.k > rate_k) {
+        rate_k = c.k;
+        rate_r2 = c.rnorm2;
+      }
+      return close;
+    };
     while (hs.done == kDoneRunning && launched < max_iter) {
       if (h->prof.on) {  // one iteration at a time, so that no no-op iteration is timed
         enqueue_iteration(h, lab, d1, b, x, s);
@@ -1507,6 +1527,10 @@ int solve_impl(npsolve *h, const uint8_t *lab, int nx, int ny, int nz, const flo
         hs = w.h_st[(nb - 1) & 1];
       }
       nb += 1;
+      if (hs.done == kDoneRunning && (near || (near = near_convergence(hs)))) {
+        CK(h, cudaEventSynchronize(w.ev[(nb - 1) & 1]));  // the batch just queued, before any more
+        hs = w.h_st[(nb - 1) & 1];
+      }
     }
     // The end of a pass, decided on the device and read back with one host
     // synchronisation: the last pending residual step (a no-op when none is
