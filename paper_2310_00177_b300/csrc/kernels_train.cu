@@ -97,10 +97,13 @@ struct PureK {
 constexpr int kSKWarps = 4;
 
 // One window cell's features and input value (0 outside the grid; the input
-// zeroed off fluid when mask_input).
+// zeroed off fluid when mask_input).  SRC: where the features come from,
+// kSrcLabels (level 1), kSrcCounts (coarser levels) or kSrcEither (lab if set).
+enum { kSrcEither = 0, kSrcLabels = 1, kSrcCounts = 2 };
+template <int SRC = kSrcEither>
 __device__ __forceinline__ void window_cell(const uint8_t *lab, const ushort2 *counts, const float *v, long long q,
                                             int mask_input, float &f, float &a, float &val) {
-  if (lab) {
+  if (SRC == kSrcLabels || (SRC == kSrcEither && lab)) {
     const uint8_t l = lab[q];
     f = l == kFluid ? 1.f : 0.f;
     a = l == kAir ? 1.f : 0.f;
@@ -117,6 +120,7 @@ __device__ __forceinline__ void window_cell(const uint8_t *lab, const ushort2 *c
 // lane i holding cell x0+i's: each of the nine window rows is loaded once,
 // coalesced, the x-1 and x+1 taps taken from the neighbouring lanes (lanes 0
 // and 31 load the halo columns).
+template <int SRC = kSrcEither>
 __device__ __forceinline__ void window_rows(const uint8_t *lab, const ushort2 *counts, const float *v, const Dims &d,
                                             int mask_input, long long p0, int lane, float (&nf)[27], float (&na)[27],
                                             float (&vv)[27]) {
@@ -128,10 +132,10 @@ __device__ __forceinline__ void window_rows(const uint8_t *lab, const ushort2 *c
     float cf = 0.f, ca = 0.f, cv = 0.f, hf = 0.f, ha = 0.f, hv = 0.f;
     if (yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz) {  // the same for the whole warp
       const long long rb = ((long long)zz * d.ny + yy) * d.nx;
-      window_cell(lab, counts, v, rb + x0 + lane, mask_input, cf, ca, cv);
+      window_cell<SRC>(lab, counts, v, rb + x0 + lane, mask_input, cf, ca, cv);
       const int hx = lane == 0 ? x0 - 1 : x0 + 32;  // the halo columns, read by lanes 0 and 31
       if ((lane == 0 || lane == 31) && hx >= 0 && hx < d.nx)
-        window_cell(lab, counts, v, rb + hx, mask_input, hf, ha, hv);
+        window_cell<SRC>(lab, counts, v, rb + hx, mask_input, hf, ha, hv);
     }
     float lf = __shfl_up_sync(0xffffffffu, cf, 1), la = __shfl_up_sync(0xffffffffu, ca, 1);
     float lv = __shfl_up_sync(0xffffffffu, cv, 1);
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(kSKWarps * 32) k_cconv_store_K(const uint8_t *
 // windows take their class kernel; BF16 rounding (RK), the output sum and the
 // stores are those of k_cconv_store_K.  A timed-out MMA wait sets *err.
 constexpr int kSTCells = 128;
-template <bool RK>
+template <bool RK, int SRC>
 __global__ void __launch_bounds__(kSTCells) k_cconv_store_K_tc(const uint8_t *__restrict__ lab,
                                                                const ushort2 *__restrict__ counts, Dims d,
                                                                const uint8_t *__restrict__ wsplit, int nsplit,
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kSTCells) k_cconv_store_K_tc(const uint8_t *__
     uint32_t fw[32];
     int cls = 0;
     if (act) {
-      window_rows(lab, counts, v, d, mask_input, wt * 32, lane, nf, na, vv);
+      window_rows<SRC>(lab, counts, v, d, mask_input, wt * 32, lane, nf, na, vv);
       cls = window_class(nf, na, full);
       uint32_t wc[27];  // (fluid, air) of each window cell as a BF16 pair: exact, the counts are at most 256
 #pragma unroll
@@ -956,12 +960,11 @@ void launch_cconv_store_K_tc(const uint8_t *lab, const ushort2 *counts, Dims d, 
   if (g < 1) g = 1;
   PureK pk;
   memcpy(&pk, kpure, sizeof(pk));
-  if (round_k)
-    k_cconv_store_K_tc<true><<<(int)g, kSTCells, 0, s>>>(lab, counts, d, wsplit, nsplit, pk, full, v, mask_input, K,
-                                                          out, err);
-  else
-    k_cconv_store_K_tc<false><<<(int)g, kSTCells, 0, s>>>(lab, counts, d, wsplit, nsplit, pk, full, v, mask_input, K,
-                                                           out, err);
+  auto go = [&](auto kern) {
+    kern<<<(int)g, kSTCells, 0, s>>>(lab, counts, d, wsplit, nsplit, pk, full, v, mask_input, K, out, err);
+  };
+  if (lab) round_k ? go(k_cconv_store_K_tc<true, kSrcLabels>) : go(k_cconv_store_K_tc<false, kSrcLabels>);
+  else round_k ? go(k_cconv_store_K_tc<true, kSrcCounts>) : go(k_cconv_store_K_tc<false, kSrcCounts>);
 }
 void launch_cconv_transpose(const float *K, const float *g, Dims d, float *gv, cudaStream_t s) {
   k_cconv_transpose<<<gridn(d.n(), 256), 256, 0, s>>>(K, g, d, gv);
