@@ -527,6 +527,7 @@ struct WgRaw {
 };
 static_assert(kWgThreads >= (kWgCells / 8) * 9, "one staging task per thread");
 
+template <bool LABELS>
 __device__ __forceinline__ WgRaw wg_load_run(const uint8_t *__restrict__ lab, const ushort2 *__restrict__ counts,
                                              const Dims &d, const float *__restrict__ v,
                                              const float *__restrict__ g, long long ch, int tid) {
@@ -548,7 +549,7 @@ __device__ __forceinline__ WgRaw wg_load_run(const uint8_t *__restrict__ lab, co
   const bool rowin = w.valid && yy >= 0 && yy < d.ny && zz >= 0 && zz < d.nz;
   const long long rb = rowin ? ((long long)zz * d.ny + yy) * d.nx + x0 : 0;  // cell x0 of the row
   const bool has_l = rowin && x0 > 0, has_r = rowin && x0 + 8 < d.nx;
-  if (lab) {
+  if (LABELS) {
     if (rowin) {
       const uint2 m = *(const uint2 *)(lab + rb);
       w.i0.x = m.x;
@@ -577,11 +578,12 @@ __device__ __forceinline__ WgRaw wg_load_run(const uint8_t *__restrict__ lab, co
   return w;
 }
 
-__device__ __forceinline__ void wg_store_run(const WgRaw &w, bool labels, uint8_t *A, uint8_t *B) {
+template <bool LABELS>
+__device__ __forceinline__ void wg_store_run(const WgRaw &w, uint8_t *A, uint8_t *B) {
   if (w.r < 0) return;
   // the fluid and air features at x0-1 .. x0+8 as BF16 bits (0 outside the grid)
   uint32_t hf[10], ha[10];
-  if (labels) {
+  if (LABELS) {
     hf[0] = w.el == kFluid ? 0x3F80u : 0u;
     ha[0] = w.el == kAir ? 0x3F80u : 0u;
 #pragma unroll
@@ -669,7 +671,9 @@ __device__ __forceinline__ void wg_stage_cells(const uint8_t *__restrict__ lab, 
   }
 }
 
-template <bool RUNS>
+// STAGE: kStageCells (any grid), kStageRunsLabels / kStageRunsCounts (8-cell runs of level 1 / coarser levels)
+enum { kStageCells = 0, kStageRunsLabels = 1, kStageRunsCounts = 2 };
+template <int STAGE>
 __global__ void __launch_bounds__(kWgThreads) k_cconv_wgrad_tc(const uint8_t *__restrict__ lab,
                                                              const ushort2 *__restrict__ counts, Dims d,
                                                              const float *__restrict__ v, const float *__restrict__ g,
@@ -714,7 +718,8 @@ __global__ void __launch_bounds__(kWgThreads) k_cconv_wgrad_tc(const uint8_t *__
       issued[b] = 0;
     }
     uint8_t *A = sm + b * kWgBufBytes, *B = A + kWgABytes;
-    if (RUNS) wg_store_run(wg_load_run(lab, counts, d, v, g, ch, tid), lab != nullptr, A, B);
+    if (STAGE == kStageRunsLabels) wg_store_run<true>(wg_load_run<true>(lab, counts, d, v, g, ch, tid), A, B);
+    else if (STAGE == kStageRunsCounts) wg_store_run<false>(wg_load_run<false>(lab, counts, d, v, g, ch, tid), A, B);
     else wg_stage_cells(lab, counts, d, v, g, ch, A, B, tid);
     fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
     fence_before_sync();
@@ -989,8 +994,9 @@ void launch_cconv_wgrad_tc(const uint8_t *lab, const ushort2 *counts, Dims d, co
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaFuncSetAttribute(k_cconv_wgrad_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
-    cudaFuncSetAttribute(k_cconv_wgrad_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    cudaFuncSetAttribute(k_cconv_wgrad_tc<kStageCells>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    cudaFuncSetAttribute(k_cconv_wgrad_tc<kStageRunsLabels>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
+    cudaFuncSetAttribute(k_cconv_wgrad_tc<kStageRunsCounts>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
     configured[dev] = 1;
   }
   const long long nch = (d.n() + kWgCells - 1) / kWgCells;
@@ -1001,8 +1007,10 @@ void launch_cconv_wgrad_tc(const uint8_t *lab, const ushort2 *counts, Dims d, co
   // the 8- and 16-byte loads (the level buffers are; user labels may not be)
   const bool runs = d.nx % 8 == 0 && ((uintptr_t)lab % 8) == 0 && ((uintptr_t)counts % 16) == 0 &&
                     ((uintptr_t)v % 16) == 0 && ((uintptr_t)g % 16) == 0;
-  if (runs) k_cconv_wgrad_tc<true><<<(int)nb, kWgThreads, kWgSmem, s>>>(lab, counts, d, v, g, part, err);
-  else k_cconv_wgrad_tc<false><<<(int)nb, kWgThreads, kWgSmem, s>>>(lab, counts, d, v, g, part, err);
+  auto go = [&](auto kern) { kern<<<(int)nb, kWgThreads, kWgSmem, s>>>(lab, counts, d, v, g, part, err); };
+  if (!runs) go(k_cconv_wgrad_tc<kStageCells>);
+  else if (lab) go(k_cconv_wgrad_tc<kStageRunsLabels>);
+  else go(k_cconv_wgrad_tc<kStageRunsCounts>);
   k_wgrad_final<<<(kWG + 31) / 32, kWFSlices * 32, 0, s>>>(part, (int)nb, out);
 }
 void launch_pool_adjoint_add(const float *gc, Dims fine, float *gf, cudaStream_t s) {
